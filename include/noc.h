@@ -1,0 +1,181 @@
+/*
+ * noc.h -- C ABI of libnoc.so, the B300 (sm_103a) simulator of a W x H mesh
+ * chip multicore joined by a bufferless, deflection-routed NoC with a
+ * logically-shared, physically-distributed (LSPD) L2 (Kumar & Sahu,
+ * "Bufferless NOC Simulation of Large Multicore System on GPU Hardware",
+ * arXiv 1508.03235).
+ *
+ * Every simulated cycle: each tile advances its core / L1 / L2-slice /
+ * directory state (Sec. 7.1 "Work in phase one"), each router ejects one flit,
+ * may inject one, sorts its flits oldest-first and gives each a productive or
+ * a deflected output port (Sec. 4.2, Sec. 4.3, Sec. 7.1 "phase two"), and the
+ * ejected flit is handled at its tile (Sec. 7.1 "phase three").
+ *
+ * Conventions for every entry point:
+ *   - Status: an int, NOC_OK (0) or one of the NOC_ERR_* codes below;
+ *     noc_last_error() returns a thread-local message for the last failure.
+ *   - Pointers named `out`/`bins`/`buf` are HOST memory owned by the caller,
+ *     large enough for the stated element count; the library only writes them.
+ *   - Handles are owned by the caller and released with noc_destroy().
+ *   - Device work is enqueued on the stream set by noc_set_stream (default:
+ *     the legacy default stream).  noc_step returns after enqueueing; the
+ *     query functions (noc_stats, noc_state_hash, ...) synchronise that stream
+ *     first.  A handle must not be used from two host threads at once.
+ *   - Results depend only on the arguments: never on the stream, the CTA tile
+ *     shape, or on what else runs on the GPU.
+ */
+#ifndef NOC_H
+#define NOC_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NOC_OK 0
+#define NOC_ERR_ARG 1            /* invalid argument or configuration            */
+#define NOC_ERR_OOM 2            /* device or host allocation failed             */
+#define NOC_ERR_QUEUE_OVERFLOW 3 /* a service queue or memory FIFO overflowed    */
+#define NOC_ERR_TIMEOUT 4        /* a device-side wait ran past its limit        */
+#define NOC_ERR_CUDA 5           /* a CUDA runtime call failed                   */
+#define NOC_ERR_PROTOCOL 6       /* a reply arrived that matches no request      */
+#define NOC_ERR_STATE 7          /* call not valid in the handle's current state */
+
+/* L2 placement (Sec. 3): interleaved homes; LSPD with local placement and a
+ * home-tile directory (Sec. 3.2, Sec. 6.2.2); LSPD plus migration and
+ * redirection (Sec. 3.3). */
+#define NOC_L2_INTERLEAVED 0
+#define NOC_L2_LSPD_LOCAL 1
+#define NOC_L2_LSPD_MIGRATE 2
+
+/* reference streams: Philox cache traffic (the synthetic stand-in for the
+ * paper's trace-driven input, Sec. 6.2.3), network-only probes, or
+ * caller-supplied per-core traces */
+#define NOC_MODE_CACHE 0
+#define NOC_MODE_NETWORK 1
+#define NOC_MODE_TRACE 2
+
+/* Cache geometry and latencies (64 B lines).  Paper Sec. 3.1 (private L1,
+ * equal L2 slices), Table 4 (set/way/line configurations). */
+typedef struct {
+  int32_t l1_sets, l1_ways;   /* ways 1..16 */
+  int32_t l2_sets, l2_ways;   /* ways 1..16 */
+  int32_t l1_miss_cycles;     /* L1 miss wait before the L2 step (Sec. 7.1) */
+  int32_t mem_latency;        /* cycles of an off-chip access, >= 1         */
+  int32_t mig_window;         /* accessors remembered per L2 block (Sec. 3.1), 1..30 */
+  int32_t mig_threshold;      /* occurrences of one requester that migrate the block */
+  int32_t core_q;             /* core send-queue capacity (back-pressure)    */
+  int32_t svc_q;              /* service-queue capacity (overflow = error)   */
+  int32_t mem_q;              /* memory-return FIFO capacity (overflow = error) */
+  int32_t fwd_entries;        /* redirection forward-table entries per tile  */
+} noc_cache_cfg;
+
+/* Reference stream.  Fractions are q16 fixed point (65536 = 1).  Reference k
+ * of core c is eligible at cycle k*period and is drawn from
+ * Philox4x64-10(counter=(k, c, stream, 0), key=(seed, 0x4E4F43)). */
+typedef struct {
+  int32_t mode;               /* NOC_MODE_*; period 0 = no references        */
+  int32_t period;
+  uint32_t write_q16, priv_q16, shared_q16; /* remote = the rest            */
+  uint32_t hot_q16;           /* share of shared refs sent to the hot block  */
+  int32_t hot_side;           /* side of the hot block of tiles at the centre (0 = none) */
+  uint32_t priv_lines, shared_lines, remote_lines;
+  uint32_t stream;            /* Philox counter word 2                       */
+} noc_traffic;
+
+/* Totals over all tiles (lat_max is a maximum).  Counter definitions follow
+ * the paper's statistics list (Sec. 6.2.2, Table 3 columns). */
+typedef struct {
+  uint64_t cycle;
+  uint64_t injected, ejected, in_flight, deflections, lat_sum, lat_max, refs;
+  uint64_t l1_hit, l1_miss, l2_hit, l2_miss;
+  uint64_t req_made, req_rcvd, reply_sent, reply_rcvd, dir_search, mem_req;
+  uint64_t mem_write, mem_wb, wt_sent, wt_hit, trap, redir, migrations;
+  uint64_t l2lat_sum, l2lat_cnt, cq_stall, mm_stall, mig_sent;
+} noc_stats_t;
+
+#define NOC_HIST_BINS 1025 /* 1-cycle bins 0..1023 plus one overflow bin */
+
+typedef struct noc_sim noc_sim;
+
+/* Create a simulation handle (host-side only; device memory is taken at the
+ * first call that needs it, from noc_bind_memory or else cudaMalloc on the
+ * current device).  Returns NOC_ERR_ARG for an invalid configuration
+ * (mesh_w * mesh_h above the co-resident limit, bad geometry). */
+int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* cache, int l2_policy,
+               const noc_traffic* traffic, uint64_t seed, noc_sim** out);
+void noc_destroy(noc_sim* sim);
+
+/* Device bytes the handle needs; give the library caller-owned device memory
+ * (at least that many bytes, 256-byte aligned) that it will never free. */
+size_t noc_required_bytes(const noc_sim* sim);
+int noc_bind_memory(noc_sim* sim, void* dev_ptr, size_t bytes);
+
+/* cudaStream_t to enqueue on (NULL = default stream). */
+int noc_set_stream(noc_sim* sim, void* cuda_stream);
+
+/* Return to cycle 0: empty caches, links, queues, counters (enqueued). */
+int noc_reset(noc_sim* sim);
+
+/* Enqueue n_cycles simulated cycles (Sec. 7.2 main loop) as persistent
+ * cooperative launches.  Returns the first error of earlier work if one is
+ * already known, else NOC_OK. */
+int noc_step(noc_sim* sim, int64_t n_cycles);
+
+/* Stop issuing references and run until nothing is in flight, queued or
+ * outstanding, or max_cycles pass.  *taken = cycles run.  Synchronous.
+ * NOC_ERR_TIMEOUT if not quiescent after max_cycles. */
+int noc_drain(noc_sim* sim, int64_t max_cycles, int64_t* taken);
+
+/* Wait for enqueued work; return the first device error (NOC_OK if none) and,
+ * if err_cycle != NULL, the simulated cycle it happened in (-1 if none). */
+int noc_sync(noc_sim* sim, int64_t* err_cycle);
+
+/* Totals (tile < 0) or one tile's counters, copied to host memory. */
+int noc_stats(noc_sim* sim, int tile, noc_stats_t* out);
+/* which: 0 = flit latency, 1 = L2 access latency; bins: nbins >= NOC_HIST_BINS */
+int noc_latency_hist(noc_sim* sim, int which, uint64_t* bins, int nbins);
+
+/* Order-free hashes of the simulation state (definitions in the model text):
+ * the dynamic state after the last cycle, and the full state. */
+int noc_dyn_hash(noc_sim* sim, uint64_t* out);
+int noc_state_hash(noc_sim* sim, uint64_t* out);
+/* Record the dynamic hash after every cycle of the following noc_step calls
+ * (enable != 0), and read the records of the last step: buf has n slots. */
+int noc_set_hash_trace(noc_sim* sim, int enable);
+int noc_hash_trace(noc_sim* sim, uint64_t* buf, int64_t n);
+
+/* CTA rectangle grid (gx x gy rectangles of the mesh, one CTA each).
+ * 0,0 = the library's choice.  Results never depend on it. */
+int noc_set_tiling(noc_sim* sim, int gx, int gy);
+int noc_get_tiling(const noc_sim* sim, int* gx, int* gy);
+
+/* Trace mode: reference list of one core (line | write << 31), copied. */
+int noc_set_trace(noc_sim* sim, int core, int64_t n, const uint32_t* refs);
+
+/* Test and inspection entry points (synchronous, between steps).
+ * Flits are 7 host words: type, src, dst, inject_cycle, line, a, e. */
+int noc_debug_enqueue(noc_sim* sim, int tile, int queue /*0 core,1 service*/,
+                      const uint32_t* flit7);
+int noc_debug_link(noc_sim* sim, int tile, int dir /*0 N,1 S,2 E,3 W*/,
+                   const uint32_t* flit7);
+int noc_get_links(noc_sim* sim, uint32_t* out /* N*4*7 */);
+int noc_get_cache(noc_sim* sim, int tile, int which /*1 L1, 2 L2*/,
+                  uint32_t* out /* sets*ways*4: valid, line, aux, rank */);
+int noc_dir_get(noc_sim* sim, uint32_t line, uint32_t* out);
+int noc_get_core(noc_sim* sim, int tile, uint32_t* out17);
+/* Device-wait limit in nanoseconds (default 2e9) and a test fault: CTA
+ * `silent_cta` stops publishing its cycle (-1 = none), so its neighbours'
+ * bounded waits run out and the step ends with NOC_ERR_TIMEOUT. */
+int noc_debug_wait_limit(noc_sim* sim, int64_t ns, int silent_cta);
+
+/* Number of this library's kernels launched through this handle. */
+int64_t noc_kernel_launches(const noc_sim* sim);
+
+const char* noc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

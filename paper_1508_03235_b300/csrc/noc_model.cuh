@@ -1,0 +1,1021 @@
+// noc_model.cuh -- device-side model of one tile of the simulated multicore.
+//
+// One CUDA thread owns one tile for a whole launch and keeps its core state,
+// queue heads and counters in registers; caches, queues and the directory stay
+// in HBM.  The three phases of the paper's cycle (Sec. 7.1) are the functions
+// phase1 / route / phase3 below; the persistent kernel in noc_kernel.cu calls
+// them in the order P2(t) -> P3(t) -> P1(t+1) so that the cache work of a tile
+// overlaps the wait for its neighbours' outputs.
+#pragma once
+#include <cstdint>
+
+namespace noc {
+
+// ---------------------------------------------------------------- constants
+enum : uint32_t {
+  T_NONE = 0, T_REQ = 1, T_DATA = 2, T_WT = 3, T_DA = 4, T_DRPOS = 5, T_DRNEG = 6,
+  T_NACK = 7, T_DINV = 8, T_MIG = 9, T_DIRUPD = 10, T_INV = 11, T_PROBE = 12
+};
+enum : uint32_t { FSM_IDLE = 0, FSM_L2WAIT = 1, FSM_STALL = 2 };
+enum : uint32_t { OM_NONE = 0, OM_WAIT_DR = 1, OM_WAIT_DATA = 2, OM_MEM_L2 = 3, OM_MEM_L1 = 4 };
+enum : int { P_N = 0, P_S = 1, P_E = 2, P_W = 3 };
+enum : int { POL_INTERLEAVED = 0, POL_LOCAL = 1, POL_MIGRATE = 2 };
+enum : int { MODE_CACHE = 0, MODE_NETWORK = 1, MODE_TRACE = 2 };
+enum : int { ERR_OVERFLOW = 3, ERR_TIMEOUT = 4, ERR_PROTOCOL = 6 };
+
+constexpr uint32_t NO_TILE = 0xFFFFu;
+constexpr uint32_t DIR_NONE = 0xFFFFFFFFu;
+constexpr int HIST_BINS = 1025;
+constexpr int MAX_WAYS = 16;
+constexpr int HIST_STRIDE = 32;  // u16 per L2 way: [n, migrating, who x30]
+
+// cache way word: bit31 valid | bits27-30 LRU rank | bit26 dirty | bits0-25 line
+constexpr uint32_t W_VALID = 1u << 31;
+constexpr uint32_t W_DIRTY = 1u << 26;
+constexpr uint32_t W_LINE = (1u << 26) - 1;
+constexpr int W_RANK_SHIFT = 27;
+
+// counters kept per tile (order = the model's statistics list)
+enum : int {
+  S_INJ = 0, S_EJ, S_DEFL, S_LATSUM, S_LATMAX, S_REFS, S_L1H, S_L1M, S_L2H, S_L2M,
+  S_REQM, S_REQR, S_REPS, S_REPR, S_DIRS, S_MEMREQ, S_MEMW, S_MEMWB, S_WTS, S_WTH,
+  S_TRAP, S_REDIR, S_MIGR, S_L2LSUM, S_L2LCNT, S_CQST, S_MMST, S_MIGS, NSTAT
+};
+// counters from S_REFS on are 32-bit per-launch deltas in registers (the
+// L2-latency sum is kept separately as 64 bits)
+constexpr int NSMALL = NSTAT - S_REFS;
+
+// core-state SoA fields ([field][tile] u32), saved between launches
+enum : int {
+  C_NEXT = 0, C_FSMB, C_FLINE, C_FTIMER, C_FSTART, C_OLINE, C_OSTART, C_OTIMER, C_EPOCH,
+  C_CQ, C_SQ, C_MQ, C_FWD, NCORE
+};
+
+// ---------------------------------------------------------------- parameters
+struct Params {
+  int W, H, N, policy, mode, period;
+  int l1_sets, l1_ways, l2_sets, l2_ways;
+  int l1_miss, mem_lat, mig_window, mig_threshold;
+  int core_q, svc_q, mem_q, fwd_cap;
+  uint32_t write_q16, priv_q16, shared_q16, hot_q16;
+  int hot_side, hot_x0, hot_y0;
+  uint32_t priv_lines, shared_lines, remote_lines, total_lines;
+  unsigned long long seed;
+  uint32_t stream;
+  // device arrays
+  uint4* glink;          // [2][4][N] out-links by parity, port, tile
+  uint32_t* core;        // [NCORE][N]
+  uint4* cq;             // [N][core_q]
+  uint4* sq;             // [N][svc_q]
+  uint4* mq;             // [N][mem_q]  (ready, line, requester, 0)
+  uint32_t* l1;          // [N][l1_sets][l1_ways] way words
+  uint16_t* l1own;       // [N][l1_sets][l1_ways]
+  uint32_t* l2;          // [N][l2_sets][l2_ways] way words
+  uint16_t* l2ep;        // [N][l2_sets][l2_ways]    (LSPD)
+  uint16_t* l2hist;      // [N][l2_sets][l2_ways][HIST_STRIDE] (migrate)
+  uint32_t* dir;         // [total_lines]            (LSPD)
+  uint32_t* fwd;         // [N][fwd_cap][2]          (migrate)
+  uint32_t* trace_off;   // [N+1]                    (trace mode)
+  uint32_t* trace;       // refs                     (trace mode)
+  unsigned long long* stats;  // [NSTAT][N]
+  unsigned long long* hist;   // [2][HIST_BINS]
+  unsigned int* flags;        // [CTAs] last completed cycle + 1
+  unsigned long long* err;    // min over (cycle << 8 | code); ~0 = none
+};
+
+// ---------------------------------------------------------------- flits
+// uint4 flit: x = inject cycle, y = src | dst << 16, z = line | type << 26,
+// w = a | e << 16.  All-zero = empty link.
+__device__ __forceinline__ uint4 mkflit(uint32_t type, uint32_t src, uint32_t dst, uint32_t line,
+                                        uint32_t a, uint32_t e) {
+  return make_uint4(0u, src | (dst << 16), line | (type << 26), a | (e << 16));
+}
+__device__ __forceinline__ uint32_t ftype(uint4 f) { return f.z >> 26; }
+__device__ __forceinline__ uint32_t fline(uint4 f) { return f.z & W_LINE; }
+__device__ __forceinline__ uint32_t fsrc(uint4 f) { return f.y & 0xFFFFu; }
+__device__ __forceinline__ uint32_t fdst(uint4 f) { return f.y >> 16; }
+__device__ __forceinline__ uint32_t fa(uint4 f) { return f.w & 0xFFFFu; }
+__device__ __forceinline__ uint32_t fe(uint4 f) { return f.w >> 16; }
+// priority key: older (smaller inject cycle) first, then smaller source
+__device__ __forceinline__ unsigned long long fkey(uint4 f) {
+  return ((unsigned long long)f.x << 16) | (f.y & 0xFFFFu);
+}
+
+// ---------------------------------------------------------------- hashing
+// splitmix64 finaliser and the fold used by every state hash
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned long long hstart(unsigned long long w) {
+  return mix64(w + 0x9E3779B97F4A7C15ull);
+}
+__device__ __forceinline__ unsigned long long hfold(unsigned long long h, unsigned long long w) {
+  return mix64(h ^ w);
+}
+__device__ __forceinline__ unsigned long long hflit(unsigned long long h, uint4 f) {
+  uint32_t ty = ftype(f);
+  unsigned long long w0 = 0, w1 = 0, w2 = 0;
+  if (ty) {
+    w0 = (unsigned long long)ty | ((unsigned long long)fsrc(f) << 16) |
+         ((unsigned long long)fdst(f) << 32) | ((unsigned long long)fa(f) << 48);
+    w1 = (unsigned long long)fline(f) | ((unsigned long long)f.x << 32);
+    w2 = fe(f);
+  }
+  h = hfold(h, w0);
+  h = hfold(h, w1);
+  return hfold(h, w2);
+}
+
+// ---------------------------------------------------------------- Philox
+// Philox4x64-10 from its published definition (Salmon, Moraes, Dror, Shaw,
+// SC'11): ten rounds; each multiplies words 0 and 2 by the round constants,
+// swaps the halves in and xors in the key; the key is bumped between rounds.
+__device__ __forceinline__ void philox4x64_10(unsigned long long c0, unsigned long long c1,
+                                              unsigned long long c2, unsigned long long c3,
+                                              unsigned long long k0, unsigned long long k1,
+                                              unsigned long long out[4]) {
+  const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B97F4A7C15ull;
+      k1 += 0xBB67AE8584CAA73Bull;
+    }
+    unsigned long long hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    unsigned long long hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    unsigned long long n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+// ---------------------------------------------------------------- tile state
+struct Tile {
+  uint32_t r, x, y;
+  uint32_t next_ref, fsm, fsm_write, fsm_line, fsm_timer, fsm_start;
+  uint32_t om_kind, om_write, om_line, om_start, om_timer, om_epoch, epoch;
+  uint32_t cq_head, cq_len, sq_head, sq_len, mq_head, mq_len, fwd_next, fwd_n;
+  uint4 cq_front, sq_front, mq_front;  // cached queue heads (valid when len > 0)
+  uint4 ej;                            // flit ejected this cycle (or empty)
+  unsigned long long inj, ejc, defl, latsum, latmax, l2lsum;
+  uint32_t sm[NSMALL];                 // small per-launch counter deltas
+};
+#define SMALL(i) T.sm[(i)-S_REFS]
+
+__device__ __forceinline__ void set_error(const Params& P, uint32_t t, int code) {
+  atomicMin(P.err, ((unsigned long long)t << 8) | (unsigned long long)code);
+}
+
+__device__ __forceinline__ uint32_t home_of(const Params& P, uint32_t line) {
+  return line % (uint32_t)P.N;
+}
+__device__ __forceinline__ uint32_t l1_set(const Params& P, uint32_t line) {
+  return line % (uint32_t)P.l1_sets;
+}
+__device__ __forceinline__ uint32_t l2_set(const Params& P, uint32_t line) {
+  if (P.policy == POL_INTERLEAVED) return (line / (uint32_t)P.N) % (uint32_t)P.l2_sets;
+  return line % (uint32_t)P.l2_sets;
+}
+
+// ---------------------------------------------------------------- queues
+__device__ __forceinline__ void count_sent(Tile& T, uint32_t ty) {
+  if (ty == T_WT) SMALL(S_WTS)++;
+  if (ty == T_REQ) SMALL(S_REQM)++;
+  if (ty == T_DATA || ty == T_DRPOS || ty == T_DRNEG || ty == T_NACK) SMALL(S_REPS)++;
+}
+__device__ __forceinline__ void send_svc(const Params& P, Tile& T, uint4 f, uint32_t t) {
+  if (T.sq_len >= (uint32_t)P.svc_q) {
+    set_error(P, t, ERR_OVERFLOW);
+    return;
+  }
+  count_sent(T, ftype(f));
+  uint32_t slot = T.sq_head + T.sq_len;
+  if (slot >= (uint32_t)P.svc_q) slot -= P.svc_q;
+  P.sq[(size_t)T.r * P.svc_q + slot] = f;
+  if (T.sq_len == 0) T.sq_front = f;
+  T.sq_len++;
+}
+__device__ __forceinline__ void send_core(const Params& P, Tile& T, uint4 f) {
+  count_sent(T, ftype(f));
+  uint32_t slot = T.cq_head + T.cq_len;
+  if (slot >= (uint32_t)P.core_q) slot -= P.core_q;
+  P.cq[(size_t)T.r * P.core_q + slot] = f;
+  if (T.cq_len == 0) T.cq_front = f;
+  T.cq_len++;
+}
+__device__ __forceinline__ bool cq_full(const Params& P, const Tile& T) {
+  return T.cq_len >= (uint32_t)P.core_q;
+}
+
+// ---------------------------------------------------------------- cache sets
+// A set's way words live in registers while it is worked on; the loops are
+// fully unrolled over MAX_WAYS so the array never leaves the register file.
+__device__ __forceinline__ void load_set(const uint32_t* p, int ways, uint32_t (&w)[MAX_WAYS]) {
+#pragma unroll
+  for (int i = 0; i < MAX_WAYS; ++i) w[i] = 0;
+  if ((ways & 3) == 0) {
+#pragma unroll
+    for (int q = 0; q < MAX_WAYS / 4; ++q)
+      if (q * 4 < ways) {
+        uint4 v = reinterpret_cast<const uint4*>(p)[q];
+        w[q * 4] = v.x;
+        w[q * 4 + 1] = v.y;
+        w[q * 4 + 2] = v.z;
+        w[q * 4 + 3] = v.w;
+      }
+  } else {
+#pragma unroll
+    for (int i = 0; i < MAX_WAYS; ++i)
+      if (i < ways) w[i] = p[i];
+  }
+}
+__device__ __forceinline__ void store_set(uint32_t* p, int ways, const uint32_t (&w)[MAX_WAYS]) {
+  if ((ways & 3) == 0) {
+#pragma unroll
+    for (int q = 0; q < MAX_WAYS / 4; ++q)
+      if (q * 4 < ways)
+        reinterpret_cast<uint4*>(p)[q] = make_uint4(w[q * 4], w[q * 4 + 1], w[q * 4 + 2], w[q * 4 + 3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < MAX_WAYS; ++i)
+      if (i < ways) p[i] = w[i];
+  }
+}
+__device__ __forceinline__ uint32_t wrank(uint32_t v) { return (v >> W_RANK_SHIFT) & 15u; }
+__device__ __forceinline__ uint32_t wset_rank(uint32_t v, uint32_t r) {
+  return (v & ~(15u << W_RANK_SHIFT)) | (r << W_RANK_SHIFT);
+}
+__device__ __forceinline__ int set_find(const uint32_t (&w)[MAX_WAYS], int ways, uint32_t line) {
+  int found = -1;
+#pragma unroll
+  for (int i = MAX_WAYS - 1; i >= 0; --i)
+    if (i < ways && (w[i] & W_VALID) && (w[i] & W_LINE) == line) found = i;
+  return found;
+}
+// make way `way` the most recently used; `prev_rank` is its rank before (the
+// number of valid ways for a way that was invalid)
+__device__ __forceinline__ void set_promote(uint32_t (&w)[MAX_WAYS], int ways, int way,
+                                            uint32_t prev_rank) {
+#pragma unroll
+  for (int i = 0; i < MAX_WAYS; ++i)
+    if (i < ways && i != way && (w[i] & W_VALID) && wrank(w[i]) < prev_rank)
+      w[i] = wset_rank(w[i], wrank(w[i]) + 1);
+#pragma unroll
+  for (int i = 0; i < MAX_WAYS; ++i)
+    if (i == way) w[i] = wset_rank(w[i], 0);
+}
+__device__ __forceinline__ uint32_t set_get(const uint32_t (&w)[MAX_WAYS], int way) {
+  uint32_t v = 0;
+#pragma unroll
+  for (int i = 0; i < MAX_WAYS; ++i)
+    if (i == way) v = w[i];
+  return v;
+}
+__device__ __forceinline__ void set_put(uint32_t (&w)[MAX_WAYS], int way, uint32_t v) {
+#pragma unroll
+  for (int i = 0; i < MAX_WAYS; ++i)
+    if (i == way) w[i] = v;
+}
+__device__ __forceinline__ void set_touch(uint32_t (&w)[MAX_WAYS], int ways, int way) {
+  set_promote(w, ways, way, wrank(set_get(w, way)));
+}
+// victim: lowest-index invalid way, else the least recently used way
+__device__ __forceinline__ int set_victim(const uint32_t (&w)[MAX_WAYS], int ways) {
+  int inv = -1, lru = 0;
+#pragma unroll
+  for (int i = MAX_WAYS - 1; i >= 0; --i)
+    if (i < ways) {
+      if (!(w[i] & W_VALID)) inv = i;
+      else if (wrank(w[i]) == (uint32_t)(ways - 1)) lru = i;
+    }
+  return inv >= 0 ? inv : lru;
+}
+__device__ __forceinline__ uint32_t set_nvalid(const uint32_t (&w)[MAX_WAYS], int ways) {
+  uint32_t n = 0;
+#pragma unroll
+  for (int i = 0; i < MAX_WAYS; ++i)
+    if (i < ways && (w[i] & W_VALID)) n++;
+  return n;
+}
+// remove way `way`; the ways it was more recent than move up one rank
+__device__ __forceinline__ void set_invalidate(uint32_t (&w)[MAX_WAYS], int ways, int way) {
+  uint32_t rk = wrank(set_get(w, way));
+#pragma unroll
+  for (int i = 0; i < MAX_WAYS; ++i)
+    if (i < ways && i != way && (w[i] & W_VALID) && wrank(w[i]) > rk)
+      w[i] = wset_rank(w[i], wrank(w[i]) - 1);
+  set_put(w, way, 0u);
+}
+
+__device__ __forceinline__ size_t l1_base(const Params& P, uint32_t r, uint32_t set) {
+  return ((size_t)r * P.l1_sets + set) * P.l1_ways;
+}
+__device__ __forceinline__ size_t l2_base(const Params& P, uint32_t r, uint32_t set) {
+  return ((size_t)r * P.l2_sets + set) * P.l2_ways;
+}
+
+// fill the L1 with `line` (insert if absent, else touch); L1 victims are clean
+__device__ void l1_fill(const Params& P, Tile& T, uint32_t line, uint32_t owner) {
+  uint32_t set = l1_set(P, line);
+  size_t base = l1_base(P, T.r, set);
+  uint32_t w[MAX_WAYS];
+  load_set(P.l1 + base, P.l1_ways, w);
+  int way = set_find(w, P.l1_ways, line);
+  if (way >= 0) {
+    set_touch(w, P.l1_ways, way);
+  } else {
+    way = set_victim(w, P.l1_ways);
+    uint32_t old = set_get(w, way);
+    uint32_t prev = (old & W_VALID) ? wrank(old) : set_nvalid(w, P.l1_ways);
+    set_put(w, way, W_VALID | line);
+    set_promote(w, P.l1_ways, way, prev);
+  }
+  store_set(P.l1 + base, P.l1_ways, w);
+  P.l1own[base + way] = (uint16_t)owner;
+}
+
+__device__ __forceinline__ uint16_t* hist_ptr(const Params& P, size_t way_index) {
+  return P.l2hist + way_index * HIST_STRIDE;
+}
+
+// directory entry delete for an evicted L2 victim (Sec. 3.4)
+__device__ void send_dinv(const Params& P, Tile& T, uint32_t vline, uint32_t vepoch, uint32_t t) {
+  uint32_t h = home_of(P, vline);
+  if (h == T.r) {
+    if (P.dir[vline] == (T.r | (vepoch << 16))) P.dir[vline] = DIR_NONE;
+  } else {
+    send_svc(P, T, mkflit(T_DINV, T.r, h, vline, 0, vepoch), t);
+  }
+}
+
+// install `line` in this tile's L2 slice: insert if absent (evicting the
+// victim), else touch; returns the way index
+__device__ int l2_install(const Params& P, Tile& T, uint32_t line, uint32_t epoch, uint32_t t) {
+  uint32_t set = l2_set(P, line);
+  size_t base = l2_base(P, T.r, set);
+  uint32_t w[MAX_WAYS];
+  load_set(P.l2 + base, P.l2_ways, w);
+  int way = set_find(w, P.l2_ways, line);
+  if (way >= 0) {
+    set_touch(w, P.l2_ways, way);
+  } else {
+    way = set_victim(w, P.l2_ways);
+    uint32_t old = set_get(w, way);
+    uint32_t prev;
+    if (old & W_VALID) {
+      prev = wrank(old);
+      if (old & W_DIRTY) SMALL(S_MEMWB)++;
+      if (P.policy != POL_INTERLEAVED) send_dinv(P, T, old & W_LINE, P.l2ep[base + way], t);
+    } else {
+      prev = set_nvalid(w, P.l2_ways);
+    }
+    set_put(w, way, W_VALID | line);
+    set_promote(w, P.l2_ways, way, prev);
+    if (P.policy == POL_MIGRATE) {
+      uint16_t* hp = hist_ptr(P, base + way);
+      hp[0] = 0;
+      hp[1] = 0;
+    }
+  }
+  store_set(P.l2 + base, P.l2_ways, w);
+  if (P.policy != POL_INTERLEAVED) P.l2ep[base + way] = (uint16_t)epoch;
+  return way;
+}
+
+// write-through performed at this tile's own slice
+__device__ void local_wt(const Params& P, Tile& T, uint32_t line) {
+  uint32_t set = l2_set(P, line);
+  size_t base = l2_base(P, T.r, set);
+  uint32_t w[MAX_WAYS];
+  load_set(P.l2 + base, P.l2_ways, w);
+  int way = set_find(w, P.l2_ways, line);
+  if (way >= 0) {
+    set_put(w, way, set_get(w, way) | W_DIRTY);
+    set_touch(w, P.l2_ways, way);
+    store_set(P.l2 + base, P.l2_ways, w);
+    SMALL(S_WTH)++;
+  } else {
+    SMALL(S_MEMW)++;
+  }
+}
+
+// record accessor `who` in the block's history of the last mig_window accessors
+__device__ void hist_push(const Params& P, size_t way_index, uint32_t who) {
+  uint16_t* hp = hist_ptr(P, way_index);
+  uint32_t n = hp[0];
+  if (n < (uint32_t)P.mig_window) {
+    hp[2 + n] = (uint16_t)who;
+    hp[0] = (uint16_t)(n + 1);
+  } else {
+    for (int i = 0; i + 1 < P.mig_window; ++i) hp[2 + i] = hp[3 + i];
+    hp[2 + P.mig_window - 1] = (uint16_t)who;
+  }
+}
+
+__device__ __forceinline__ void l2lat_sample(Tile& T, uint32_t t, uint32_t start,
+                                             uint32_t* sh_hist) {
+  uint32_t lat = t - start;
+  T.l2lsum += lat;
+  SMALL(S_L2LCNT)++;
+  atomicAdd(&sh_hist[HIST_BINS + (lat < HIST_BINS - 1 ? lat : HIST_BINS - 1)], 1u);
+}
+
+__device__ __forceinline__ void set_om(Tile& T, uint32_t kind, uint32_t line, uint32_t write,
+                                       uint32_t start) {
+  T.om_kind = kind;
+  T.om_line = line;
+  T.om_write = write;
+  T.om_start = start;
+  T.om_timer = 0;
+  T.om_epoch = 0;
+}
+
+// ---------------------------------------------------------------- Phase 1
+// the L1 lookup of a reference; returns false if the action was not taken
+__device__ bool l1_step(const Params& P, Tile& T, uint32_t t, uint32_t line, uint32_t write) {
+  uint32_t set = l1_set(P, line);
+  size_t base = l1_base(P, T.r, set);
+  uint32_t w[MAX_WAYS];
+  load_set(P.l1 + base, P.l1_ways, w);
+  int way = set_find(w, P.l1_ways, line);
+  if (way >= 0) {
+    if (write) {
+      uint32_t owner = P.l1own[base + way];
+      if (owner == T.r) {
+        local_wt(P, T, line);
+      } else if (owner == NO_TILE) {
+        SMALL(S_MEMW)++;
+      } else {
+        if (cq_full(P, T)) {
+          SMALL(S_CQST)++;
+          return false;
+        }
+        send_core(P, T, mkflit(T_WT, T.r, owner, line, 0, 0));
+      }
+    }
+    set_touch(w, P.l1_ways, way);
+    store_set(P.l1 + base, P.l1_ways, w);
+    SMALL(S_L1H)++;
+    T.fsm = FSM_IDLE;
+    return true;
+  }
+  SMALL(S_L1M)++;
+  T.fsm = FSM_L2WAIT;
+  T.fsm_line = line;
+  T.fsm_write = write;
+  T.fsm_start = t;
+  T.fsm_timer = t + (uint32_t)P.l1_miss;
+  return true;
+}
+
+__device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* sh_hist) {
+  const uint32_t line = T.fsm_line, start = T.fsm_start, write = T.fsm_write;
+  const bool busy = T.om_kind != OM_NONE;
+  uint32_t set = l2_set(P, line);
+  size_t base = l2_base(P, T.r, set);
+
+  if (P.policy == POL_INTERLEAVED) {
+    uint32_t h = home_of(P, line);
+    if (h == T.r) {
+      uint32_t w[MAX_WAYS];
+      load_set(P.l2 + base, P.l2_ways, w);
+      int way = set_find(w, P.l2_ways, line);
+      if (way >= 0) {
+        SMALL(S_L2H)++;
+        set_touch(w, P.l2_ways, way);
+        store_set(P.l2 + base, P.l2_ways, w);
+        l1_fill(P, T, line, T.r);
+        if (write) local_wt(P, T, line);
+        l2lat_sample(T, t, start, sh_hist);
+        T.fsm = FSM_IDLE;
+        return;
+      }
+      if (busy) {
+        SMALL(S_MMST)++;
+        T.fsm = FSM_STALL;
+        return;
+      }
+      SMALL(S_L2M)++;
+      SMALL(S_MEMREQ)++;
+      set_om(T, OM_MEM_L2, line, write, start);
+      T.om_timer = t + (uint32_t)P.mem_lat;
+      T.fsm = FSM_IDLE;
+      return;
+    }
+    if (busy) {
+      SMALL(S_MMST)++;
+      T.fsm = FSM_STALL;
+      return;
+    }
+    if (cq_full(P, T)) {
+      SMALL(S_CQST)++;
+      return;
+    }
+    send_core(P, T, mkflit(T_REQ, T.r, h, line, T.r, 0));
+    set_om(T, OM_WAIT_DATA, line, write, start);
+    T.fsm = FSM_IDLE;
+    return;
+  }
+
+  // LSPD: the requester's own slice first (local placement, Sec. 3.3)
+  uint32_t w[MAX_WAYS];
+  load_set(P.l2 + base, P.l2_ways, w);
+  int way = set_find(w, P.l2_ways, line);
+  if (way >= 0) {
+    SMALL(S_L2H)++;
+    set_touch(w, P.l2_ways, way);
+    store_set(P.l2 + base, P.l2_ways, w);
+    if (P.policy == POL_MIGRATE) hist_push(P, base + way, T.r);
+    l1_fill(P, T, line, T.r);
+    if (write) local_wt(P, T, line);
+    l2lat_sample(T, t, start, sh_hist);
+    T.fsm = FSM_IDLE;
+    return;
+  }
+  if (busy) {
+    SMALL(S_MMST)++;
+    T.fsm = FSM_STALL;
+    return;
+  }
+  uint32_t h = home_of(P, line);
+  if (h == T.r) {
+    uint32_t D = P.dir[line];
+    if (D == DIR_NONE || (D & 0xFFFFu) == T.r) {
+      SMALL(S_L2M)++;
+      SMALL(S_DIRS)++;
+      T.epoch = (T.epoch + 1) & 0xFFFFu;
+      P.dir[line] = T.r | (T.epoch << 16);
+      set_om(T, OM_MEM_L2, line, write, start);
+      T.om_timer = t + (uint32_t)P.mem_lat;
+      T.om_epoch = T.epoch;
+      SMALL(S_MEMREQ)++;
+      T.fsm = FSM_IDLE;
+      return;
+    }
+    if (cq_full(P, T)) {
+      SMALL(S_CQST)++;
+      return;
+    }
+    SMALL(S_L2M)++;
+    SMALL(S_DIRS)++;
+    send_core(P, T, mkflit(T_REQ, T.r, D & 0xFFFFu, line, T.r, 0));
+    set_om(T, OM_WAIT_DATA, line, write, start);
+    T.fsm = FSM_IDLE;
+    return;
+  }
+  if (cq_full(P, T)) {
+    SMALL(S_CQST)++;
+    return;
+  }
+  SMALL(S_L2M)++;
+  T.epoch = (T.epoch + 1) & 0xFFFFu;
+  send_core(P, T, mkflit(T_DA, T.r, h, line, 0, T.epoch));
+  set_om(T, OM_WAIT_DR, line, write, start);
+  T.fsm = FSM_IDLE;
+}
+
+// the line of reference k of this core (Philox stream, Sec. 6.2.3 stand-in)
+__device__ uint32_t draw_line(const Params& P, uint32_t core, uint32_t k, uint32_t& write) {
+  unsigned long long w[4];
+  philox4x64_10(k, core, P.stream, 0, P.seed, 0x4E4F43ull, w);
+  write = (uint32_t)(w[0] >> 48) < P.write_q16 ? 1u : 0u;
+  uint32_t r16 = (uint32_t)(w[1] >> 48);
+  const uint32_t shared_base = P.remote_lines;
+  if (r16 < P.priv_q16)
+    return P.remote_lines + P.shared_lines + core * P.priv_lines +
+           (uint32_t)__umul64hi(w[2], P.priv_lines);
+  if (r16 < P.priv_q16 + P.shared_q16) {
+    if (P.hot_side > 0 && (uint32_t)(w[3] >> 48) < P.hot_q16) {
+      const uint32_t hs = (uint32_t)P.hot_side;
+      uint32_t j = (uint32_t)__umul64hi(w[2], (unsigned long long)hs * hs);
+      uint32_t hj = (uint32_t)(P.hot_y0 + j / hs) * (uint32_t)P.W + (uint32_t)P.hot_x0 + j % hs;
+      const uint32_t N = (uint32_t)P.N;
+      uint32_t i0 = (hj + N - shared_base % N) % N;
+      uint32_t cnt = P.shared_lines > i0 ? (P.shared_lines - i0 + N - 1) / N : 0;
+      if (cnt > 0) return shared_base + i0 + (uint32_t)__umul64hi(w[3] << 16, cnt) * N;
+    }
+    return shared_base + (uint32_t)__umul64hi(w[2], P.shared_lines);
+  }
+  return (uint32_t)__umul64hi(w[2], P.remote_lines);
+}
+
+__device__ __forceinline__ void mq_pop(const Params& P, Tile& T) {
+  T.mq_head = T.mq_head + 1 == (uint32_t)P.mem_q ? 0 : T.mq_head + 1;
+  T.mq_len--;
+  if (T.mq_len > 0) T.mq_front = P.mq[(size_t)T.r * P.mem_q + T.mq_head];
+}
+
+__device__ void phase1(const Params& P, Tile& T, uint32_t t, bool draining, uint32_t* sh_hist) {
+  // (i) memory returns at an interleaved home: install, then reply
+  while (T.mq_len > 0 && T.mq_front.x <= t) {
+    uint32_t line = T.mq_front.y, req = T.mq_front.z;
+    mq_pop(P, T);
+    l2_install(P, T, line, 0, t);
+    send_svc(P, T, mkflit(T_DATA, T.r, req, line, 0, 0), t);
+  }
+  // (ii) this core's outstanding memory fetch completes
+  if ((T.om_kind == OM_MEM_L2 || T.om_kind == OM_MEM_L1) && T.om_timer <= t) {
+    if (T.om_kind == OM_MEM_L2) {
+      l2_install(P, T, T.om_line, T.om_epoch, t);
+      l1_fill(P, T, T.om_line, T.r);
+      if (T.om_write) local_wt(P, T, T.om_line);
+    } else {
+      l1_fill(P, T, T.om_line, NO_TILE);
+      if (T.om_write) SMALL(S_MEMW)++;
+    }
+    l2lat_sample(T, t, T.om_start, sh_hist);
+    set_om(T, OM_NONE, 0, 0, 0);
+  }
+  // (iii) at most one core action
+  if (T.fsm == FSM_L2WAIT) {
+    if (t >= T.fsm_timer) l2_step(P, T, t, sh_hist);
+    return;
+  }
+  if (T.fsm == FSM_STALL) {
+    if (T.om_kind == OM_NONE) l1_step(P, T, t, T.fsm_line, T.fsm_write);
+    return;
+  }
+  if (draining || P.period <= 0) return;
+  if ((unsigned long long)t < (unsigned long long)T.next_ref * (unsigned long long)P.period) return;
+
+  if (P.mode == MODE_NETWORK) {
+    if (P.N < 2) return;
+    if (cq_full(P, T)) {
+      SMALL(S_CQST)++;
+      return;
+    }
+    unsigned long long w[4];
+    philox4x64_10(T.next_ref, T.r, P.stream, 0, P.seed, 0x4E4F43ull, w);
+    uint32_t dst = (uint32_t)__umul64hi(w[1], (unsigned long long)(P.N - 1));
+    if (dst >= T.r) dst++;
+    send_core(P, T, mkflit(T_PROBE, T.r, dst, 0, 0, 0));
+    T.next_ref++;
+    SMALL(S_REFS)++;
+    return;
+  }
+  uint32_t line, write;
+  if (P.mode == MODE_TRACE) {
+    uint32_t off = P.trace_off[T.r], n = P.trace_off[T.r + 1] - off;
+    if (T.next_ref >= n) return;
+    uint32_t ref = P.trace[off + T.next_ref];
+    line = ref & 0x7FFFFFFFu;
+    write = ref >> 31;
+  } else {
+    line = draw_line(P, T.r, T.next_ref, write);
+  }
+  if (l1_step(P, T, t, line, write)) {
+    T.next_ref++;
+    SMALL(S_REFS)++;
+  }
+}
+
+// ---------------------------------------------------------------- Phase 2
+// compare-and-swap of two (key, flit) slots, smaller key first
+__device__ __forceinline__ void cswap(unsigned long long& ka, uint4& fa_, unsigned long long& kb,
+                                      uint4& fb_) {
+  if (kb < ka) {
+    unsigned long long tk = ka;
+    ka = kb;
+    kb = tk;
+    uint4 tf = fa_;
+    fa_ = fb_;
+    fb_ = tf;
+  }
+}
+
+// One bufferless router (Sec. 4.3): eject, inject, rank, select ports.
+// `in` are this cycle's arrivals by input port, `exists` the port mask.
+__device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint4 (&in)[4],
+                                      uint32_t exists, uint4 (&out)[4]) {
+  const unsigned long long NOKEY = ~0ull;
+  unsigned long long k[4];
+  int n_arr = 0;
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    bool v = ftype(in[d]) != T_NONE;
+    n_arr += v;
+    k[d] = v ? fkey(in[d]) : NOKEY;
+  }
+  // eject the highest-priority arrival addressed to this tile
+  int ej = -1;
+  unsigned long long ejk = NOKEY;
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+    if (k[d] != NOKEY && fdst(in[d]) == T.r && k[d] < ejk) {
+      ejk = k[d];
+      ej = d;
+    }
+  T.ej = make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+    if (d == ej) {
+      T.ej = in[d];
+      k[d] = NOKEY;
+    }
+  // rank the remaining arrivals oldest first: 4-input sorting network
+  cswap(k[0], in[0], k[1], in[1]);
+  cswap(k[2], in[2], k[3], in[3]);
+  cswap(k[0], in[0], k[2], in[2]);
+  cswap(k[1], in[1], k[3], in[3]);
+  cswap(k[1], in[1], k[2], in[2]);
+  // inject when an input port is free: service queue first, then core queue
+  uint4 inj = make_uint4(0, 0, 0, 0);
+  bool has_inj = false;
+  if (n_arr < __popc(exists)) {
+    if (T.sq_len > 0) {
+      inj = T.sq_front;
+      T.sq_head = T.sq_head + 1 == (uint32_t)P.svc_q ? 0 : T.sq_head + 1;
+      T.sq_len--;
+      if (T.sq_len > 0) T.sq_front = P.sq[(size_t)T.r * P.svc_q + T.sq_head];
+      has_inj = true;
+    } else if (T.cq_len > 0) {
+      inj = T.cq_front;
+      T.cq_head = T.cq_head + 1 == (uint32_t)P.core_q ? 0 : T.cq_head + 1;
+      T.cq_len--;
+      if (T.cq_len > 0) T.cq_front = P.cq[(size_t)T.r * P.core_q + T.cq_head];
+      has_inj = true;
+    }
+    if (has_inj) {
+      inj.x = t;
+      inj.y = (inj.y & 0xFFFF0000u) | T.r;
+      T.inj++;
+    }
+  }
+  // port selection: first free port of [X-productive, Y-productive, N, S, E, W]
+  uint32_t freem = exists;
+#pragma unroll
+  for (int d = 0; d < 4; ++d) out[d] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    uint4 f = i < 4 ? in[i] : inj;
+    bool valid = i < 4 ? (k[i] != NOKEY) : has_inj;
+    if (!valid) continue;
+    uint32_t dst = fdst(f);
+    int dx = (int)(dst % (uint32_t)P.W) - (int)T.x;
+    int dy = (int)(dst / (uint32_t)P.W) - (int)T.y;
+    uint32_t xb = dx > 0 ? (1u << P_E) : (dx < 0 ? (1u << P_W) : 0u);
+    uint32_t yb = dy > 0 ? (1u << P_S) : (dy < 0 ? (1u << P_N) : 0u);
+    uint32_t pick;
+    if (freem & xb) pick = xb;
+    else if (freem & yb) pick = yb;
+    else {
+      pick = freem & (0u - freem);  // lowest free port: N, S, E, W order
+      T.defl++;
+    }
+    freem &= ~pick;
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+      if (pick == (1u << d)) out[d] = f;
+  }
+}
+
+// ---------------------------------------------------------------- Phase 3
+__device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh_hist) {
+  uint4 f = T.ej;
+  uint32_t ty = ftype(f);
+  if (ty == T_NONE) return;
+  uint32_t lat = t - f.x;
+  T.ejc++;
+  T.latsum += lat;
+  if (lat > T.latmax) T.latmax = lat;
+  atomicAdd(&sh_hist[lat < HIST_BINS - 1 ? lat : HIST_BINS - 1], 1u);
+
+  const uint32_t line = fline(f);
+  const uint32_t set = l2_set(P, line);
+  const size_t base = l2_base(P, T.r, set);
+  switch (ty) {
+    case T_PROBE:
+      break;
+
+    case T_REQ: {
+      uint32_t q = fa(f);
+      SMALL(S_REQR)++;
+      uint32_t w[MAX_WAYS];
+      load_set(P.l2 + base, P.l2_ways, w);
+      int way = set_find(w, P.l2_ways, line);
+      if (way >= 0) {
+        SMALL(S_L2H)++;
+        set_touch(w, P.l2_ways, way);
+        store_set(P.l2 + base, P.l2_ways, w);
+        send_svc(P, T, mkflit(T_DATA, T.r, q, line, 0, 0), t);
+        if (P.policy == POL_MIGRATE) {
+          hist_push(P, base + way, q);
+          uint16_t* hp = hist_ptr(P, base + way);
+          uint32_t n = hp[0], cnt = 0;
+          for (uint32_t i = 0; i < n; ++i) cnt += hp[2 + i] == q;
+          if (n == (uint32_t)P.mig_window && cnt >= (uint32_t)P.mig_threshold && !hp[1]) {
+            hp[1] = 1;
+            SMALL(S_MIGS)++;
+            send_svc(P, T, mkflit(T_MIG, T.r, q, line, 0, 0), t);
+          }
+        }
+        break;
+      }
+      SMALL(S_L2M)++;
+      if (P.policy == POL_INTERLEAVED) {
+        if (T.mq_len >= (uint32_t)P.mem_q) {
+          set_error(P, t, ERR_OVERFLOW);
+          break;
+        }
+        uint32_t slot = T.mq_head + T.mq_len;
+        if (slot >= (uint32_t)P.mem_q) slot -= P.mem_q;
+        uint4 m = make_uint4(t + (uint32_t)P.mem_lat, line, q, 0);
+        P.mq[(size_t)T.r * P.mem_q + slot] = m;
+        if (T.mq_len == 0) T.mq_front = m;
+        T.mq_len++;
+        SMALL(S_MEMREQ)++;
+        break;
+      }
+      if (P.policy == POL_MIGRATE) {
+        // redirection (Sec. 3.3): the newest forward entry for the line
+        const uint32_t* fw = P.fwd + (size_t)T.r * P.fwd_cap * 2;
+        for (uint32_t i = 0; i < T.fwd_n; ++i) {
+          int slot = ((int)T.fwd_next - 1 - (int)i) % P.fwd_cap;
+          if (slot < 0) slot += P.fwd_cap;
+          if (fw[slot * 2] == line) {
+            uint32_t m = fw[slot * 2 + 1];
+            if (m != q) {
+              SMALL(S_REDIR)++;
+              send_svc(P, T, mkflit(T_REQ, T.r, m, line, q, 0), t);
+              return;
+            }
+            break;
+          }
+        }
+      }
+      SMALL(S_TRAP)++;
+      send_svc(P, T, mkflit(T_NACK, T.r, q, line, 0, 0), t);
+      break;
+    }
+
+    case T_DATA:
+      SMALL(S_REPR)++;
+      if (T.om_kind != OM_WAIT_DATA || T.om_line != line) {
+        set_error(P, t, ERR_PROTOCOL);
+        break;
+      }
+      l1_fill(P, T, line, fsrc(f));
+      if (T.om_write) send_svc(P, T, mkflit(T_WT, T.r, fsrc(f), line, 0, 0), t);
+      l2lat_sample(T, t, T.om_start, sh_hist);
+      set_om(T, OM_NONE, 0, 0, 0);
+      break;
+
+    case T_WT: {
+      uint32_t w[MAX_WAYS];
+      load_set(P.l2 + base, P.l2_ways, w);
+      int way = set_find(w, P.l2_ways, line);
+      if (way >= 0) {
+        set_put(w, way, set_get(w, way) | W_DIRTY);
+        set_touch(w, P.l2_ways, way);
+        store_set(P.l2 + base, P.l2_ways, w);
+        SMALL(S_WTH)++;
+      } else {
+        SMALL(S_MEMW)++;
+      }
+      break;
+    }
+
+    case T_DA: {
+      uint32_t q = fsrc(f), D = P.dir[line];
+      SMALL(S_DIRS)++;
+      if (D == DIR_NONE || (D & 0xFFFFu) == q) {
+        P.dir[line] = q | (fe(f) << 16);
+        send_svc(P, T, mkflit(T_DRNEG, T.r, q, line, 0, fe(f)), t);
+      } else {
+        send_svc(P, T, mkflit(T_DRPOS, T.r, q, line, D & 0xFFFFu, 0), t);
+      }
+      break;
+    }
+
+    case T_DRNEG:
+      SMALL(S_REPR)++;
+      if (T.om_kind != OM_WAIT_DR || T.om_line != line) {
+        set_error(P, t, ERR_PROTOCOL);
+        break;
+      }
+      T.om_kind = OM_MEM_L2;
+      T.om_timer = t + (uint32_t)P.mem_lat;
+      T.om_epoch = fe(f);
+      SMALL(S_MEMREQ)++;
+      break;
+
+    case T_DRPOS:
+      SMALL(S_REPR)++;
+      if (T.om_kind != OM_WAIT_DR || T.om_line != line) {
+        set_error(P, t, ERR_PROTOCOL);
+        break;
+      }
+      send_svc(P, T, mkflit(T_REQ, T.r, fa(f), line, T.r, 0), t);
+      T.om_kind = OM_WAIT_DATA;
+      break;
+
+    case T_NACK:
+      SMALL(S_REPR)++;
+      if (T.om_kind != OM_WAIT_DATA || T.om_line != line) {
+        set_error(P, t, ERR_PROTOCOL);
+        break;
+      }
+      T.om_kind = OM_MEM_L1;
+      T.om_timer = t + (uint32_t)P.mem_lat;
+      SMALL(S_MEMREQ)++;
+      break;
+
+    case T_DINV:
+      if (P.dir[line] == (fsrc(f) | (fe(f) << 16))) P.dir[line] = DIR_NONE;
+      break;
+
+    case T_MIG: {
+      uint32_t o = fsrc(f);
+      T.epoch = (T.epoch + 1) & 0xFFFFu;
+      int way = l2_install(P, T, line, T.epoch, t);
+      uint16_t* hp = hist_ptr(P, base + way);
+      hp[0] = 0;
+      hp[1] = 0;
+      uint32_t h = home_of(P, line);
+      if (h == T.r) {
+        P.dir[line] = T.r | (T.epoch << 16);
+        SMALL(S_MIGR)++;
+        send_svc(P, T, mkflit(T_INV, T.r, o, line, T.r, 0), t);
+      } else {
+        send_svc(P, T, mkflit(T_DIRUPD, T.r, h, line, o, T.epoch), t);
+      }
+      break;
+    }
+
+    case T_DIRUPD:
+    case T_INV: {
+      uint32_t m;
+      if (ty == T_DIRUPD) {
+        m = fsrc(f);
+        uint32_t o = fa(f);
+        P.dir[line] = m | (fe(f) << 16);
+        SMALL(S_MIGR)++;
+        if (o != T.r) {
+          send_svc(P, T, mkflit(T_INV, T.r, o, line, m, 0), t);
+          break;
+        }
+      } else {
+        m = fa(f);
+      }
+      // invalidate the source copy and remember where the block went
+      uint32_t w[MAX_WAYS];
+      load_set(P.l2 + base, P.l2_ways, w);
+      int way = set_find(w, P.l2_ways, line);
+      if (way >= 0) {
+        if (set_get(w, way) & W_DIRTY) SMALL(S_MEMWB)++;
+        set_invalidate(w, P.l2_ways, way);
+        store_set(P.l2 + base, P.l2_ways, w);
+        P.l2ep[base + way] = 0;
+        uint16_t* hp = hist_ptr(P, base + way);
+        hp[0] = 0;
+        hp[1] = 0;
+      }
+      uint32_t* fw = P.fwd + (size_t)T.r * P.fwd_cap * 2;
+      fw[T.fwd_next * 2] = line;
+      fw[T.fwd_next * 2 + 1] = m;
+      T.fwd_next = T.fwd_next + 1 == (uint32_t)P.fwd_cap ? 0 : T.fwd_next + 1;
+      if (T.fwd_n < (uint32_t)P.fwd_cap) T.fwd_n++;
+      break;
+    }
+
+    default:
+      set_error(P, t, ERR_PROTOCOL);
+  }
+}
+
+// ---------------------------------------------------------------- hash
+// dynamic hash of one tile after a cycle (model text, "dynamic hash")
+__device__ unsigned long long tile_hash(const Tile& T, const uint4 (&out)[4]) {
+  unsigned long long h = hstart(T.r);
+#pragma unroll
+  for (int d = 0; d < 4; ++d) h = hflit(h, out[d]);
+  bool busy = T.fsm != FSM_IDLE, wait = T.fsm == FSM_L2WAIT, om = T.om_kind != OM_NONE;
+  bool mem = T.om_kind == OM_MEM_L2 || T.om_kind == OM_MEM_L1;
+  h = hfold(h, T.next_ref);
+  h = hfold(h, (unsigned long long)T.fsm | ((unsigned long long)(busy ? T.fsm_write : 0) << 8) |
+                   ((unsigned long long)T.om_kind << 16) |
+                   ((unsigned long long)(om ? T.om_write : 0) << 24) |
+                   ((unsigned long long)T.epoch << 32));
+  h = hfold(h, (unsigned long long)(busy ? T.fsm_line : 0) |
+                   ((unsigned long long)(wait ? T.fsm_timer : 0) << 32));
+  h = hfold(h, (unsigned long long)(wait ? T.fsm_start : 0) |
+                   ((unsigned long long)(T.om_kind == OM_MEM_L2 ? T.om_epoch : 0) << 32));
+  h = hfold(h, (unsigned long long)(om ? T.om_line : 0) |
+                   ((unsigned long long)(mem ? T.om_timer : 0) << 32));
+  h = hfold(h, om ? T.om_start : 0);
+  h = hfold(h, (unsigned long long)T.cq_len | ((unsigned long long)T.sq_len << 16) |
+                   ((unsigned long long)T.mq_len << 32) | ((unsigned long long)T.fwd_n << 48));
+  h = hfold(h, T.inj);
+  h = hfold(h, T.ejc);
+  return hfold(h, T.defl);
+}
+
+}  // namespace noc
