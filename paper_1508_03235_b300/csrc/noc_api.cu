@@ -1,0 +1,769 @@
+// noc_api.cu -- host side of the C ABI declared in include/noc.h.
+//
+// A handle owns the host description of one simulation and one device arena
+// (all state arrays, 256-byte aligned).  The arena is either caller memory
+// bound with noc_bind_memory (e.g. a torch tensor) or taken with cudaMalloc on
+// first use.  All device work is enqueued on the handle's stream.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "noc.h"
+#include "noc_internal.h"
+
+using namespace noc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(NOC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CU(call, what)                          \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+constexpr uint32_t kMaxChunk = 1u << 20;  // cycles per launch (32-bit counter deltas)
+
+}  // namespace
+
+struct noc_sim {
+  Params P;
+  noc_cache_cfg cache;
+  noc_traffic traf;
+  uint64_t seed;
+  // arena layout (byte offsets)
+  size_t o_glink, o_core, o_cq, o_sq, o_mq, o_l1, o_l1own, o_l2, o_l2ep, o_l2hist, o_dir, o_fwd,
+      o_stats, o_hist, o_flags, o_err, o_abort, o_scratch, bytes;
+  size_t n_flags;
+  unsigned char* base = nullptr;
+  bool owned = false;
+  bool ready = false;
+  cudaStream_t stream = nullptr;
+  int gx = 0, gy = 0;          // requested tiling (0 = automatic)
+  int run_gx = 0, run_gy = 0;  // tiling in use
+  uint32_t cycle = 0;
+  // hash trace
+  bool hash_on = false;
+  unsigned long long* d_hash = nullptr;
+  size_t hash_cap = 0;
+  int64_t hash_n = 0;
+  // drain
+  unsigned int* d_busy = nullptr;
+  size_t busy_cap = 0;
+  // trace mode
+  std::vector<std::vector<uint32_t>> traces;
+  bool trace_dirty = true;
+  uint32_t* d_trace = nullptr;
+  size_t trace_cap = 0;
+  uint32_t* d_trace_off = nullptr;
+  // debug knobs
+  long long wait_ns = 2000000000ll;
+  int silent_cta = -1;
+  int64_t launches = 0;
+};
+
+namespace {
+
+void layout(noc_sim* s) {
+  const size_t N = (size_t)s->P.N;
+  const Params& P = s->P;
+  size_t cur = 0;
+  auto take = [&](size_t b) {
+    size_t o = align256(cur);
+    cur = o + b;
+    return o;
+  };
+  const size_t w1 = N * P.l1_sets * P.l1_ways, w2 = N * P.l2_sets * P.l2_ways;
+  const bool lspd = P.policy != POL_INTERLEAVED, mig = P.policy == POL_MIGRATE;
+  s->n_flags = 4096;
+  s->o_glink = take(2 * 4 * N * sizeof(uint4));
+  s->o_core = take(NCORE * N * sizeof(uint32_t));
+  s->o_cq = take(N * P.core_q * sizeof(uint4));
+  s->o_sq = take(N * P.svc_q * sizeof(uint4));
+  s->o_mq = take(N * P.mem_q * sizeof(uint4));
+  s->o_l1 = take(w1 * sizeof(uint32_t));
+  s->o_l1own = take(w1 * sizeof(uint16_t));
+  s->o_l2 = take(w2 * sizeof(uint32_t));
+  s->o_l2ep = take(lspd ? w2 * sizeof(uint16_t) : 0);
+  s->o_l2hist = take(mig ? w2 * HIST_STRIDE * sizeof(uint16_t) : 0);
+  s->o_dir = take(lspd ? (size_t)P.total_lines * sizeof(uint32_t) : 0);
+  s->o_fwd = take(mig ? N * P.fwd_cap * 2 * sizeof(uint32_t) : 0);
+  s->o_stats = take((size_t)NSTAT * N * sizeof(unsigned long long));
+  s->o_hist = take(2 * HIST_BINS * sizeof(unsigned long long));
+  s->o_flags = take(s->n_flags * sizeof(unsigned int));
+  s->o_err = take(sizeof(unsigned long long));
+  s->o_abort = take(sizeof(unsigned int));
+  s->o_scratch = take(64 * sizeof(unsigned long long));
+  s->bytes = align256(cur);
+}
+
+void set_pointers(noc_sim* s) {
+  Params& P = s->P;
+  unsigned char* b = s->base;
+  const bool lspd = P.policy != POL_INTERLEAVED, mig = P.policy == POL_MIGRATE;
+  P.glink = reinterpret_cast<uint4*>(b + s->o_glink);
+  P.core = reinterpret_cast<uint32_t*>(b + s->o_core);
+  P.cq = reinterpret_cast<uint4*>(b + s->o_cq);
+  P.sq = reinterpret_cast<uint4*>(b + s->o_sq);
+  P.mq = reinterpret_cast<uint4*>(b + s->o_mq);
+  P.l1 = reinterpret_cast<uint32_t*>(b + s->o_l1);
+  P.l1own = reinterpret_cast<uint16_t*>(b + s->o_l1own);
+  P.l2 = reinterpret_cast<uint32_t*>(b + s->o_l2);
+  P.l2ep = lspd ? reinterpret_cast<uint16_t*>(b + s->o_l2ep) : nullptr;
+  P.l2hist = mig ? reinterpret_cast<uint16_t*>(b + s->o_l2hist) : nullptr;
+  P.dir = lspd ? reinterpret_cast<uint32_t*>(b + s->o_dir) : nullptr;
+  P.fwd = mig ? reinterpret_cast<uint32_t*>(b + s->o_fwd) : nullptr;
+  P.stats = reinterpret_cast<unsigned long long*>(b + s->o_stats);
+  P.hist = reinterpret_cast<unsigned long long*>(b + s->o_hist);
+  P.flags = reinterpret_cast<unsigned int*>(b + s->o_flags);
+  P.err = reinterpret_cast<unsigned long long*>(b + s->o_err);
+}
+
+unsigned int* abort_ptr(noc_sim* s) { return reinterpret_cast<unsigned int*>(s->base + s->o_abort); }
+unsigned long long* scratch_ptr(noc_sim* s) {
+  return reinterpret_cast<unsigned long long*>(s->base + s->o_scratch);
+}
+
+int do_reset(noc_sim* s) {
+  Params& P = s->P;
+  cudaStream_t st = s->stream;
+  const size_t N = (size_t)P.N;
+  const size_t w1 = N * P.l1_sets * P.l1_ways, w2 = N * P.l2_sets * P.l2_ways;
+  CU(cudaMemsetAsync(P.glink, 0, 2 * 4 * N * sizeof(uint4), st), "reset links");
+  CU(cudaMemsetAsync(P.core, 0, NCORE * N * sizeof(uint32_t), st), "reset cores");
+  CU(cudaMemsetAsync(P.l1, 0, w1 * sizeof(uint32_t), st), "reset L1");
+  CU(cudaMemsetAsync(P.l1own, 0, w1 * sizeof(uint16_t), st), "reset L1 owners");
+  CU(cudaMemsetAsync(P.l2, 0, w2 * sizeof(uint32_t), st), "reset L2");
+  if (P.l2ep) CU(cudaMemsetAsync(P.l2ep, 0, w2 * sizeof(uint16_t), st), "reset L2 epochs");
+  if (P.l2hist)
+    CU(cudaMemsetAsync(P.l2hist, 0, w2 * HIST_STRIDE * sizeof(uint16_t), st), "reset history");
+  if (P.dir) CU(cudaMemsetAsync(P.dir, 0xFF, (size_t)P.total_lines * 4, st), "reset directory");
+  if (P.fwd) CU(cudaMemsetAsync(P.fwd, 0, N * P.fwd_cap * 8, st), "reset forward tables");
+  CU(cudaMemsetAsync(P.stats, 0, (size_t)NSTAT * N * 8, st), "reset counters");
+  CU(cudaMemsetAsync(P.hist, 0, 2 * HIST_BINS * 8, st), "reset histograms");
+  CU(cudaMemsetAsync(P.flags, 0, s->n_flags * 4, st), "reset flags");
+  CU(cudaMemsetAsync(P.err, 0xFF, 8, st), "reset error word");
+  CU(cudaMemsetAsync(abort_ptr(s), 0, 4, st), "reset abort flag");
+  s->cycle = 0;
+  s->hash_n = 0;
+  return NOC_OK;
+}
+
+int ensure_memory(noc_sim* s) {
+  if (s->ready) return NOC_OK;
+  if (!s->base) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, s->bytes);
+    if (e != cudaSuccess) return fail(NOC_ERR_OOM, "cudaMalloc(%zu): %s", s->bytes, cudaGetErrorString(e));
+    s->base = static_cast<unsigned char*>(p);
+    s->owned = true;
+  }
+  set_pointers(s);
+  int rc = do_reset(s);
+  if (rc) return rc;
+  s->ready = true;
+  return NOC_OK;
+}
+
+// choose the CTA rectangle grid: the fewest CTAs whose rectangles hold at most
+// 128 tiles, else the smallest rectangles that still fit co-resident
+int choose_tiling(noc_sim* s, int* gx_out, int* gy_out) {
+  const int W = s->P.W, H = s->P.H;
+  if (s->gx > 0 && s->gy > 0) {
+    *gx_out = s->gx;
+    *gy_out = s->gy;
+    return NOC_OK;
+  }
+  int best_gx = 0, best_gy = 0;
+  long best_g = 0, best_a = 0, best_p = 0;
+  bool best_small = false;
+  for (int gy = 1; gy <= H; ++gy)
+    for (int gx = 1; gx <= W; ++gx) {
+      const int threads = block_threads(W, H, gx, gy);
+      if (threads > 384) continue;
+      const long G = (long)gx * gy;
+      if (G > (long)s->n_flags) continue;
+      int cap = 0;
+      if (max_coresident_ctas(threads, &cap) != cudaSuccess) return cuda_fail(cudaGetLastError(), "occupancy");
+      if (G > cap) continue;
+      const long bw = (W + gx - 1) / gx, bh = (H + gy - 1) / gy, a = bw * bh, per = bw + bh;
+      const bool small = a <= 128;
+      bool better;
+      if (!best_gx) better = true;
+      else if (small != best_small) better = small;
+      else if (small) better = G < best_g || (G == best_g && (a < best_a || (a == best_a && per < best_p)));
+      else better = a < best_a || (a == best_a && (G < best_g || (G == best_g && per < best_p)));
+      if (better) {
+        best_gx = gx;
+        best_gy = gy;
+        best_g = G;
+        best_a = a;
+        best_p = per;
+        best_small = small;
+      }
+    }
+  if (!best_gx) return fail(NOC_ERR_ARG, "mesh %dx%d does not fit one co-resident launch", W, H);
+  *gx_out = best_gx;
+  *gy_out = best_gy;
+  return NOC_OK;
+}
+
+int upload_traces(noc_sim* s) {
+  if (s->P.mode != MODE_TRACE || !s->trace_dirty) return NOC_OK;
+  const size_t N = (size_t)s->P.N;
+  std::vector<uint32_t> off(N + 1, 0), all;
+  for (size_t r = 0; r < N; ++r) {
+    off[r] = (uint32_t)all.size();
+    if (r < s->traces.size()) all.insert(all.end(), s->traces[r].begin(), s->traces[r].end());
+  }
+  off[N] = (uint32_t)all.size();
+  if (!s->d_trace_off) CU(cudaMalloc(&s->d_trace_off, (N + 1) * 4), "trace offsets");
+  if (all.size() > s->trace_cap || !s->d_trace) {
+    if (s->d_trace) cudaFree(s->d_trace);
+    s->trace_cap = all.size() ? all.size() : 1;
+    CU(cudaMalloc(&s->d_trace, s->trace_cap * 4), "trace buffer");
+  }
+  CU(cudaMemcpyAsync(s->d_trace_off, off.data(), (N + 1) * 4, cudaMemcpyHostToDevice, s->stream),
+     "trace offsets copy");
+  if (!all.empty())
+    CU(cudaMemcpyAsync(s->d_trace, all.data(), all.size() * 4, cudaMemcpyHostToDevice, s->stream),
+       "trace copy");
+  CU(cudaStreamSynchronize(s->stream), "trace upload");
+  s->P.trace_off = s->d_trace_off;
+  s->P.trace = s->d_trace;
+  s->trace_dirty = false;
+  return NOC_OK;
+}
+
+int read_error(noc_sim* s, int64_t* cyc) {
+  unsigned long long e = ~0ull;
+  CU(cudaMemcpyAsync(&e, s->P.err, 8, cudaMemcpyDeviceToHost, s->stream), "error word");
+  CU(cudaStreamSynchronize(s->stream), "sync");
+  if (cyc) *cyc = e == ~0ull ? -1 : (int64_t)(e >> 8);
+  if (e == ~0ull) return NOC_OK;
+  int code = (int)(e & 0xFF);
+  return fail(code, "simulation error %d at cycle %lld", code, (long long)(e >> 8));
+}
+
+// run n cycles as one or more cooperative launches
+int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
+  int rc = upload_traces(s);
+  if (rc) return rc;
+  if (!s->run_gx) {
+    rc = choose_tiling(s, &s->run_gx, &s->run_gy);
+    if (rc) return rc;
+  }
+  const int threads = block_threads(s->P.W, s->P.H, s->run_gx, s->run_gy);
+  int cap = 0;
+  CU(max_coresident_ctas(threads, &cap), "occupancy");
+  if (threads > 384 || s->run_gx * s->run_gy > cap || s->run_gx * s->run_gy > (int)s->n_flags)
+    return fail(NOC_ERR_ARG, "tiling %dx%d does not fit one co-resident launch", s->run_gx, s->run_gy);
+  uint32_t done = 0;
+  while (done < n) {
+    uint32_t c = n - done < kMaxChunk ? n - done : kMaxChunk;
+    RunArgs A;
+    A.t0 = s->cycle;
+    A.n = c;
+    A.draining = draining ? 1 : 0;
+    A.gx = s->run_gx;
+    A.gy = s->run_gy;
+    A.hash_trace = (s->hash_on && !busy) ? s->d_hash + done : nullptr;
+    A.busy = busy ? busy + done : nullptr;
+    A.abort_flag = abort_ptr(s);
+    A.wait_ns = s->wait_ns;
+    A.silent_cta = s->silent_cta;
+    CU(launch_run(s->P, A, s->stream), "cycle kernel launch");
+    s->launches++;
+    s->cycle += c;
+    done += c;
+  }
+  return NOC_OK;
+}
+
+uint4 pack_flit(const uint32_t* f7, uint32_t src) {
+  return make_uint4(f7[3], (src & 0xFFFFu) | (f7[2] << 16), (f7[4] & W_LINE) | (f7[0] << 26),
+                    (f7[5] & 0xFFFFu) | (f7[6] << 16));
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+extern "C" {
+
+const char* noc_last_error(void) { return g_last_error.c_str(); }
+
+int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, const noc_traffic* tr,
+               uint64_t seed, noc_sim** out) {
+  if (!c || !tr || !out) return fail(NOC_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (mesh_w < 1 || mesh_h < 1 || (long)mesh_w * mesh_h > 65535)
+    return fail(NOC_ERR_ARG, "mesh %dx%d: need 1..65535 tiles", mesh_w, mesh_h);
+  if (l2_policy < 0 || l2_policy > 2) return fail(NOC_ERR_ARG, "l2_policy %d", l2_policy);
+  auto pow2_ways = [](int w) { return w == 1 || w == 2 || w == 4 || w == 8 || w == 16; };
+  if (c->l1_sets < 1 || !pow2_ways(c->l1_ways) || c->l2_sets < 1 || !pow2_ways(c->l2_ways))
+    return fail(NOC_ERR_ARG, "cache geometry: sets >= 1, ways in {1,2,4,8,16}");
+  if (c->l1_miss_cycles < 0 || c->mem_latency < 1) return fail(NOC_ERR_ARG, "latencies");
+  if (c->core_q < 1 || c->svc_q < 1 || c->mem_q < 1 || c->core_q > 65535 || c->svc_q > 65535 ||
+      c->mem_q > 65535)
+    return fail(NOC_ERR_ARG, "queue capacities must be 1..65535");
+  if (l2_policy == NOC_L2_LSPD_MIGRATE &&
+      (c->mig_window < 1 || c->mig_window > HIST_STRIDE - 2 || c->mig_threshold < 1 ||
+       c->fwd_entries < 1 || c->fwd_entries > 65535))
+    return fail(NOC_ERR_ARG, "migration: window 1..30, threshold >= 1, forward entries >= 1");
+  if (tr->mode < 0 || tr->mode > 2 || tr->period < 0) return fail(NOC_ERR_ARG, "traffic mode/period");
+  if (tr->write_q16 > 65536 || tr->priv_q16 + (uint64_t)tr->shared_q16 > 65536 || tr->hot_q16 > 65536)
+    return fail(NOC_ERR_ARG, "q16 fractions out of range");
+  if (tr->mode == NOC_MODE_CACHE) {
+    if (tr->priv_q16 > 0 && tr->priv_lines < 1) return fail(NOC_ERR_ARG, "priv_lines");
+    if (tr->shared_q16 > 0 && tr->shared_lines < 1) return fail(NOC_ERR_ARG, "shared_lines");
+    if (tr->priv_q16 + tr->shared_q16 < 65536 && tr->remote_lines < 1)
+      return fail(NOC_ERR_ARG, "remote_lines");
+  }
+  if (tr->hot_side < 0 || tr->hot_side > mesh_w || tr->hot_side > mesh_h)
+    return fail(NOC_ERR_ARG, "hot_side");
+  const uint64_t N = (uint64_t)mesh_w * mesh_h;
+  const uint64_t total = (uint64_t)tr->remote_lines + tr->shared_lines + (uint64_t)tr->priv_lines * N;
+  if (total >= (1ull << 26)) return fail(NOC_ERR_ARG, "address space above 2^26 lines");
+
+  noc_sim* s = new (std::nothrow) noc_sim();
+  if (!s) return fail(NOC_ERR_OOM, "host allocation");
+  s->cache = *c;
+  s->traf = *tr;
+  s->seed = seed;
+  Params& P = s->P;
+  memset(&P, 0, sizeof P);
+  P.W = mesh_w;
+  P.H = mesh_h;
+  P.N = (int)N;
+  P.policy = l2_policy;
+  P.mode = tr->mode;
+  P.period = tr->period;
+  P.l1_sets = c->l1_sets;
+  P.l1_ways = c->l1_ways;
+  P.l2_sets = c->l2_sets;
+  P.l2_ways = c->l2_ways;
+  P.l1_miss = c->l1_miss_cycles;
+  P.mem_lat = c->mem_latency;
+  P.mig_window = c->mig_window;
+  P.mig_threshold = c->mig_threshold;
+  P.core_q = c->core_q;
+  P.svc_q = c->svc_q;
+  P.mem_q = c->mem_q;
+  P.fwd_cap = c->fwd_entries > 0 ? c->fwd_entries : 1;
+  P.write_q16 = tr->write_q16;
+  P.priv_q16 = tr->priv_q16;
+  P.shared_q16 = tr->shared_q16;
+  P.hot_q16 = tr->hot_q16;
+  P.hot_side = tr->hot_side;
+  P.hot_x0 = mesh_w / 2 - tr->hot_side / 2;
+  P.hot_y0 = mesh_h / 2 - tr->hot_side / 2;
+  P.priv_lines = tr->priv_lines;
+  P.shared_lines = tr->shared_lines;
+  P.remote_lines = tr->remote_lines;
+  P.total_lines = (uint32_t)total;
+  P.seed = seed;
+  P.stream = tr->stream;
+  s->traces.resize(N);
+  layout(s);
+  *out = s;
+  return NOC_OK;
+}
+
+void noc_destroy(noc_sim* s) {
+  if (!s) return;
+  if (s->base && s->owned) cudaFree(s->base);
+  if (s->d_hash) cudaFree(s->d_hash);
+  if (s->d_busy) cudaFree(s->d_busy);
+  if (s->d_trace) cudaFree(s->d_trace);
+  if (s->d_trace_off) cudaFree(s->d_trace_off);
+  delete s;
+}
+
+size_t noc_required_bytes(const noc_sim* s) { return s ? s->bytes : 0; }
+
+int noc_bind_memory(noc_sim* s, void* p, size_t bytes) {
+  if (!s || !p) return fail(NOC_ERR_ARG, "null argument");
+  if (s->base) return fail(NOC_ERR_STATE, "memory already bound or allocated");
+  if (bytes < s->bytes) return fail(NOC_ERR_ARG, "need %zu bytes, got %zu", s->bytes, bytes);
+  if (reinterpret_cast<uintptr_t>(p) & 255) return fail(NOC_ERR_ARG, "memory must be 256-byte aligned");
+  s->base = static_cast<unsigned char*>(p);
+  s->owned = false;
+  return NOC_OK;
+}
+
+int noc_set_stream(noc_sim* s, void* stream) {
+  if (!s) return fail(NOC_ERR_ARG, "null handle");
+  s->stream = static_cast<cudaStream_t>(stream);
+  return NOC_OK;
+}
+
+int noc_reset(noc_sim* s) {
+  if (!s) return fail(NOC_ERR_ARG, "null handle");
+  if (!s->ready) return ensure_memory(s);
+  return do_reset(s);
+}
+
+int noc_step(noc_sim* s, int64_t n) {
+  if (!s || n < 0) return fail(NOC_ERR_ARG, "bad argument");
+  int rc = ensure_memory(s);
+  if (rc) return rc;
+  if (n == 0) return NOC_OK;
+  if ((uint64_t)s->cycle + (uint64_t)n >= (1ull << 32) - 2) return fail(NOC_ERR_ARG, "cycle count above 2^32");
+  if (s->hash_on) {
+    if ((size_t)n > s->hash_cap) {
+      if (s->d_hash) cudaFree(s->d_hash);
+      s->d_hash = nullptr;
+      CU(cudaMalloc(&s->d_hash, (size_t)n * 8), "hash trace buffer");
+      s->hash_cap = (size_t)n;
+    }
+    CU(cudaMemsetAsync(s->d_hash, 0, (size_t)n * 8, s->stream), "hash trace clear");
+    s->hash_n = n;
+  }
+  return run_cycles(s, (uint32_t)n, false, nullptr);
+}
+
+int noc_sync(noc_sim* s, int64_t* err_cycle) {
+  if (!s) return fail(NOC_ERR_ARG, "null handle");
+  if (err_cycle) *err_cycle = -1;
+  if (!s->ready) return NOC_OK;
+  CU(cudaStreamSynchronize(s->stream), "stream synchronize");
+  return read_error(s, err_cycle);
+}
+
+int noc_drain(noc_sim* s, int64_t max_cycles, int64_t* taken) {
+  if (!s || max_cycles < 0) return fail(NOC_ERR_ARG, "bad argument");
+  if (taken) *taken = 0;
+  int rc = ensure_memory(s);
+  if (rc) return rc;
+  rc = noc_sync(s, nullptr);
+  if (rc) return rc;
+  unsigned int busy0 = 0;
+  unsigned int* d_b0 = reinterpret_cast<unsigned int*>(scratch_ptr(s));
+  CU(cudaMemsetAsync(d_b0, 0, 4, s->stream), "busy clear");
+  CU(launch_count_busy(s->P, s->cycle, d_b0, s->stream), "busy count");
+  CU(cudaMemcpyAsync(&busy0, d_b0, 4, cudaMemcpyDeviceToHost, s->stream), "busy copy");
+  CU(cudaStreamSynchronize(s->stream), "sync");
+  if (busy0 == 0) return NOC_OK;
+  const uint32_t chunk_max = 4096;
+  if (s->busy_cap < chunk_max) {
+    if (s->d_busy) cudaFree(s->d_busy);
+    s->d_busy = nullptr;
+    CU(cudaMalloc(&s->d_busy, chunk_max * 4), "busy buffer");
+    s->busy_cap = chunk_max;
+  }
+  std::vector<unsigned int> hb(chunk_max);
+  int64_t left = max_cycles, run = 0;
+  uint32_t chunk = 64;
+  while (left > 0) {
+    uint32_t c = (int64_t)chunk < left ? chunk : (uint32_t)left;
+    const uint32_t before = s->cycle;
+    CU(cudaMemsetAsync(s->d_busy, 0, c * 4, s->stream), "busy clear");
+    rc = run_cycles(s, c, true, s->d_busy);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(hb.data(), s->d_busy, c * 4, cudaMemcpyDeviceToHost, s->stream), "busy copy");
+    rc = read_error(s, nullptr);
+    if (rc) return rc;
+    for (uint32_t j = 0; j < c; ++j)
+      if (hb[j] == 0) {
+        // quiet after cycle before+j: the state is a fixed point from there on,
+        // so the extra cycles changed nothing but the cycle number
+        s->cycle = before + j + 1;
+        CU(cudaMemsetAsync(s->P.glink, 0, 2 * 4 * (size_t)s->P.N * sizeof(uint4), s->stream),
+           "links clear");
+        CU(launch_fill_u32(s->P.flags, s->cycle, s->n_flags, s->stream), "flags rewind");
+        CU(cudaStreamSynchronize(s->stream), "sync");
+        if (taken) *taken = run + j + 1;
+        return NOC_OK;
+      }
+    run += c;
+    left -= c;
+    if (chunk < chunk_max) chunk *= 2;
+  }
+  if (taken) *taken = run;
+  return fail(NOC_ERR_TIMEOUT, "not quiescent after %lld cycles", (long long)max_cycles);
+}
+
+int noc_stats(noc_sim* s, int tile, noc_stats_t* out) {
+  if (!s || !out || tile >= s->P.N) return fail(NOC_ERR_ARG, "bad argument");
+  int rc = ensure_memory(s);
+  if (rc) return rc;
+  unsigned long long h[NSTAT];
+  CU(launch_reduce_stats(s->P, tile, scratch_ptr(s), s->stream), "stats reduce");
+  CU(cudaMemcpyAsync(h, scratch_ptr(s), sizeof h, cudaMemcpyDeviceToHost, s->stream), "stats copy");
+  CU(cudaStreamSynchronize(s->stream), "sync");
+  out->cycle = s->cycle;
+  out->injected = h[S_INJ];
+  out->ejected = h[S_EJ];
+  out->in_flight = h[S_INJ] - h[S_EJ];
+  out->deflections = h[S_DEFL];
+  out->lat_sum = h[S_LATSUM];
+  out->lat_max = h[S_LATMAX];
+  out->refs = h[S_REFS];
+  out->l1_hit = h[S_L1H];
+  out->l1_miss = h[S_L1M];
+  out->l2_hit = h[S_L2H];
+  out->l2_miss = h[S_L2M];
+  out->req_made = h[S_REQM];
+  out->req_rcvd = h[S_REQR];
+  out->reply_sent = h[S_REPS];
+  out->reply_rcvd = h[S_REPR];
+  out->dir_search = h[S_DIRS];
+  out->mem_req = h[S_MEMREQ];
+  out->mem_write = h[S_MEMW];
+  out->mem_wb = h[S_MEMWB];
+  out->wt_sent = h[S_WTS];
+  out->wt_hit = h[S_WTH];
+  out->trap = h[S_TRAP];
+  out->redir = h[S_REDIR];
+  out->migrations = h[S_MIGR];
+  out->l2lat_sum = h[S_L2LSUM];
+  out->l2lat_cnt = h[S_L2LCNT];
+  out->cq_stall = h[S_CQST];
+  out->mm_stall = h[S_MMST];
+  out->mig_sent = h[S_MIGS];
+  return NOC_OK;
+}
+
+int noc_latency_hist(noc_sim* s, int which, uint64_t* bins, int nbins) {
+  if (!s || !bins || which < 0 || which > 1 || nbins < HIST_BINS) return fail(NOC_ERR_ARG, "bad argument");
+  int rc = ensure_memory(s);
+  if (rc) return rc;
+  CU(cudaMemcpyAsync(bins, s->P.hist + which * HIST_BINS, HIST_BINS * 8, cudaMemcpyDeviceToHost,
+                     s->stream),
+     "histogram copy");
+  CU(cudaStreamSynchronize(s->stream), "sync");
+  return NOC_OK;
+}
+
+static int hash_common(noc_sim* s, uint64_t* out, bool full) {
+  if (!s || !out) return fail(NOC_ERR_ARG, "null argument");
+  int rc = ensure_memory(s);
+  if (rc) return rc;
+  unsigned long long* d = scratch_ptr(s) + 48;
+  CU(cudaMemsetAsync(d, 0, 8, s->stream), "hash clear");
+  if (full) CU(launch_state_hash(s->P, s->cycle, d, s->stream), "state hash");
+  else CU(launch_dyn_hash(s->P, s->cycle, d, s->stream), "dynamic hash");
+  s->launches += full ? 2 : 1;
+  CU(cudaMemcpyAsync(out, d, 8, cudaMemcpyDeviceToHost, s->stream), "hash copy");
+  CU(cudaStreamSynchronize(s->stream), "sync");
+  return NOC_OK;
+}
+
+int noc_dyn_hash(noc_sim* s, uint64_t* out) { return hash_common(s, out, false); }
+int noc_state_hash(noc_sim* s, uint64_t* out) { return hash_common(s, out, true); }
+
+int noc_set_hash_trace(noc_sim* s, int enable) {
+  if (!s) return fail(NOC_ERR_ARG, "null handle");
+  s->hash_on = enable != 0;
+  return NOC_OK;
+}
+
+int noc_hash_trace(noc_sim* s, uint64_t* buf, int64_t n) {
+  if (!s || !buf || n < 0) return fail(NOC_ERR_ARG, "bad argument");
+  if (n > s->hash_n) return fail(NOC_ERR_ARG, "only %lld cycles recorded", (long long)s->hash_n);
+  if (n == 0) return NOC_OK;
+  CU(cudaMemcpyAsync(buf, s->d_hash, (size_t)n * 8, cudaMemcpyDeviceToHost, s->stream), "trace copy");
+  CU(cudaStreamSynchronize(s->stream), "sync");
+  return NOC_OK;
+}
+
+int noc_set_tiling(noc_sim* s, int gx, int gy) {
+  if (!s) return fail(NOC_ERR_ARG, "null handle");
+  if (gx == 0 && gy == 0) {
+    s->gx = s->gy = 0;
+    s->run_gx = s->run_gy = 0;
+    return NOC_OK;
+  }
+  if (gx < 1 || gy < 1 || gx > s->P.W || gy > s->P.H || block_threads(s->P.W, s->P.H, gx, gy) > 512 ||
+      (long)gx * gy > (long)s->n_flags)
+    return fail(NOC_ERR_ARG, "tiling %dx%d invalid for mesh %dx%d", gx, gy, s->P.W, s->P.H);
+  s->gx = s->run_gx = gx;
+  s->gy = s->run_gy = gy;
+  return NOC_OK;
+}
+
+int noc_get_tiling(const noc_sim* s, int* gx, int* gy) {
+  if (!s || !gx || !gy) return fail(NOC_ERR_ARG, "null argument");
+  *gx = s->run_gx;
+  *gy = s->run_gy;
+  return NOC_OK;
+}
+
+int noc_set_trace(noc_sim* s, int core, int64_t n, const uint32_t* refs) {
+  if (!s || core < 0 || core >= s->P.N || n < 0 || (n > 0 && !refs)) return fail(NOC_ERR_ARG, "bad argument");
+  for (int64_t k = 0; k < n; ++k)
+    if ((refs[k] & 0x7FFFFFFFu) >= s->P.total_lines) return fail(NOC_ERR_ARG, "trace line out of range");
+  s->traces[core].assign(refs, refs + n);
+  s->trace_dirty = true;
+  return NOC_OK;
+}
+
+int noc_debug_enqueue(noc_sim* s, int tile, int queue, const uint32_t* f7) {
+  if (!s || !f7 || tile < 0 || tile >= s->P.N || queue < 0 || queue > 1) return fail(NOC_ERR_ARG, "bad argument");
+  if (f7[0] == 0 || f7[0] > T_PROBE || f7[2] >= (uint32_t)s->P.N || f7[2] == (uint32_t)tile)
+    return fail(NOC_ERR_ARG, "bad flit");
+  int rc = ensure_memory(s);
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(s->stream), "sync");
+  const size_t N = (size_t)s->P.N;
+  uint32_t* fld = s->P.core + (queue == 0 ? C_CQ : C_SQ) * N + tile;
+  uint32_t q;
+  CU(cudaMemcpy(&q, fld, 4, cudaMemcpyDeviceToHost), "queue read");
+  const uint32_t cap = queue == 0 ? s->P.core_q : s->P.svc_q, head = q & 0xFFFFu, len = q >> 16;
+  if (len >= cap) return fail(NOC_ERR_QUEUE_OVERFLOW, "queue full");
+  uint4 f = pack_flit(f7, (uint32_t)tile);
+  f.x = 0;
+  uint4* buf = (queue == 0 ? s->P.cq : s->P.sq) + (size_t)tile * cap + (head + len) % cap;
+  CU(cudaMemcpy(buf, &f, sizeof f, cudaMemcpyHostToDevice), "queue write");
+  q = head | ((len + 1) << 16);
+  CU(cudaMemcpy(fld, &q, 4, cudaMemcpyHostToDevice), "queue update");
+  return NOC_OK;
+}
+
+int noc_debug_link(noc_sim* s, int tile, int dir, const uint32_t* f7) {
+  if (!s || !f7 || tile < 0 || tile >= s->P.N || dir < 0 || dir > 3) return fail(NOC_ERR_ARG, "bad argument");
+  const int W = s->P.W, H = s->P.H, x = tile % W, y = tile / W;
+  int nb = -1;
+  if (dir == P_N && y > 0) nb = tile - W;
+  if (dir == P_S && y < H - 1) nb = tile + W;
+  if (dir == P_E && x < W - 1) nb = tile + 1;
+  if (dir == P_W && x > 0) nb = tile - 1;
+  if (nb < 0) return fail(NOC_ERR_ARG, "no neighbour in that direction");
+  if (f7[0] == 0 || f7[0] > T_PROBE || f7[2] >= (uint32_t)s->P.N) return fail(NOC_ERR_ARG, "bad flit");
+  int rc = ensure_memory(s);
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(s->stream), "sync");
+  const size_t N = (size_t)s->P.N;
+  const uint32_t par = (s->cycle - 1u) & 1u;
+  uint4 f = pack_flit(f7, f7[1]);
+  CU(cudaMemcpy(s->P.glink + ((size_t)par * 4 + (dir ^ 1)) * N + nb, &f, sizeof f, cudaMemcpyHostToDevice),
+     "link write");
+  // counted as injected at its source so that conservation holds
+  const uint32_t src = f7[1] < N ? f7[1] : (uint32_t)nb;
+  unsigned long long v;
+  CU(cudaMemcpy(&v, s->P.stats + S_INJ * N + src, 8, cudaMemcpyDeviceToHost), "counter read");
+  v++;
+  CU(cudaMemcpy(s->P.stats + S_INJ * N + src, &v, 8, cudaMemcpyHostToDevice), "counter write");
+  return NOC_OK;
+}
+
+int noc_get_links(noc_sim* s, uint32_t* out) {
+  if (!s || !out) return fail(NOC_ERR_ARG, "null argument");
+  int rc = ensure_memory(s);
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(s->stream), "sync");
+  const size_t N = (size_t)s->P.N;
+  std::vector<uint4> h(4 * N);
+  const uint32_t par = (s->cycle - 1u) & 1u;
+  CU(cudaMemcpy(h.data(), s->P.glink + (size_t)par * 4 * N, 4 * N * sizeof(uint4), cudaMemcpyDeviceToHost),
+     "links copy");
+  for (size_t r = 0; r < N; ++r)
+    for (int d = 0; d < 4; ++d) {
+      uint4 f = h[d * N + r];
+      uint32_t* o = out + (r * 4 + d) * 7;
+      uint32_t ty = f.z >> 26;
+      o[0] = ty;
+      o[1] = ty ? (f.y & 0xFFFFu) : 0;
+      o[2] = ty ? (f.y >> 16) : 0;
+      o[3] = ty ? f.x : 0;
+      o[4] = ty ? (f.z & W_LINE) : 0;
+      o[5] = ty ? (f.w & 0xFFFFu) : 0;
+      o[6] = ty ? (f.w >> 16) : 0;
+    }
+  return NOC_OK;
+}
+
+int noc_get_cache(noc_sim* s, int tile, int which, uint32_t* out) {
+  if (!s || !out || tile < 0 || tile >= s->P.N || which < 1 || which > 2) return fail(NOC_ERR_ARG, "bad argument");
+  int rc = ensure_memory(s);
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(s->stream), "sync");
+  const Params& P = s->P;
+  const size_t sets = which == 1 ? P.l1_sets : P.l2_sets, ways = which == 1 ? P.l1_ways : P.l2_ways;
+  const size_t n = sets * ways, base = (size_t)tile * n;
+  std::vector<uint32_t> w(n);
+  std::vector<uint16_t> aux(n, 0);
+  CU(cudaMemcpy(w.data(), (which == 1 ? P.l1 : P.l2) + base, n * 4, cudaMemcpyDeviceToHost), "cache copy");
+  if (which == 1) CU(cudaMemcpy(aux.data(), P.l1own + base, n * 2, cudaMemcpyDeviceToHost), "owner copy");
+  else if (P.l2ep) CU(cudaMemcpy(aux.data(), P.l2ep + base, n * 2, cudaMemcpyDeviceToHost), "epoch copy");
+  for (size_t k = 0; k < n; ++k) {
+    uint32_t v = w[k];
+    bool valid = (v & W_VALID) != 0;
+    uint32_t* o = out + k * 4;
+    o[0] = valid;
+    o[1] = valid ? (v & W_LINE) : 0;
+    o[2] = !valid ? 0 : (which == 1 ? aux[k] : (((v & W_DIRTY) ? 1u : 0u) | ((uint32_t)aux[k] << 16)));
+    o[3] = valid ? ((v >> W_RANK_SHIFT) & 15u) : 0;
+  }
+  return NOC_OK;
+}
+
+int noc_dir_get(noc_sim* s, uint32_t line, uint32_t* out) {
+  if (!s || !out) return fail(NOC_ERR_ARG, "null argument");
+  *out = DIR_NONE;
+  if (!s->P.dir || line >= s->P.total_lines) return NOC_OK;
+  int rc = ensure_memory(s);
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(s->stream), "sync");
+  CU(cudaMemcpy(out, s->P.dir + line, 4, cudaMemcpyDeviceToHost), "directory copy");
+  return NOC_OK;
+}
+
+int noc_get_core(noc_sim* s, int tile, uint32_t* o) {
+  if (!s || !o || tile < 0 || tile >= s->P.N) return fail(NOC_ERR_ARG, "bad argument");
+  int rc = ensure_memory(s);
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(s->stream), "sync");
+  const size_t N = (size_t)s->P.N;
+  uint32_t c[NCORE];
+  for (int k = 0; k < NCORE; ++k)
+    CU(cudaMemcpy(&c[k], s->P.core + k * N + tile, 4, cudaMemcpyDeviceToHost), "core copy");
+  o[0] = c[C_NEXT];
+  o[1] = c[C_FSMB] & 0xFFu;
+  o[2] = c[C_FLINE];
+  o[3] = (c[C_FSMB] >> 8) & 0xFFu;
+  o[4] = c[C_FTIMER];
+  o[5] = c[C_FSTART];
+  o[6] = (c[C_FSMB] >> 16) & 0xFFu;
+  o[7] = c[C_OLINE];
+  o[8] = c[C_FSMB] >> 24;
+  o[9] = c[C_OSTART];
+  o[10] = c[C_OTIMER];
+  o[11] = c[C_EPOCH] >> 16;
+  o[12] = c[C_EPOCH] & 0xFFFFu;
+  o[13] = c[C_CQ] >> 16;
+  o[14] = c[C_SQ] >> 16;
+  o[15] = c[C_MQ] >> 16;
+  o[16] = c[C_FWD] >> 16;
+  return NOC_OK;
+}
+
+int noc_debug_wait_limit(noc_sim* s, int64_t ns, int silent_cta) {
+  if (!s || ns < 1) return fail(NOC_ERR_ARG, "bad argument");
+  s->wait_ns = ns;
+  s->silent_cta = silent_cta;
+  return NOC_OK;
+}
+
+int64_t noc_kernel_launches(const noc_sim* s) { return s ? s->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,38 @@
+// noc_internal.h -- declarations shared by the kernels (noc_kernel.cu) and the
+// host side of the C ABI (noc_api.cu).  Not installed; not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "noc_model.cuh"
+
+namespace noc {
+
+// per-launch arguments of the cycle kernel
+struct RunArgs {
+  uint32_t t0, n;        // first cycle and number of cycles of this launch
+  int draining;          // 1: no new references (drain)
+  int gx, gy;            // CTA rectangle grid
+  unsigned long long* hash_trace;  // per-cycle dynamic hash (nullptr: off)
+  unsigned int* busy;              // per-cycle count of non-quiet tiles (drain)
+  unsigned int* abort_flag;        // set when a wait ran out; all CTAs stop
+  long long wait_ns;               // limit of each device-side wait
+  int silent_cta;                  // test fault: this CTA never publishes
+};
+
+// geometry of the launch for a gx x gy rectangle grid
+int block_threads(int W, int H, int gx, int gy);
+size_t run_smem_bytes(int threads);
+
+cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s);
+cudaError_t max_coresident_ctas(int threads, int* out);
+cudaError_t launch_dyn_hash(const Params& P, uint32_t cycle, unsigned long long* out,
+                            cudaStream_t s);
+cudaError_t launch_state_hash(const Params& P, uint32_t cycle, unsigned long long* out,
+                              cudaStream_t s);
+cudaError_t launch_reduce_stats(const Params& P, int tile, unsigned long long* out,
+                                cudaStream_t s);
+cudaError_t launch_count_busy(const Params& P, uint32_t cycle, unsigned int* out,
+                              cudaStream_t s);
+cudaError_t launch_fill_u32(unsigned int* p, unsigned int v, size_t n, cudaStream_t s);
+
+}  // namespace noc

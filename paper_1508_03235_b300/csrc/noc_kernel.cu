@@ -1,0 +1,573 @@
+// noc_kernel.cu -- the persistent cooperative cycle kernel and its helpers.
+//
+// Mapping (B300, sm_103a): the mesh is cut into gx x gy rectangles, one CTA
+// each, one thread per tile.  A launch runs many simulated cycles.  Links
+// between tiles of the same rectangle are exchanged through shared memory;
+// links that cross a rectangle edge go through an L2-resident global buffer,
+// and each CTA waits only for its (up to four) neighbouring CTAs to publish the
+// previous cycle -- a neighbour-flag barrier instead of a grid-wide one.  The
+// tile's own work of the next cycle (Phase 3 of this cycle, Phase 1 of the
+// next) runs before that wait, so cache latency and barrier latency overlap.
+#include <cstdio>
+
+#include "noc_internal.h"
+
+namespace noc {
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait until *flag >= target (cycle counts, wrap-safe).  Returns 1 on success,
+// 0 when the time limit ran out, -1 when another CTA already gave up.  The
+// iteration count is bounded as well, so the wait always ends.
+__device__ int wait_ge(const unsigned* flag, unsigned target, const unsigned* abort_flag,
+                       long long limit_ns) {
+  const unsigned long long start = global_ns();
+  for (unsigned it = 0; it < (1u << 28); ++it) {
+    if ((int)(ld_acquire_u32(flag) - target) >= 0) return 1;
+    if ((it & 31u) == 31u) {
+      if (ld_acquire_u32(abort_flag)) return -1;
+      if ((long long)(global_ns() - start) > limit_ns) return 0;
+    }
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------- tile state I/O
+__device__ void load_tile(const Params& P, uint32_t r, Tile& T) {
+  const size_t N = (size_t)P.N;
+  const uint32_t* C = P.core;
+  T.r = r;
+  T.x = r % (uint32_t)P.W;
+  T.y = r / (uint32_t)P.W;
+  T.next_ref = C[C_NEXT * N + r];
+  uint32_t b = C[C_FSMB * N + r];
+  T.fsm = b & 0xFFu;
+  T.fsm_write = (b >> 8) & 0xFFu;
+  T.om_kind = (b >> 16) & 0xFFu;
+  T.om_write = b >> 24;
+  T.fsm_line = C[C_FLINE * N + r];
+  T.fsm_timer = C[C_FTIMER * N + r];
+  T.fsm_start = C[C_FSTART * N + r];
+  T.om_line = C[C_OLINE * N + r];
+  T.om_start = C[C_OSTART * N + r];
+  T.om_timer = C[C_OTIMER * N + r];
+  uint32_t e = C[C_EPOCH * N + r];
+  T.epoch = e & 0xFFFFu;
+  T.om_epoch = e >> 16;
+  uint32_t q = C[C_CQ * N + r];
+  T.cq_head = q & 0xFFFFu;
+  T.cq_len = q >> 16;
+  q = C[C_SQ * N + r];
+  T.sq_head = q & 0xFFFFu;
+  T.sq_len = q >> 16;
+  q = C[C_MQ * N + r];
+  T.mq_head = q & 0xFFFFu;
+  T.mq_len = q >> 16;
+  q = C[C_FWD * N + r];
+  T.fwd_next = q & 0xFFFFu;
+  T.fwd_n = q >> 16;
+  const uint4 z = make_uint4(0, 0, 0, 0);
+  T.cq_front = T.cq_len ? P.cq[(size_t)r * P.core_q + T.cq_head] : z;
+  T.sq_front = T.sq_len ? P.sq[(size_t)r * P.svc_q + T.sq_head] : z;
+  T.mq_front = T.mq_len ? P.mq[(size_t)r * P.mem_q + T.mq_head] : z;
+  T.ej = z;
+  T.inj = P.stats[S_INJ * N + r];
+  T.ejc = P.stats[S_EJ * N + r];
+  T.defl = P.stats[S_DEFL * N + r];
+  T.latsum = P.stats[S_LATSUM * N + r];
+  T.latmax = P.stats[S_LATMAX * N + r];
+  T.l2lsum = 0;
+#pragma unroll
+  for (int k = 0; k < NSMALL; ++k) T.sm[k] = 0;
+}
+
+__device__ void store_tile(const Params& P, const Tile& T) {
+  const size_t N = (size_t)P.N;
+  const uint32_t r = T.r;
+  uint32_t* C = P.core;
+  C[C_NEXT * N + r] = T.next_ref;
+  C[C_FSMB * N + r] = T.fsm | (T.fsm_write << 8) | (T.om_kind << 16) | (T.om_write << 24);
+  C[C_FLINE * N + r] = T.fsm_line;
+  C[C_FTIMER * N + r] = T.fsm_timer;
+  C[C_FSTART * N + r] = T.fsm_start;
+  C[C_OLINE * N + r] = T.om_line;
+  C[C_OSTART * N + r] = T.om_start;
+  C[C_OTIMER * N + r] = T.om_timer;
+  C[C_EPOCH * N + r] = T.epoch | (T.om_epoch << 16);
+  C[C_CQ * N + r] = T.cq_head | (T.cq_len << 16);
+  C[C_SQ * N + r] = T.sq_head | (T.sq_len << 16);
+  C[C_MQ * N + r] = T.mq_head | (T.mq_len << 16);
+  C[C_FWD * N + r] = T.fwd_next | (T.fwd_n << 16);
+  P.stats[S_INJ * N + r] = T.inj;
+  P.stats[S_EJ * N + r] = T.ejc;
+  P.stats[S_DEFL * N + r] = T.defl;
+  P.stats[S_LATSUM * N + r] = T.latsum;
+  P.stats[S_LATMAX * N + r] = T.latmax;
+  if (T.l2lsum) P.stats[S_L2LSUM * N + r] += T.l2lsum;
+#pragma unroll
+  for (int k = 0; k < NSMALL; ++k)
+    if (k + S_REFS != S_L2LSUM && T.sm[k]) P.stats[(size_t)(k + S_REFS) * N + r] += T.sm[k];
+}
+
+__device__ __forceinline__ bool tile_quiet(const Tile& T, const uint4 (&out)[4]) {
+  bool q = T.cq_len == 0 && T.sq_len == 0 && T.mq_len == 0 && T.fsm == FSM_IDLE &&
+           T.om_kind == OM_NONE;
+#pragma unroll
+  for (int d = 0; d < 4; ++d) q = q && ftype(out[d]) == T_NONE;
+  return q;
+}
+
+// sum a 64-bit value over the CTA; the result is valid in thread 0
+__device__ unsigned long long block_sum(unsigned long long v, unsigned long long* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  unsigned long long s = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) s += red[w];
+  return s;
+}
+
+// ---------------------------------------------------------------- cycle kernel
+constexpr int MAX_THREADS = 384;
+
+size_t run_smem_bytes(int threads) {
+  return (size_t)threads * 8 * sizeof(uint4) + (2 * HIST_BINS + 2) * sizeof(uint32_t) +
+         32 * sizeof(unsigned long long);
+}
+
+int block_threads(int W, int H, int gx, int gy) {
+  int bw = (W + gx - 1) / gx, bh = (H + gy - 1) / gy;
+  int a = bw * bh;
+  return ((a + 31) / 32) * 32;
+}
+
+template <bool HASH, bool DRAIN>
+__global__ void __launch_bounds__(MAX_THREADS, 1) run_kernel(const Params P, const RunArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nt = blockDim.x;
+  uint4* sl = reinterpret_cast<uint4*>(smem_raw);  // [2 parity][4 port][nt]
+  uint32_t* sh_hist = reinterpret_cast<uint32_t*>(sl + 8 * nt);
+  unsigned long long* sh_red = reinterpret_cast<unsigned long long*>(sh_hist + 2 * HIST_BINS + 2);
+  __shared__ int sh_abort;
+
+  const int b = blockIdx.x;
+  const int cx = b % A.gx, cy = b / A.gx;
+  const int X0 = cx * P.W / A.gx, X1 = (cx + 1) * P.W / A.gx;
+  const int Y0 = cy * P.H / A.gy, Y1 = (cy + 1) * P.H / A.gy;
+  const int bw = X1 - X0, bh = Y1 - Y0;
+  const int i = threadIdx.x;
+  const bool active = i < bw * bh;
+  const int lx = active ? i % bw : 0, ly = active ? i / bw : 0;
+  const uint32_t x = X0 + lx, y = Y0 + ly, r = y * P.W + x;
+  const size_t N = (size_t)P.N;
+  const uint32_t exists = (y > 0 ? 1u << P_N : 0u) | (y + 1 < (uint32_t)P.H ? 1u << P_S : 0u) |
+                          (x + 1 < (uint32_t)P.W ? 1u << P_E : 0u) | (x > 0 ? 1u << P_W : 0u);
+  // links that leave the rectangle also go to the global buffer
+  const uint32_t boundary = exists & ((ly == 0 ? 1u << P_N : 0u) | (ly == bh - 1 ? 1u << P_S : 0u) |
+                                      (lx == bw - 1 ? 1u << P_E : 0u) | (lx == 0 ? 1u << P_W : 0u));
+  // neighbouring CTAs this CTA waits for: N, S, E, W
+  int wait_cta = -1;
+  if (i < 4) {
+    if (i == 0 && cy > 0) wait_cta = b - A.gx;
+    if (i == 1 && cy + 1 < A.gy) wait_cta = b + A.gx;
+    if (i == 2 && cx + 1 < A.gx) wait_cta = b + 1;
+    if (i == 3 && cx > 0) wait_cta = b - 1;
+  }
+
+  for (int k = i; k < 2 * HIST_BINS; k += nt) sh_hist[k] = 0;
+  if (i == 0) sh_abort = 0;
+
+  Tile T;
+  uint4 out[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) out[d] = make_uint4(0, 0, 0, 0);
+  const uint32_t t0 = A.t0, tend = A.t0 + A.n;
+  if (active) {
+    load_tile(P, r, T);
+    const uint32_t pin = (t0 - 1u) & 1u;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      out[d] = P.glink[((size_t)pin * 4 + d) * N + r];
+      sl[(pin * 4 + d) * nt + i] = out[d];
+    }
+  }
+  __syncthreads();
+  if (active) phase1(P, T, t0, A.draining != 0, sh_hist);
+
+  uint32_t t = t0;
+  for (; t < tend; ++t) {
+    const uint32_t pin = (t - 1u) & 1u, pout = t & 1u;
+    // ---- Phase 2: gather arrivals, route, publish outputs
+    if (active) {
+      uint4 in[4];
+      const uint4 z = make_uint4(0, 0, 0, 0);
+      const uint4* gl = P.glink + (size_t)pin * 4 * N;
+      const uint4* sp = sl + pin * 4 * nt;
+      in[P_N] = !(exists & (1u << P_N)) ? z
+                : (ly > 0 ? sp[P_S * nt + i - bw] : __ldcg(&gl[P_S * N + r - P.W]));
+      in[P_S] = !(exists & (1u << P_S)) ? z
+                : (ly < bh - 1 ? sp[P_N * nt + i + bw] : __ldcg(&gl[P_N * N + r + P.W]));
+      in[P_E] = !(exists & (1u << P_E)) ? z
+                : (lx < bw - 1 ? sp[P_W * nt + i + 1] : __ldcg(&gl[P_W * N + r + 1]));
+      in[P_W] = !(exists & (1u << P_W)) ? z
+                : (lx > 0 ? sp[P_E * nt + i - 1] : __ldcg(&gl[P_E * N + r - 1]));
+      route(P, T, t, in, exists, out);
+      uint4* so = sl + pout * 4 * nt;
+      uint4* go = P.glink + (size_t)pout * 4 * N;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        so[d * nt + i] = out[d];
+        if (boundary & (1u << d)) __stcg(&go[d * N + r], out[d]);
+      }
+    }
+    __syncthreads();
+    if (i == 0 && b != A.silent_cta) {
+      __threadfence();
+      st_release_u32(&P.flags[b], t + 1);
+    }
+    // ---- Phase 3 of this cycle
+    if (active) phase3(P, T, t, sh_hist);
+    if (HASH) {
+      unsigned long long h = active ? tile_hash(T, out) : 0ull;
+      h = block_sum(h, sh_red);
+      if (i == 0) atomicAdd(&A.hash_trace[t - t0], h);
+    }
+    if (DRAIN) {
+      unsigned long long q = (active && !tile_quiet(T, out)) ? 1ull : 0ull;
+      q = block_sum(q, sh_red);
+      if (i == 0 && q) atomicAdd(&A.busy[t - t0], (unsigned)q);
+    }
+    if (t + 1 == tend) break;
+    // ---- Phase 1 of the next cycle, then wait for the neighbours' outputs
+    if (active) phase1(P, T, t + 1, A.draining != 0, sh_hist);
+    if (wait_cta >= 0) {
+      int w = wait_ge(&P.flags[wait_cta], t + 1, A.abort_flag, A.wait_ns);
+      if (w <= 0) {
+        if (w == 0) {
+          atomicExch(A.abort_flag, 1u);
+          set_error(P, t + 1, ERR_TIMEOUT);
+        }
+        sh_abort = 1;
+      }
+    }
+    __syncthreads();
+    if (sh_abort) break;
+  }
+
+  // ---- end of launch: full link state of the last cycle, tile state, counters
+  if (active) {
+    const uint32_t plast = (t - (t == tend ? 1u : 0u)) & 1u;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) P.glink[((size_t)plast * 4 + d) * N + r] = out[d];
+    store_tile(P, T);
+  }
+  __syncthreads();
+  for (int k = i; k < 2 * HIST_BINS; k += nt)
+    if (sh_hist[k]) atomicAdd(&P.hist[k], (unsigned long long)sh_hist[k]);
+}
+
+template <bool H, bool D>
+static cudaError_t prepare_run() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(run_kernel<H, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)run_smem_bytes(MAX_THREADS));
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+cudaError_t max_coresident_ctas(int threads, int* out) {
+  cudaError_t e = prepare_run<false, false>();
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, run_kernel<false, false>, threads,
+                                                    run_smem_bytes(threads));
+  if (e != cudaSuccess) return e;
+  *out = per * sms;
+  return cudaSuccess;
+}
+
+template <bool H, bool D>
+static cudaError_t launch_run_t(const Params& P, const RunArgs& A, cudaStream_t s) {
+  cudaError_t e = prepare_run<H, D>();
+  if (e != cudaSuccess) return e;
+  const int threads = block_threads(P.W, P.H, A.gx, A.gy);
+  void* args[] = {(void*)&P, (void*)&A};
+  return cudaLaunchCooperativeKernel((const void*)run_kernel<H, D>, dim3(A.gx * A.gy),
+                                     dim3(threads), args, run_smem_bytes(threads), s);
+}
+
+cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
+  if (A.hash_trace && A.busy) return launch_run_t<true, true>(P, A, s);
+  if (A.hash_trace) return launch_run_t<true, false>(P, A, s);
+  if (A.busy) return launch_run_t<false, true>(P, A, s);
+  return launch_run_t<false, false>(P, A, s);
+}
+
+// ---------------------------------------------------------------- hashes
+__global__ void dyn_hash_kernel(const Params P, uint32_t cycle, unsigned long long* out) {
+  __shared__ unsigned long long red[32];
+  unsigned long long acc = 0;
+  const size_t N = (size_t)P.N;
+  const uint32_t par = (cycle - 1u) & 1u;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < (uint32_t)P.N;
+       r += gridDim.x * blockDim.x) {
+    Tile T;
+    load_tile(P, r, T);
+    uint4 o[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) o[d] = P.glink[((size_t)par * 4 + d) * N + r];
+    acc += tile_hash(T, o);
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+
+__device__ __forceinline__ void flit_words(uint4 f, unsigned long long& w0, unsigned long long& w1,
+                                           unsigned long long& w2) {
+  uint32_t ty = ftype(f);
+  w0 = w1 = w2 = 0;
+  if (!ty) return;
+  w0 = (unsigned long long)ty | ((unsigned long long)fsrc(f) << 16) |
+       ((unsigned long long)fdst(f) << 32) | ((unsigned long long)fa(f) << 48);
+  w1 = (unsigned long long)fline(f) | ((unsigned long long)f.x << 32);
+  w2 = fe(f);
+}
+
+// full-state terms other than the dynamic hash (model text, "full state hash")
+__global__ void state_terms_kernel(const Params P, uint32_t cycle, unsigned long long* out) {
+  __shared__ unsigned long long red[32];
+  unsigned long long acc = 0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t N = (size_t)P.N;
+  if (tid == 0) acc += hfold(hstart(0x18), cycle);
+  // L1 ways
+  const size_t n1 = N * P.l1_sets * P.l1_ways;
+  for (size_t k = tid; k < n1; k += stride) {
+    uint32_t v = P.l1[k];
+    if (!(v & W_VALID)) continue;
+    size_t way = k % P.l1_ways, set = (k / P.l1_ways) % P.l1_sets, r = k / ((size_t)P.l1_ways * P.l1_sets);
+    unsigned long long h = hstart(0x11);
+    h = hfold(h, r);
+    h = hfold(h, set);
+    h = hfold(h, way);
+    h = hfold(h, v & W_LINE);
+    h = hfold(h, P.l1own[k]);
+    h = hfold(h, wrank(v));
+    acc += h;
+  }
+  // L2 ways
+  const size_t n2 = N * P.l2_sets * P.l2_ways;
+  for (size_t k = tid; k < n2; k += stride) {
+    uint32_t v = P.l2[k];
+    if (!(v & W_VALID)) continue;
+    size_t way = k % P.l2_ways, set = (k / P.l2_ways) % P.l2_sets, r = k / ((size_t)P.l2_ways * P.l2_sets);
+    unsigned long long h = hstart(0x12);
+    h = hfold(h, r);
+    h = hfold(h, set);
+    h = hfold(h, way);
+    h = hfold(h, v & W_LINE);
+    h = hfold(h, (v & W_DIRTY) ? 1u : 0u);
+    h = hfold(h, wrank(v));
+    h = hfold(h, P.policy != POL_INTERLEAVED ? P.l2ep[k] : 0u);
+    uint32_t mig = 0, hn = 0;
+    const uint16_t* hp = nullptr;
+    if (P.policy == POL_MIGRATE) {
+      hp = P.l2hist + k * HIST_STRIDE;
+      hn = hp[0];
+      mig = hp[1];
+    }
+    h = hfold(h, mig);
+    h = hfold(h, hn);
+    for (uint32_t j = 0; j < hn; ++j) h = hfold(h, hp[2 + j]);
+    acc += h;
+  }
+  // core and service queues
+  for (int qi = 0; qi < 2; ++qi) {
+    const int cap = qi == 0 ? P.core_q : P.svc_q;
+    const uint4* buf = qi == 0 ? P.cq : P.sq;
+    const int field = qi == 0 ? C_CQ : C_SQ;
+    const size_t nq = N * cap;
+    for (size_t k = tid; k < nq; k += stride) {
+      size_t r = k / cap, slot = k % cap;
+      uint32_t q = P.core[field * N + r], head = q & 0xFFFFu, len = q >> 16;
+      uint32_t pos = (uint32_t)((slot + cap - head) % cap);
+      if (pos >= len) continue;
+      unsigned long long w0, w1, w2;
+      flit_words(buf[k], w0, w1, w2);
+      unsigned long long h = hstart(0x13 + qi);
+      h = hfold(h, r);
+      h = hfold(h, pos);
+      h = hfold(h, w0);
+      h = hfold(h, w1);
+      h = hfold(h, w2);
+      acc += h;
+    }
+  }
+  // memory-return FIFOs
+  {
+    const size_t nq = N * P.mem_q;
+    for (size_t k = tid; k < nq; k += stride) {
+      size_t r = k / P.mem_q, slot = k % P.mem_q;
+      uint32_t q = P.core[C_MQ * N + r], head = q & 0xFFFFu, len = q >> 16;
+      uint32_t pos = (uint32_t)((slot + P.mem_q - head) % P.mem_q);
+      if (pos >= len) continue;
+      uint4 m = P.mq[k];
+      unsigned long long h = hstart(0x15);
+      h = hfold(h, r);
+      h = hfold(h, pos);
+      h = hfold(h, m.x);
+      h = hfold(h, m.y);
+      h = hfold(h, m.z);
+      acc += h;
+    }
+  }
+  // directory
+  if (P.policy != POL_INTERLEAVED)
+    for (size_t k = tid; k < P.total_lines; k += stride) {
+      uint32_t D = P.dir[k];
+      if (D == DIR_NONE) continue;
+      unsigned long long h = hstart(0x16);
+      h = hfold(h, k);
+      h = hfold(h, D & 0xFFFFu);
+      h = hfold(h, D >> 16);
+      acc += h;
+    }
+  // forward tables
+  if (P.policy == POL_MIGRATE) {
+    const size_t nf = N * P.fwd_cap;
+    for (size_t k = tid; k < nf; k += stride) {
+      size_t r = k / P.fwd_cap, slot = k % P.fwd_cap;
+      uint32_t q = P.core[C_FWD * N + r], next = q & 0xFFFFu, n = q >> 16;
+      uint32_t pos = (uint32_t)((next + 2 * P.fwd_cap - 1 - slot) % P.fwd_cap);
+      if (pos >= n) continue;
+      unsigned long long h = hstart(0x17);
+      h = hfold(h, r);
+      h = hfold(h, pos);
+      h = hfold(h, P.fwd[k * 2]);
+      h = hfold(h, P.fwd[k * 2 + 1]);
+      acc += h;
+    }
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+
+static int grid_for(size_t n, int threads) {
+  size_t g = (n + threads - 1) / threads;
+  if (g > 4096) g = 4096;
+  return (int)(g ? g : 1);
+}
+
+cudaError_t launch_dyn_hash(const Params& P, uint32_t cycle, unsigned long long* out,
+                            cudaStream_t s) {
+  dyn_hash_kernel<<<grid_for(P.N, 256), 256, 0, s>>>(P, cycle, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_state_hash(const Params& P, uint32_t cycle, unsigned long long* out,
+                              cudaStream_t s) {
+  dyn_hash_kernel<<<grid_for(P.N, 256), 256, 0, s>>>(P, cycle, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  size_t n = (size_t)P.N * P.l2_sets * P.l2_ways;
+  state_terms_kernel<<<grid_for(n, 256), 256, 0, s>>>(P, cycle, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- statistics
+// block k reduces counter k over all tiles (a maximum for the latency max)
+__global__ void reduce_stats_kernel(const Params P, int tile, unsigned long long* out) {
+  __shared__ unsigned long long red[32];
+  const int k = blockIdx.x;
+  const size_t N = (size_t)P.N;
+  unsigned long long acc = 0;
+  if (tile >= 0) {
+    if (threadIdx.x == 0) out[k] = P.stats[k * N + tile];
+    return;
+  }
+  for (size_t r = threadIdx.x; r < N; r += blockDim.x) {
+    unsigned long long v = P.stats[k * N + r];
+    acc = k == S_LATMAX ? (v > acc ? v : acc) : acc + v;
+  }
+  if (k == S_LATMAX) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long u = __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+      acc = u > acc ? u : acc;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long m = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
+      out[k] = m;
+    }
+    return;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) out[k] = acc;
+}
+
+cudaError_t launch_reduce_stats(const Params& P, int tile, unsigned long long* out,
+                                cudaStream_t s) {
+  reduce_stats_kernel<<<NSTAT, 256, 0, s>>>(P, tile, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- drain helpers
+__global__ void count_busy_kernel(const Params P, uint32_t cycle, unsigned int* out) {
+  __shared__ unsigned long long red[32];
+  const size_t N = (size_t)P.N;
+  const uint32_t par = (cycle - 1u) & 1u;
+  unsigned long long c = 0;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < (uint32_t)P.N;
+       r += gridDim.x * blockDim.x) {
+    Tile T;
+    load_tile(P, r, T);
+    uint4 o[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) o[d] = P.glink[((size_t)par * 4 + d) * N + r];
+    c += tile_quiet(T, o) ? 0 : 1;
+  }
+  c = block_sum(c, red);
+  if (threadIdx.x == 0 && c) atomicAdd(out, (unsigned)c);
+}
+
+cudaError_t launch_count_busy(const Params& P, uint32_t cycle, unsigned int* out, cudaStream_t s) {
+  count_busy_kernel<<<grid_for(P.N, 256), 256, 0, s>>>(P, cycle, out);
+  return cudaGetLastError();
+}
+
+__global__ void fill_u32_kernel(unsigned int* p, unsigned int v, size_t n) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x)
+    p[k] = v;
+}
+
+cudaError_t launch_fill_u32(unsigned int* p, unsigned int v, size_t n, cudaStream_t s) {
+  fill_u32_kernel<<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
+  return cudaGetLastError();
+}
+
+}  // namespace noc

@@ -323,7 +323,7 @@ __device__ __forceinline__ size_t l2_base(const Params& P, uint32_t r, uint32_t 
 }
 
 // fill the L1 with `line` (insert if absent, else touch); L1 victims are clean
-__device__ void l1_fill(const Params& P, Tile& T, uint32_t line, uint32_t owner) {
+static __device__ void l1_fill(const Params& P, Tile& T, uint32_t line, uint32_t owner) {
   uint32_t set = l1_set(P, line);
   size_t base = l1_base(P, T.r, set);
   uint32_t w[MAX_WAYS];
@@ -347,7 +347,7 @@ __device__ __forceinline__ uint16_t* hist_ptr(const Params& P, size_t way_index)
 }
 
 // directory entry delete for an evicted L2 victim (Sec. 3.4)
-__device__ void send_dinv(const Params& P, Tile& T, uint32_t vline, uint32_t vepoch, uint32_t t) {
+static __device__ void send_dinv(const Params& P, Tile& T, uint32_t vline, uint32_t vepoch, uint32_t t) {
   uint32_t h = home_of(P, vline);
   if (h == T.r) {
     if (P.dir[vline] == (T.r | (vepoch << 16))) P.dir[vline] = DIR_NONE;
@@ -358,7 +358,7 @@ __device__ void send_dinv(const Params& P, Tile& T, uint32_t vline, uint32_t vep
 
 // install `line` in this tile's L2 slice: insert if absent (evicting the
 // victim), else touch; returns the way index
-__device__ int l2_install(const Params& P, Tile& T, uint32_t line, uint32_t epoch, uint32_t t) {
+static __device__ int l2_install(const Params& P, Tile& T, uint32_t line, uint32_t epoch, uint32_t t) {
   uint32_t set = l2_set(P, line);
   size_t base = l2_base(P, T.r, set);
   uint32_t w[MAX_WAYS];
@@ -391,7 +391,7 @@ __device__ int l2_install(const Params& P, Tile& T, uint32_t line, uint32_t epoc
 }
 
 // write-through performed at this tile's own slice
-__device__ void local_wt(const Params& P, Tile& T, uint32_t line) {
+static __device__ void local_wt(const Params& P, Tile& T, uint32_t line) {
   uint32_t set = l2_set(P, line);
   size_t base = l2_base(P, T.r, set);
   uint32_t w[MAX_WAYS];
@@ -408,7 +408,7 @@ __device__ void local_wt(const Params& P, Tile& T, uint32_t line) {
 }
 
 // record accessor `who` in the block's history of the last mig_window accessors
-__device__ void hist_push(const Params& P, size_t way_index, uint32_t who) {
+static __device__ void hist_push(const Params& P, size_t way_index, uint32_t who) {
   uint16_t* hp = hist_ptr(P, way_index);
   uint32_t n = hp[0];
   if (n < (uint32_t)P.mig_window) {
@@ -440,7 +440,7 @@ __device__ __forceinline__ void set_om(Tile& T, uint32_t kind, uint32_t line, ui
 
 // ---------------------------------------------------------------- Phase 1
 // the L1 lookup of a reference; returns false if the action was not taken
-__device__ bool l1_step(const Params& P, Tile& T, uint32_t t, uint32_t line, uint32_t write) {
+static __device__ bool l1_step(const Params& P, Tile& T, uint32_t t, uint32_t line, uint32_t write) {
   uint32_t set = l1_set(P, line);
   size_t base = l1_base(P, T.r, set);
   uint32_t w[MAX_WAYS];
@@ -476,7 +476,7 @@ __device__ bool l1_step(const Params& P, Tile& T, uint32_t t, uint32_t line, uin
   return true;
 }
 
-__device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* sh_hist) {
+static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* sh_hist) {
   const uint32_t line = T.fsm_line, start = T.fsm_start, write = T.fsm_write;
   const bool busy = T.om_kind != OM_NONE;
   uint32_t set = l2_set(P, line);
@@ -583,7 +583,7 @@ __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* sh_hist)
 }
 
 // the line of reference k of this core (Philox stream, Sec. 6.2.3 stand-in)
-__device__ uint32_t draw_line(const Params& P, uint32_t core, uint32_t k, uint32_t& write) {
+static __device__ uint32_t draw_line(const Params& P, uint32_t core, uint32_t k, uint32_t& write) {
   unsigned long long w[4];
   philox4x64_10(k, core, P.stream, 0, P.seed, 0x4E4F43ull, w);
   write = (uint32_t)(w[0] >> 48) < P.write_q16 ? 1u : 0u;
@@ -613,7 +613,7 @@ __device__ __forceinline__ void mq_pop(const Params& P, Tile& T) {
   if (T.mq_len > 0) T.mq_front = P.mq[(size_t)T.r * P.mem_q + T.mq_head];
 }
 
-__device__ void phase1(const Params& P, Tile& T, uint32_t t, bool draining, uint32_t* sh_hist) {
+static __device__ void phase1(const Params& P, Tile& T, uint32_t t, bool draining, uint32_t* sh_hist) {
   // (i) memory returns at an interleaved home: install, then reply
   while (T.mq_len > 0 && T.mq_front.x <= t) {
     uint32_t line = T.mq_front.y, req = T.mq_front.z;
@@ -778,7 +778,7 @@ __device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint
 }
 
 // ---------------------------------------------------------------- Phase 3
-__device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh_hist) {
+static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh_hist) {
   uint4 f = T.ej;
   uint32_t ty = ftype(f);
   if (ty == T_NONE) return;
@@ -993,7 +993,7 @@ __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh_hist) 
 
 // ---------------------------------------------------------------- hash
 // dynamic hash of one tile after a cycle (model text, "dynamic hash")
-__device__ unsigned long long tile_hash(const Tile& T, const uint4 (&out)[4]) {
+static __device__ unsigned long long tile_hash(const Tile& T, const uint4 (&out)[4]) {
   unsigned long long h = hstart(T.r);
 #pragma unroll
   for (int d = 0; d < 4; ++d) h = hflit(h, out[d]);
