@@ -193,6 +193,8 @@ int choose_tiling(noc_sim* s, int* gx_out, int* gy_out) {
     *gy_out = s->gy;
     return NOC_OK;
   }
+  int cap_of[384 / 32 + 1];
+  for (int k = 0; k <= 384 / 32; ++k) cap_of[k] = -1;
   int best_gx = 0, best_gy = 0;
   long best_g = 0, best_a = 0, best_p = 0;
   bool best_small = false;
@@ -202,8 +204,11 @@ int choose_tiling(noc_sim* s, int* gx_out, int* gy_out) {
       if (threads > 384) continue;
       const long G = (long)gx * gy;
       if (G > (long)s->n_flags) continue;
-      int cap = 0;
-      if (max_coresident_ctas(threads, &cap) != cudaSuccess) return cuda_fail(cudaGetLastError(), "occupancy");
+      int& cap = cap_of[threads / 32];
+      if (cap < 0) {
+        cudaError_t e = max_coresident_ctas(threads, &cap);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+      }
       if (G > cap) continue;
       const long bw = (W + gx - 1) / gx, bh = (H + gy - 1) / gy, a = bw * bh, per = bw + bh;
       const bool small = a <= 128;

@@ -1,0 +1,297 @@
+"""ctypes binding of libnoc.so (the CUDA path); argument marshalling only.
+
+Every simulated cycle runs in the library's sm_103a kernels.  PyTorch provides
+the device arena (a uint8 tensor bound with noc_bind_memory) and the stream.
+There is no CPU fallback: importing this module raises if the library or a
+CUDA device is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnoc.so")
+
+NOC_OK = 0
+ERR_NAMES = {1: "NOC_ERR_ARG", 2: "NOC_ERR_OOM", 3: "NOC_ERR_QUEUE_OVERFLOW", 4: "NOC_ERR_TIMEOUT",
+             5: "NOC_ERR_CUDA", 6: "NOC_ERR_PROTOCOL", 7: "NOC_ERR_STATE"}
+HIST_BINS = 1025
+FLIT_TYPES = dict(NONE=0, REQ=1, DATA=2, WT=3, DA=4, DRPOS=5, DRNEG=6, NACK=7, DINV=8, MIG=9,
+                  DIRUPD=10, INV=11, PROBE=12)
+
+
+class CacheCfg(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in (
+        "l1_sets", "l1_ways", "l2_sets", "l2_ways", "l1_miss_cycles", "mem_latency",
+        "mig_window", "mig_threshold", "core_q", "svc_q", "mem_q", "fwd_entries")]
+
+
+class Traffic(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("period", C.c_int32), ("write_q16", C.c_uint32),
+                ("priv_q16", C.c_uint32), ("shared_q16", C.c_uint32), ("hot_q16", C.c_uint32),
+                ("hot_side", C.c_int32), ("priv_lines", C.c_uint32), ("shared_lines", C.c_uint32),
+                ("remote_lines", C.c_uint32), ("stream", C.c_uint32)]
+
+
+STATS_FIELDS = ("cycle", "injected", "ejected", "in_flight", "deflections", "lat_sum", "lat_max",
+                "refs", "l1_hit", "l1_miss", "l2_hit", "l2_miss", "req_made", "req_rcvd",
+                "reply_sent", "reply_rcvd", "dir_search", "mem_req", "mem_write", "mem_wb",
+                "wt_sent", "wt_hit", "trap", "redir", "migrations", "l2lat_sum", "l2lat_cnt",
+                "cq_stall", "mm_stall", "mig_sent")
+
+
+class Stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in STATS_FIELDS]
+
+
+class NocError(RuntimeError):
+    def __init__(self, code, msg, cycle=-1):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+        self.cycle = cycle
+
+
+_lib = None
+
+
+def lib():
+    """Load libnoc.so; raises if it was not built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python paper_1508_03235_b300/build.py`")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, u32, P64, P32 = (C.c_void_p, C.c_int, C.c_int64, C.c_uint32,
+                                       C.POINTER(C.c_uint64), C.POINTER(C.c_uint32))
+        sig = {
+            "noc_create": (i32, [i32, i32, C.POINTER(CacheCfg), i32, C.POINTER(Traffic), C.c_uint64,
+                                 C.POINTER(vp)]),
+            "noc_destroy": (None, [vp]),
+            "noc_required_bytes": (C.c_size_t, [vp]),
+            "noc_bind_memory": (i32, [vp, vp, C.c_size_t]),
+            "noc_set_stream": (i32, [vp, vp]),
+            "noc_reset": (i32, [vp]),
+            "noc_step": (i32, [vp, i64]),
+            "noc_drain": (i32, [vp, i64, C.POINTER(i64)]),
+            "noc_sync": (i32, [vp, C.POINTER(i64)]),
+            "noc_stats": (i32, [vp, i32, C.POINTER(Stats)]),
+            "noc_latency_hist": (i32, [vp, i32, P64, i32]),
+            "noc_dyn_hash": (i32, [vp, P64]),
+            "noc_state_hash": (i32, [vp, P64]),
+            "noc_set_hash_trace": (i32, [vp, i32]),
+            "noc_hash_trace": (i32, [vp, P64, i64]),
+            "noc_set_tiling": (i32, [vp, i32, i32]),
+            "noc_get_tiling": (i32, [vp, C.POINTER(i32), C.POINTER(i32)]),
+            "noc_set_trace": (i32, [vp, i32, i64, P32]),
+            "noc_debug_enqueue": (i32, [vp, i32, i32, P32]),
+            "noc_debug_link": (i32, [vp, i32, i32, P32]),
+            "noc_get_links": (i32, [vp, P32]),
+            "noc_get_cache": (i32, [vp, i32, i32, P32]),
+            "noc_dir_get": (i32, [vp, u32, P32]),
+            "noc_get_core": (i32, [vp, i32, P32]),
+            "noc_debug_wait_limit": (i32, [vp, i64, i32]),
+            "noc_kernel_launches": (i64, [vp]),
+            "noc_last_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, cycle=-1):
+    if rc != NOC_OK:
+        raise NocError(rc, lib().noc_last_error().decode(), cycle)
+
+
+def _p64(a):
+    return a.ctypes.data_as(C.POINTER(C.c_uint64))
+
+
+def _p32(a):
+    return a.ctypes.data_as(C.POINTER(C.c_uint32))
+
+
+def cache_struct(p: dict) -> CacheCfg:
+    c = CacheCfg()
+    for n, _ in CacheCfg._fields_:
+        setattr(c, n, int(p.get(n, 0)))
+    return c
+
+
+def traffic_struct(p: dict) -> Traffic:
+    t = Traffic()
+    for n, _ in Traffic._fields_:
+        setattr(t, n, int(p.get(n, 0)))
+    return t
+
+
+class Sim:
+    """One simulation on the current CUDA device.  `params` is a flat dict from
+    paper_1508_03235_b300.inputs.sim_params()."""
+
+    def __init__(self, params: dict, stream=None, tiling=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the simulator needs a CUDA device")
+        self.params = dict(params)
+        self.N = params["mesh_w"] * params["mesh_h"]
+        h = C.c_void_p()
+        rc = lib().noc_create(params["mesh_w"], params["mesh_h"], C.byref(cache_struct(params)),
+                              params.get("policy", 0), C.byref(traffic_struct(params)),
+                              params.get("seed", 1), C.byref(h))
+        _check(rc)
+        self._h = h
+        nbytes = lib().noc_required_bytes(h)
+        self._mem = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        ptr = self._mem.data_ptr()
+        ptr += (-ptr) % 256
+        _check(lib().noc_bind_memory(h, C.c_void_p(ptr), nbytes))
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self._stream = st
+        _check(lib().noc_set_stream(h, C.c_void_p(st.cuda_stream)))
+        if tiling is not None:
+            self.set_tiling(*tiling)
+        _check(lib().noc_reset(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().noc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- running -----------------------------------------------------------
+    def reset(self):
+        _check(lib().noc_reset(self._h))
+
+    def step(self, n: int, trace: bool = False, sync: bool = True):
+        if trace:
+            _check(lib().noc_set_hash_trace(self._h, 1))
+        try:
+            _check(lib().noc_step(self._h, n))
+            if trace or sync:
+                self.sync()
+            if trace:
+                buf = np.zeros(max(n, 1), dtype=np.uint64)
+                _check(lib().noc_hash_trace(self._h, _p64(buf), n))
+                return buf[:n]
+        finally:
+            if trace:
+                lib().noc_set_hash_trace(self._h, 0)
+        return None
+
+    def step_async(self, n: int):
+        _check(lib().noc_step(self._h, n))
+
+    def sync(self):
+        cyc = C.c_int64()
+        rc = lib().noc_sync(self._h, C.byref(cyc))
+        _check(rc, cyc.value)
+
+    def error(self):
+        cyc = C.c_int64()
+        rc = lib().noc_sync(self._h, C.byref(cyc))
+        return rc, cyc.value
+
+    def drain(self, max_cycles: int) -> int:
+        taken = C.c_int64()
+        _check(lib().noc_drain(self._h, max_cycles, C.byref(taken)))
+        return taken.value
+
+    def set_tiling(self, gx: int, gy: int):
+        _check(lib().noc_set_tiling(self._h, gx, gy))
+
+    def tiling(self):
+        gx, gy = C.c_int(), C.c_int()
+        _check(lib().noc_get_tiling(self._h, C.byref(gx), C.byref(gy)))
+        return gx.value, gy.value
+
+    def wait_limit(self, ns: int, silent_cta: int = -1):
+        _check(lib().noc_debug_wait_limit(self._h, ns, silent_cta))
+
+    @property
+    def launches(self) -> int:
+        return lib().noc_kernel_launches(self._h)
+
+    # --- results -----------------------------------------------------------
+    def stats(self, tile: int = -1) -> dict:
+        s = Stats()
+        _check(lib().noc_stats(self._h, tile, C.byref(s)))
+        return {n: int(getattr(s, n)) for n in STATS_FIELDS}
+
+    @property
+    def cycle(self) -> int:
+        return self.stats()["cycle"]
+
+    def hist(self, which: int) -> np.ndarray:
+        out = np.zeros(HIST_BINS, dtype=np.uint64)
+        _check(lib().noc_latency_hist(self._h, which, _p64(out), HIST_BINS))
+        return out
+
+    def dyn_hash(self) -> int:
+        v = np.zeros(1, dtype=np.uint64)
+        _check(lib().noc_dyn_hash(self._h, _p64(v)))
+        return int(v[0])
+
+    def state_hash(self) -> int:
+        v = np.zeros(1, dtype=np.uint64)
+        _check(lib().noc_state_hash(self._h, _p64(v)))
+        return int(v[0])
+
+    # --- scripted inputs and introspection ---------------------------------
+    def set_trace(self, core: int, refs):
+        a = np.ascontiguousarray(refs, dtype=np.uint32)
+        _check(lib().noc_set_trace(self._h, core, len(a), _p32(a)))
+
+    @staticmethod
+    def _flit(f):
+        if isinstance(f, dict):
+            f = [FLIT_TYPES[f["type"]] if isinstance(f["type"], str) else f["type"],
+                 f.get("src", 0), f["dst"], f.get("inject", 0), f.get("line", 0),
+                 f.get("a", 0), f.get("e", 0)]
+        return np.ascontiguousarray(f, dtype=np.uint32)
+
+    def debug_enqueue(self, tile: int, queue: int, flit):
+        a = self._flit(flit)
+        _check(lib().noc_debug_enqueue(self._h, tile, queue, _p32(a)))
+
+    def debug_link(self, tile: int, direction: int, flit):
+        a = self._flit(flit)
+        _check(lib().noc_debug_link(self._h, tile, direction, _p32(a)))
+
+    def links(self) -> np.ndarray:
+        out = np.zeros(self.N * 4 * 7, dtype=np.uint32)
+        _check(lib().noc_get_links(self._h, _p32(out)))
+        return out.reshape(self.N, 4, 7)
+
+    def cache(self, tile: int, which: int) -> np.ndarray:
+        p = self.params
+        sets, ways = (p["l1_sets"], p["l1_ways"]) if which == 1 else (p["l2_sets"], p["l2_ways"])
+        out = np.zeros(sets * ways * 4, dtype=np.uint32)
+        _check(lib().noc_get_cache(self._h, tile, which, _p32(out)))
+        return out.reshape(sets, ways, 4)
+
+    def dir_get(self, line: int) -> int:
+        v = np.zeros(1, dtype=np.uint32)
+        _check(lib().noc_dir_get(self._h, line, _p32(v)))
+        return int(v[0])
+
+    CORE_FIELDS = ("next_ref", "fsm", "fsm_line", "fsm_write", "fsm_timer", "fsm_start",
+                   "om_kind", "om_line", "om_write", "om_start", "om_timer", "om_epoch",
+                   "epoch", "cq_len", "sq_len", "mq_len", "fwd_n")
+
+    def core(self, tile: int) -> dict:
+        out = np.zeros(17, dtype=np.uint32)
+        _check(lib().noc_get_core(self._h, tile, _p32(out)))
+        return dict(zip(self.CORE_FIELDS, (int(v) for v in out)))
