@@ -1,0 +1,318 @@
+"""Benchmark: simulated router-cycles/s on the 208x208 mesh (43,264 tiles).
+
+One step = the paper's largest configuration swept over injection periods
+{40, 20, 10, 5, 2}: for each period, reset the simulation to cycle 0 and run
+50,000 cycles (five persistent cooperative launches in all).  Timed on the
+device with CUDA events on the simulator's stream; the state touched per run
+(1.4 GB of L2 tags plus L1s, queues and links) is larger than the GPU's L2.
+
+`--impl reference` times the oracle (the serial C simulator) on the host cores
+for the same metric on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1508_03235_b300 import inputs as I  # noqa: E402
+
+METRIC = "router-cycles/s at 208x208 mesh (bit-exact simulation)"
+UNIT = "router-cycles/s"
+PERIODS = I.MESH_208_PERIODS
+CYCLES = I.MESH_208_CYCLES
+TILES = 208 * 208
+
+
+def workload_config(extra=None):
+    cfg = {"workload": "mesh208_period_sweep", "mesh": "208x208", "tiles": TILES,
+           "periods": list(PERIODS), "cycles_per_run": CYCLES, "runs_per_step": len(PERIODS),
+           "seed": I.MESH_208_SEED, "l1": "32KB 4-way", "l2": "512KB 16-way per tile",
+           "l2_policy": "interleaved (home = line mod N)",
+           "traffic": "Philox stream: 30% writes, 70/20/10 private 16KB/shared 4MB/remote 1GB",
+           "l2_flush": "inputs larger than L2: 1.4 GB of L2 tags plus L1/queue/link state per run"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path).read().splitlines()[1:]:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- roofline
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+def algorithmic_bytes(stats_delta, router_cycles, p):
+    """State bytes a cycle-stepped simulator must touch (model text, Sec. 5 of
+    the design notes): per router-cycle the four in-link and four out-link
+    slots (8 x 16 B) and the tile's 13-word core record read and written
+    (2 x 52 B); per L1 lookup or fill one L1 set read and written; per L2
+    access (lookup, install, write-through) one L2 set read and written; per
+    injected flit one 16 B queue push and pop."""
+    l1set = 4 * p["l1_ways"]
+    l2set = 4 * p["l2_ways"]
+    d = stats_delta
+    l1_ops = d["l1_hit"] + d["l1_miss"] + d["l2lat_cnt"]          # lookups + fills
+    l2_ops = d["l2_hit"] + d["l2_miss"] + d["wt_hit"] + d["mem_write"] + d["mem_req"]
+    return (router_cycles * (8 * 16 + 2 * 52) + l1_ops * 2 * l1set + l2_ops * 2 * l2set
+            + d["injected"] * 2 * 16)
+
+
+# --------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1508_03235_b300 import noc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    sims = [noc.Sim(I.mesh_208(P), stream=stream) for P in PERIODS]
+    tiling = sims[0].tiling()
+    cycles = args.cycles
+
+    def one_step(record=None):
+        for s in sims:
+            s.reset()
+            if record is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            s.step_async(cycles)
+            if record is not None:
+                e1.record(stream)
+                record.append((e0, e1))
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    for s in sims:
+        s.sync()
+    tiling = sims[0].tiling()
+    launches0 = sum(s.launches for s in sims)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    records = []
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        one_step(records)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    for s in sims:
+        s.sync()
+    ms = t_start.elapsed_time(t_end)
+    gpu_launches = sum(s.launches for s in sims) - launches0
+    if world > 1:
+        tm = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms = float(tm.item())
+    rc_per_rank = args.steps * len(PERIODS) * TILES * cycles
+    value = rc_per_rank * world / (ms / 1e3)
+
+    # roofline of the cycle kernel: algorithmic bytes / its event-timed duration
+    launch_ms = [a.elapsed_time(b) for a, b in records]
+    stats = [s.stats() for s in sims]          # the last step's counters per period
+    alg = sum(algorithmic_bytes(st, TILES * cycles, sims[0].params) for st in stats) / len(sims)
+    avg_launch_s = statistics.mean(launch_ms) / 1e3
+    peak, peak_kind = measured_peaks()
+    achieved = alg / avg_launch_s / 1e9
+
+    # end to end through the public API: reset, run, read the counters back
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for s in sims:
+            s.reset()
+            s.step_async(cycles)
+            s.stats()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = e2e_steps * len(PERIODS) * TILES * cycles * world / e2e_s
+    from paper_1508_03235_b300.noc import CacheCfg, Stats, Traffic
+    import ctypes
+    h2d = len(PERIODS) * (ctypes.sizeof(CacheCfg) + ctypes.sizeof(Traffic))
+    d2h = len(PERIODS) * ctypes.sizeof(Stats)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cycles_per_period=args.cpu_cycles)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (seeded Philox reference streams; the paper's traces are unavailable)",
+            "config": workload_config({"cycles_per_run": cycles, "tiling": list(tiling),
+                                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind, "kernel": "noc::run_kernel",
+                         "avg_launch_ms": statistics.mean(launch_ms),
+                         "alg_bytes_per_launch": alg},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": gpu_launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------- CPU arms
+def cpu_baseline(cycles_per_period=400):
+    """The oracle as it stands, single-threaded, on the first
+    `cycles_per_period` cycles of each period's run."""
+    from oracle import oracle
+    oracle.build()
+    rc = 0
+    t = 0.0
+    for P in PERIODS:
+        o = oracle.OracleSim(I.mesh_208(P))
+        t0 = time.perf_counter()
+        o.step(cycles_per_period)
+        t += time.perf_counter() - t0
+        rc += TILES * cycles_per_period
+        o.close()
+    return {"value": rc / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {cycles_per_period} cycles of each of the {len(PERIODS)} period runs "
+                      f"of the 208x208 workload ({rc} router-cycles, {t:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle
+    oracle.build()
+    cyc = args.ref_cycles
+    for _ in range(args.warmup):
+        o = oracle.OracleSim(I.mesh_208(PERIODS[0]))
+        o.step(max(1, cyc // 4))
+        o.close()
+    times = []
+    for _ in range(args.steps):
+        t = 0.0
+        for P in PERIODS:
+            o = oracle.OracleSim(I.mesh_208(P))
+            t0 = time.perf_counter()
+            o.step(cyc)
+            t += time.perf_counter() - t0
+            o.close()
+        times.append(t)
+    total = sum(times)
+    value = args.steps * len(PERIODS) * TILES * cyc / total
+    sample = (f"each step: first {cyc} cycles of each of the {len(PERIODS)} period runs of the "
+              f"208x208 workload, single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (seeded Philox reference streams)",
+            "config": workload_config({"cycles_per_run": cyc}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cycles", type=int, default=CYCLES, help="cycles per period run")
+    ap.add_argument("--cpu-cycles", type=int, default=400)
+    ap.add_argument("--ref-cycles", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -125,7 +125,8 @@ int noc_step(noc_sim* sim, int64_t n_cycles);
 
 /* Stop issuing references and run until nothing is in flight, queued or
  * outstanding, or max_cycles pass.  *taken = cycles run.  Synchronous.
- * NOC_ERR_TIMEOUT if not quiescent after max_cycles. */
+ * NOC_ERR_TIMEOUT if not quiescent after max_cycles.  References stay stopped
+ * for later noc_step calls until noc_reset. */
 int noc_drain(noc_sim* sim, int64_t max_cycles, int64_t* taken);
 
 /* Wait for enqueued work; return the first device error (NOC_OK if none) and,

@@ -61,6 +61,7 @@ struct noc_sim {
   int gx = 0, gy = 0;          // requested tiling (0 = automatic)
   int run_gx = 0, run_gy = 0;  // tiling in use
   uint32_t cycle = 0;
+  bool draining = false;       // set by noc_drain, cleared by noc_reset
   // hash trace
   bool hash_on = false;
   unsigned long long* d_hash = nullptr;
@@ -165,6 +166,7 @@ int do_reset(noc_sim* s) {
   CU(cudaMemsetAsync(abort_ptr(s), 0, 4, st), "reset abort flag");
   s->cycle = 0;
   s->hash_n = 0;
+  s->draining = false;
   return NOC_OK;
 }
 
@@ -443,7 +445,7 @@ int noc_step(noc_sim* s, int64_t n) {
     CU(cudaMemsetAsync(s->d_hash, 0, (size_t)n * 8, s->stream), "hash trace clear");
     s->hash_n = n;
   }
-  return run_cycles(s, (uint32_t)n, false, nullptr);
+  return run_cycles(s, (uint32_t)n, s->draining, nullptr);
 }
 
 int noc_sync(noc_sim* s, int64_t* err_cycle) {
@@ -461,6 +463,7 @@ int noc_drain(noc_sim* s, int64_t max_cycles, int64_t* taken) {
   if (rc) return rc;
   rc = noc_sync(s, nullptr);
   if (rc) return rc;
+  s->draining = true;
   unsigned int busy0 = 0;
   unsigned int* d_b0 = reinterpret_cast<unsigned int*>(scratch_ptr(s));
   CU(cudaMemsetAsync(d_b0, 0, 4, s->stream), "busy clear");
