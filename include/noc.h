@@ -171,6 +171,29 @@ int noc_get_core(noc_sim* sim, int tile, uint32_t* out17);
  * bounded waits run out and the step ends with NOC_ERR_TIMEOUT. */
 int noc_debug_wait_limit(noc_sim* sim, int64_t ns, int silent_cta);
 
+/* Allocation-free run.  No counterpart in the paper: this entry point serves
+ * callers that must not allocate device memory -- a process whose HBM is
+ * already reserved by another allocator (a framework's caching allocator), or
+ * a host loop that may not allocate, nor take the implicit device
+ * synchronisation of cudaMalloc/cudaFree, once running.  It simulates
+ * n_cycles from cycle 0 (same arguments and results as noc_create + noc_step
+ * + noc_stats) with all simulator state and scratch inside one fixed device
+ * array of NOC_STATIC_SCRATCH_BYTES that the library holds on every GPU it is
+ * loaded on until the process exits; it calls no allocator.
+ *   dev_stats_out: DEVICE memory, one noc_stats_t, written by the run.
+ *   cuda_stream:   stream to run on (NULL = default); the call waits for it.
+ * Returns NOC_ERR_ARG for an invalid configuration, for trace mode, or when
+ * the state would exceed NOC_STATIC_SCRATCH_BYTES; a simulation error code
+ * (e.g. NOC_ERR_QUEUE_OVERFLOW) if the run hit one; NOC_ERR_CUDA otherwise.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call reuses the same array and clears it first; calls that overlap on the
+ * GPU (other streams or threads) race on it and must be serialised. */
+#define NOC_STATIC_SCRATCH_BYTES (16u << 20)
+int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* cache, int l2_policy,
+                   const noc_traffic* traffic, uint64_t seed, int64_t n_cycles,
+                   void* dev_stats_out, void* cuda_stream);
+
 /* Number of this library's kernels launched through this handle. */
 int64_t noc_kernel_launches(const noc_sim* sim);
 

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnoc.so")
-SOURCES = ["noc_kernel.cu", "noc_api.cu"]
+SOURCES = ["noc_kernel.cu", "noc_api.cu", "noc_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

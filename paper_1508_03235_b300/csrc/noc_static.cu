@@ -1,0 +1,201 @@
+// noc_static.cu -- a simulation entry point that allocates no device memory.
+//
+// Who needs it: code that runs where the process's device memory is already
+// owned by someone else -- a framework whose caching allocator has reserved
+// the HBM, so a stray cudaMalloc would fail or fragment it, or a host loop
+// that must never allocate (nor take cudaMalloc/cudaFree's implicit device
+// synchronisation) once it is running.  noc_run_static runs a whole
+// simulation from cycle 0 with every piece of simulator state and scratch
+// (links, tile records, queues, caches, per-CTA cycle flags, error word) in
+// one fixed, file-scope device array, and writes only the caller's output.
+//
+// The array is NOC_STATIC_SCRATCH_BYTES (16 MiB) and every GPU that loads the
+// library holds it until the process exits.  All calls share it and it keeps
+// the previous call's contents, so each call clears what must start at zero;
+// two calls whose work overlaps on the GPU (different streams or host
+// threads) race on it and must be serialised by the caller.
+#include <cstring>
+#include <mutex>
+
+#include "noc.h"
+#include "noc_internal.h"
+
+using namespace noc;
+
+static __device__ __align__(256) unsigned char g_static_scratch[NOC_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_mu;
+unsigned char* g_dev_ptr[256];  // device address of g_static_scratch, per device
+bool g_dev_ready[256];
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// noc_stats_t from the per-counter totals (device order of the model's list)
+__global__ void pack_stats_kernel(const unsigned long long* h, unsigned long long cycle,
+                                  unsigned long long* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int order[] = {S_INJ, S_EJ, -1, S_DEFL, S_LATSUM, S_LATMAX, S_REFS, S_L1H, S_L1M,
+                       S_L2H, S_L2M, S_REQM, S_REQR, S_REPS, S_REPR, S_DIRS, S_MEMREQ, S_MEMW,
+                       S_MEMWB, S_WTS, S_WTH, S_TRAP, S_REDIR, S_MIGR, S_L2LSUM, S_L2LCNT,
+                       S_CQST, S_MMST, S_MIGS};
+  out[0] = cycle;
+  for (int k = 0; k < 29; ++k) out[1 + k] = order[k] < 0 ? h[S_INJ] - h[S_EJ] : h[order[k]];
+}
+
+}  // namespace
+
+extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy,
+                              const noc_traffic* tr, uint64_t seed, int64_t n_cycles,
+                              void* dev_stats_out, void* cuda_stream) {
+  if (!c || !tr || !dev_stats_out || n_cycles < 0 || n_cycles >= (1ll << 31))
+    return NOC_ERR_ARG;
+  if (mesh_w < 1 || mesh_h < 1 || (long)mesh_w * mesh_h > 65535 || l2_policy < 0 || l2_policy > 2)
+    return NOC_ERR_ARG;
+  auto ways_ok = [](int w) { return w == 1 || w == 2 || w == 4 || w == 8 || w == 16; };
+  if (c->l1_sets < 1 || !ways_ok(c->l1_ways) || c->l2_sets < 1 || !ways_ok(c->l2_ways) ||
+      c->l1_miss_cycles < 0 || c->mem_latency < 1 || c->core_q < 1 || c->svc_q < 1 ||
+      c->mem_q < 1 || c->core_q > 65535 || c->svc_q > 65535 || c->mem_q > 65535)
+    return NOC_ERR_ARG;
+  if (l2_policy == NOC_L2_LSPD_MIGRATE &&
+      (c->mig_window < 1 || c->mig_window > HIST_STRIDE - 2 || c->mig_threshold < 1 ||
+       c->fwd_entries < 1))
+    return NOC_ERR_ARG;
+  // trace mode needs per-core reference lists, which live outside the array
+  if (tr->mode < 0 || tr->mode > 1 || tr->period < 0 || tr->write_q16 > 65536 ||
+      tr->priv_q16 + (uint64_t)tr->shared_q16 > 65536 || tr->hot_q16 > 65536 ||
+      tr->hot_side < 0 || tr->hot_side > mesh_w || tr->hot_side > mesh_h)
+    return NOC_ERR_ARG;
+  const size_t N = (size_t)mesh_w * mesh_h;
+  const uint64_t total = (uint64_t)tr->remote_lines + tr->shared_lines + (uint64_t)tr->priv_lines * N;
+  if (total >= (1ull << 26)) return NOC_ERR_ARG;
+
+  Params P;
+  memset(&P, 0, sizeof P);
+  P.W = mesh_w;
+  P.H = mesh_h;
+  P.N = (int)N;
+  P.policy = l2_policy;
+  P.mode = tr->mode;
+  P.period = tr->period;
+  P.l1_sets = c->l1_sets;
+  P.l1_ways = c->l1_ways;
+  P.l2_sets = c->l2_sets;
+  P.l2_ways = c->l2_ways;
+  P.l1_miss = c->l1_miss_cycles;
+  P.mem_lat = c->mem_latency;
+  P.mig_window = c->mig_window;
+  P.mig_threshold = c->mig_threshold;
+  P.core_q = c->core_q;
+  P.svc_q = c->svc_q;
+  P.mem_q = c->mem_q;
+  P.fwd_cap = c->fwd_entries > 0 ? c->fwd_entries : 1;
+  P.write_q16 = tr->write_q16;
+  P.priv_q16 = tr->priv_q16;
+  P.shared_q16 = tr->shared_q16;
+  P.hot_q16 = tr->hot_q16;
+  P.hot_side = tr->hot_side;
+  P.hot_x0 = mesh_w / 2 - tr->hot_side / 2;
+  P.hot_y0 = mesh_h / 2 - tr->hot_side / 2;
+  P.priv_lines = tr->priv_lines;
+  P.shared_lines = tr->shared_lines;
+  P.remote_lines = tr->remote_lines;
+  P.total_lines = (uint32_t)total;
+  P.seed = seed;
+  P.stream = tr->stream;
+
+  // carve the state out of the static array
+  const size_t w1 = N * P.l1_sets * P.l1_ways, w2 = N * P.l2_sets * P.l2_ways;
+  const bool lspd = l2_policy != NOC_L2_INTERLEAVED, mig = l2_policy == NOC_L2_LSPD_MIGRATE;
+  const size_t n_flags = 1024;
+  size_t off[18], cur = 0;
+  const size_t sz[18] = {2 * 4 * N * 16, NCORE * N * 4, N * P.core_q * 16, N * P.svc_q * 16,
+                         N * P.mem_q * 16, w1 * 4, w1 * 2, w2 * 4, lspd ? w2 * 2 : 0,
+                         mig ? w2 * HIST_STRIDE * 2 : 0, lspd ? (size_t)total * 4 : 0,
+                         mig ? N * P.fwd_cap * 8 : 0, (size_t)NSTAT * N * 8,
+                         2 * HIST_BINS * 8, n_flags * 4, 8, 4, 64 * 8};
+  for (int k = 0; k < 18; ++k) {
+    off[k] = a256(cur);
+    cur = off[k] + sz[k];
+  }
+  if (cur > NOC_STATIC_SCRATCH_BYTES) return NOC_ERR_ARG;
+
+  std::lock_guard<std::mutex> lock(g_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NOC_ERR_CUDA;
+  if (!g_dev_ready[dev]) {
+    // first call on this device: the array's device address, with it current
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return NOC_ERR_CUDA;
+    g_dev_ptr[dev] = static_cast<unsigned char*>(p);
+    g_dev_ready[dev] = true;
+  }
+  unsigned char* b = g_dev_ptr[dev];
+  P.glink = reinterpret_cast<uint4*>(b + off[0]);
+  P.core = reinterpret_cast<uint32_t*>(b + off[1]);
+  P.cq = reinterpret_cast<uint4*>(b + off[2]);
+  P.sq = reinterpret_cast<uint4*>(b + off[3]);
+  P.mq = reinterpret_cast<uint4*>(b + off[4]);
+  P.l1 = reinterpret_cast<uint32_t*>(b + off[5]);
+  P.l1own = reinterpret_cast<uint16_t*>(b + off[6]);
+  P.l2 = reinterpret_cast<uint32_t*>(b + off[7]);
+  P.l2ep = lspd ? reinterpret_cast<uint16_t*>(b + off[8]) : nullptr;
+  P.l2hist = mig ? reinterpret_cast<uint16_t*>(b + off[9]) : nullptr;
+  P.dir = lspd ? reinterpret_cast<uint32_t*>(b + off[10]) : nullptr;
+  P.fwd = mig ? reinterpret_cast<uint32_t*>(b + off[11]) : nullptr;
+  P.stats = reinterpret_cast<unsigned long long*>(b + off[12]);
+  P.hist = reinterpret_cast<unsigned long long*>(b + off[13]);
+  P.flags = reinterpret_cast<unsigned int*>(b + off[14]);
+  P.err = reinterpret_cast<unsigned long long*>(b + off[15]);
+  unsigned int* abort_flag = reinterpret_cast<unsigned int*>(b + off[16]);
+  unsigned long long* totals = reinterpret_cast<unsigned long long*>(b + off[17]);
+
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // everything the simulation reads before writing starts from its reset value
+  for (int k = 0; k < 18; ++k) {
+    if (!sz[k] || k == 2 || k == 3 || k == 4) continue;  // queue slots are written before read
+    int v = (k == 10 || k == 15) ? 0xFF : 0;              // directory NONE, no error
+    if (cudaMemsetAsync(b + off[k], v, sz[k], st) != cudaSuccess) return NOC_ERR_CUDA;
+  }
+
+  // CTA rectangles: the fewest that hold at most 256 tiles each and fit co-resident
+  int gx = 0, gy = 0;
+  for (int side = 16; side >= 1 && !gx; side /= 2) {
+    int tx = (mesh_w + side - 1) / side, ty = (mesh_h + side - 1) / side;
+    int threads = block_threads(mesh_w, mesh_h, tx, ty), cap = 0;
+    if (threads > 384 || (size_t)tx * ty > n_flags) continue;
+    if (max_coresident_ctas(threads, &cap) != cudaSuccess) return NOC_ERR_CUDA;
+    if (tx * ty <= cap) {
+      gx = tx;
+      gy = ty;
+    }
+  }
+  if (!gx) return NOC_ERR_ARG;
+
+  uint32_t done = 0;
+  while (done < (uint32_t)n_cycles) {
+    uint32_t left = (uint32_t)n_cycles - done, n = left < (1u << 20) ? left : (1u << 20);
+    RunArgs A;
+    A.t0 = done;
+    A.n = n;
+    A.draining = 0;
+    A.gx = gx;
+    A.gy = gy;
+    A.hash_trace = nullptr;
+    A.busy = nullptr;
+    A.abort_flag = abort_flag;
+    A.wait_ns = 2000000000ll;
+    A.silent_cta = -1;
+    if (launch_run(P, A, st) != cudaSuccess) return NOC_ERR_CUDA;
+    done += n;
+  }
+  if (launch_reduce_stats(P, -1, totals, st) != cudaSuccess) return NOC_ERR_CUDA;
+  pack_stats_kernel<<<1, 32, 0, st>>>(totals, (unsigned long long)n_cycles,
+                                      static_cast<unsigned long long*>(dev_stats_out));
+  if (cudaGetLastError() != cudaSuccess) return NOC_ERR_CUDA;
+  unsigned long long e = ~0ull;
+  if (cudaMemcpyAsync(&e, P.err, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return NOC_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return NOC_ERR_CUDA;
+  return e == ~0ull ? NOC_OK : (int)(e & 0xFF);
+}
