@@ -137,8 +137,11 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1508_03235_b300 import tune
     stream = torch.cuda.current_stream()
-    sims = [noc.Sim(I.mesh_208(P), stream=stream) for P in PERIODS]
+    # tiling: the autotuner's cached choice for this configuration, if any
+    sims = [noc.Sim(I.mesh_208(P), stream=stream, tiling=tune.cached_tiling(I.mesh_208(P)))
+            for P in PERIODS]
     tiling = sims[0].tiling()
     cycles = args.cycles
 

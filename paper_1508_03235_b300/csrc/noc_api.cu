@@ -387,6 +387,7 @@ int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, co
   P.shared_lines = tr->shared_lines;
   P.remote_lines = tr->remote_lines;
   P.total_lines = (uint32_t)total;
+  set_divisors(P);
   P.seed = seed;
   P.stream = tr->stream;
   s->traces.resize(N);

@@ -84,6 +84,9 @@ __device__ void load_tile(const Params& P, uint32_t r, Tile& T) {
   T.sq_front = T.sq_len ? P.sq[(size_t)r * P.svc_q + T.sq_head] : z;
   T.mq_front = T.mq_len ? P.mq[(size_t)r * P.mem_q + T.mq_head] : z;
   T.ej = z;
+  T.pf_ok = 0;
+  T.pf_line = 0;
+  T.pf_write = 0;
   T.inj = P.stats[S_INJ * N + r];
   T.ejc = P.stats[S_EJ * N + r];
   T.defl = P.stats[S_DEFL * N + r];
@@ -182,14 +185,10 @@ __global__ void __launch_bounds__(MAX_THREADS, 1) run_kernel(const Params P, con
   // links that leave the rectangle also go to the global buffer
   const uint32_t boundary = exists & ((ly == 0 ? 1u << P_N : 0u) | (ly == bh - 1 ? 1u << P_S : 0u) |
                                       (lx == bw - 1 ? 1u << P_E : 0u) | (lx == 0 ? 1u << P_W : 0u));
-  // neighbouring CTAs this CTA waits for: N, S, E, W
-  int wait_cta = -1;
-  if (i < 4) {
-    if (i == 0 && cy > 0) wait_cta = b - A.gx;
-    if (i == 1 && cy + 1 < A.gy) wait_cta = b + A.gx;
-    if (i == 2 && cx + 1 < A.gx) wait_cta = b + 1;
-    if (i == 3 && cx > 0) wait_cta = b - 1;
-  }
+  // neighbouring CTA on each side (N, S, E, W), or -1
+  const int nbr[4] = {cy > 0 ? b - A.gx : -1, cy + 1 < A.gy ? b + A.gx : -1,
+                      cx + 1 < A.gx ? b + 1 : -1, cx > 0 ? b - 1 : -1};
+  const bool alone = A.gx * A.gy == 1;
 
   for (int k = i; k < 2 * HIST_BINS; k += nt) sh_hist[k] = 0;
   if (i == 0) sh_abort = 0;
@@ -218,8 +217,8 @@ __global__ void __launch_bounds__(MAX_THREADS, 1) run_kernel(const Params P, con
     if (active) {
       uint4 in[4];
       const uint4 z = make_uint4(0, 0, 0, 0);
-      const uint4* gl = P.glink + (size_t)pin * 4 * N;
       const uint4* sp = sl + pin * 4 * nt;
+      const uint4* gl = P.glink + (size_t)pin * 4 * N;
       in[P_N] = !(exists & (1u << P_N)) ? z
                 : (ly > 0 ? sp[P_S * nt + i - bw] : __ldcg(&gl[P_S * N + r - P.W]));
       in[P_S] = !(exists & (1u << P_S)) ? z
@@ -238,10 +237,9 @@ __global__ void __launch_bounds__(MAX_THREADS, 1) run_kernel(const Params P, con
       }
     }
     __syncthreads();
-    if (i == 0 && b != A.silent_cta) {
-      __threadfence();
-      st_release_u32(&P.flags[b], t + 1);
-    }
+    // publish: the release store orders this CTA's link stores (made visible
+    // to thread 0 by the barrier) before the flag
+    if (i == 0 && !alone && b != A.silent_cta) st_release_u32(&P.flags[b], t + 1);
     // ---- Phase 3 of this cycle
     if (active) phase3(P, T, t, sh_hist);
     if (HASH) {
@@ -255,10 +253,11 @@ __global__ void __launch_bounds__(MAX_THREADS, 1) run_kernel(const Params P, con
       if (i == 0 && q) atomicAdd(&A.busy[t - t0], (unsigned)q);
     }
     if (t + 1 == tend) break;
-    // ---- Phase 1 of the next cycle, then wait for the neighbours' outputs
+    // ---- Phase 1 of the next cycle, then the neighbours' outputs of this one
     if (active) phase1(P, T, t + 1, A.draining != 0, sh_hist);
-    if (wait_cta >= 0) {
-      int w = wait_ge(&P.flags[wait_cta], t + 1, A.abort_flag, A.wait_ns);
+    // lanes 0..3 each wait for one neighbouring CTA (N, S, E, W)
+    if (i < 4 && nbr[i] >= 0) {
+      int w = wait_ge(&P.flags[nbr[i]], t + 1, A.abort_flag, A.wait_ns);
       if (w <= 0) {
         if (w == 0) {
           atomicExch(A.abort_flag, 1u);

@@ -62,6 +62,9 @@ struct Params {
   uint32_t priv_lines, shared_lines, remote_lines, total_lines;
   unsigned long long seed;
   uint32_t stream;
+  // multiply-high reciprocals: n / d == umul64hi(n, m) for d >= 2 (m = 2^64 / d
+  // rounded up), exact for every n < 2^32; see set_divisors()
+  unsigned long long mW, mN, mL1, mL2;
   // device arrays
   uint4* glink;          // [2][4][N] out-links by parity, port, tile
   uint32_t* core;        // [NCORE][N]
@@ -82,6 +85,19 @@ struct Params {
   unsigned int* flags;        // [CTAs] last completed cycle + 1
   unsigned long long* err;    // min over (cycle << 8 | code); ~0 = none
 };
+
+// n / d with the reciprocal m of d (m = 0 encodes d == 1)
+__device__ __forceinline__ uint32_t qdiv(uint32_t n, unsigned long long m) {
+  return m ? (uint32_t)__umul64hi((unsigned long long)n, m) : n;
+}
+// host: reciprocals of the divisors used on the hot path
+inline unsigned long long recip64(uint32_t d) { return d <= 1 ? 0ull : (~0ull) / d + 1; }
+inline void set_divisors(Params& P) {
+  P.mW = recip64((uint32_t)P.W);
+  P.mN = recip64((uint32_t)P.N);
+  P.mL1 = recip64((uint32_t)P.l1_sets);
+  P.mL2 = recip64((uint32_t)P.l2_sets);
+}
 
 // ---------------------------------------------------------------- flits
 // uint4 flit: x = inject cycle, y = src | dst << 16, z = line | type << 26,
@@ -165,6 +181,7 @@ struct Tile {
   uint32_t cq_head, cq_len, sq_head, sq_len, mq_head, mq_len, fwd_next, fwd_n;
   uint4 cq_front, sq_front, mq_front;  // cached queue heads (valid when len > 0)
   uint4 ej;                            // flit ejected this cycle (or empty)
+  uint32_t pf_line, pf_write, pf_ok;   // reference next_ref, kept for a retry
   unsigned long long inj, ejc, defl, latsum, latmax, l2lsum;
   uint32_t sm[NSMALL];                 // small per-launch counter deltas
 };
@@ -175,14 +192,14 @@ __device__ __forceinline__ void set_error(const Params& P, uint32_t t, int code)
 }
 
 __device__ __forceinline__ uint32_t home_of(const Params& P, uint32_t line) {
-  return line % (uint32_t)P.N;
+  return line - qdiv(line, P.mN) * (uint32_t)P.N;
 }
 __device__ __forceinline__ uint32_t l1_set(const Params& P, uint32_t line) {
-  return line % (uint32_t)P.l1_sets;
+  return line - qdiv(line, P.mL1) * (uint32_t)P.l1_sets;
 }
 __device__ __forceinline__ uint32_t l2_set(const Params& P, uint32_t line) {
-  if (P.policy == POL_INTERLEAVED) return (line / (uint32_t)P.N) % (uint32_t)P.l2_sets;
-  return line % (uint32_t)P.l2_sets;
+  uint32_t v = P.policy == POL_INTERLEAVED ? qdiv(line, P.mN) : line;
+  return v - qdiv(v, P.mL2) * (uint32_t)P.l2_sets;
 }
 
 // ---------------------------------------------------------------- queues
@@ -613,7 +630,23 @@ __device__ __forceinline__ void mq_pop(const Params& P, Tile& T) {
   if (T.mq_len > 0) T.mq_front = P.mq[(size_t)T.r * P.mem_q + T.mq_head];
 }
 
-static __device__ void phase1(const Params& P, Tile& T, uint32_t t, bool draining, uint32_t* sh_hist) {
+// line and write flag of reference k of core `core`; false past a trace's end
+static __device__ bool ref_of(const Params& P, uint32_t core, uint32_t k, uint32_t& line,
+                              uint32_t& write) {
+  if (P.mode == MODE_TRACE) {
+    uint32_t off = P.trace_off[core], n = P.trace_off[core + 1] - off;
+    if (k >= n) return false;
+    uint32_t ref = P.trace[off + k];
+    line = ref & 0x7FFFFFFFu;
+    write = ref >> 31;
+    return true;
+  }
+  line = draw_line(P, core, k, write);
+  return true;
+}
+
+// Phase 1; returns true if the core took an action this cycle
+static __device__ bool phase1(const Params& P, Tile& T, uint32_t t, bool draining, uint32_t* sh_hist) {
   // (i) memory returns at an interleaved home: install, then reply
   while (T.mq_len > 0 && T.mq_front.x <= t) {
     uint32_t line = T.mq_front.y, req = T.mq_front.z;
@@ -636,21 +669,23 @@ static __device__ void phase1(const Params& P, Tile& T, uint32_t t, bool drainin
   }
   // (iii) at most one core action
   if (T.fsm == FSM_L2WAIT) {
-    if (t >= T.fsm_timer) l2_step(P, T, t, sh_hist);
-    return;
+    if (t < T.fsm_timer) return false;
+    l2_step(P, T, t, sh_hist);
+    return true;
   }
   if (T.fsm == FSM_STALL) {
-    if (T.om_kind == OM_NONE) l1_step(P, T, t, T.fsm_line, T.fsm_write);
-    return;
+    if (T.om_kind != OM_NONE) return false;
+    l1_step(P, T, t, T.fsm_line, T.fsm_write);
+    return true;
   }
-  if (draining || P.period <= 0) return;
-  if ((unsigned long long)t < (unsigned long long)T.next_ref * (unsigned long long)P.period) return;
+  if (draining || P.period <= 0) return false;
+  if ((unsigned long long)t < (unsigned long long)T.next_ref * (unsigned long long)P.period) return false;
 
   if (P.mode == MODE_NETWORK) {
-    if (P.N < 2) return;
+    if (P.N < 2) return false;
     if (cq_full(P, T)) {
       SMALL(S_CQST)++;
-      return;
+      return true;
     }
     unsigned long long w[4];
     philox4x64_10(T.next_ref, T.r, P.stream, 0, P.seed, 0x4E4F43ull, w);
@@ -659,22 +694,24 @@ static __device__ void phase1(const Params& P, Tile& T, uint32_t t, bool drainin
     send_core(P, T, mkflit(T_PROBE, T.r, dst, 0, 0, 0));
     T.next_ref++;
     SMALL(S_REFS)++;
-    return;
+    return true;
   }
   uint32_t line, write;
-  if (P.mode == MODE_TRACE) {
-    uint32_t off = P.trace_off[T.r], n = P.trace_off[T.r + 1] - off;
-    if (T.next_ref >= n) return;
-    uint32_t ref = P.trace[off + T.next_ref];
-    line = ref & 0x7FFFFFFFu;
-    write = ref >> 31;
+  if (T.pf_ok) {
+    line = T.pf_line;
+    write = T.pf_write;
   } else {
-    line = draw_line(P, T.r, T.next_ref, write);
+    if (!ref_of(P, T.r, T.next_ref, line, write)) return false;
+    T.pf_line = line;
+    T.pf_write = write;
+    T.pf_ok = 1;
   }
   if (l1_step(P, T, t, line, write)) {
     T.next_ref++;
     SMALL(S_REFS)++;
+    T.pf_ok = 0;
   }
+  return true;
 }
 
 // ---------------------------------------------------------------- Phase 2
@@ -759,8 +796,9 @@ __device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint
     bool valid = i < 4 ? (k[i] != NOKEY) : has_inj;
     if (!valid) continue;
     uint32_t dst = fdst(f);
-    int dx = (int)(dst % (uint32_t)P.W) - (int)T.x;
-    int dy = (int)(dst / (uint32_t)P.W) - (int)T.y;
+    const uint32_t dsty = qdiv(dst, P.mW);
+    int dx = (int)(dst - dsty * (uint32_t)P.W) - (int)T.x;
+    int dy = (int)dsty - (int)T.y;
     uint32_t xb = dx > 0 ? (1u << P_E) : (dx < 0 ? (1u << P_W) : 0u);
     uint32_t yb = dy > 0 ? (1u << P_S) : (dy < 0 ? (1u << P_N) : 0u);
     uint32_t pick;

@@ -102,6 +102,7 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
   P.shared_lines = tr->shared_lines;
   P.remote_lines = tr->remote_lines;
   P.total_lines = (uint32_t)total;
+  set_divisors(P);
   P.seed = seed;
   P.stream = tr->stream;
 

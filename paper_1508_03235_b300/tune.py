@@ -1,0 +1,105 @@
+"""Autotuner for the CTA tiling of the cycle kernel.
+
+The mesh is cut into gx x gy rectangles, one CTA each (one thread per tile).
+Simulation results never depend on the tiling (the GPU tests check every
+tiling against the oracle); only the time per simulated cycle does.  The
+tuner times a handful of candidate tilings on a short run of the actual
+configuration and keeps the fastest in a JSON cache next to this file.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE = os.path.join(HERE, "tuning_cache.json")
+MAX_THREADS = 384
+
+
+def key(params: dict) -> str:
+    p = params
+    return (f"{p['mesh_w']}x{p['mesh_h']}/pol{p['policy']}/mode{p['mode']}"
+            f"/l1_{p['l1_sets']}x{p['l1_ways']}/l2_{p['l2_sets']}x{p['l2_ways']}")
+
+
+def candidates(W: int, H: int, targets=(384, 320, 256, 192, 160, 128, 96, 64, 32)):
+    """For each rectangle-size target, the grid with the fewest CTAs whose
+    rectangles hold at most that many tiles, preferring aspect ratios <= 2.5."""
+    out = []
+    for target in targets:
+        best = None
+        for gy in range(1, H + 1):
+            bh = -(-H // gy)
+            for gx in range(1, W + 1):
+                bw = -(-W // gx)
+                if bw * bh > min(target, MAX_THREADS):
+                    continue
+                skew = abs(math.log(bw / bh))
+                k = (skew > math.log(2.5), gx * gy, skew)
+                if best is None or k < best[0]:
+                    best = (k, (gx, gy))
+                break                      # larger gx only adds CTAs for this gy
+        if best and best[1] not in out:
+            out.append(best[1])
+    return out
+
+
+def load_cache() -> dict:
+    if os.path.exists(CACHE):
+        with open(CACHE) as f:
+            return json.load(f)
+    return {}
+
+
+def cached_tiling(params: dict):
+    t = load_cache().get(key(params))
+    return tuple(t["tiling"]) if t else None
+
+
+def tune(params: dict, cycles: int = 400, warm: int = 100, max_cands: int = 10,
+         save: bool = True, verbose: bool = False):
+    """Time candidate tilings; return (best tiling, {tiling: us per cycle})."""
+    import torch
+
+    from . import noc
+
+    sim = noc.Sim(params)
+    timings = {}
+    for gx, gy in candidates(params["mesh_w"], params["mesh_h"])[:max_cands]:
+        try:
+            sim.set_tiling(gx, gy)
+            sim.reset()
+            sim.step(warm)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.step(cycles)
+            dt = time.perf_counter() - t0
+        except noc.NocError:
+            continue                       # not co-resident on this GPU
+        timings[(gx, gy)] = 1e6 * dt / cycles
+        if verbose:
+            print(f"  tiling {gx}x{gy}: {timings[(gx, gy)]:.2f} us/cycle", flush=True)
+    sim.close()
+    best = min(timings, key=timings.get)
+    if save:
+        cache = load_cache()
+        cache[key(params)] = {"tiling": list(best), "us_per_cycle": timings[best],
+                              "timings": {f"{a}x{b}": v for (a, b), v in timings.items()},
+                              "device": torch.cuda.get_device_name()}
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+    return best, timings
+
+
+if __name__ == "__main__":
+    import sys
+    sys.path.insert(0, os.path.dirname(HERE))
+    from paper_1508_03235_b300 import inputs as I
+    from paper_1508_03235_b300.tune import tune as _tune
+    for name, p in (("mesh208", I.mesh_208(10)), ("mesh64", I.mesh_64(1)),
+                    ("mesh8", I.MESH_8["params"])):
+        print(name, flush=True)
+        b, _ = _tune(p, verbose=True)
+        print(f"  best {b}", flush=True)
