@@ -171,6 +171,49 @@ int noc_get_core(noc_sim* sim, int tile, uint32_t* out17);
  * bounded waits run out and the step ends with NOC_ERR_TIMEOUT. */
 int noc_debug_wait_limit(noc_sim* sim, int64_t ns, int silent_cta);
 
+/* ------------------------------------------------------------------------
+ * Batch engine: many independent simulations of uneven size, seed and L2
+ * policy in one persistent cooperative launch per memory wave.  CTAs pop
+ * (instance, rectangle) items from a device work queue; each instance's
+ * rectangles run together with the neighbour-flag barrier of noc_step.  Each
+ * instance's results are bit-identical to running it alone through
+ * noc_create / noc_step (trace mode is not supported in a batch).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t mesh_w, mesh_h, l2_policy, reserved;
+  noc_cache_cfg cache;
+  noc_traffic traffic;
+  uint64_t seed;
+  int64_t cycles;             /* cycles to simulate from cycle 0, < 2^20 */
+} noc_instance_desc;
+
+typedef struct noc_batch noc_batch;
+
+int noc_batch_create(int n, const noc_instance_desc* descs, noc_batch** out);
+void noc_batch_destroy(noc_batch* batch);
+/* Device bytes of the largest instance (the least memory a run can use) and
+ * of all instances at once (what one wave needs). */
+size_t noc_batch_min_bytes(const noc_batch* batch);
+size_t noc_batch_total_bytes(const noc_batch* batch);
+/* Caller-owned device pool the instances' state is placed in, wave by wave
+ * (never freed by the library); without it the run takes a pool with
+ * cudaMalloc sized to the smaller of the total and 80% of free memory. */
+int noc_batch_bind_memory(noc_batch* batch, void* dev_ptr, size_t bytes);
+int noc_batch_set_stream(noc_batch* batch, void* cuda_stream);
+/* CTA rectangle side in tiles (1..19; default 8): a tuning knob only. */
+int noc_batch_set_rect(noc_batch* batch, int side);
+/* Collect each instance's full state hash after its wave (default on). */
+int noc_batch_set_collect_hash(noc_batch* batch, int enable);
+/* Run every instance to its cycle count.  Synchronous.  Returns the first
+ * instance error (see noc_batch_error for each). */
+int noc_batch_run(noc_batch* batch);
+int noc_batch_waves(const noc_batch* batch);
+int noc_batch_error(const noc_batch* batch, int i, int64_t* err_cycle);
+int noc_batch_stats(const noc_batch* batch, int i, noc_stats_t* out);
+int noc_batch_state_hash(const noc_batch* batch, int i, uint64_t* out);
+int noc_batch_latency_hist(const noc_batch* batch, int i, int which, uint64_t* bins, int nbins);
+int64_t noc_batch_kernel_launches(const noc_batch* batch);
+
 /* Allocation-free run.  No counterpart in the paper: this entry point serves
  * callers that must not allocate device memory -- a process whose HBM is
  * already reserved by another allocator (a framework's caching allocator), or

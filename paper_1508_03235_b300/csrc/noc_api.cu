@@ -6,6 +6,7 @@
 // first use.  All device work is enqueued on the handle's stream.
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -774,5 +775,297 @@ int noc_debug_wait_limit(noc_sim* s, int64_t ns, int silent_cta) {
 }
 
 int64_t noc_kernel_launches(const noc_sim* s) { return s ? s->launches : -1; }
+
+}  // extern "C"
+
+// ============================================================== batch engine
+struct noc_batch {
+  std::vector<noc_sim*> sims;
+  std::vector<int64_t> cycles;
+  unsigned char* pool = nullptr;
+  size_t pool_bytes = 0;
+  bool pool_owned = false;
+  cudaStream_t stream = nullptr;
+  int rect = 8;
+  bool collect_hash = true;
+  int waves = 0;
+  int64_t launches = 0;
+  bool done = false;
+  std::vector<noc_stats_t> stats;
+  std::vector<uint64_t> hash;
+  std::vector<std::vector<uint64_t>> hist;
+  std::vector<int> err;
+  std::vector<int64_t> err_cycle;
+  // device tables
+  void* d_tab = nullptr;
+  size_t tab_bytes = 0;
+};
+
+extern "C" {
+
+int noc_batch_create(int n, const noc_instance_desc* d, noc_batch** out) {
+  if (n < 1 || !d || !out) return fail(NOC_ERR_ARG, "bad argument");
+  *out = nullptr;
+  noc_batch* b = new (std::nothrow) noc_batch();
+  if (!b) return fail(NOC_ERR_OOM, "host allocation");
+  for (int i = 0; i < n; ++i) {
+    if (d[i].traffic.mode == NOC_MODE_TRACE || d[i].cycles < 0 || d[i].cycles >= (int64_t)kMaxChunk) {
+      noc_batch_destroy(b);
+      return fail(NOC_ERR_ARG, "instance %d: trace mode or cycles outside [0, 2^20)", i);
+    }
+    noc_sim* s = nullptr;
+    int rc = noc_create(d[i].mesh_w, d[i].mesh_h, &d[i].cache, d[i].l2_policy, &d[i].traffic,
+                        d[i].seed, &s);
+    if (rc) {
+      noc_batch_destroy(b);
+      return rc;
+    }
+    b->sims.push_back(s);
+    b->cycles.push_back(d[i].cycles);
+  }
+  b->stats.resize(n);
+  b->hash.assign(n, 0);
+  b->hist.assign(n, std::vector<uint64_t>(2 * HIST_BINS, 0));
+  b->err.assign(n, 0);
+  b->err_cycle.assign(n, -1);
+  *out = b;
+  return NOC_OK;
+}
+
+void noc_batch_destroy(noc_batch* b) {
+  if (!b) return;
+  for (noc_sim* s : b->sims) {
+    s->base = nullptr;  // pool memory is released below, not per instance
+    noc_destroy(s);
+  }
+  if (b->pool && b->pool_owned) cudaFree(b->pool);
+  if (b->d_tab) cudaFree(b->d_tab);
+  delete b;
+}
+
+size_t noc_batch_min_bytes(const noc_batch* b) {
+  size_t m = 0;
+  if (b)
+    for (const noc_sim* s : b->sims) m = std::max(m, s->bytes);
+  return m;
+}
+
+size_t noc_batch_total_bytes(const noc_batch* b) {
+  size_t t = 0;
+  if (b)
+    for (const noc_sim* s : b->sims) t += s->bytes;
+  return t;
+}
+
+int noc_batch_bind_memory(noc_batch* b, void* p, size_t bytes) {
+  if (!b || !p) return fail(NOC_ERR_ARG, "null argument");
+  if (reinterpret_cast<uintptr_t>(p) & 255) return fail(NOC_ERR_ARG, "pool must be 256-byte aligned");
+  if (b->pool && b->pool_owned) cudaFree(b->pool);
+  b->pool = static_cast<unsigned char*>(p);
+  b->pool_bytes = bytes;
+  b->pool_owned = false;
+  return NOC_OK;
+}
+
+int noc_batch_set_stream(noc_batch* b, void* stream) {
+  if (!b) return fail(NOC_ERR_ARG, "null handle");
+  b->stream = static_cast<cudaStream_t>(stream);
+  for (noc_sim* s : b->sims) s->stream = b->stream;
+  return NOC_OK;
+}
+
+int noc_batch_set_rect(noc_batch* b, int side) {
+  if (!b || side < 1 || side * side > 384) return fail(NOC_ERR_ARG, "rectangle side 1..19");
+  b->rect = side;
+  return NOC_OK;
+}
+
+int noc_batch_set_collect_hash(noc_batch* b, int enable) {
+  if (!b) return fail(NOC_ERR_ARG, "null handle");
+  b->collect_hash = enable != 0;
+  return NOC_OK;
+}
+
+int noc_batch_run(noc_batch* b) {
+  if (!b) return fail(NOC_ERR_ARG, "null handle");
+  const int n = (int)b->sims.size();
+  if (!b->pool) {
+    size_t fr = 0, tot = 0;
+    CU(cudaMemGetInfo(&fr, &tot), "memory info");
+    size_t want = std::min(noc_batch_total_bytes(b), (size_t)(fr * 0.8));
+    want = std::max(want, noc_batch_min_bytes(b));
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) return fail(NOC_ERR_OOM, "batch pool of %zu bytes: %s", want, cudaGetErrorString(e));
+    b->pool = static_cast<unsigned char*>(p);
+    b->pool_bytes = want;
+    b->pool_owned = true;
+  }
+  if (noc_batch_min_bytes(b) > b->pool_bytes)
+    return fail(NOC_ERR_OOM, "pool of %zu bytes is below the largest instance (%zu)", b->pool_bytes,
+                noc_batch_min_bytes(b));
+  const int side = b->rect;
+  const int threads = ((side * side + 31) / 32) * 32;
+  int cap = 0;
+  CU(max_coresident_batch(threads, &cap), "occupancy");
+  // largest first, so the tail of each wave holds the small instances
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    return (double)b->sims[a]->P.N * b->cycles[a] > (double)b->sims[c]->P.N * b->cycles[c];
+  });
+  for (int i : order) {
+    noc_sim* s = b->sims[i];
+    int gx = (s->P.W + side - 1) / side, gy = (s->P.H + side - 1) / side;
+    if (gx * gy > cap || gx * gy > (int)s->n_flags)
+      return fail(NOC_ERR_ARG, "instance %d needs %d CTAs, %d fit co-resident", i, gx * gy, cap);
+    s->run_gx = gx;
+    s->run_gy = gy;
+  }
+  b->waves = 0;
+  int first_err = NOC_OK;
+  size_t pos = 0;
+  while (pos < order.size()) {
+    // admit instances in order while their state fits the pool
+    std::vector<int> wave;
+    size_t used = 0;
+    while (pos < order.size()) {
+      noc_sim* s = b->sims[order[pos]];
+      size_t need = align256(s->bytes);
+      if (used + need > b->pool_bytes) break;
+      s->base = b->pool + used;
+      s->owned = false;
+      s->ready = false;
+      s->stream = b->stream;
+      used += need;
+      wave.push_back(order[pos++]);
+    }
+    b->waves++;
+    // reset every instance of the wave and build the work queue
+    std::vector<Params> hp;
+    std::vector<RunArgs> ha;
+    std::vector<int> item_inst, item_rect, need;
+    for (int k = 0; k < (int)wave.size(); ++k) {
+      noc_sim* s = b->sims[wave[k]];
+      int rc = ensure_memory(s);
+      if (rc) return rc;
+      RunArgs A;
+      memset(&A, 0, sizeof A);
+      A.t0 = 0;
+      A.n = (uint32_t)b->cycles[wave[k]];
+      A.gx = s->run_gx;
+      A.gy = s->run_gy;
+      A.abort_flag = abort_ptr(s);
+      A.wait_ns = s->wait_ns;
+      A.silent_cta = -1;
+      hp.push_back(s->P);
+      ha.push_back(A);
+      const int G = s->run_gx * s->run_gy;
+      need.push_back(A.n ? G : 0);
+      if (A.n)
+        for (int r = 0; r < G; ++r) {
+          item_inst.push_back(k);
+          item_rect.push_back(r);
+        }
+    }
+    const int m = (int)wave.size(), ni = (int)item_inst.size();
+    size_t o_p = 0, o_a = align256(o_p + m * sizeof(Params)), o_ii = align256(o_a + m * sizeof(RunArgs)),
+           o_ir = align256(o_ii + ni * 4), o_nd = align256(o_ir + ni * 4), o_cl = align256(o_nd + m * 4),
+           o_nx = align256(o_cl + m * 4), bytes = align256(o_nx + 4);
+    if (bytes > b->tab_bytes) {
+      if (b->d_tab) cudaFree(b->d_tab);
+      b->d_tab = nullptr;
+      CU(cudaMalloc(&b->d_tab, bytes), "batch tables");
+      b->tab_bytes = bytes;
+    }
+    unsigned char* t = static_cast<unsigned char*>(b->d_tab);
+    cudaStream_t st = b->stream;
+    CU(cudaMemcpyAsync(t + o_p, hp.data(), m * sizeof(Params), cudaMemcpyHostToDevice, st), "params");
+    CU(cudaMemcpyAsync(t + o_a, ha.data(), m * sizeof(RunArgs), cudaMemcpyHostToDevice, st), "args");
+    if (ni) {
+      CU(cudaMemcpyAsync(t + o_ii, item_inst.data(), ni * 4, cudaMemcpyHostToDevice, st), "items");
+      CU(cudaMemcpyAsync(t + o_ir, item_rect.data(), ni * 4, cudaMemcpyHostToDevice, st), "items");
+    }
+    CU(cudaMemcpyAsync(t + o_nd, need.data(), m * 4, cudaMemcpyHostToDevice, st), "need");
+    CU(cudaMemsetAsync(t + o_cl, 0, m * 4, st), "claimed");
+    CU(cudaMemsetAsync(t + o_nx, 0, 4, st), "queue head");
+    BatchArgs B;
+    B.params = reinterpret_cast<const Params*>(t + o_p);
+    B.args = reinterpret_cast<const RunArgs*>(t + o_a);
+    B.item_inst = reinterpret_cast<const int*>(t + o_ii);
+    B.item_rect = reinterpret_cast<const int*>(t + o_ir);
+    B.need = reinterpret_cast<const int*>(t + o_nd);
+    B.claimed = reinterpret_cast<unsigned int*>(t + o_cl);
+    B.next_item = reinterpret_cast<unsigned int*>(t + o_nx);
+    B.n_items = ni;
+    B.gang_ns = 300ll * 1000000000ll;
+    if (ni) {
+      CU(launch_batch(B, std::min(cap, ni), threads, st), "batch kernel launch");
+      b->launches++;
+    }
+    CU(cudaStreamSynchronize(st), "batch wave");
+    // read each instance's results before its memory is reused
+    for (int k = 0; k < m; ++k) {
+      const int i = wave[k];
+      noc_sim* s = b->sims[i];
+      s->cycle = (uint32_t)b->cycles[i];
+      int64_t ec = -1;
+      int rc = read_error(s, &ec);
+      b->err[i] = rc;
+      b->err_cycle[i] = ec;
+      if (rc && !first_err) first_err = rc;
+      rc = noc_stats(s, -1, &b->stats[i]);
+      if (rc) return rc;
+      b->launches++;
+      rc = noc_latency_hist(s, 0, b->hist[i].data(), HIST_BINS);
+      if (!rc) rc = noc_latency_hist(s, 1, b->hist[i].data() + HIST_BINS, HIST_BINS);
+      if (rc) return rc;
+      if (b->collect_hash) {
+        uint64_t h = 0;
+        rc = noc_state_hash(s, &h);
+        if (rc) return rc;
+        b->hash[i] = h;
+        b->launches += 2;
+      }
+      s->ready = false;
+      s->base = nullptr;
+    }
+  }
+  b->done = true;
+  if (first_err) return fail(first_err, "an instance ended with error %d", first_err);
+  return NOC_OK;
+}
+
+int noc_batch_waves(const noc_batch* b) { return b ? b->waves : -1; }
+
+int noc_batch_error(const noc_batch* b, int i, int64_t* err_cycle) {
+  if (!b || i < 0 || i >= (int)b->sims.size()) return fail(NOC_ERR_ARG, "bad argument");
+  if (err_cycle) *err_cycle = b->err_cycle[i];
+  return b->err[i];
+}
+
+int noc_batch_stats(const noc_batch* b, int i, noc_stats_t* out) {
+  if (!b || !out || i < 0 || i >= (int)b->sims.size()) return fail(NOC_ERR_ARG, "bad argument");
+  if (!b->done) return fail(NOC_ERR_STATE, "batch has not run");
+  *out = b->stats[i];
+  return NOC_OK;
+}
+
+int noc_batch_state_hash(const noc_batch* b, int i, uint64_t* out) {
+  if (!b || !out || i < 0 || i >= (int)b->sims.size()) return fail(NOC_ERR_ARG, "bad argument");
+  if (!b->done || !b->collect_hash) return fail(NOC_ERR_STATE, "no hashes collected");
+  *out = b->hash[i];
+  return NOC_OK;
+}
+
+int noc_batch_latency_hist(const noc_batch* b, int i, int which, uint64_t* bins, int nbins) {
+  if (!b || !bins || i < 0 || i >= (int)b->sims.size() || which < 0 || which > 1 || nbins < HIST_BINS)
+    return fail(NOC_ERR_ARG, "bad argument");
+  if (!b->done) return fail(NOC_ERR_STATE, "batch has not run");
+  memcpy(bins, b->hist[i].data() + which * HIST_BINS, HIST_BINS * 8);
+  return NOC_OK;
+}
+
+int64_t noc_batch_kernel_launches(const noc_batch* b) { return b ? b->launches : -1; }
 
 }  // extern "C"

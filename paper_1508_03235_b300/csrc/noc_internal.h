@@ -19,6 +19,22 @@ struct RunArgs {
   int silent_cta;                  // test fault: this CTA never publishes
 };
 
+// batch work queue: per-instance parameters, and items (instance, rectangle)
+// ordered instance by instance
+struct BatchArgs {
+  const Params* params;
+  const RunArgs* args;
+  const int* item_inst;
+  const int* item_rect;
+  const int* need;          // rectangles per instance
+  unsigned int* claimed;    // rectangles popped per instance
+  unsigned int* next_item;  // queue head
+  int n_items;
+  long long gang_ns;        // limit of the wait for an instance's rectangles
+};
+cudaError_t launch_batch(const BatchArgs& B, int grid, int threads, cudaStream_t s);
+cudaError_t max_coresident_batch(int threads, int* out);
+
 // geometry of the launch for a gx x gy rectangle grid
 int block_threads(int W, int H, int gx, int gy);
 size_t run_smem_bytes(int threads);

@@ -1,325 +1,19 @@
-// noc_kernel.cu -- the persistent cooperative cycle kernel and its helpers.
-//
-// Mapping (B300, sm_103a): the mesh is cut into gx x gy rectangles, one CTA
-// each, one thread per tile.  A launch runs many simulated cycles.  Links
-// between tiles of the same rectangle are exchanged through shared memory;
-// links that cross a rectangle edge go through an L2-resident global buffer,
-// and each CTA waits only for its (up to four) neighbouring CTAs to publish the
-// previous cycle -- a neighbour-flag barrier instead of a grid-wide one.  The
-// tile's own work of the next cycle (Phase 3 of this cycle, Phase 1 of the
-// next) runs before that wait, so cache latency and barrier latency overlap.
-#include <cstdio>
-
-#include "noc_internal.h"
+// noc_kernel.cu -- state-hash, statistics and drain helper kernels, and the
+// dispatch to the cycle-kernel variants.
+#include "noc_kernel.cuh"
 
 namespace noc {
 
-// ---------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// wait until *flag >= target (cycle counts, wrap-safe).  Returns 1 on success,
-// 0 when the time limit ran out, -1 when another CTA already gave up.  The
-// iteration count is bounded as well, so the wait always ends.
-__device__ int wait_ge(const unsigned* flag, unsigned target, const unsigned* abort_flag,
-                       long long limit_ns) {
-  const unsigned long long start = global_ns();
-  for (unsigned it = 0; it < (1u << 28); ++it) {
-    if ((int)(ld_acquire_u32(flag) - target) >= 0) return 1;
-    if ((it & 31u) == 31u) {
-      if (ld_acquire_u32(abort_flag)) return -1;
-      if ((long long)(global_ns() - start) > limit_ns) return 0;
-    }
-  }
-  return 0;
-}
-
-// ---------------------------------------------------------------- tile state I/O
-__device__ void load_tile(const Params& P, uint32_t r, Tile& T) {
-  const size_t N = (size_t)P.N;
-  const uint32_t* C = P.core;
-  T.r = r;
-  T.x = r % (uint32_t)P.W;
-  T.y = r / (uint32_t)P.W;
-  T.next_ref = C[C_NEXT * N + r];
-  uint32_t b = C[C_FSMB * N + r];
-  T.fsm = b & 0xFFu;
-  T.fsm_write = (b >> 8) & 0xFFu;
-  T.om_kind = (b >> 16) & 0xFFu;
-  T.om_write = b >> 24;
-  T.fsm_line = C[C_FLINE * N + r];
-  T.fsm_timer = C[C_FTIMER * N + r];
-  T.fsm_start = C[C_FSTART * N + r];
-  T.om_line = C[C_OLINE * N + r];
-  T.om_start = C[C_OSTART * N + r];
-  T.om_timer = C[C_OTIMER * N + r];
-  uint32_t e = C[C_EPOCH * N + r];
-  T.epoch = e & 0xFFFFu;
-  T.om_epoch = e >> 16;
-  uint32_t q = C[C_CQ * N + r];
-  T.cq_head = q & 0xFFFFu;
-  T.cq_len = q >> 16;
-  q = C[C_SQ * N + r];
-  T.sq_head = q & 0xFFFFu;
-  T.sq_len = q >> 16;
-  q = C[C_MQ * N + r];
-  T.mq_head = q & 0xFFFFu;
-  T.mq_len = q >> 16;
-  q = C[C_FWD * N + r];
-  T.fwd_next = q & 0xFFFFu;
-  T.fwd_n = q >> 16;
-  const uint4 z = make_uint4(0, 0, 0, 0);
-  T.cq_front = T.cq_len ? P.cq[(size_t)r * P.core_q + T.cq_head] : z;
-  T.sq_front = T.sq_len ? P.sq[(size_t)r * P.svc_q + T.sq_head] : z;
-  T.mq_front = T.mq_len ? P.mq[(size_t)r * P.mem_q + T.mq_head] : z;
-  T.ej = z;
-  T.pf_ok = 0;
-  T.pf_line = 0;
-  T.pf_write = 0;
-  T.inj = P.stats[S_INJ * N + r];
-  T.ejc = P.stats[S_EJ * N + r];
-  T.defl = P.stats[S_DEFL * N + r];
-  T.latsum = P.stats[S_LATSUM * N + r];
-  T.latmax = P.stats[S_LATMAX * N + r];
-  T.l2lsum = 0;
-#pragma unroll
-  for (int k = 0; k < NSMALL; ++k) T.sm[k] = 0;
-}
-
-__device__ void store_tile(const Params& P, const Tile& T) {
-  const size_t N = (size_t)P.N;
-  const uint32_t r = T.r;
-  uint32_t* C = P.core;
-  C[C_NEXT * N + r] = T.next_ref;
-  C[C_FSMB * N + r] = T.fsm | (T.fsm_write << 8) | (T.om_kind << 16) | (T.om_write << 24);
-  C[C_FLINE * N + r] = T.fsm_line;
-  C[C_FTIMER * N + r] = T.fsm_timer;
-  C[C_FSTART * N + r] = T.fsm_start;
-  C[C_OLINE * N + r] = T.om_line;
-  C[C_OSTART * N + r] = T.om_start;
-  C[C_OTIMER * N + r] = T.om_timer;
-  C[C_EPOCH * N + r] = T.epoch | (T.om_epoch << 16);
-  C[C_CQ * N + r] = T.cq_head | (T.cq_len << 16);
-  C[C_SQ * N + r] = T.sq_head | (T.sq_len << 16);
-  C[C_MQ * N + r] = T.mq_head | (T.mq_len << 16);
-  C[C_FWD * N + r] = T.fwd_next | (T.fwd_n << 16);
-  P.stats[S_INJ * N + r] = T.inj;
-  P.stats[S_EJ * N + r] = T.ejc;
-  P.stats[S_DEFL * N + r] = T.defl;
-  P.stats[S_LATSUM * N + r] = T.latsum;
-  P.stats[S_LATMAX * N + r] = T.latmax;
-  if (T.l2lsum) P.stats[S_L2LSUM * N + r] += T.l2lsum;
-#pragma unroll
-  for (int k = 0; k < NSMALL; ++k)
-    if (k + S_REFS != S_L2LSUM && T.sm[k]) P.stats[(size_t)(k + S_REFS) * N + r] += T.sm[k];
-}
-
-__device__ __forceinline__ bool tile_quiet(const Tile& T, const uint4 (&out)[4]) {
-  bool q = T.cq_len == 0 && T.sq_len == 0 && T.mq_len == 0 && T.fsm == FSM_IDLE &&
-           T.om_kind == OM_NONE;
-#pragma unroll
-  for (int d = 0; d < 4; ++d) q = q && ftype(out[d]) == T_NONE;
-  return q;
-}
-
-// sum a 64-bit value over the CTA; the result is valid in thread 0
-__device__ unsigned long long block_sum(unsigned long long v, unsigned long long* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  unsigned long long s = 0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) s += red[w];
-  return s;
-}
-
-// ---------------------------------------------------------------- cycle kernel
-constexpr int MAX_THREADS = 384;
-
-size_t run_smem_bytes(int threads) {
-  return (size_t)threads * 8 * sizeof(uint4) + (2 * HIST_BINS + 2) * sizeof(uint32_t) +
-         32 * sizeof(unsigned long long);
-}
-
-int block_threads(int W, int H, int gx, int gy) {
-  int bw = (W + gx - 1) / gx, bh = (H + gy - 1) / gy;
-  int a = bw * bh;
-  return ((a + 31) / 32) * 32;
-}
-
-template <bool HASH, bool DRAIN>
-__global__ void __launch_bounds__(MAX_THREADS, 1) run_kernel(const Params P, const RunArgs A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nt = blockDim.x;
-  uint4* sl = reinterpret_cast<uint4*>(smem_raw);  // [2 parity][4 port][nt]
-  uint32_t* sh_hist = reinterpret_cast<uint32_t*>(sl + 8 * nt);
-  unsigned long long* sh_red = reinterpret_cast<unsigned long long*>(sh_hist + 2 * HIST_BINS + 2);
-  __shared__ int sh_abort;
-
-  const int b = blockIdx.x;
-  const int cx = b % A.gx, cy = b / A.gx;
-  const int X0 = cx * P.W / A.gx, X1 = (cx + 1) * P.W / A.gx;
-  const int Y0 = cy * P.H / A.gy, Y1 = (cy + 1) * P.H / A.gy;
-  const int bw = X1 - X0, bh = Y1 - Y0;
-  const int i = threadIdx.x;
-  const bool active = i < bw * bh;
-  const int lx = active ? i % bw : 0, ly = active ? i / bw : 0;
-  const uint32_t x = X0 + lx, y = Y0 + ly, r = y * P.W + x;
-  const size_t N = (size_t)P.N;
-  const uint32_t exists = (y > 0 ? 1u << P_N : 0u) | (y + 1 < (uint32_t)P.H ? 1u << P_S : 0u) |
-                          (x + 1 < (uint32_t)P.W ? 1u << P_E : 0u) | (x > 0 ? 1u << P_W : 0u);
-  // links that leave the rectangle also go to the global buffer
-  const uint32_t boundary = exists & ((ly == 0 ? 1u << P_N : 0u) | (ly == bh - 1 ? 1u << P_S : 0u) |
-                                      (lx == bw - 1 ? 1u << P_E : 0u) | (lx == 0 ? 1u << P_W : 0u));
-  // neighbouring CTA on each side (N, S, E, W), or -1
-  const int nbr[4] = {cy > 0 ? b - A.gx : -1, cy + 1 < A.gy ? b + A.gx : -1,
-                      cx + 1 < A.gx ? b + 1 : -1, cx > 0 ? b - 1 : -1};
-  const bool alone = A.gx * A.gy == 1;
-
-  for (int k = i; k < 2 * HIST_BINS; k += nt) sh_hist[k] = 0;
-  if (i == 0) sh_abort = 0;
-
-  Tile T;
-  uint4 out[4];
-#pragma unroll
-  for (int d = 0; d < 4; ++d) out[d] = make_uint4(0, 0, 0, 0);
-  const uint32_t t0 = A.t0, tend = A.t0 + A.n;
-  if (active) {
-    load_tile(P, r, T);
-    const uint32_t pin = (t0 - 1u) & 1u;
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      out[d] = P.glink[((size_t)pin * 4 + d) * N + r];
-      sl[(pin * 4 + d) * nt + i] = out[d];
-    }
-  }
-  __syncthreads();
-  if (active) phase1(P, T, t0, A.draining != 0, sh_hist);
-
-  uint32_t t = t0;
-  for (; t < tend; ++t) {
-    const uint32_t pin = (t - 1u) & 1u, pout = t & 1u;
-    // ---- Phase 2: gather arrivals, route, publish outputs
-    if (active) {
-      uint4 in[4];
-      const uint4 z = make_uint4(0, 0, 0, 0);
-      const uint4* sp = sl + pin * 4 * nt;
-      const uint4* gl = P.glink + (size_t)pin * 4 * N;
-      in[P_N] = !(exists & (1u << P_N)) ? z
-                : (ly > 0 ? sp[P_S * nt + i - bw] : __ldcg(&gl[P_S * N + r - P.W]));
-      in[P_S] = !(exists & (1u << P_S)) ? z
-                : (ly < bh - 1 ? sp[P_N * nt + i + bw] : __ldcg(&gl[P_N * N + r + P.W]));
-      in[P_E] = !(exists & (1u << P_E)) ? z
-                : (lx < bw - 1 ? sp[P_W * nt + i + 1] : __ldcg(&gl[P_W * N + r + 1]));
-      in[P_W] = !(exists & (1u << P_W)) ? z
-                : (lx > 0 ? sp[P_E * nt + i - 1] : __ldcg(&gl[P_E * N + r - 1]));
-      route(P, T, t, in, exists, out);
-      uint4* so = sl + pout * 4 * nt;
-      uint4* go = P.glink + (size_t)pout * 4 * N;
-#pragma unroll
-      for (int d = 0; d < 4; ++d) {
-        so[d * nt + i] = out[d];
-        if (boundary & (1u << d)) __stcg(&go[d * N + r], out[d]);
-      }
-    }
-    __syncthreads();
-    // publish: the release store orders this CTA's link stores (made visible
-    // to thread 0 by the barrier) before the flag
-    if (i == 0 && !alone && b != A.silent_cta) st_release_u32(&P.flags[b], t + 1);
-    // ---- Phase 3 of this cycle
-    if (active) phase3(P, T, t, sh_hist);
-    if (HASH) {
-      unsigned long long h = active ? tile_hash(T, out) : 0ull;
-      h = block_sum(h, sh_red);
-      if (i == 0) atomicAdd(&A.hash_trace[t - t0], h);
-    }
-    if (DRAIN) {
-      unsigned long long q = (active && !tile_quiet(T, out)) ? 1ull : 0ull;
-      q = block_sum(q, sh_red);
-      if (i == 0 && q) atomicAdd(&A.busy[t - t0], (unsigned)q);
-    }
-    if (t + 1 == tend) break;
-    // ---- Phase 1 of the next cycle, then the neighbours' outputs of this one
-    if (active) phase1(P, T, t + 1, A.draining != 0, sh_hist);
-    // lanes 0..3 each wait for one neighbouring CTA (N, S, E, W)
-    if (i < 4 && nbr[i] >= 0) {
-      int w = wait_ge(&P.flags[nbr[i]], t + 1, A.abort_flag, A.wait_ns);
-      if (w <= 0) {
-        if (w == 0) {
-          atomicExch(A.abort_flag, 1u);
-          set_error(P, t + 1, ERR_TIMEOUT);
-        }
-        sh_abort = 1;
-      }
-    }
-    __syncthreads();
-    if (sh_abort) break;
-  }
-
-  // ---- end of launch: full link state of the last cycle, tile state, counters
-  if (active) {
-    const uint32_t plast = (t - (t == tend ? 1u : 0u)) & 1u;
-#pragma unroll
-    for (int d = 0; d < 4; ++d) P.glink[((size_t)plast * 4 + d) * N + r] = out[d];
-    store_tile(P, T);
-  }
-  __syncthreads();
-  for (int k = i; k < 2 * HIST_BINS; k += nt)
-    if (sh_hist[k]) atomicAdd(&P.hist[k], (unsigned long long)sh_hist[k]);
-}
-
-template <bool H, bool D>
-static cudaError_t prepare_run() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(run_kernel<H, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)run_smem_bytes(MAX_THREADS));
-  if (e == cudaSuccess) done = true;
-  return e;
-}
-
-cudaError_t max_coresident_ctas(int threads, int* out) {
-  cudaError_t e = prepare_run<false, false>();
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, run_kernel<false, false>, threads,
-                                                    run_smem_bytes(threads));
-  if (e != cudaSuccess) return e;
-  *out = per * sms;
-  return cudaSuccess;
-}
-
-template <bool H, bool D>
-static cudaError_t launch_run_t(const Params& P, const RunArgs& A, cudaStream_t s) {
-  cudaError_t e = prepare_run<H, D>();
-  if (e != cudaSuccess) return e;
-  const int threads = block_threads(P.W, P.H, A.gx, A.gy);
-  void* args[] = {(void*)&P, (void*)&A};
-  return cudaLaunchCooperativeKernel((const void*)run_kernel<H, D>, dim3(A.gx * A.gy),
-                                     dim3(threads), args, run_smem_bytes(threads), s);
-}
+cudaError_t launch_run00(const Params& P, const RunArgs& A, cudaStream_t s);
+cudaError_t launch_run10(const Params& P, const RunArgs& A, cudaStream_t s);
+cudaError_t launch_run01(const Params& P, const RunArgs& A, cudaStream_t s);
+cudaError_t launch_run11(const Params& P, const RunArgs& A, cudaStream_t s);
 
 cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
-  if (A.hash_trace && A.busy) return launch_run_t<true, true>(P, A, s);
-  if (A.hash_trace) return launch_run_t<true, false>(P, A, s);
-  if (A.busy) return launch_run_t<false, true>(P, A, s);
-  return launch_run_t<false, false>(P, A, s);
+  if (A.hash_trace && A.busy) return launch_run11(P, A, s);
+  if (A.hash_trace) return launch_run10(P, A, s);
+  if (A.busy) return launch_run01(P, A, s);
+  return launch_run00(P, A, s);
 }
 
 // ---------------------------------------------------------------- hashes

@@ -295,3 +295,122 @@ class Sim:
         out = np.zeros(17, dtype=np.uint32)
         _check(lib().noc_get_core(self._h, tile, _p32(out)))
         return dict(zip(self.CORE_FIELDS, (int(v) for v in out)))
+
+
+# --------------------------------------------------------------------------- batch
+class InstanceDesc(C.Structure):
+    _fields_ = [("mesh_w", C.c_int32), ("mesh_h", C.c_int32), ("l2_policy", C.c_int32),
+                ("reserved", C.c_int32), ("cache", CacheCfg), ("traffic", Traffic),
+                ("seed", C.c_uint64), ("cycles", C.c_int64)]
+
+
+def _batch_sigs(L):
+    vp, i32, i64 = C.c_void_p, C.c_int, C.c_int64
+    sig = {
+        "noc_batch_create": (i32, [i32, C.POINTER(InstanceDesc), C.POINTER(vp)]),
+        "noc_batch_destroy": (None, [vp]),
+        "noc_batch_min_bytes": (C.c_size_t, [vp]),
+        "noc_batch_total_bytes": (C.c_size_t, [vp]),
+        "noc_batch_bind_memory": (i32, [vp, vp, C.c_size_t]),
+        "noc_batch_set_stream": (i32, [vp, vp]),
+        "noc_batch_set_rect": (i32, [vp, i32]),
+        "noc_batch_set_collect_hash": (i32, [vp, i32]),
+        "noc_batch_run": (i32, [vp]),
+        "noc_batch_waves": (i32, [vp]),
+        "noc_batch_error": (i32, [vp, i32, C.POINTER(i64)]),
+        "noc_batch_stats": (i32, [vp, i32, C.POINTER(Stats)]),
+        "noc_batch_state_hash": (i32, [vp, i32, C.POINTER(C.c_uint64)]),
+        "noc_batch_latency_hist": (i32, [vp, i32, i32, C.POINTER(C.c_uint64), i32]),
+        "noc_batch_kernel_launches": (i64, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+class Batch:
+    """Independent simulations run together by the batch engine.  `params_list`
+    holds inputs.sim_params() dicts; `cycles` is one count or one per instance.
+    The instances' state lives in a torch uint8 pool of `pool_bytes` (default:
+    all instances at once, capped at 80% of free device memory); instances
+    that do not fit run in later waves."""
+
+    def __init__(self, params_list, cycles, stream=None, rect=8, collect_hash=True,
+                 pool_bytes=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the batch engine needs a CUDA device")
+        L = lib()
+        _batch_sigs(L)
+        n = len(params_list)
+        if isinstance(cycles, int):
+            cycles = [cycles] * n
+        arr = (InstanceDesc * n)()
+        for d, p, c in zip(arr, params_list, cycles):
+            d.mesh_w, d.mesh_h, d.l2_policy = p["mesh_w"], p["mesh_h"], p.get("policy", 0)
+            d.cache = cache_struct(p)
+            d.traffic = traffic_struct(p)
+            d.seed = p.get("seed", 1)
+            d.cycles = int(c)
+        h = C.c_void_p()
+        _check(L.noc_batch_create(n, arr, C.byref(h)))
+        self._h = h
+        self.n = n
+        total = L.noc_batch_total_bytes(h)
+        free, _ = torch.cuda.mem_get_info()
+        want = pool_bytes if pool_bytes is not None else min(total, int(free * 0.8))
+        want = max(int(want), L.noc_batch_min_bytes(h))
+        self._pool = torch.empty(want + 256, dtype=torch.uint8, device="cuda")
+        ptr = self._pool.data_ptr()
+        ptr += (-ptr) % 256
+        _check(L.noc_batch_bind_memory(h, C.c_void_p(ptr), want))
+        st = stream if stream is not None else torch.cuda.current_stream()
+        _check(L.noc_batch_set_stream(h, C.c_void_p(st.cuda_stream)))
+        _check(L.noc_batch_set_rect(h, rect))
+        _check(L.noc_batch_set_collect_hash(h, 1 if collect_hash else 0))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().noc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, check=True):
+        rc = lib().noc_batch_run(self._h)
+        if check:
+            _check(rc)
+        return rc
+
+    @property
+    def waves(self) -> int:
+        return lib().noc_batch_waves(self._h)
+
+    @property
+    def launches(self) -> int:
+        return lib().noc_batch_kernel_launches(self._h)
+
+    def error(self, i):
+        cyc = C.c_int64()
+        rc = lib().noc_batch_error(self._h, i, C.byref(cyc))
+        return rc, cyc.value
+
+    def stats(self, i) -> dict:
+        s = Stats()
+        _check(lib().noc_batch_stats(self._h, i, C.byref(s)))
+        return {n: int(getattr(s, n)) for n in STATS_FIELDS}
+
+    def state_hash(self, i) -> int:
+        v = C.c_uint64()
+        _check(lib().noc_batch_state_hash(self._h, i, C.byref(v)))
+        return int(v.value)
+
+    def hist(self, i, which) -> np.ndarray:
+        out = np.zeros(HIST_BINS, dtype=np.uint64)
+        _check(lib().noc_batch_latency_hist(self._h, i, which, _p64(out), HIST_BINS))
+        return out
