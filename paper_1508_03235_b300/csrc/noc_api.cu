@@ -106,7 +106,7 @@ void layout(noc_sim* s) {
   s->o_l1own = take(w1 * sizeof(uint16_t));
   s->o_l2 = take(w2 * sizeof(uint32_t));
   s->o_l2ep = take(lspd ? w2 * sizeof(uint16_t) : 0);
-  s->o_l2hist = take(mig ? w2 * HIST_STRIDE * sizeof(uint16_t) : 0);
+  s->o_l2hist = take(mig ? w2 * hist_stride(P.mig_window) * sizeof(uint16_t) : 0);
   s->o_dir = take(lspd ? (size_t)P.total_lines * sizeof(uint32_t) : 0);
   s->o_fwd = take(mig ? N * P.fwd_cap * 2 * sizeof(uint32_t) : 0);
   s->o_stats = take((size_t)NSTAT * N * sizeof(unsigned long long));
@@ -157,7 +157,7 @@ int do_reset(noc_sim* s) {
   CU(cudaMemsetAsync(P.l2, 0, w2 * sizeof(uint32_t), st), "reset L2");
   if (P.l2ep) CU(cudaMemsetAsync(P.l2ep, 0, w2 * sizeof(uint16_t), st), "reset L2 epochs");
   if (P.l2hist)
-    CU(cudaMemsetAsync(P.l2hist, 0, w2 * HIST_STRIDE * sizeof(uint16_t), st), "reset history");
+    CU(cudaMemsetAsync(P.l2hist, 0, w2 * hist_stride(P.mig_window) * sizeof(uint16_t), st), "reset history");
   if (P.dir) CU(cudaMemsetAsync(P.dir, 0xFF, (size_t)P.total_lines * 4, st), "reset directory");
   if (P.fwd) CU(cudaMemsetAsync(P.fwd, 0, N * P.fwd_cap * 8, st), "reset forward tables");
   CU(cudaMemsetAsync(P.stats, 0, (size_t)NSTAT * N * 8, st), "reset counters");
@@ -334,7 +334,7 @@ int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, co
       c->mem_q > 65535)
     return fail(NOC_ERR_ARG, "queue capacities must be 1..65535");
   if (l2_policy == NOC_L2_LSPD_MIGRATE &&
-      (c->mig_window < 1 || c->mig_window > HIST_STRIDE - 2 || c->mig_threshold < 1 ||
+      (c->mig_window < 1 || c->mig_window > HIST_MAX || c->mig_threshold < 1 ||
        c->fwd_entries < 1 || c->fwd_entries > 65535))
     return fail(NOC_ERR_ARG, "migration: window 1..30, threshold >= 1, forward entries >= 1");
   if (tr->mode < 0 || tr->mode > 2 || tr->period < 0) return fail(NOC_ERR_ARG, "traffic mode/period");

@@ -86,7 +86,7 @@ __global__ void state_terms_kernel(const Params P, uint32_t cycle, unsigned long
     uint32_t mig = 0, hn = 0;
     const uint16_t* hp = nullptr;
     if (P.policy == POL_MIGRATE) {
-      hp = P.l2hist + k * HIST_STRIDE;
+      hp = P.l2hist + k * (size_t)P.hist_stride;
       hn = hp[0];
       mig = hp[1];
     }

@@ -27,7 +27,9 @@ constexpr uint32_t NO_TILE = 0xFFFFu;
 constexpr uint32_t DIR_NONE = 0xFFFFFFFFu;
 constexpr int HIST_BINS = 1025;
 constexpr int MAX_WAYS = 16;
-constexpr int HIST_STRIDE = 32;  // u16 per L2 way: [n, migrating, who x30]
+constexpr int HIST_MAX = 30;  // longest access history kept per L2 way
+// u16 words per L2 way in the history array: [n, migrating, who x mig_window]
+inline int hist_stride(int mig_window) { return (mig_window + 3) & ~1; }
 
 // cache way word: bit31 valid | bits27-30 LRU rank | bit26 dirty | bits0-25 line
 constexpr uint32_t W_VALID = 1u << 31;
@@ -55,7 +57,7 @@ enum : int {
 struct Params {
   int W, H, N, policy, mode, period;
   int l1_sets, l1_ways, l2_sets, l2_ways;
-  int l1_miss, mem_lat, mig_window, mig_threshold;
+  int l1_miss, mem_lat, mig_window, mig_threshold, hist_stride;
   int core_q, svc_q, mem_q, fwd_cap;
   uint32_t write_q16, priv_q16, shared_q16, hot_q16;
   int hot_side, hot_x0, hot_y0;
@@ -75,7 +77,7 @@ struct Params {
   uint16_t* l1own;       // [N][l1_sets][l1_ways]
   uint32_t* l2;          // [N][l2_sets][l2_ways] way words
   uint16_t* l2ep;        // [N][l2_sets][l2_ways]    (LSPD)
-  uint16_t* l2hist;      // [N][l2_sets][l2_ways][HIST_STRIDE] (migrate)
+  uint16_t* l2hist;      // [N][l2_sets][l2_ways][hist_stride] (migrate)
   uint32_t* dir;         // [total_lines]            (LSPD)
   uint32_t* fwd;         // [N][fwd_cap][2]          (migrate)
   uint32_t* trace_off;   // [N+1]                    (trace mode)
@@ -93,6 +95,7 @@ __device__ __forceinline__ uint32_t qdiv(uint32_t n, unsigned long long m) {
 // host: reciprocals of the divisors used on the hot path
 inline unsigned long long recip64(uint32_t d) { return d <= 1 ? 0ull : (~0ull) / d + 1; }
 inline void set_divisors(Params& P) {
+  P.hist_stride = hist_stride(P.mig_window);
   P.mW = recip64((uint32_t)P.W);
   P.mN = recip64((uint32_t)P.N);
   P.mL1 = recip64((uint32_t)P.l1_sets);
@@ -360,7 +363,7 @@ static __device__ void l1_fill(const Params& P, Tile& T, uint32_t line, uint32_t
 }
 
 __device__ __forceinline__ uint16_t* hist_ptr(const Params& P, size_t way_index) {
-  return P.l2hist + way_index * HIST_STRIDE;
+  return P.l2hist + way_index * (size_t)P.hist_stride;
 }
 
 // directory entry delete for an evicted L2 victim (Sec. 3.4)

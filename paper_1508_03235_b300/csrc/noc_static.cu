@@ -59,7 +59,7 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
       c->mem_q < 1 || c->core_q > 65535 || c->svc_q > 65535 || c->mem_q > 65535)
     return NOC_ERR_ARG;
   if (l2_policy == NOC_L2_LSPD_MIGRATE &&
-      (c->mig_window < 1 || c->mig_window > HIST_STRIDE - 2 || c->mig_threshold < 1 ||
+      (c->mig_window < 1 || c->mig_window > HIST_MAX || c->mig_threshold < 1 ||
        c->fwd_entries < 1))
     return NOC_ERR_ARG;
   // trace mode needs per-core reference lists, which live outside the array
@@ -113,7 +113,7 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
   size_t off[18], cur = 0;
   const size_t sz[18] = {2 * 4 * N * 16, NCORE * N * 4, N * P.core_q * 16, N * P.svc_q * 16,
                          N * P.mem_q * 16, w1 * 4, w1 * 2, w2 * 4, lspd ? w2 * 2 : 0,
-                         mig ? w2 * HIST_STRIDE * 2 : 0, lspd ? (size_t)total * 4 : 0,
+                         mig ? w2 * hist_stride(P.mig_window) * 2 : 0, lspd ? (size_t)total * 4 : 0,
                          mig ? N * P.fwd_cap * 8 : 0, (size_t)NSTAT * N * 8,
                          2 * HIST_BINS * 8, n_flags * 4, 8, 4, 64 * 8};
   for (int k = 0; k < 18; ++k) {

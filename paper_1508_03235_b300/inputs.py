@@ -135,7 +135,7 @@ def batch_design_points(n=512, seed=0, sides=tuple(range(8, 129, 8)), period_lo=
         traf = traffic(period=period, write=0.0, priv=0.0, shared=0.0, priv_kb=ws_kb)
         traf.update(write_q16=q16(write), priv_q16=pq, shared_q16=sq)
         p = sim_params(side, side, policy=pol, seed=i + 1, traf=traf,
-                       cache=cache_cfg(svc_q=1024))
+                       cache=cache_cfg(svc_q=512))
         p["design"] = dict(side=side, period=period, priv=pq / Q16, shared=sq / Q16,
                            remote=1.0 - (pq + sq) / Q16, write=write, ws_kb=ws_kb, policy=pol)
         out.append(p)
