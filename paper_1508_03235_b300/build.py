@@ -9,8 +9,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnoc.so")
-SOURCES = ["noc_run00.cu", "noc_run10.cu", "noc_run01.cu", "noc_run11.cu", "noc_batch.cu",
-           "noc_kernel.cu", "noc_api.cu", "noc_static.cu"]
+# (source, preprocessor defines): the cycle kernel is compiled once per variant
+WAY_BOUNDS = ((4, 8), (4, 16), (16, 16))
+UNITS = ([("noc_run_variant.cu", {"NOC_HASH": h, "NOC_DRAIN": d, "NOC_W1": w1, "NOC_W2": w2})
+          for (w1, w2) in WAY_BOUNDS for h in (0, 1) for d in (0, 1)]
+         + [("noc_batch.cu", {"NOC_W1": w1, "NOC_W2": w2}) for (w1, w2) in WAY_BOUNDS]
+         + [("noc_kernel.cu", {}), ("noc_api.cu", {}), ("noc_static.cu", {})])
+SOURCES = sorted({u[0] for u in UNITS})
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -42,10 +47,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         flags.append("-Xptxas=-v")
     objs, procs = [], []
-    for src in sources():           # one nvcc per translation unit, in parallel
-        obj = os.path.join(BUILD, os.path.basename(src) + f".{os.getpid()}.o")
+    for k, (src, defs) in enumerate(UNITS):   # one nvcc per unit, run in parallel
+        obj = os.path.join(BUILD, f"{k:02d}_{src}.{os.getpid()}.o")
         objs.append(obj)
-        procs.append(subprocess.Popen([nvcc, *flags, "-c", src, "-o", obj]))
+        dflags = [f"-D{n}={v}" for n, v in defs.items()]
+        procs.append(subprocess.Popen([nvcc, *flags, *dflags, "-c", os.path.join(CSRC, src),
+                                       "-o", obj]))
     if any(p.wait() != 0 for p in procs):
         raise subprocess.CalledProcessError(1, "nvcc")
     subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs])

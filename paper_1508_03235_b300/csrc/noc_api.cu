@@ -209,7 +209,7 @@ int choose_tiling(noc_sim* s, int* gx_out, int* gy_out) {
       if (G > (long)s->n_flags) continue;
       int& cap = cap_of[threads / 32];
       if (cap < 0) {
-        cudaError_t e = max_coresident_ctas(threads, &cap);
+        cudaError_t e = max_coresident_ctas(s->P, threads, &cap);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy");
       }
       if (G > cap) continue;
@@ -282,7 +282,7 @@ int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
   }
   const int threads = block_threads(s->P.W, s->P.H, s->run_gx, s->run_gy);
   int cap = 0;
-  CU(max_coresident_ctas(threads, &cap), "occupancy");
+  CU(max_coresident_ctas(s->P, threads, &cap), "occupancy");
   if (threads > 384 || s->run_gx * s->run_gy > cap || s->run_gx * s->run_gy > (int)s->n_flags)
     return fail(NOC_ERR_ARG, "tiling %dx%d does not fit one co-resident launch", s->run_gx, s->run_gy);
   uint32_t done = 0;
@@ -906,8 +906,13 @@ int noc_batch_run(noc_batch* b) {
                 noc_batch_min_bytes(b));
   const int side = b->rect;
   const int threads = ((side * side + 31) / 32) * 32;
+  int w1 = 1, w2 = 1;  // one kernel variant serves all instances: the largest way bounds
+  for (noc_sim* s : b->sims) {
+    w1 = std::max(w1, s->P.l1_ways);
+    w2 = std::max(w2, s->P.l2_ways);
+  }
   int cap = 0;
-  CU(max_coresident_batch(threads, &cap), "occupancy");
+  CU(max_coresident_batch(w1, w2, threads, &cap), "occupancy");
   // largest first, so the tail of each wave holds the small instances
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
@@ -1000,7 +1005,7 @@ int noc_batch_run(noc_batch* b) {
     B.n_items = ni;
     B.gang_ns = 300ll * 1000000000ll;
     if (ni) {
-      CU(launch_batch(B, std::min(cap, ni), threads, st), "batch kernel launch");
+      CU(launch_batch(B, std::min(cap, ni), threads, w1, w2, st), "batch kernel launch");
       b->launches++;
     }
     CU(cudaStreamSynchronize(st), "batch wave");

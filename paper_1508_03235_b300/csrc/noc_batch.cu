@@ -1,5 +1,12 @@
-// noc_batch.cu -- the batch engine's persistent work-queue kernel
+// noc_batch.cu -- the batch engine's persistent work-queue kernel (compiled once
+// per L1/L2 way bound)
 #include "noc_kernel.cuh"
+
+#if !defined(NOC_W1) || !defined(NOC_W2)
+#error "compile with -DNOC_W1= -DNOC_W2="
+#endif
+#define NOC_PASTE3(a, b, c) a##_##b##_##c
+#define NOC_NAME(a, b, c) NOC_PASTE3(a, b, c)
 
 namespace noc {
 
@@ -10,6 +17,7 @@ namespace noc {
 // (so the instance's neighbour waits start together), then runs it to the end
 // of the instance's cycles.  Items are popped in order, so every instance
 // before the current one is already running to completion: the waits end.
+template <int W1, int W2>
 __global__ void __launch_bounds__(MAX_THREADS, 1) batch_kernel(const __grid_constant__ BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Params sP;
@@ -40,28 +48,29 @@ __global__ void __launch_bounds__(MAX_THREADS, 1) batch_kernel(const __grid_cons
       for (int k = threadIdx.x; k < (int)(sizeof(RunArgs) / 4); k += blockDim.x) dsta[k] = srca[k];
     }
     __syncthreads();
-    if (s_ok) run_rect<false, false>(sP, sA, B.item_rect[item], smem_raw);
+    if (s_ok) run_rect<false, false, W1, W2>(sP, sA, B.item_rect[item], smem_raw);
     __syncthreads();
   }
 }
 
-cudaError_t launch_batch(const BatchArgs& B, int grid, int threads, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+cudaError_t NOC_NAME(launch_batch, NOC_W1, NOC_W2)(const BatchArgs& B, int grid, int threads,
+                                                  cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(batch_kernel<NOC_W1, NOC_W2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)run_smem_bytes_impl(MAX_THREADS));
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&B};
-  return cudaLaunchCooperativeKernel((const void*)batch_kernel, dim3(grid), dim3(threads), args,
+  return cudaLaunchCooperativeKernel((const void*)batch_kernel<NOC_W1, NOC_W2>, dim3(grid), dim3(threads), args,
                                      run_smem_bytes_impl(threads), s);
 }
 
-cudaError_t max_coresident_batch(int threads, int* out) {
-  cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+cudaError_t NOC_NAME(max_coresident_batch, NOC_W1, NOC_W2)(int threads, int* out) {
+  cudaError_t e = cudaFuncSetAttribute(batch_kernel<NOC_W1, NOC_W2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)run_smem_bytes_impl(MAX_THREADS));
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel, threads, run_smem_bytes_impl(threads));
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<NOC_W1, NOC_W2>, threads, run_smem_bytes_impl(threads));
   if (e != cudaSuccess) return e;
   *out = per * sms;
   return cudaSuccess;

@@ -32,15 +32,16 @@ struct BatchArgs {
   int n_items;
   long long gang_ns;        // limit of the wait for an instance's rectangles
 };
-cudaError_t launch_batch(const BatchArgs& B, int grid, int threads, cudaStream_t s);
-cudaError_t max_coresident_batch(int threads, int* out);
+cudaError_t launch_batch(const BatchArgs& B, int grid, int threads, int l1_ways, int l2_ways,
+                         cudaStream_t s);
+cudaError_t max_coresident_batch(int l1_ways, int l2_ways, int threads, int* out);
 
 // geometry of the launch for a gx x gy rectangle grid
 int block_threads(int W, int H, int gx, int gy);
 size_t run_smem_bytes(int threads);
 
 cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s);
-cudaError_t max_coresident_ctas(int threads, int* out);
+cudaError_t max_coresident_ctas(const Params& P, int threads, int* out);
 cudaError_t launch_dyn_hash(const Params& P, uint32_t cycle, unsigned long long* out,
                             cudaStream_t s);
 cudaError_t launch_state_hash(const Params& P, uint32_t cycle, unsigned long long* out,

@@ -4,17 +4,72 @@
 
 namespace noc {
 
-cudaError_t launch_run00(const Params& P, const RunArgs& A, cudaStream_t s);
-cudaError_t launch_run10(const Params& P, const RunArgs& A, cudaStream_t s);
-cudaError_t launch_run01(const Params& P, const RunArgs& A, cudaStream_t s);
-cudaError_t launch_run11(const Params& P, const RunArgs& A, cudaStream_t s);
+// ---------------------------------------------------------------- dispatch
+// Kernel variants shipped: per-cycle hash / drain records on or off, and the
+// compile-time way bounds (L1, L2) of the cache-set code: (4, 8), (4, 16) and
+// the general (16, 16).
+#define NOC_DECL_RUN(h, d, w1, w2) \
+  cudaError_t launch_run_##h##_##d##_##w1##_##w2(const Params&, const RunArgs&, cudaStream_t);
+#define NOC_DECL_WAYS(w1, w2)                                                   \
+  NOC_DECL_RUN(0, 0, w1, w2)                                                    \
+  NOC_DECL_RUN(1, 0, w1, w2)                                                    \
+  NOC_DECL_RUN(0, 1, w1, w2)                                                    \
+  NOC_DECL_RUN(1, 1, w1, w2)                                                    \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2(int threads, int* out);       \
+  cudaError_t launch_batch_##w1##_##w2(const BatchArgs&, int, int, cudaStream_t); \
+  cudaError_t max_coresident_batch_##w1##_##w2(int threads, int* out);
+NOC_DECL_WAYS(4, 8)
+NOC_DECL_WAYS(4, 16)
+NOC_DECL_WAYS(16, 16)
+
+// way-bound class of a configuration: 0 = (4, 8), 1 = (4, 16), 2 = (16, 16)
+static int way_class(int l1_ways, int l2_ways) {
+  if (l1_ways > 4) return 2;
+  return l2_ways <= 8 ? 0 : 1;
+}
+
+#define NOC_PICK_RUN(h, d)                                        \
+  switch (way_class(P.l1_ways, P.l2_ways)) {                      \
+    case 0: return launch_run_##h##_##d##_4_8(P, A, s);           \
+    case 1: return launch_run_##h##_##d##_4_16(P, A, s);          \
+    default: return launch_run_##h##_##d##_16_16(P, A, s);        \
+  }
 
 cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
-  if (A.hash_trace && A.busy) return launch_run11(P, A, s);
-  if (A.hash_trace) return launch_run10(P, A, s);
-  if (A.busy) return launch_run01(P, A, s);
-  return launch_run00(P, A, s);
+  if (A.hash_trace && A.busy) { NOC_PICK_RUN(1, 1) }
+  if (A.hash_trace) { NOC_PICK_RUN(1, 0) }
+  if (A.busy) { NOC_PICK_RUN(0, 1) }
+  NOC_PICK_RUN(0, 0)
 }
+
+cudaError_t max_coresident_ctas(const Params& P, int threads, int* out) {
+  switch (way_class(P.l1_ways, P.l2_ways)) {
+    case 0: return max_coresident_run_0_0_4_8(threads, out);
+    case 1: return max_coresident_run_0_0_4_16(threads, out);
+    default: return max_coresident_run_0_0_16_16(threads, out);
+  }
+}
+
+cudaError_t launch_batch(const BatchArgs& B, int grid, int threads, int l1_ways, int l2_ways,
+                         cudaStream_t s) {
+  switch (way_class(l1_ways, l2_ways)) {
+    case 0: return launch_batch_4_8(B, grid, threads, s);
+    case 1: return launch_batch_4_16(B, grid, threads, s);
+    default: return launch_batch_16_16(B, grid, threads, s);
+  }
+}
+
+cudaError_t max_coresident_batch(int l1_ways, int l2_ways, int threads, int* out) {
+  switch (way_class(l1_ways, l2_ways)) {
+    case 0: return max_coresident_batch_4_8(threads, out);
+    case 1: return max_coresident_batch_4_16(threads, out);
+    default: return max_coresident_batch_16_16(threads, out);
+  }
+}
+
+size_t run_smem_bytes(int threads) { return run_smem_bytes_impl(threads); }
+
+int block_threads(int W, int H, int gx, int gy) { return block_threads_impl(W, H, gx, gy); }
 
 // ---------------------------------------------------------------- hashes
 __global__ void dyn_hash_kernel(const Params P, uint32_t cycle, unsigned long long* out) {

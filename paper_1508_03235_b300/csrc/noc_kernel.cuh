@@ -164,7 +164,7 @@ inline int block_threads_impl(int W, int H, int gx, int gy) {
 }
 
 // One CTA runs rectangle b of one simulation for A.n cycles.
-template <bool HASH, bool DRAIN>
+template <bool HASH, bool DRAIN, int W1, int W2>
 __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, const int b,
                                          unsigned char* smem_raw) {
   const int nt = blockDim.x;
@@ -210,7 +210,7 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
     }
   }
   __syncthreads();
-  if (active) phase1(P, T, t0, A.draining != 0, sh_hist);
+  if (active) phase1<W1, W2>(P, T, t0, A.draining != 0, sh_hist);
 
   uint32_t t = t0;
   for (; t < tend; ++t) {
@@ -243,7 +243,7 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
     // to thread 0 by the barrier) before the flag
     if (i == 0 && !alone && b != A.silent_cta) st_release_u32(&P.flags[b], t + 1);
     // ---- Phase 3 of this cycle
-    if (active) phase3(P, T, t, sh_hist);
+    if (active) phase3<W1, W2>(P, T, t, sh_hist);
     if (HASH) {
       unsigned long long h = active ? tile_hash(T, out) : 0ull;
       h = block_sum(h, sh_red);
@@ -256,7 +256,7 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
     }
     if (t + 1 == tend) break;
     // ---- Phase 1 of the next cycle, then the neighbours' outputs of this one
-    if (active) phase1(P, T, t + 1, A.draining != 0, sh_hist);
+    if (active) phase1<W1, W2>(P, T, t + 1, A.draining != 0, sh_hist);
     // lanes 0..3 each wait for one neighbouring CTA (N, S, E, W)
     if (i < 4 && nbr[i] >= 0) {
       int w = wait_ge(&P.flags[nbr[i]], t + 1, A.abort_flag, A.wait_ns);
@@ -284,31 +284,45 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
     if (sh_hist[k]) atomicAdd(&P.hist[k], (unsigned long long)sh_hist[k]);
 }
 
-template <bool HASH, bool DRAIN>
+template <bool HASH, bool DRAIN, int W1, int W2>
 __global__ void __launch_bounds__(MAX_THREADS, 1)
     run_kernel(const __grid_constant__ Params P, const __grid_constant__ RunArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  run_rect<HASH, DRAIN>(P, A, blockIdx.x, smem_raw);
+  run_rect<HASH, DRAIN, W1, W2>(P, A, blockIdx.x, smem_raw);
 }
 
-template <bool H, bool D>
+template <bool H, bool D, int W1, int W2>
 static cudaError_t prepare_run() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(run_kernel<H, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(run_kernel<H, D, W1, W2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)run_smem_bytes_impl(MAX_THREADS));
   if (e == cudaSuccess) done = true;
   return e;
 }
 
-template <bool H, bool D>
+template <bool H, bool D, int W1, int W2>
 static cudaError_t launch_run_t(const Params& P, const RunArgs& A, cudaStream_t s) {
-  cudaError_t e = prepare_run<H, D>();
+  cudaError_t e = prepare_run<H, D, W1, W2>();
   if (e != cudaSuccess) return e;
   const int threads = block_threads_impl(P.W, P.H, A.gx, A.gy);
   void* args[] = {(void*)&P, (void*)&A};
-  return cudaLaunchCooperativeKernel((const void*)run_kernel<H, D>, dim3(A.gx * A.gy),
+  return cudaLaunchCooperativeKernel((const void*)run_kernel<H, D, W1, W2>, dim3(A.gx * A.gy),
                                      dim3(threads), args, run_smem_bytes_impl(threads), s);
+}
+
+template <int W1, int W2>
+static cudaError_t max_coresident_run_t(int threads, int* out) {
+  cudaError_t e = prepare_run<false, false, W1, W2>();
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, run_kernel<false, false, W1, W2>, threads,
+                                                    run_smem_bytes_impl(threads));
+  if (e != cudaSuccess) return e;
+  *out = per * sms;
+  return cudaSuccess;
 }
 
 }  // namespace noc

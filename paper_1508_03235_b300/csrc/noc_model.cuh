@@ -26,7 +26,7 @@ enum : int { ERR_OVERFLOW = 3, ERR_TIMEOUT = 4, ERR_PROTOCOL = 6 };
 constexpr uint32_t NO_TILE = 0xFFFFu;
 constexpr uint32_t DIR_NONE = 0xFFFFFFFFu;
 constexpr int HIST_BINS = 1025;
-constexpr int MAX_WAYS = 16;
+constexpr int MAX_WAYS = 16;  // most ways a cache may have
 constexpr int HIST_MAX = 30;  // longest access history kept per L2 way
 // u16 words per L2 way in the history array: [n, migrating, who x mig_window]
 inline int hist_stride(int mig_window) { return (mig_window + 3) & ~1; }
@@ -237,13 +237,15 @@ __device__ __forceinline__ bool cq_full(const Params& P, const Tile& T) {
 
 // ---------------------------------------------------------------- cache sets
 // A set's way words live in registers while it is worked on; the loops are
-// fully unrolled over MAX_WAYS so the array never leaves the register file.
-__device__ __forceinline__ void load_set(const uint32_t* p, int ways, uint32_t (&w)[MAX_WAYS]) {
+// fully unrolled over MW (a compile-time bound >= the configured ways, chosen
+// at launch) so the array never leaves the register file.
+template <int MW>
+__device__ __forceinline__ void load_set(const uint32_t* p, int ways, uint32_t (&w)[MW]) {
 #pragma unroll
-  for (int i = 0; i < MAX_WAYS; ++i) w[i] = 0;
+  for (int i = 0; i < MW; ++i) w[i] = 0;
   if ((ways & 3) == 0) {
 #pragma unroll
-    for (int q = 0; q < MAX_WAYS / 4; ++q)
+    for (int q = 0; q < MW / 4; ++q)
       if (q * 4 < ways) {
         uint4 v = reinterpret_cast<const uint4*>(p)[q];
         w[q * 4] = v.x;
@@ -253,19 +255,20 @@ __device__ __forceinline__ void load_set(const uint32_t* p, int ways, uint32_t (
       }
   } else {
 #pragma unroll
-    for (int i = 0; i < MAX_WAYS; ++i)
+    for (int i = 0; i < MW; ++i)
       if (i < ways) w[i] = p[i];
   }
 }
-__device__ __forceinline__ void store_set(uint32_t* p, int ways, const uint32_t (&w)[MAX_WAYS]) {
+template <int MW>
+__device__ __forceinline__ void store_set(uint32_t* p, int ways, const uint32_t (&w)[MW]) {
   if ((ways & 3) == 0) {
 #pragma unroll
-    for (int q = 0; q < MAX_WAYS / 4; ++q)
+    for (int q = 0; q < MW / 4; ++q)
       if (q * 4 < ways)
         reinterpret_cast<uint4*>(p)[q] = make_uint4(w[q * 4], w[q * 4 + 1], w[q * 4 + 2], w[q * 4 + 3]);
   } else {
 #pragma unroll
-    for (int i = 0; i < MAX_WAYS; ++i)
+    for (int i = 0; i < MW; ++i)
       if (i < ways) p[i] = w[i];
   }
 }
@@ -273,63 +276,71 @@ __device__ __forceinline__ uint32_t wrank(uint32_t v) { return (v >> W_RANK_SHIF
 __device__ __forceinline__ uint32_t wset_rank(uint32_t v, uint32_t r) {
   return (v & ~(15u << W_RANK_SHIFT)) | (r << W_RANK_SHIFT);
 }
-__device__ __forceinline__ int set_find(const uint32_t (&w)[MAX_WAYS], int ways, uint32_t line) {
+template <int MW>
+__device__ __forceinline__ int set_find(const uint32_t (&w)[MW], int ways, uint32_t line) {
   int found = -1;
 #pragma unroll
-  for (int i = MAX_WAYS - 1; i >= 0; --i)
+  for (int i = MW - 1; i >= 0; --i)
     if (i < ways && (w[i] & W_VALID) && (w[i] & W_LINE) == line) found = i;
   return found;
 }
 // make way `way` the most recently used; `prev_rank` is its rank before (the
 // number of valid ways for a way that was invalid)
-__device__ __forceinline__ void set_promote(uint32_t (&w)[MAX_WAYS], int ways, int way,
+template <int MW>
+__device__ __forceinline__ void set_promote(uint32_t (&w)[MW], int ways, int way,
                                             uint32_t prev_rank) {
 #pragma unroll
-  for (int i = 0; i < MAX_WAYS; ++i)
+  for (int i = 0; i < MW; ++i)
     if (i < ways && i != way && (w[i] & W_VALID) && wrank(w[i]) < prev_rank)
       w[i] = wset_rank(w[i], wrank(w[i]) + 1);
 #pragma unroll
-  for (int i = 0; i < MAX_WAYS; ++i)
+  for (int i = 0; i < MW; ++i)
     if (i == way) w[i] = wset_rank(w[i], 0);
 }
-__device__ __forceinline__ uint32_t set_get(const uint32_t (&w)[MAX_WAYS], int way) {
+template <int MW>
+__device__ __forceinline__ uint32_t set_get(const uint32_t (&w)[MW], int way) {
   uint32_t v = 0;
 #pragma unroll
-  for (int i = 0; i < MAX_WAYS; ++i)
+  for (int i = 0; i < MW; ++i)
     if (i == way) v = w[i];
   return v;
 }
-__device__ __forceinline__ void set_put(uint32_t (&w)[MAX_WAYS], int way, uint32_t v) {
+template <int MW>
+__device__ __forceinline__ void set_put(uint32_t (&w)[MW], int way, uint32_t v) {
 #pragma unroll
-  for (int i = 0; i < MAX_WAYS; ++i)
+  for (int i = 0; i < MW; ++i)
     if (i == way) w[i] = v;
 }
-__device__ __forceinline__ void set_touch(uint32_t (&w)[MAX_WAYS], int ways, int way) {
+template <int MW>
+__device__ __forceinline__ void set_touch(uint32_t (&w)[MW], int ways, int way) {
   set_promote(w, ways, way, wrank(set_get(w, way)));
 }
 // victim: lowest-index invalid way, else the least recently used way
-__device__ __forceinline__ int set_victim(const uint32_t (&w)[MAX_WAYS], int ways) {
+template <int MW>
+__device__ __forceinline__ int set_victim(const uint32_t (&w)[MW], int ways) {
   int inv = -1, lru = 0;
 #pragma unroll
-  for (int i = MAX_WAYS - 1; i >= 0; --i)
+  for (int i = MW - 1; i >= 0; --i)
     if (i < ways) {
       if (!(w[i] & W_VALID)) inv = i;
       else if (wrank(w[i]) == (uint32_t)(ways - 1)) lru = i;
     }
   return inv >= 0 ? inv : lru;
 }
-__device__ __forceinline__ uint32_t set_nvalid(const uint32_t (&w)[MAX_WAYS], int ways) {
+template <int MW>
+__device__ __forceinline__ uint32_t set_nvalid(const uint32_t (&w)[MW], int ways) {
   uint32_t n = 0;
 #pragma unroll
-  for (int i = 0; i < MAX_WAYS; ++i)
+  for (int i = 0; i < MW; ++i)
     if (i < ways && (w[i] & W_VALID)) n++;
   return n;
 }
 // remove way `way`; the ways it was more recent than move up one rank
-__device__ __forceinline__ void set_invalidate(uint32_t (&w)[MAX_WAYS], int ways, int way) {
+template <int MW>
+__device__ __forceinline__ void set_invalidate(uint32_t (&w)[MW], int ways, int way) {
   uint32_t rk = wrank(set_get(w, way));
 #pragma unroll
-  for (int i = 0; i < MAX_WAYS; ++i)
+  for (int i = 0; i < MW; ++i)
     if (i < ways && i != way && (w[i] & W_VALID) && wrank(w[i]) > rk)
       w[i] = wset_rank(w[i], wrank(w[i]) - 1);
   set_put(w, way, 0u);
@@ -343,10 +354,11 @@ __device__ __forceinline__ size_t l2_base(const Params& P, uint32_t r, uint32_t 
 }
 
 // fill the L1 with `line` (insert if absent, else touch); L1 victims are clean
+template <int W1>
 static __device__ void l1_fill(const Params& P, Tile& T, uint32_t line, uint32_t owner) {
   uint32_t set = l1_set(P, line);
   size_t base = l1_base(P, T.r, set);
-  uint32_t w[MAX_WAYS];
+  uint32_t w[W1];
   load_set(P.l1 + base, P.l1_ways, w);
   int way = set_find(w, P.l1_ways, line);
   if (way >= 0) {
@@ -378,10 +390,11 @@ static __device__ void send_dinv(const Params& P, Tile& T, uint32_t vline, uint3
 
 // install `line` in this tile's L2 slice: insert if absent (evicting the
 // victim), else touch; returns the way index
+template <int W2>
 static __device__ int l2_install(const Params& P, Tile& T, uint32_t line, uint32_t epoch, uint32_t t) {
   uint32_t set = l2_set(P, line);
   size_t base = l2_base(P, T.r, set);
-  uint32_t w[MAX_WAYS];
+  uint32_t w[W2];
   load_set(P.l2 + base, P.l2_ways, w);
   int way = set_find(w, P.l2_ways, line);
   if (way >= 0) {
@@ -411,10 +424,11 @@ static __device__ int l2_install(const Params& P, Tile& T, uint32_t line, uint32
 }
 
 // write-through performed at this tile's own slice
+template <int W2>
 static __device__ void local_wt(const Params& P, Tile& T, uint32_t line) {
   uint32_t set = l2_set(P, line);
   size_t base = l2_base(P, T.r, set);
-  uint32_t w[MAX_WAYS];
+  uint32_t w[W2];
   load_set(P.l2 + base, P.l2_ways, w);
   int way = set_find(w, P.l2_ways, line);
   if (way >= 0) {
@@ -460,17 +474,18 @@ __device__ __forceinline__ void set_om(Tile& T, uint32_t kind, uint32_t line, ui
 
 // ---------------------------------------------------------------- Phase 1
 // the L1 lookup of a reference; returns false if the action was not taken
+template <int W1, int W2>
 static __device__ bool l1_step(const Params& P, Tile& T, uint32_t t, uint32_t line, uint32_t write) {
   uint32_t set = l1_set(P, line);
   size_t base = l1_base(P, T.r, set);
-  uint32_t w[MAX_WAYS];
+  uint32_t w[W1];
   load_set(P.l1 + base, P.l1_ways, w);
   int way = set_find(w, P.l1_ways, line);
   if (way >= 0) {
     if (write) {
       uint32_t owner = P.l1own[base + way];
       if (owner == T.r) {
-        local_wt(P, T, line);
+        local_wt<W2>(P, T, line);
       } else if (owner == NO_TILE) {
         SMALL(S_MEMW)++;
       } else {
@@ -496,6 +511,7 @@ static __device__ bool l1_step(const Params& P, Tile& T, uint32_t t, uint32_t li
   return true;
 }
 
+template <int W1, int W2>
 static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* sh_hist) {
   const uint32_t line = T.fsm_line, start = T.fsm_start, write = T.fsm_write;
   const bool busy = T.om_kind != OM_NONE;
@@ -505,15 +521,15 @@ static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* s
   if (P.policy == POL_INTERLEAVED) {
     uint32_t h = home_of(P, line);
     if (h == T.r) {
-      uint32_t w[MAX_WAYS];
+      uint32_t w[W2];
       load_set(P.l2 + base, P.l2_ways, w);
       int way = set_find(w, P.l2_ways, line);
       if (way >= 0) {
         SMALL(S_L2H)++;
         set_touch(w, P.l2_ways, way);
         store_set(P.l2 + base, P.l2_ways, w);
-        l1_fill(P, T, line, T.r);
-        if (write) local_wt(P, T, line);
+        l1_fill<W1>(P, T, line, T.r);
+        if (write) local_wt<W2>(P, T, line);
         l2lat_sample(T, t, start, sh_hist);
         T.fsm = FSM_IDLE;
         return;
@@ -546,7 +562,7 @@ static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* s
   }
 
   // LSPD: the requester's own slice first (local placement, Sec. 3.3)
-  uint32_t w[MAX_WAYS];
+  uint32_t w[W2];
   load_set(P.l2 + base, P.l2_ways, w);
   int way = set_find(w, P.l2_ways, line);
   if (way >= 0) {
@@ -554,8 +570,8 @@ static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* s
     set_touch(w, P.l2_ways, way);
     store_set(P.l2 + base, P.l2_ways, w);
     if (P.policy == POL_MIGRATE) hist_push(P, base + way, T.r);
-    l1_fill(P, T, line, T.r);
-    if (write) local_wt(P, T, line);
+    l1_fill<W1>(P, T, line, T.r);
+    if (write) local_wt<W2>(P, T, line);
     l2lat_sample(T, t, start, sh_hist);
     T.fsm = FSM_IDLE;
     return;
@@ -649,22 +665,23 @@ static __device__ bool ref_of(const Params& P, uint32_t core, uint32_t k, uint32
 }
 
 // Phase 1; returns true if the core took an action this cycle
+template <int W1, int W2>
 static __device__ bool phase1(const Params& P, Tile& T, uint32_t t, bool draining, uint32_t* sh_hist) {
   // (i) memory returns at an interleaved home: install, then reply
   while (T.mq_len > 0 && T.mq_front.x <= t) {
     uint32_t line = T.mq_front.y, req = T.mq_front.z;
     mq_pop(P, T);
-    l2_install(P, T, line, 0, t);
+    l2_install<W2>(P, T, line, 0, t);
     send_svc(P, T, mkflit(T_DATA, T.r, req, line, 0, 0), t);
   }
   // (ii) this core's outstanding memory fetch completes
   if ((T.om_kind == OM_MEM_L2 || T.om_kind == OM_MEM_L1) && T.om_timer <= t) {
     if (T.om_kind == OM_MEM_L2) {
-      l2_install(P, T, T.om_line, T.om_epoch, t);
-      l1_fill(P, T, T.om_line, T.r);
-      if (T.om_write) local_wt(P, T, T.om_line);
+      l2_install<W2>(P, T, T.om_line, T.om_epoch, t);
+      l1_fill<W1>(P, T, T.om_line, T.r);
+      if (T.om_write) local_wt<W2>(P, T, T.om_line);
     } else {
-      l1_fill(P, T, T.om_line, NO_TILE);
+      l1_fill<W1>(P, T, T.om_line, NO_TILE);
       if (T.om_write) SMALL(S_MEMW)++;
     }
     l2lat_sample(T, t, T.om_start, sh_hist);
@@ -673,12 +690,12 @@ static __device__ bool phase1(const Params& P, Tile& T, uint32_t t, bool drainin
   // (iii) at most one core action
   if (T.fsm == FSM_L2WAIT) {
     if (t < T.fsm_timer) return false;
-    l2_step(P, T, t, sh_hist);
+    l2_step<W1, W2>(P, T, t, sh_hist);
     return true;
   }
   if (T.fsm == FSM_STALL) {
     if (T.om_kind != OM_NONE) return false;
-    l1_step(P, T, t, T.fsm_line, T.fsm_write);
+    l1_step<W1, W2>(P, T, t, T.fsm_line, T.fsm_write);
     return true;
   }
   if (draining || P.period <= 0) return false;
@@ -709,7 +726,7 @@ static __device__ bool phase1(const Params& P, Tile& T, uint32_t t, bool drainin
     T.pf_write = write;
     T.pf_ok = 1;
   }
-  if (l1_step(P, T, t, line, write)) {
+  if (l1_step<W1, W2>(P, T, t, line, write)) {
     T.next_ref++;
     SMALL(S_REFS)++;
     T.pf_ok = 0;
@@ -819,6 +836,7 @@ __device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint
 }
 
 // ---------------------------------------------------------------- Phase 3
+template <int W1, int W2>
 static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh_hist) {
   uint4 f = T.ej;
   uint32_t ty = ftype(f);
@@ -839,7 +857,7 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
     case T_REQ: {
       uint32_t q = fa(f);
       SMALL(S_REQR)++;
-      uint32_t w[MAX_WAYS];
+      uint32_t w[W2];
       load_set(P.l2 + base, P.l2_ways, w);
       int way = set_find(w, P.l2_ways, line);
       if (way >= 0) {
@@ -903,14 +921,14 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
         set_error(P, t, ERR_PROTOCOL);
         break;
       }
-      l1_fill(P, T, line, fsrc(f));
+      l1_fill<W1>(P, T, line, fsrc(f));
       if (T.om_write) send_svc(P, T, mkflit(T_WT, T.r, fsrc(f), line, 0, 0), t);
       l2lat_sample(T, t, T.om_start, sh_hist);
       set_om(T, OM_NONE, 0, 0, 0);
       break;
 
     case T_WT: {
-      uint32_t w[MAX_WAYS];
+      uint32_t w[W2];
       load_set(P.l2 + base, P.l2_ways, w);
       int way = set_find(w, P.l2_ways, line);
       if (way >= 0) {
@@ -976,7 +994,7 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
     case T_MIG: {
       uint32_t o = fsrc(f);
       T.epoch = (T.epoch + 1) & 0xFFFFu;
-      int way = l2_install(P, T, line, T.epoch, t);
+      int way = l2_install<W2>(P, T, line, T.epoch, t);
       uint16_t* hp = hist_ptr(P, base + way);
       hp[0] = 0;
       hp[1] = 0;
@@ -1007,7 +1025,7 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
         m = fa(f);
       }
       // invalidate the source copy and remember where the block went
-      uint32_t w[MAX_WAYS];
+      uint32_t w[W2];
       load_set(P.l2 + base, P.l2_ways, w);
       int way = set_find(w, P.l2_ways, line);
       if (way >= 0) {

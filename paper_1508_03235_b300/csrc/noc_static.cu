@@ -166,7 +166,7 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
     int tx = (mesh_w + side - 1) / side, ty = (mesh_h + side - 1) / side;
     int threads = block_threads(mesh_w, mesh_h, tx, ty), cap = 0;
     if (threads > 384 || (size_t)tx * ty > n_flags) continue;
-    if (max_coresident_ctas(threads, &cap) != cudaSuccess) return NOC_ERR_CUDA;
+    if (max_coresident_ctas(P, threads, &cap) != cudaSuccess) return NOC_ERR_CUDA;
     if (tx * ty <= cap) {
       gx = tx;
       gy = ty;

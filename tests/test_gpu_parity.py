@@ -236,3 +236,15 @@ def test_bounded_wait_times_out(noc):
     h = noc.Sim(I.MESH_8["params"])
     h.step(100)
     assert h.stats()["cycle"] == 100
+
+
+def test_general_way_bounds(noc, oracle_mod):
+    """8-way L1 and 16-way L2 run the general (16, 16) kernel variant."""
+    cache = I.cache_cfg(l1_kb=4, l1_ways=8, l2_kb=16, l2_ways=16, mig_window=6, mig_threshold=3)
+    traf = I.traffic(period=3, priv=0.4, shared=0.5, shared_mb=0)
+    traf.update(shared_lines=900)
+    for policy in (0, 2):
+        p = I.sim_params(7, 6, policy=policy, cache=cache, traf=traf, seed=13)
+        g, o = pair(noc, oracle_mod, p, tiling=(2, 2))
+        run_traced(g, o, 1500)
+        assert_same(g, o)
