@@ -14,7 +14,7 @@ WAY_BOUNDS = ((4, 8), (4, 16), (16, 16))
 UNITS = ([("noc_run_variant.cu", {"NOC_HASH": h, "NOC_DRAIN": d, "NOC_W1": w1, "NOC_W2": w2})
           for (w1, w2) in WAY_BOUNDS for h in (0, 1) for d in (0, 1)]
          + [("noc_batch.cu", {"NOC_W1": w1, "NOC_W2": w2}) for (w1, w2) in WAY_BOUNDS]
-         + [("noc_kernel.cu", {}), ("noc_api.cu", {}), ("noc_static.cu", {})])
+         + [("noc_kernel.cu", {}), ("noc_api.cu", {}), ("noc_static.cu", {}), ("mlp.cu", {})])
 SOURCES = sorted({u[0] for u in UNITS})
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

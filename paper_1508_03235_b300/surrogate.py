@@ -1,0 +1,242 @@
+"""The learned surrogate: a BF16 MLP trained on the batch simulator's outputs.
+
+Inputs (10, padded to 16): mesh side, injection period, private / shared /
+remote address fractions, write fraction, private working set (KB), L2 policy
+one-hot (interleaved, LSPD-local, LSPD-migrate).  Outputs (3, padded to 16):
+log mean L2 access latency, deflections per flit, accepted flits per node per
+cycle -- each computed from a simulation's counters (metric definitions in
+the model text).  Network: 16 -> 256 -> 256 -> 256 -> 256 -> 16, GELU,
+trained with AdamW on the standardised outputs by the library's own tensor-core
+forward / backward kernels (include/mlp.h); torch only holds the buffers.
+
+The exact simulator is both the training-data source and the judge: the
+relative error of each output against fresh simulations is reported with the
+epsilon floors of the model text (0.01 deflections/flit, 1e-3 flits/node/cycle,
+latency on its natural scale).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import inputs as I
+from . import noc
+
+DIMS = (16, 256, 256, 256, 256, 16)
+N_IN, N_OUT = 10, 3
+OUT_NAMES = ("log_l2_latency", "deflections_per_flit", "accepted_per_node_cycle")
+EPS_FLOOR = (None, 0.01, 1e-3)
+
+
+class Shape(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("dims", C.c_int32 * 9)]
+
+
+def _mlp_lib():
+    L = noc.lib()
+    if not getattr(L, "_mlp_sigs", False):
+        vp, i32, sz = C.c_void_p, C.c_int, C.c_size_t
+        f = C.c_float
+        for name, res, args in (
+            ("mlp_param_count", sz, [C.POINTER(Shape)]),
+            ("mlp_workspace_bytes", sz, [C.POINTER(Shape), i32]),
+            ("mlp_forward", i32, [C.POINTER(Shape), vp, vp, i32, vp, vp, vp]),
+            ("mlp_backward", i32, [C.POINTER(Shape), vp, vp, i32, vp, vp, vp, vp]),
+            ("mlp_mse", i32, [vp, vp, i32, i32, i32, vp, vp, vp]),
+            ("mlp_adamw", i32, [sz, vp, vp, vp, vp, vp, f, f, f, f, f, i32, vp]),
+            ("mlp_to_bf16", i32, [vp, vp, sz, vp]),
+        ):
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        L._mlp_sigs = True
+    return L
+
+
+def _ok(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"{what} failed with status {rc}")
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class MLP:
+    """Parameters, AdamW state and workspaces on the current CUDA device."""
+
+    def __init__(self, dims=DIMS, seed=0, max_batch=4096):
+        import torch
+        self.torch = torch
+        self.dims = tuple(dims)
+        self.shape = Shape()
+        self.shape.n_layers = len(dims) - 1
+        for i, d in enumerate(dims):
+            self.shape.dims[i] = d
+        L = _mlp_lib()
+        self.n = L.mlp_param_count(C.byref(self.shape))
+        g = torch.Generator().manual_seed(seed)
+        parts = []
+        for l in range(len(dims) - 1):
+            k, n = dims[l], dims[l + 1]
+            bound = math.sqrt(6.0 / k) if l < len(dims) - 2 else math.sqrt(1.0 / k)
+            parts.append((torch.rand(n * k, generator=g, dtype=torch.float64) * 2 - 1) * bound)
+            parts.append(torch.zeros(n, dtype=torch.float64))
+        self.params = torch.cat(parts).float().cuda()
+        assert self.params.numel() == self.n
+        self.params_bf16 = torch.empty(self.n, dtype=torch.bfloat16, device="cuda")
+        self.grads = torch.zeros(self.n, dtype=torch.float32, device="cuda")
+        self.m = torch.zeros_like(self.grads)
+        self.v = torch.zeros_like(self.grads)
+        self.step = 0
+        self.max_batch = max_batch
+        self.ws = torch.empty(L.mlp_workspace_bytes(C.byref(self.shape), max_batch) + 256,
+                              dtype=torch.uint8, device="cuda")
+        self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        self.sync_bf16()
+
+    def _stream(self):
+        return C.c_void_p(self.torch.cuda.current_stream().cuda_stream)
+
+    def _ws(self):
+        p = self.ws.data_ptr()
+        return C.c_void_p(p + (-p) % 256)
+
+    def sync_bf16(self):
+        _ok(_mlp_lib().mlp_to_bf16(_p(self.params), _p(self.params_bf16), self.n, self._stream()),
+            "mlp_to_bf16")
+
+    def load_params(self, flat):
+        self.params.copy_(self.torch.as_tensor(flat, dtype=self.torch.float32))
+        self.sync_bf16()
+
+    def forward(self, xb):
+        """xb: BF16 [B, dims[0]] CUDA tensor -> FP32 [B, dims[-1]]."""
+        B = xb.shape[0]
+        assert B <= self.max_batch and xb.dtype == self.torch.bfloat16
+        y = self.torch.empty(B, self.dims[-1], dtype=self.torch.float32, device="cuda")
+        _ok(_mlp_lib().mlp_forward(C.byref(self.shape), _p(self.params_bf16), _p(xb), B, _p(y),
+                                   self._ws(), self._stream()), "mlp_forward")
+        return y
+
+    def backward(self, xb, dy):
+        _ok(_mlp_lib().mlp_backward(C.byref(self.shape), _p(self.params_bf16), _p(xb),
+                                    xb.shape[0], _p(dy), _p(self.grads), self._ws(),
+                                    self._stream()), "mlp_backward")
+        return self.grads
+
+    def mse(self, y, t, used):
+        dy = self.torch.empty_like(y)
+        _ok(_mlp_lib().mlp_mse(_p(y), _p(t), y.shape[0], y.shape[1], used, _p(self.loss), _p(dy),
+                               self._stream()), "mlp_mse")
+        return self.loss, dy
+
+    def adamw(self, lr, b1=0.9, b2=0.999, eps=1e-8, wd=1e-4):
+        self.step += 1
+        _ok(_mlp_lib().mlp_adamw(self.n, _p(self.params), _p(self.params_bf16), _p(self.grads),
+                                 _p(self.m), _p(self.v), lr, b1, b2, eps, wd, self.step,
+                                 self._stream()), "mlp_adamw")
+
+    def train_step(self, xb, tb, lr):
+        y = self.forward(xb)
+        loss, dy = self.mse(y, tb, N_OUT)
+        self.backward(xb, dy)
+        self.adamw(lr)
+        return loss
+
+
+# ----------------------------------------------------------------- data
+def features(design: dict) -> np.ndarray:
+    d = design
+    f = np.zeros(DIMS[0], dtype=np.float32)
+    f[0] = d["side"] / 128.0
+    f[1] = d["period"] / 40.0
+    f[2], f[3], f[4] = d["priv"], d["shared"], d["remote"]
+    f[5] = d["write"]
+    f[6] = d["ws_kb"] / 64.0
+    f[7 + d["policy"]] = 1.0
+    return f
+
+
+def targets(stats: dict, tiles: int) -> np.ndarray:
+    """(log mean L2 access latency, deflections per flit, accepted throughput)."""
+    lat = stats["l2lat_sum"] / max(stats["l2lat_cnt"], 1)
+    defl = stats["deflections"] / max(stats["ejected"], 1)
+    acc = stats["ejected"] / (tiles * max(stats["cycle"], 1))
+    return np.array([math.log(max(lat, 1e-9)), defl, acc], dtype=np.float64)
+
+
+def simulate(designs_params, cycles, rect=8):
+    """Exact outputs of design points through the batch engine."""
+    b = noc.Batch([{k: v for k, v in p.items() if k != "design"} for p in designs_params], cycles,
+                  rect=rect, collect_hash=False)
+    b.run()
+    ys = np.stack([targets(b.stats(i), p["mesh_w"] * p["mesh_h"])
+                   for i, p in enumerate(designs_params)])
+    b.close()
+    return ys
+
+
+def make_dataset(n, cycles, seed=0, **kw):
+    pts = I.batch_design_points(n, seed=seed, **kw)
+    X = np.stack([features(p["design"]) for p in pts])
+    Y = simulate(pts, cycles)
+    return X, Y, pts
+
+
+def relative_errors(pred, true):
+    """Per-output relative error with the model text's epsilon floors; latency
+    is compared on its natural (not log) scale."""
+    err = np.empty_like(true)
+    lp, lt = np.exp(pred[:, 0]), np.exp(true[:, 0])
+    err[:, 0] = np.abs(lp - lt) / np.abs(lt)
+    for j in (1, 2):
+        err[:, j] = np.abs(pred[:, j] - true[:, j]) / np.maximum(np.abs(true[:, j]), EPS_FLOOR[j])
+    return err
+
+
+class Surrogate:
+    """Standardisation + MLP + training loop."""
+
+    def __init__(self, seed=0, max_batch=4096):
+        self.net = MLP(seed=seed, max_batch=max_batch)
+        self.torch = self.net.torch
+        self.mu = np.zeros(N_OUT)
+        self.sd = np.ones(N_OUT)
+
+    def _x(self, X):
+        return self.torch.as_tensor(X, dtype=self.torch.float32).cuda().to(self.torch.bfloat16)
+
+    def fit(self, X, Y, epochs=200, batch=1024, lr=2e-3, seed=0, verbose=False):
+        torch = self.torch
+        self.mu = Y.mean(axis=0)
+        self.sd = Y.std(axis=0) + 1e-12
+        T = np.zeros((len(Y), DIMS[-1]), dtype=np.float32)
+        T[:, :N_OUT] = (Y - self.mu) / self.sd
+        xs = self._x(X)
+        ts = torch.as_tensor(T).cuda()
+        g = torch.Generator(device="cuda").manual_seed(seed)
+        n = len(X)
+        steps = 0
+        total = epochs * max(1, n // batch)
+        for ep in range(epochs):
+            perm = torch.randperm(n, device="cuda", generator=g)
+            for s in range(0, n - batch + 1, batch):
+                idx = perm[s:s + batch]
+                frac = steps / max(total, 1)
+                cur = lr * 0.5 * (1 + math.cos(math.pi * frac))     # cosine decay
+                loss = self.net.train_step(xs[idx].contiguous(), ts[idx].contiguous(), cur)
+                steps += 1
+            if verbose and (ep % max(1, epochs // 10) == 0 or ep == epochs - 1):
+                print(f"  epoch {ep}: loss {float(loss.item()):.5f}", flush=True)
+        return float(loss.item())
+
+    def predict(self, X):
+        out = []
+        for s in range(0, len(X), self.net.max_batch):
+            y = self.net.forward(self._x(X[s:s + self.net.max_batch]))
+            out.append(y[:, :N_OUT].double().cpu().numpy())
+        Z = np.concatenate(out)
+        return Z * self.sd + self.mu

@@ -1,0 +1,112 @@
+"""The surrogate's tensor-core kernels against the fp64 oracle (oracle/
+mlp_oracle.py, which rounds weights and activations to BF16 as the network
+stores them): forward outputs, parameter gradients, the MSE loss, AdamW; then
+training convergence and a small end-to-end surrogate of the simulator.
+
+Tolerances: the GPU accumulates in FP32 and rounds each activation to BF16; a
+pre-activation that differs from the fp64 value by FP32 rounding can land in
+the neighbouring BF16 step (2^-8 relative), so outputs and gradients are
+compared by relative norm at 1e-2 and element-wise at a few BF16 steps."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sur():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_03235_b300 import surrogate
+    return surrogate
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+@pytest.mark.parametrize("B", [300, 64, 1])
+def test_forward_and_gradients_match_oracle(sur, B):
+    import torch
+    net = sur.MLP(seed=5, max_batch=512)
+    rng = np.random.default_rng(B)
+    x = rng.normal(size=(B, 16)).astype(np.float32)
+    xb = torch.as_tensor(x).cuda().to(torch.bfloat16)
+    y = net.forward(xb).double().cpu().numpy()
+    p = net.params.double().cpu().numpy()
+    want, _ = M.forward(list(sur.DIMS), p, x)
+    assert rel(y, want) < 1e-2
+    assert np.allclose(y, want, rtol=3e-2, atol=3e-2 * np.abs(want).max())
+    dy = rng.normal(size=(B, 16)).astype(np.float32)
+    g = net.backward(xb, torch.as_tensor(dy).cuda()).double().cpu().numpy()
+    gw = M.backward(list(sur.DIMS), p, x, dy.astype(np.float64))
+    off = 0
+    for l in range(len(sur.DIMS) - 1):
+        n, k = sur.DIMS[l + 1], sur.DIMS[l]
+        for size in (n * k, n):
+            a, b = g[off:off + size], gw[off:off + size]
+            assert rel(a, b) < 2e-2, (l, size)
+            off += size
+
+
+def test_mse_and_adamw_match_oracle(sur):
+    import torch
+    net = sur.MLP(seed=1, max_batch=128)
+    rng = np.random.default_rng(7)
+    y = rng.normal(size=(100, 16)).astype(np.float32)
+    t = rng.normal(size=(100, 16)).astype(np.float32)
+    loss, dy = net.mse(torch.as_tensor(y).cuda(), torch.as_tensor(t).cuda(), 3)
+    wl, wdy = M.mse(y, t, 3)
+    assert abs(loss.item() - wl) < 1e-5 * wl
+    assert np.allclose(dy.cpu().numpy(), wdy, rtol=1e-5, atol=1e-9)
+    p = net.params.double().cpu().numpy()
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for step in range(1, 4):
+        g = rng.normal(size=p.size).astype(np.float32)
+        net.grads.copy_(torch.as_tensor(g))
+        net.adamw(1e-3, wd=0.01)
+        p, m, v = M.adamw(p, g.astype(np.float64), m, v, 1e-3, 0.9, 0.999, 1e-8, 0.01, step)
+    got = net.params.double().cpu().numpy()
+    assert np.allclose(got, p, rtol=1e-5, atol=1e-6)
+    assert np.array_equal(net.params_bf16.float().cpu().numpy(),
+                          M.bf16_round(net.params.cpu().numpy()).astype(np.float32))
+
+
+def test_training_fits_a_smooth_function(sur):
+    import torch
+    s = sur.Surrogate(seed=3, max_batch=1024)
+    rng = np.random.default_rng(0)
+    X = np.zeros((4096, 16), dtype=np.float32)
+    X[:, :10] = rng.uniform(-1, 1, size=(4096, 10))
+    Y = np.stack([np.sin(2 * X[:, 0]) + X[:, 1] * X[:, 2], X[:, 3] ** 2 - X[:, 4],
+                  np.exp(0.5 * X[:, 5])], axis=1)
+    first = s.fit(X, Y, epochs=1, batch=512, lr=2e-3)
+    last = s.fit(X, Y, epochs=60, batch=512, lr=2e-3)
+    assert last < 0.1 * first
+    pred = s.predict(X[:512])
+    assert np.abs(pred - Y[:512]).mean() < 0.1
+
+
+def test_small_surrogate_of_the_simulator_and_screening(sur):
+    """Train on simulated design points, judge on fresh simulations, and show
+    what screening with the network gains over random screening at the same
+    simulation budget (the lowest mean L2 access latency found)."""
+    kw = dict(sides=(8, 16, 24), period_lo=2, period_hi=40)
+    X, Y, _ = sur.make_dataset(600, 3000, seed=1, **kw)
+    s = sur.Surrogate(seed=0, max_batch=1024)
+    s.fit(X, Y, epochs=150, batch=128, lr=2e-3)
+    Xh, Yh, _ = sur.make_dataset(100, 3000, seed=2, **kw)
+    err = sur.relative_errors(s.predict(Xh), Yh)
+    assert err.mean(axis=0).max() < 0.35
+    # screening: 400 candidates, simulate 10 chosen by the network vs 10 random
+    Xc, _, pc = sur.make_dataset(400, 1, seed=3, **kw)
+    pred = s.predict(Xc)
+    top = np.argsort(pred[:, 0])[:10]
+    rnd = np.random.default_rng(9).choice(400, size=10, replace=False)
+    y_top = sur.simulate([pc[i] for i in top], 3000)
+    y_rnd = sur.simulate([pc[i] for i in rnd], 3000)
+    assert y_top[:, 0].min() < y_rnd[:, 0].min()
