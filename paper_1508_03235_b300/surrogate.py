@@ -240,3 +240,80 @@ class Surrogate:
             out.append(y[:, :N_OUT].double().cpu().numpy())
         Z = np.concatenate(out)
         return Z * self.sd + self.mu
+
+
+# ----------------------------------------------------------------- full run
+def run(points=50_000, holdout=5_000, cycles=20_000, chunk=2_000, epochs=300, batch=1024,
+        lr=2e-3, data_path=None, seed=0, log=print):
+    """Simulate `points` design points with the batch engine, train on all but
+    `holdout`, judge the held-out ones against their exact simulations, and time
+    batch-4096 inference against the batched simulator."""
+    import json
+    import time
+
+    import torch
+
+    t0 = time.perf_counter()
+    Xs, Ys = [], []
+    pts_all = I.batch_design_points(points, seed=seed)
+    sim_s = 0.0
+    for s in range(0, points, chunk):
+        pts = pts_all[s:s + chunk]
+        a = time.perf_counter()
+        Ys.append(simulate(pts, cycles))
+        sim_s += time.perf_counter() - a
+        Xs.append(np.stack([features(p["design"]) for p in pts]))
+        log(f"simulated {min(s + chunk, points)}/{points} design points ({sim_s:.0f} s)")
+    X, Y = np.concatenate(Xs), np.concatenate(Ys)
+    if data_path:
+        np.savez_compressed(data_path, X=X, Y=Y, cycles=cycles, seed=seed)
+    ntr = points - holdout
+    model = Surrogate(seed=seed, max_batch=4096)
+    a = time.perf_counter()
+    loss = model.fit(X[:ntr], Y[:ntr], epochs=epochs, batch=batch, lr=lr)
+    train_s = time.perf_counter() - a
+    err = relative_errors(model.predict(X[ntr:]), Y[ntr:])
+    mre = err.mean(axis=0)
+    # inference throughput at batch 4096 (device time, CUDA events)
+    xb = model._x(np.tile(X[:4096], (max(1, 4096 // min(4096, len(X))), 1))[:4096])
+    for _ in range(5):
+        model.net.forward(xb)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 200
+    e0.record()
+    for _ in range(reps):
+        model.net.forward(xb)
+    e1.record()
+    torch.cuda.synchronize()
+    inf_pts_s = reps * 4096 / (e0.elapsed_time(e1) / 1e3)
+    sim_pts_s = points / sim_s
+    res = {"points": points, "holdout": holdout, "cycles": cycles, "train_loss": loss,
+           "train_s": train_s, "simulate_s": sim_s, "mre": dict(zip(OUT_NAMES, map(float, mre))),
+           "mre_max": float(mre.max()), "p90_rel_err": dict(zip(OUT_NAMES, map(float, np.quantile(err, 0.9, axis=0)))),
+           "inference_points_per_s": inf_pts_s, "simulator_points_per_s": sim_pts_s,
+           "speedup": inf_pts_s / sim_pts_s, "epochs": epochs, "batch": batch, "lr": lr,
+           "wall_s": time.perf_counter() - t0}
+    log(json.dumps(res))
+    return res, model
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    ap = argparse.ArgumentParser(description="simulate, train and judge the surrogate")
+    ap.add_argument("--points", type=int, default=50_000)
+    ap.add_argument("--holdout", type=int, default=5_000)
+    ap.add_argument("--cycles", type=int, default=20_000)
+    ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--data", default=None, help="save the simulated dataset (.npz)")
+    ap.add_argument("--out", default=None, help="write the result JSON here")
+    a = ap.parse_args()
+    from paper_1508_03235_b300 import surrogate as S
+    res, _ = S.run(points=a.points, holdout=a.holdout, cycles=a.cycles, epochs=a.epochs,
+                   data_path=a.data, log=lambda m: print(m, flush=True))
+    if a.out:
+        with open(a.out, "w") as f:
+            json.dump(res, f, indent=1)
