@@ -216,6 +216,11 @@ def run_gpu(args):
     h2d = len(PERIODS) * (ctypes.sizeof(CacheCfg) + ctypes.sizeof(Traffic))
     d2h = len(PERIODS) * ctypes.sizeof(Stats)
 
+    batch = surrogate = None
+    if not args.no_batch:
+        batch = batch_section(args.batch_n, args.batch_cycles, args.batch_rect)
+        surrogate = surrogate_section()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cycles_per_period=args.cpu_cycles)
@@ -237,11 +242,76 @@ def run_gpu(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": gpu_launches,
             "clocks": clk,
+            "batch": batch,
+            "surrogate": surrogate,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------- batch + surrogate
+def batch_section(n, cycles, rect):
+    """The batched-engine half of the metric: n independent design points
+    (mixed sizes, loads, mixes and L2 policies) in one persistent launch per
+    memory wave, against the same instances run one at a time through the
+    single-simulation path on the same GPU."""
+    import torch
+
+    from paper_1508_03235_b300 import noc
+    pts = I.batch_design_points(n, seed=0)
+    for p in pts:
+        p.pop("design")
+    tiles = sum(p["mesh_w"] * p["mesh_h"] for p in pts)
+    b = noc.Batch(pts, cycles, rect=rect, collect_hash=False)
+    b.run()                                   # warm-up (also checks every instance)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.run()
+    tb = time.perf_counter() - t0
+    waves, launches = b.waves, b.launches
+    b.close()
+    sims = [noc.Sim(p) for p in pts]
+    for s in sims[:2]:
+        s.step(100)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in sims:
+        s.reset()
+        s.step_async(cycles)
+        s.stats()
+    t1 = time.perf_counter() - t0
+    for s in sims:
+        s.close()
+    return {"instances": n, "cycles": cycles, "rect": rect, "waves": waves,
+            "batched_sims_per_s": n / tb, "one_at_a_time_sims_per_s": n / t1,
+            "speedup": t1 / tb, "batched_router_cycles_per_s": tiles * cycles / tb,
+            "one_at_a_time_router_cycles_per_s": tiles * cycles / t1,
+            "workload": "design points: side U{8..128}, period U{2..40}, Dirichlet(2,2,1) "
+                        "private/shared/remote, policy U{interleaved, LSPD, LSPD+migration}"}
+
+
+def surrogate_section(reps=200):
+    """Design points per second of the surrogate's tensor-core forward pass at
+    batch 4096 (device time)."""
+    import torch
+
+    from paper_1508_03235_b300 import surrogate as S
+    net = S.MLP(seed=0, max_batch=4096)
+    xb = torch.rand(4096, S.DIMS[0], device="cuda").to(torch.bfloat16)
+    for _ in range(10):
+        net.forward(xb)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        net.forward(xb)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    flops = 2 * 4096 * sum(S.DIMS[l] * S.DIMS[l + 1] for l in range(len(S.DIMS) - 1))
+    return {"batch": 4096, "design_points_per_s": reps * 4096 / sec,
+            "tflops": reps * flops / sec / 1e12, "network": list(S.DIMS)}
 
 
 # --------------------------------------------------------------------- CPU arms
@@ -310,6 +380,10 @@ def main():
     ap.add_argument("--cpu-cycles", type=int, default=400)
     ap.add_argument("--ref-cycles", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-n", type=int, default=64)
+    ap.add_argument("--batch-cycles", type=int, default=20_000)
+    ap.add_argument("--batch-rect", type=int, default=19)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
