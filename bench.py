@@ -185,12 +185,8 @@ def run_gpu(args):
         s.sync()
     ms = t_start.elapsed_time(t_end)
     gpu_launches = sum(s.launches for s in sims) - launches0
-    if world > 1:
-        tm = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ms = float(tm.item())
     rc_per_rank = args.steps * len(PERIODS) * TILES * cycles
-    value = rc_per_rank * world / (ms / 1e3)
+    ms, value = replica_throughput(ms, rc_per_rank, world, device="cuda")
 
     # roofline of the cycle kernel: algorithmic bytes / its event-timed duration
     launch_ms = [a.elapsed_time(b) for a, b in records]
@@ -249,6 +245,18 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def replica_throughput(ms, units_per_rank, world, device="cpu"):
+    """Whole-job throughput of `world` independent replicas: every rank did
+    `units_per_rank` units; the job took the slowest rank's time."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tm = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms = float(tm.item())
+    return ms, units_per_rank * world / (ms / 1e3)
 
 
 # --------------------------------------------------------------------- batch + surrogate
