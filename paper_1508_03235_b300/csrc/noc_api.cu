@@ -53,7 +53,8 @@ struct noc_sim {
   uint64_t seed;
   // arena layout (byte offsets)
   size_t o_glink, o_core, o_cq, o_sq, o_mq, o_l1, o_l1own, o_l2, o_l2ep, o_l2hist, o_dir, o_fwd,
-      o_stats, o_hist, o_flags, o_err, o_abort, o_scratch, bytes;
+      o_stats, o_hist, o_flags, o_err, o_abort, o_scratch, o_refbuf, o_refk0, o_refcnt, bytes;
+  int refcap = 512;              // references drawn ahead per tile (0 = draw in place)
   size_t n_flags;
   unsigned char* base = nullptr;
   bool owned = false;
@@ -115,6 +116,9 @@ void layout(noc_sim* s) {
   s->o_err = take(sizeof(unsigned long long));
   s->o_abort = take(sizeof(unsigned int));
   s->o_scratch = take(64 * sizeof(unsigned long long));
+  s->o_refbuf = take(N * (size_t)s->refcap * sizeof(uint32_t));
+  s->o_refk0 = take(s->refcap ? N * sizeof(uint32_t) : 0);
+  s->o_refcnt = take(s->refcap ? N * sizeof(uint32_t) : 0);
   s->bytes = align256(cur);
 }
 
@@ -138,6 +142,10 @@ void set_pointers(noc_sim* s) {
   P.hist = reinterpret_cast<unsigned long long*>(b + s->o_hist);
   P.flags = reinterpret_cast<unsigned int*>(b + s->o_flags);
   P.err = reinterpret_cast<unsigned long long*>(b + s->o_err);
+  P.refcap = s->refcap;
+  P.refbuf = s->refcap ? reinterpret_cast<uint32_t*>(b + s->o_refbuf) : nullptr;
+  P.refk0 = s->refcap ? reinterpret_cast<uint32_t*>(b + s->o_refk0) : nullptr;
+  P.refcnt = s->refcap ? reinterpret_cast<uint32_t*>(b + s->o_refcnt) : nullptr;
 }
 
 unsigned int* abort_ptr(noc_sim* s) { return reinterpret_cast<unsigned int*>(s->base + s->o_abort); }
@@ -165,6 +173,7 @@ int do_reset(noc_sim* s) {
   CU(cudaMemsetAsync(P.flags, 0, s->n_flags * 4, st), "reset flags");
   CU(cudaMemsetAsync(P.err, 0xFF, 8, st), "reset error word");
   CU(cudaMemsetAsync(abort_ptr(s), 0, 4, st), "reset abort flag");
+  if (P.refcnt) CU(cudaMemsetAsync(P.refcnt, 0, N * 4, st), "reset reference window");
   s->cycle = 0;
   s->hash_n = 0;
   s->draining = false;
@@ -285,9 +294,18 @@ int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
   CU(max_coresident_ctas(s->P, threads, &cap), "occupancy");
   if (threads > 384 || s->run_gx * s->run_gy > cap || s->run_gx * s->run_gy > (int)s->n_flags)
     return fail(NOC_ERR_ARG, "tiling %dx%d does not fit one co-resident launch", s->run_gx, s->run_gy);
+  // with references drawn ahead, a launch covers at most refcap references of
+  // an on-schedule core
+  uint32_t chunk_max = kMaxChunk;
+  const bool ahead = s->P.refbuf && s->P.period > 0 && s->P.mode != MODE_TRACE;
+  if (ahead) chunk_max = std::min<uint64_t>(kMaxChunk, (uint64_t)s->P.refcap * s->P.period);
   uint32_t done = 0;
   while (done < n) {
-    uint32_t c = n - done < kMaxChunk ? n - done : kMaxChunk;
+    uint32_t c = n - done < chunk_max ? n - done : chunk_max;
+    if (ahead) {
+      CU(launch_gen_refs(s->P, s->cycle, c, s->stream), "reference draw launch");
+      s->launches++;
+    }
     RunArgs A;
     A.t0 = s->cycle;
     A.n = c;
@@ -820,6 +838,8 @@ int noc_batch_create(int n, const noc_instance_desc* d, noc_batch** out) {
       noc_batch_destroy(b);
       return rc;
     }
+    s->refcap = 0;  // batch instances draw their references in place
+    layout(s);
     b->sims.push_back(s);
     b->cycles.push_back(d[i].cycles);
   }

@@ -50,6 +50,7 @@ cudaError_t launch_reduce_stats(const Params& P, int tile, unsigned long long* o
                                 cudaStream_t s);
 cudaError_t launch_count_busy(const Params& P, uint32_t cycle, unsigned int* out,
                               cudaStream_t s);
+cudaError_t launch_gen_refs(const Params& P, uint32_t t0, uint32_t n, cudaStream_t s);
 cudaError_t launch_fill_u32(unsigned int* p, unsigned int v, size_t n, cudaStream_t s);
 
 }  // namespace noc

@@ -71,6 +71,42 @@ size_t run_smem_bytes(int threads) { return run_smem_bytes_impl(threads); }
 
 int block_threads(int W, int H, int gx, int gy) { return block_threads_impl(W, H, gx, gy); }
 
+static int grid_for(size_t n, int threads) {
+  size_t g = (n + threads - 1) / threads;
+  if (g > 4096) g = 4096;
+  return (int)(g ? g : 1);
+}
+
+// ---------------------------------------------------------------- references
+// Draw ahead, for every tile, the references it can issue in cycles
+// [t0, t0 + n): those eligible by cycle t0 + n - 1 from its next_ref on, at most
+// refcap.  One thread per (tile, slot), so the Philox work runs at full width
+// instead of on the cycle kernel's serial path.
+__global__ void gen_refs_kernel(const Params P, uint32_t t0, uint32_t n) {
+  const size_t N = (size_t)P.N, total = N * P.refcap;
+  for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < total;
+       it += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t c = (uint32_t)(it / P.refcap), j = (uint32_t)(it % P.refcap);
+    const uint32_t k0 = P.core[C_NEXT * N + c];
+    uint32_t cnt = 0;
+    if (P.period > 0 && P.mode != MODE_TRACE) {
+      const unsigned long long last = (unsigned long long)(t0 + n - 1) / (unsigned)P.period;
+      if (last + 1 > k0) cnt = (uint32_t)min(last + 1 - k0, (unsigned long long)P.refcap);
+    }
+    if (j == 0) {
+      P.refk0[c] = k0;
+      P.refcnt[c] = cnt;
+    }
+    uint32_t raw;
+    if (j < cnt && draw_ref(P, c, k0 + j, raw)) P.refbuf[c * (size_t)P.refcap + j] = raw;
+  }
+}
+
+cudaError_t launch_gen_refs(const Params& P, uint32_t t0, uint32_t n, cudaStream_t s) {
+  gen_refs_kernel<<<grid_for((size_t)P.N * P.refcap, 256), 256, 0, s>>>(P, t0, n);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- hashes
 __global__ void dyn_hash_kernel(const Params P, uint32_t cycle, unsigned long long* out) {
   __shared__ unsigned long long red[32];
@@ -221,11 +257,6 @@ __global__ void state_terms_kernel(const Params P, uint32_t cycle, unsigned long
   if (threadIdx.x == 0) atomicAdd(out, acc);
 }
 
-static int grid_for(size_t n, int threads) {
-  size_t g = (n + threads - 1) / threads;
-  if (g > 4096) g = 4096;
-  return (int)(g ? g : 1);
-}
 
 cudaError_t launch_dyn_hash(const Params& P, uint32_t cycle, unsigned long long* out,
                             cudaStream_t s) {

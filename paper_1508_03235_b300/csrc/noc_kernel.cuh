@@ -86,9 +86,9 @@ static __device__ void load_tile(const Params& P, uint32_t r, Tile& T) {
   T.sq_front = T.sq_len ? P.sq[(size_t)r * P.svc_q + T.sq_head] : z;
   T.mq_front = T.mq_len ? P.mq[(size_t)r * P.mem_q + T.mq_head] : z;
   T.ej = z;
-  T.pf_ok = 0;
-  T.pf_line = 0;
-  T.pf_write = 0;
+  T.rk0 = P.refbuf ? P.refk0[r] : 0;
+  T.rcnt = P.refbuf ? P.refcnt[r] : 0;
+  prefetch_next_ref(P, T);
   T.inj = P.stats[S_INJ * N + r];
   T.ejc = P.stats[S_EJ * N + r];
   T.defl = P.stats[S_DEFL * N + r];

@@ -82,6 +82,13 @@ struct Params {
   uint32_t* fwd;         // [N][fwd_cap][2]          (migrate)
   uint32_t* trace_off;   // [N+1]                    (trace mode)
   uint32_t* trace;       // refs                     (trace mode)
+  // references drawn ahead by gen_refs_kernel: refbuf[tile][j] is reference
+  // refk0[tile] + j (line | write << 31, or the probe destination), for
+  // j < refcnt[tile]; refbuf == nullptr or j >= refcnt: drawn in place
+  uint32_t* refbuf;      // [N][refcap]
+  uint32_t* refk0;       // [N]
+  uint32_t* refcnt;      // [N]
+  int refcap;
   unsigned long long* stats;  // [NSTAT][N]
   unsigned long long* hist;   // [2][HIST_BINS]
   unsigned int* flags;        // [CTAs] last completed cycle + 1
@@ -184,7 +191,8 @@ struct Tile {
   uint32_t cq_head, cq_len, sq_head, sq_len, mq_head, mq_len, fwd_next, fwd_n;
   uint4 cq_front, sq_front, mq_front;  // cached queue heads (valid when len > 0)
   uint4 ej;                            // flit ejected this cycle (or empty)
-  uint32_t pf_line, pf_write, pf_ok;   // reference next_ref, kept for a retry
+  uint32_t pf_raw, pf_ok;              // reference next_ref (encoded), if pf_ok
+  uint32_t rk0, rcnt;                  // this tile's window of drawn-ahead references
   unsigned long long inj, ejc, defl, latsum, latmax, l2lsum;
   uint32_t sm[NSMALL];                 // small per-launch counter deltas
 };
@@ -649,19 +657,48 @@ __device__ __forceinline__ void mq_pop(const Params& P, Tile& T) {
   if (T.mq_len > 0) T.mq_front = P.mq[(size_t)T.r * P.mem_q + T.mq_head];
 }
 
-// line and write flag of reference k of core `core`; false past a trace's end
-static __device__ bool ref_of(const Params& P, uint32_t core, uint32_t k, uint32_t& line,
-                              uint32_t& write) {
+// Reference k of core `core`, encoded (line | write << 31 for cache traffic,
+// the destination tile for network-only probes); false past a trace's end.
+// This is the definition; gen_refs_kernel and the in-place draw both use it.
+static __device__ bool draw_ref(const Params& P, uint32_t core, uint32_t k, uint32_t& raw) {
   if (P.mode == MODE_TRACE) {
     uint32_t off = P.trace_off[core], n = P.trace_off[core + 1] - off;
     if (k >= n) return false;
-    uint32_t ref = P.trace[off + k];
-    line = ref & 0x7FFFFFFFu;
-    write = ref >> 31;
+    raw = P.trace[off + k];
     return true;
   }
-  line = draw_line(P, core, k, write);
+  if (P.mode == MODE_NETWORK) {
+    unsigned long long w[4];
+    philox4x64_10(k, core, P.stream, 0, P.seed, 0x4E4F43ull, w);
+    uint32_t dst = (uint32_t)__umul64hi(w[1], (unsigned long long)(P.N - 1));
+    raw = dst >= core ? dst + 1 : dst;
+    return true;
+  }
+  uint32_t write;
+  uint32_t line = draw_line(P, core, k, write);
+  raw = line | (write << 31);
   return true;
+}
+
+// reference next_ref from the drawn-ahead window if it is there, else drawn now
+__device__ __forceinline__ bool next_ref_raw(const Params& P, const Tile& T, uint32_t& raw) {
+  const uint32_t j = T.next_ref - T.rk0;
+  if (j < T.rcnt) {
+    raw = P.refbuf[(size_t)T.r * P.refcap + j];
+    return true;
+  }
+  return draw_ref(P, T.r, T.next_ref, raw);
+}
+
+// start loading the next reference into a register (used cycles later)
+__device__ __forceinline__ void prefetch_next_ref(const Params& P, Tile& T) {
+  const uint32_t j = T.next_ref - T.rk0;
+  if (j < T.rcnt) {
+    T.pf_raw = P.refbuf[(size_t)T.r * P.refcap + j];
+    T.pf_ok = 1;
+  } else {
+    T.pf_ok = 0;
+  }
 }
 
 // Phase 1; returns true if the core took an action this cycle
@@ -701,35 +738,30 @@ static __device__ bool phase1(const Params& P, Tile& T, uint32_t t, bool drainin
   if (draining || P.period <= 0) return false;
   if ((unsigned long long)t < (unsigned long long)T.next_ref * (unsigned long long)P.period) return false;
 
+  if (P.mode == MODE_NETWORK && P.N < 2) return false;
+  uint32_t raw;
+  if (T.pf_ok) {
+    raw = T.pf_raw;
+  } else {
+    if (!next_ref_raw(P, T, raw)) return false;
+    T.pf_raw = raw;          // kept for a retry after a full core queue
+    T.pf_ok = 1;
+  }
   if (P.mode == MODE_NETWORK) {
-    if (P.N < 2) return false;
     if (cq_full(P, T)) {
       SMALL(S_CQST)++;
       return true;
     }
-    unsigned long long w[4];
-    philox4x64_10(T.next_ref, T.r, P.stream, 0, P.seed, 0x4E4F43ull, w);
-    uint32_t dst = (uint32_t)__umul64hi(w[1], (unsigned long long)(P.N - 1));
-    if (dst >= T.r) dst++;
-    send_core(P, T, mkflit(T_PROBE, T.r, dst, 0, 0, 0));
+    send_core(P, T, mkflit(T_PROBE, T.r, raw, 0, 0, 0));
     T.next_ref++;
     SMALL(S_REFS)++;
+    prefetch_next_ref(P, T);
     return true;
   }
-  uint32_t line, write;
-  if (T.pf_ok) {
-    line = T.pf_line;
-    write = T.pf_write;
-  } else {
-    if (!ref_of(P, T.r, T.next_ref, line, write)) return false;
-    T.pf_line = line;
-    T.pf_write = write;
-    T.pf_ok = 1;
-  }
-  if (l1_step<W1, W2>(P, T, t, line, write)) {
+  if (l1_step<W1, W2>(P, T, t, raw & 0x7FFFFFFFu, raw >> 31)) {
     T.next_ref++;
     SMALL(S_REFS)++;
-    T.pf_ok = 0;
+    prefetch_next_ref(P, T);
   }
   return true;
 }
