@@ -163,6 +163,45 @@ inline int block_threads_impl(int W, int H, int gx, int gy) {
   return ((a + 31) / 32) * 32;
 }
 
+// Thread order inside a rectangle: the perimeter tiles first (row-major), then
+// the interior (row-major).  Only perimeter tiles have links that leave the
+// rectangle, so the first warps alone hold everything the neighbouring CTAs
+// wait for.  Rectangles with a side <= 2 are all perimeter.
+__device__ __forceinline__ int perim_count(int bw, int bh) {
+  return (bw <= 2 || bh <= 2) ? bw * bh : 2 * bw + 2 * (bh - 2);
+}
+__device__ __forceinline__ int tile_index(int lx, int ly, int bw, int bh) {
+  if (bw <= 2 || bh <= 2) return ly * bw + lx;
+  if (ly == 0) return lx;
+  if (ly == bh - 1) return bw + 2 * (bh - 2) + lx;
+  if (lx == 0) return bw + 2 * (ly - 1);
+  if (lx == bw - 1) return bw + 2 * (ly - 1) + 1;
+  return perim_count(bw, bh) + (ly - 1) * (bw - 2) + (lx - 1);
+}
+__device__ __forceinline__ void tile_of(int i, int bw, int bh, int& lx, int& ly) {
+  if (bw <= 2 || bh <= 2) {
+    lx = i % bw;
+    ly = i / bw;
+    return;
+  }
+  const int np = perim_count(bw, bh);
+  if (i < bw) {
+    lx = i;
+    ly = 0;
+  } else if (i < bw + 2 * (bh - 2)) {
+    const int j = i - bw;
+    ly = 1 + j / 2;
+    lx = (j & 1) ? bw - 1 : 0;
+  } else if (i < np) {
+    lx = i - bw - 2 * (bh - 2);
+    ly = bh - 1;
+  } else {
+    const int j = i - np;
+    ly = 1 + j / (bw - 2);
+    lx = 1 + j % (bw - 2);
+  }
+}
+
 // One CTA runs rectangle b of one simulation for A.n cycles.
 template <bool HASH, bool DRAIN, int W1, int W2>
 __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, const int b,
@@ -179,7 +218,16 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
   const int bw = X1 - X0, bh = Y1 - Y0;
   const int i = threadIdx.x;
   const bool active = i < bw * bh;
-  const int lx = active ? i % bw : 0, ly = active ? i / bw : 0;
+  int lx = 0, ly = 0;
+  if (active) tile_of(i, bw, bh, lx, ly);
+  // shared-memory slots (thread indices) of the in-rectangle neighbours
+  const int in_n = ly > 0 ? tile_index(lx, ly - 1, bw, bh) : 0;
+  const int in_s = ly < bh - 1 ? tile_index(lx, ly + 1, bw, bh) : 0;
+  const int in_e = lx < bw - 1 ? tile_index(lx + 1, ly, bw, bh) : 0;
+  const int in_w = lx > 0 ? tile_index(lx - 1, ly, bw, bh) : 0;
+  // the warps that hold the perimeter, which publish the cycle on their own
+  const int edge_threads = ((perim_count(bw, bh) + 31) / 32) * 32;
+  const bool edge_warp = i < edge_threads;
   const uint32_t x = X0 + lx, y = Y0 + ly, r = y * P.W + x;
   const size_t N = (size_t)P.N;
   const uint32_t exists = (y > 0 ? 1u << P_N : 0u) | (y + 1 < (uint32_t)P.H ? 1u << P_S : 0u) |
@@ -222,13 +270,13 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
       const uint4* sp = sl + pin * 4 * nt;
       const uint4* gl = P.glink + (size_t)pin * 4 * N;
       in[P_N] = !(exists & (1u << P_N)) ? z
-                : (ly > 0 ? sp[P_S * nt + i - bw] : __ldcg(&gl[P_S * N + r - P.W]));
+                : (ly > 0 ? sp[P_S * nt + in_n] : __ldcg(&gl[P_S * N + r - P.W]));
       in[P_S] = !(exists & (1u << P_S)) ? z
-                : (ly < bh - 1 ? sp[P_N * nt + i + bw] : __ldcg(&gl[P_N * N + r + P.W]));
+                : (ly < bh - 1 ? sp[P_N * nt + in_s] : __ldcg(&gl[P_N * N + r + P.W]));
       in[P_E] = !(exists & (1u << P_E)) ? z
-                : (lx < bw - 1 ? sp[P_W * nt + i + 1] : __ldcg(&gl[P_W * N + r + 1]));
+                : (lx < bw - 1 ? sp[P_W * nt + in_e] : __ldcg(&gl[P_W * N + r + 1]));
       in[P_W] = !(exists & (1u << P_W)) ? z
-                : (lx > 0 ? sp[P_E * nt + i - 1] : __ldcg(&gl[P_E * N + r - 1]));
+                : (lx > 0 ? sp[P_E * nt + in_w] : __ldcg(&gl[P_E * N + r - 1]));
       route(P, T, t, in, exists, out);
       uint4* so = sl + pout * 4 * nt;
       uint4* go = P.glink + (size_t)pout * 4 * N;
@@ -238,10 +286,13 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
         if (boundary & (1u << d)) __stcg(&go[d * N + r], out[d]);
       }
     }
-    __syncthreads();
-    // publish: the release store orders this CTA's link stores (made visible
-    // to thread 0 by the barrier) before the flag
-    if (i == 0 && !alone && b != A.silent_cta) st_release_u32(&P.flags[b], t + 1);
+    // publish: the perimeter warps meet at a named barrier, then one release
+    // store orders all their link stores before the flag; the interior warps
+    // go on without waiting
+    if (!alone && edge_warp) {
+      asm volatile("bar.sync 1, %0;" ::"r"(edge_threads) : "memory");
+      if (i == 0 && b != A.silent_cta) st_release_u32(&P.flags[b], t + 1);
+    }
     // ---- Phase 3 of this cycle
     if (active) phase3<W1, W2>(P, T, t, sh_hist);
     if (HASH) {
