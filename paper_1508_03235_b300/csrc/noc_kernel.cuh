@@ -277,14 +277,8 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
                 : (lx < bw - 1 ? sp[P_W * nt + in_e] : __ldcg(&gl[P_W * N + r + 1]));
       in[P_W] = !(exists & (1u << P_W)) ? z
                 : (lx > 0 ? sp[P_E * nt + in_w] : __ldcg(&gl[P_E * N + r - 1]));
-      route(P, T, t, in, exists, out);
-      uint4* so = sl + pout * 4 * nt;
-      uint4* go = P.glink + (size_t)pout * 4 * N;
-#pragma unroll
-      for (int d = 0; d < 4; ++d) {
-        so[d * nt + i] = out[d];
-        if (boundary & (1u << d)) __stcg(&go[d * N + r], out[d]);
-      }
+      route(P, T, t, in, exists, sl + pout * 4 * nt + i, nt, P.glink + (size_t)pout * 4 * N + r, N,
+            boundary);
     }
     // publish: the perimeter warps meet at a named barrier, then one release
     // store orders all their link stores before the flag; the interior warps
@@ -295,6 +289,10 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
     }
     // ---- Phase 3 of this cycle
     if (active) phase3<W1, W2>(P, T, t, sh_hist);
+    if (HASH || DRAIN) {
+#pragma unroll
+      for (int d = 0; d < 4; ++d) out[d] = sl[(pout * 4 + d) * nt + i];
+    }
     if (HASH) {
       unsigned long long h = active ? tile_hash(T, out) : 0ull;
       h = block_sum(h, sh_red);
@@ -327,7 +325,7 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
   if (active) {
     const uint32_t plast = (t - (t == tend ? 1u : 0u)) & 1u;
 #pragma unroll
-    for (int d = 0; d < 4; ++d) P.glink[((size_t)plast * 4 + d) * N + r] = out[d];
+    for (int d = 0; d < 4; ++d) P.glink[((size_t)plast * 4 + d) * N + r] = sl[(plast * 4 + d) * nt + i];
     store_tile(P, T);
   }
   __syncthreads();

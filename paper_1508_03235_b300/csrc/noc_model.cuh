@@ -781,9 +781,13 @@ __device__ __forceinline__ void cswap(unsigned long long& ka, uint4& fa_, unsign
 }
 
 // One bufferless router (Sec. 4.3): eject, inject, rank, select ports.
-// `in` are this cycle's arrivals by input port, `exists` the port mask.
+// `in` are this cycle's arrivals by input port, `exists` the port mask.  Each
+// flit is stored straight to its output port's slot: so[p * so_stride] in
+// shared memory and, for ports in `edge` (links leaving the CTA's rectangle),
+// also go[p * go_stride] in global memory; unused ports get an empty flit.
 __device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint4 (&in)[4],
-                                      uint32_t exists, uint4 (&out)[4]) {
+                                      uint32_t exists, uint4* so, int so_stride, uint4* go,
+                                      size_t go_stride, uint32_t edge) {
   const unsigned long long NOKEY = ~0ull;
   unsigned long long k[4];
   int n_arr = 0;
@@ -841,18 +845,16 @@ __device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint
   // port selection: first free port of [X-productive, Y-productive, N, S, E, W]
   uint32_t freem = exists;
 #pragma unroll
-  for (int d = 0; d < 4; ++d) out[d] = make_uint4(0, 0, 0, 0);
-#pragma unroll
   for (int i = 0; i < 5; ++i) {
-    uint4 f = i < 4 ? in[i] : inj;
-    bool valid = i < 4 ? (k[i] != NOKEY) : has_inj;
+    const uint4 f = i < 4 ? in[i] : inj;
+    const bool valid = i < 4 ? (k[i] != NOKEY) : has_inj;
     if (!valid) continue;
-    uint32_t dst = fdst(f);
+    const uint32_t dst = fdst(f);
     const uint32_t dsty = qdiv(dst, P.mW);
-    int dx = (int)(dst - dsty * (uint32_t)P.W) - (int)T.x;
-    int dy = (int)dsty - (int)T.y;
-    uint32_t xb = dx > 0 ? (1u << P_E) : (dx < 0 ? (1u << P_W) : 0u);
-    uint32_t yb = dy > 0 ? (1u << P_S) : (dy < 0 ? (1u << P_N) : 0u);
+    const int dx = (int)(dst - dsty * (uint32_t)P.W) - (int)T.x;
+    const int dy = (int)dsty - (int)T.y;
+    const uint32_t xb = dx > 0 ? (1u << P_E) : (dx < 0 ? (1u << P_W) : 0u);
+    const uint32_t yb = dy > 0 ? (1u << P_S) : (dy < 0 ? (1u << P_N) : 0u);
     uint32_t pick;
     if (freem & xb) pick = xb;
     else if (freem & yb) pick = yb;
@@ -861,10 +863,18 @@ __device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint
       T.defl++;
     }
     freem &= ~pick;
-#pragma unroll
-    for (int d = 0; d < 4; ++d)
-      if (pick == (1u << d)) out[d] = f;
+    const int p = __ffs(pick) - 1;
+    so[p * so_stride] = f;
+    if (edge & pick) __stcg(&go[p * go_stride], f);
   }
+  // the ports no flit took carry nothing this cycle
+  const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+    if (freem & (1u << d) || !(exists & (1u << d))) {
+      so[d * so_stride] = z;
+      if (edge & (1u << d)) __stcg(&go[d * go_stride], z);
+    }
 }
 
 // ---------------------------------------------------------------- Phase 3
