@@ -52,7 +52,7 @@ struct noc_sim {
   noc_traffic traf;
   uint64_t seed;
   // arena layout (byte offsets)
-  size_t o_glink, o_core, o_cq, o_sq, o_mq, o_l1, o_l1own, o_l2, o_l2ep, o_l2hist, o_dir, o_fwd,
+  size_t o_glink, o_gtag, o_core, o_cq, o_sq, o_mq, o_l1, o_l1own, o_l2, o_l2ep, o_l2hist, o_dir, o_fwd,
       o_stats, o_hist, o_flags, o_err, o_abort, o_scratch, o_refbuf, o_refk0, o_refcnt, bytes;
   int refcap = 512;              // references drawn ahead per tile (0 = draw in place)
   size_t n_flags;
@@ -64,6 +64,10 @@ struct noc_sim {
   int run_gx = 0, run_gy = 0;  // tiling in use
   uint32_t cycle = 0;
   bool draining = false;       // set by noc_drain, cleared by noc_reset
+  // tagged edge slots: all zero, or last written by a plain launch ending at
+  // gtag_end (a plain launch starting anywhere else clears them first)
+  bool gtag_clean = false;
+  uint32_t gtag_end = 0;
   // hash trace
   bool hash_on = false;
   unsigned long long* d_hash = nullptr;
@@ -97,8 +101,9 @@ void layout(noc_sim* s) {
   };
   const size_t w1 = N * P.l1_sets * P.l1_ways, w2 = N * P.l2_sets * P.l2_ways;
   const bool lspd = P.policy != POL_INTERLEAVED, mig = P.policy == POL_MIGRATE;
-  s->n_flags = 4096;
+  s->n_flags = FLAG_SLOTS * std::min<size_t>(N, 4096);
   s->o_glink = take(2 * 4 * N * sizeof(uint4));
+  s->o_gtag = take(2 * 4 * N * 2 * sizeof(uint4));
   s->o_core = take(NCORE * N * sizeof(uint32_t));
   s->o_cq = take(N * P.core_q * sizeof(uint4));
   s->o_sq = take(N * P.svc_q * sizeof(uint4));
@@ -127,6 +132,7 @@ void set_pointers(noc_sim* s) {
   unsigned char* b = s->base;
   const bool lspd = P.policy != POL_INTERLEAVED, mig = P.policy == POL_MIGRATE;
   P.glink = reinterpret_cast<uint4*>(b + s->o_glink);
+  P.gtag = reinterpret_cast<uint4*>(b + s->o_gtag);
   P.core = reinterpret_cast<uint32_t*>(b + s->o_core);
   P.cq = reinterpret_cast<uint4*>(b + s->o_cq);
   P.sq = reinterpret_cast<uint4*>(b + s->o_sq);
@@ -159,6 +165,8 @@ int do_reset(noc_sim* s) {
   const size_t N = (size_t)P.N;
   const size_t w1 = N * P.l1_sets * P.l1_ways, w2 = N * P.l2_sets * P.l2_ways;
   CU(cudaMemsetAsync(P.glink, 0, 2 * 4 * N * sizeof(uint4), st), "reset links");
+  CU(cudaMemsetAsync(P.gtag, 0, 2 * 4 * N * 2 * sizeof(uint4), st), "reset edge slots");
+  s->gtag_clean = true;
   CU(cudaMemsetAsync(P.core, 0, NCORE * N * sizeof(uint32_t), st), "reset cores");
   CU(cudaMemsetAsync(P.l1, 0, w1 * sizeof(uint32_t), st), "reset L1");
   CU(cudaMemsetAsync(P.l1own, 0, w1 * sizeof(uint16_t), st), "reset L1 owners");
@@ -215,7 +223,7 @@ int choose_tiling(noc_sim* s, int* gx_out, int* gy_out) {
       const int threads = block_threads(W, H, gx, gy);
       if (threads > 384) continue;
       const long G = (long)gx * gy;
-      if (G > (long)s->n_flags) continue;
+      if (G * FLAG_SLOTS > (long)s->n_flags) continue;
       int& cap = cap_of[threads / 32];
       if (cap < 0) {
         cudaError_t e = max_coresident_ctas(s->P, threads, &cap);
@@ -292,7 +300,7 @@ int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
   const int threads = block_threads(s->P.W, s->P.H, s->run_gx, s->run_gy);
   int cap = 0;
   CU(max_coresident_ctas(s->P, threads, &cap), "occupancy");
-  if (threads > 384 || s->run_gx * s->run_gy > cap || s->run_gx * s->run_gy > (int)s->n_flags)
+  if (threads > 384 || s->run_gx * s->run_gy > cap || s->run_gx * s->run_gy * FLAG_SLOTS > (int)s->n_flags)
     return fail(NOC_ERR_ARG, "tiling %dx%d does not fit one co-resident launch", s->run_gx, s->run_gy);
   // with references drawn ahead, a launch covers at most refcap references of
   // an on-schedule core
@@ -317,8 +325,18 @@ int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
     A.abort_flag = abort_ptr(s);
     A.wait_ns = s->wait_ns;
     A.silent_cta = s->silent_cta;
+    const bool plain = !A.hash_trace && !A.busy;
+    if (plain && !s->gtag_clean && s->gtag_end != s->cycle) {
+      CU(cudaMemsetAsync(s->P.gtag, 0, 2 * 4 * (size_t)s->P.N * 2 * sizeof(uint4), s->stream),
+         "clear edge slots");
+      s->gtag_clean = true;
+    }
     CU(launch_run(s->P, A, s->stream), "cycle kernel launch");
     s->launches++;
+    if (plain) {
+      s->gtag_clean = false;
+      s->gtag_end = s->cycle + c;
+    }
     s->cycle += c;
     done += c;
   }
@@ -622,7 +640,7 @@ int noc_set_tiling(noc_sim* s, int gx, int gy) {
     return NOC_OK;
   }
   if (gx < 1 || gy < 1 || gx > s->P.W || gy > s->P.H || block_threads(s->P.W, s->P.H, gx, gy) > 512 ||
-      (long)gx * gy > (long)s->n_flags)
+      (long)gx * gy * FLAG_SLOTS > (long)s->n_flags)
     return fail(NOC_ERR_ARG, "tiling %dx%d invalid for mesh %dx%d", gx, gy, s->P.W, s->P.H);
   s->gx = s->run_gx = gx;
   s->gy = s->run_gy = gy;
@@ -942,7 +960,7 @@ int noc_batch_run(noc_batch* b) {
   for (int i : order) {
     noc_sim* s = b->sims[i];
     int gx = (s->P.W + side - 1) / side, gy = (s->P.H + side - 1) / side;
-    if (gx * gy > cap || gx * gy > (int)s->n_flags)
+    if (gx * gy > cap || gx * gy * FLAG_SLOTS > (int)s->n_flags)
       return fail(NOC_ERR_ARG, "instance %d needs %d CTAs, %d fit co-resident", i, gx * gy, cap);
     s->run_gx = gx;
     s->run_gy = gy;

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(MAX_THREADS, 1) batch_kernel(const __grid_cons
       for (int k = threadIdx.x; k < (int)(sizeof(RunArgs) / 4); k += blockDim.x) dsta[k] = srca[k];
     }
     __syncthreads();
-    if (s_ok) run_rect<false, false, W1, W2>(sP, sA, B.item_rect[item], smem_raw);
+    if (s_ok) run_rect_warps<W1, W2>(sP, sA, B.item_rect[item], smem_raw);
     __syncthreads();
   }
 }

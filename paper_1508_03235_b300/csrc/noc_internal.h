@@ -7,6 +7,10 @@
 
 namespace noc {
 
+// global cycle flags per CTA rectangle: one per warp (the plain cycle loop),
+// slot 0 for the CTA as a whole (the traced and draining loops)
+constexpr int FLAG_SLOTS = 16;
+
 // per-launch arguments of the cycle kernel
 struct RunArgs {
   uint32_t t0, n;        // first cycle and number of cycles of this launch

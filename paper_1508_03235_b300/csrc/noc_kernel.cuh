@@ -285,7 +285,7 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
     // go on without waiting
     if (!alone && edge_warp) {
       asm volatile("bar.sync 1, %0;" ::"r"(edge_threads) : "memory");
-      if (i == 0 && b != A.silent_cta) st_release_u32(&P.flags[b], t + 1);
+      if (i == 0 && b != A.silent_cta) st_release_u32(&P.flags[b * FLAG_SLOTS], t + 1);
     }
     // ---- Phase 3 of this cycle
     if (active) phase3<W1, W2>(P, T, t, sh_hist);
@@ -308,7 +308,7 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
     if (active) phase1<W1, W2>(P, T, t + 1, A.draining != 0, sh_hist);
     // lanes 0..3 each wait for one neighbouring CTA (N, S, E, W)
     if (i < 4 && nbr[i] >= 0) {
-      int w = wait_ge(&P.flags[nbr[i]], t + 1, A.abort_flag, A.wait_ns);
+      int w = wait_ge(&P.flags[nbr[i] * FLAG_SLOTS], t + 1, A.abort_flag, A.wait_ns);
       if (w <= 0) {
         if (w == 0) {
           atomicExch(A.abort_flag, 1u);
@@ -333,11 +333,184 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
     if (sh_hist[k]) atomicAdd(&P.hist[k], (unsigned long long)sh_hist[k]);
 }
 
+// ---------------------------------------------------------------- warp-flag loop
+constexpr int WARPS_PER_CTA = MAX_THREADS / 32;
+
+__device__ __forceinline__ unsigned ld_volatile_shared(const unsigned* p) {
+  return *reinterpret_cast<const volatile unsigned*>(p);
+}
+
+// One CTA runs rectangle b of one simulation for A.n cycles, with no CTA-wide
+// barrier per cycle.  Inside the rectangle every warp publishes the cycle it
+// has routed in a shared-memory flag and, before routing the next cycle, waits
+// only for the warps that hold its tiles' neighbours.  Links that leave the
+// rectangle go through tagged global slots (tag_store): the reader polls the
+// slot itself until it carries the previous cycle's tag, so neither side
+// needs a flag or a fence.  A warp is never more than one cycle ahead of a
+// warp or tile that reads its outputs or writes its inputs (every link has a
+// twin in the other direction, which the writer must have read first), which
+// is all the double-buffered links need.  Threads map to tiles perimeter
+// first, so the warps that touch global links are few.
+template <int W1, int W2>
+__device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A, const int b,
+                                               unsigned char* smem_raw) {
+  const int nt = blockDim.x;
+  uint4* sl = reinterpret_cast<uint4*>(smem_raw);  // [2 parity][4 port][nt]
+  uint32_t* sh_hist = reinterpret_cast<uint32_t*>(sl + 8 * nt);
+  __shared__ unsigned wflag[WARPS_PER_CTA];
+
+  const int cx = b % A.gx, cy = b / A.gx;
+  const int X0 = cx * P.W / A.gx, X1 = (cx + 1) * P.W / A.gx;
+  const int Y0 = cy * P.H / A.gy, Y1 = (cy + 1) * P.H / A.gy;
+  const int bw = X1 - X0, bh = Y1 - Y0;
+  const int i = threadIdx.x, lane = i & 31, warp = i >> 5;
+  const bool active = i < bw * bh;
+  int lx = 0, ly = 0;
+  if (active) tile_of(i, bw, bh, lx, ly);
+  const int in_n = ly > 0 ? tile_index(lx, ly - 1, bw, bh) : 0;
+  const int in_s = ly < bh - 1 ? tile_index(lx, ly + 1, bw, bh) : 0;
+  const int in_e = lx < bw - 1 ? tile_index(lx + 1, ly, bw, bh) : 0;
+  const int in_w = lx > 0 ? tile_index(lx - 1, ly, bw, bh) : 0;
+  const uint32_t x = X0 + lx, y = Y0 + ly, r = y * P.W + x;
+  const size_t N = (size_t)P.N;
+  const bool draining = A.draining != 0;
+  const uint32_t exists = !active ? 0u
+                          : (y > 0 ? 1u << P_N : 0u) | (y + 1 < (uint32_t)P.H ? 1u << P_S : 0u) |
+                                (x + 1 < (uint32_t)P.W ? 1u << P_E : 0u) | (x > 0 ? 1u << P_W : 0u);
+  // links that cross the rectangle's edge, in and out
+  const uint32_t boundary = exists & ((ly == 0 ? 1u << P_N : 0u) | (ly == bh - 1 ? 1u << P_S : 0u) |
+                                      (lx == bw - 1 ? 1u << P_E : 0u) | (lx == 0 ? 1u << P_W : 0u));
+  // the silent rectangle (a test of the bounded waits) never writes its edges
+  const uint32_t edge_out = b == A.silent_cta ? 0u : boundary;
+
+  // the warps of this CTA that hold in-rectangle neighbours of this warp's
+  // tiles; lane l < WARPS_PER_CTA polls warp l's flag
+  unsigned lm = 0;
+  if (active) {
+    if (ly > 0) lm |= 1u << (in_n >> 5);
+    if (ly < bh - 1) lm |= 1u << (in_s >> 5);
+    if (lx < bw - 1) lm |= 1u << (in_e >> 5);
+    if (lx > 0) lm |= 1u << (in_w >> 5);
+  }
+  lm = __reduce_or_sync(0xFFFFFFFFu, lm) & ~(1u << warp);
+  const bool poll_local = lane < WARPS_PER_CTA && ((lm >> lane) & 1u);
+  // tagged slot (in uint4) of this tile's input across each edge, parity 0:
+  // the neighbour's output port facing this tile
+  const size_t pstride = 2 * 4 * N;  // uint4 per parity
+  uint32_t rin[4] = {0, 0, 0, 0};
+  if (boundary & (1u << P_N)) rin[P_N] = (P_S * (uint32_t)N + r - P.W) * 2;
+  if (boundary & (1u << P_S)) rin[P_S] = (P_N * (uint32_t)N + r + P.W) * 2;
+  if (boundary & (1u << P_E)) rin[P_E] = (P_W * (uint32_t)N + r + 1) * 2;
+  if (boundary & (1u << P_W)) rin[P_W] = (P_E * (uint32_t)N + r - 1) * 2;
+
+  for (int k = i; k < 2 * HIST_BINS; k += nt) sh_hist[k] = 0;
+  const uint32_t t0 = A.t0, tend = A.t0 + A.n;
+  if (i < WARPS_PER_CTA) wflag[i] = t0;
+
+  Tile T;
+  if (active) {
+    load_tile(P, r, T);
+    const uint32_t pin = (t0 - 1u) & 1u;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) sl[(pin * 4 + d) * nt + i] = P.glink[((size_t)pin * 4 + d) * N + r];
+  }
+  __syncthreads();
+  if (active) phase1<W1, W2>(P, T, t0, draining, sh_hist);
+
+  uint32_t t = t0;
+  for (; t < tend; ++t) {
+    const uint32_t pin = (t - 1u) & 1u, pout = t & 1u;
+    uint4 in[4];
+    const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) in[d] = z;
+    if (t == t0) {
+      // the previous launch's last outputs, complete in the global links
+      const uint4* gl = P.glink + (size_t)pin * 4 * N;
+      if (boundary & (1u << P_N)) in[P_N] = __ldcg(&gl[P_S * N + r - P.W]);
+      if (boundary & (1u << P_S)) in[P_S] = __ldcg(&gl[P_N * N + r + P.W]);
+      if (boundary & (1u << P_E)) in[P_E] = __ldcg(&gl[P_W * N + r + 1]);
+      if (boundary & (1u << P_W)) in[P_W] = __ldcg(&gl[P_E * N + r - 1]);
+    } else {
+      // wait for the neighbours' outputs of cycle t-1: flags of the warps
+      // inside the rectangle, the tagged slots themselves across its edges
+      const uint32_t tag = link_tag(t - 1);
+      const uint4* gt = P.gtag + pin * pstride;
+      uint32_t need = boundary;
+      const unsigned long long start = global_ns();
+      bool aborted = false;
+      for (unsigned it = 0;; ++it) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+          if (need & (1u << d)) {
+            const uint4 a = ld_relaxed_v4(gt + rin[d]), c = ld_relaxed_v4(gt + rin[d] + 1);
+            if (tag_decode(a, c, tag, in[d])) need &= ~(1u << d);
+          }
+        const bool ok = need == 0 && (!poll_local || (int)(ld_volatile_shared(&wflag[lane]) - t) >= 0);
+        if (__all_sync(0xFFFFFFFFu, ok)) break;
+        if ((it & 31u) == 31u) {
+          bool stop = ld_acquire_u32(A.abort_flag) != 0 || it >= (1u << 28);
+          if (!stop && (long long)(global_ns() - start) > A.wait_ns) {
+            stop = true;
+            if (lane == 0) {
+              atomicExch(A.abort_flag, 1u);
+              set_error(P, t, ERR_TIMEOUT);
+            }
+          }
+          if (__any_sync(0xFFFFFFFFu, stop)) {
+            aborted = true;
+            break;
+          }
+        }
+      }
+      if (aborted) break;
+      __threadfence_block();
+    }
+    // ---- Phase 2 (own tile): the in-rectangle arrivals, route, store outputs
+    if (active) {
+      const uint4* sp = sl + pin * 4 * nt;
+      if ((exists & ~boundary) & (1u << P_N)) in[P_N] = sp[P_S * nt + in_n];
+      if ((exists & ~boundary) & (1u << P_S)) in[P_S] = sp[P_N * nt + in_s];
+      if ((exists & ~boundary) & (1u << P_E)) in[P_E] = sp[P_W * nt + in_e];
+      if ((exists & ~boundary) & (1u << P_W)) in[P_W] = sp[P_E * nt + in_w];
+      route<true>(P, T, t, in, exists, sl + pout * 4 * nt + i, nt, P.gtag + pout * pstride + (size_t)r * 2,
+                  2 * N, edge_out);
+    }
+    // ---- publish: this warp has routed cycle t (the warp barrier orders every
+    // lane's shared link stores before lane 0's flag store)
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      *reinterpret_cast<volatile unsigned*>(&wflag[warp]) = t + 1;
+    }
+    // ---- Phase 3 of this cycle and Phase 1 of the next (own tile only)
+    if (active) {
+      phase3<W1, W2>(P, T, t, sh_hist);
+      if (t + 1 != tend) phase1<W1, W2>(P, T, t + 1, draining, sh_hist);
+    }
+  }
+
+  // ---- end of launch: full link state of the last cycle, tile state, counters
+  __syncthreads();
+  if (active) {
+    const uint32_t plast = (t - (t == tend ? 1u : 0u)) & 1u;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) P.glink[((size_t)plast * 4 + d) * N + r] = sl[(plast * 4 + d) * nt + i];
+    store_tile(P, T);
+  }
+  __syncthreads();
+  for (int k = i; k < 2 * HIST_BINS; k += nt)
+    if (sh_hist[k]) atomicAdd(&P.hist[k], (unsigned long long)sh_hist[k]);
+}
+
 template <bool HASH, bool DRAIN, int W1, int W2>
 __global__ void __launch_bounds__(MAX_THREADS, 1)
     run_kernel(const __grid_constant__ Params P, const __grid_constant__ RunArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  run_rect<HASH, DRAIN, W1, W2>(P, A, blockIdx.x, smem_raw);
+  if constexpr (!HASH && !DRAIN)
+    run_rect_warps<W1, W2>(P, A, blockIdx.x, smem_raw);
+  else
+    run_rect<HASH, DRAIN, W1, W2>(P, A, blockIdx.x, smem_raw);
 }
 
 template <bool H, bool D, int W1, int W2>

@@ -69,6 +69,10 @@ struct Params {
   unsigned long long mW, mN, mL1, mL2;
   // device arrays
   uint4* glink;          // [2][4][N] out-links by parity, port, tile
+  // out-links that cross a CTA rectangle's edge, as written during a launch of
+  // the plain cycle loop: [2][4][N] slots of two uint4, each 32-bit word half
+  // a flit (low 16 bits) and the cycle tag (high 16 bits); see link_tag()
+  uint4* gtag;
   uint32_t* core;        // [NCORE][N]
   uint4* cq;             // [N][core_q]
   uint4* sq;             // [N][svc_q]
@@ -125,6 +129,50 @@ __device__ __forceinline__ uint32_t fe(uint4 f) { return f.w >> 16; }
 // priority key: older (smaller inject cycle) first, then smaller source
 __device__ __forceinline__ unsigned long long fkey(uint4 f) {
   return ((unsigned long long)f.x << 16) | (f.y & 0xFFFFu);
+}
+
+// Tagged link slots (cross-rectangle links of the plain cycle loop).  Every
+// 32-bit word carries 16 bits of the flit and the tag of the cycle that wrote
+// it, so a reader that sees all eight words carry the tag it expects has the
+// whole flit of that cycle: the data is its own ready flag, with no fence on
+// the writer's side.  Tags have the top bit set, so zeroed slots never match;
+// slot (t & 1) is rewritten every cycle, so within a launch a stale slot holds
+// cycle t - 2 and never matches the tag of t.
+__device__ __forceinline__ uint32_t link_tag(uint32_t t) { return 0x8000u | (t & 0x7FFFu); }
+__device__ __forceinline__ void tag_encode(uint4 f, uint32_t tag, uint4& a, uint4& b) {
+  a = make_uint4(__byte_perm(f.x, tag, 0x5410), __byte_perm(f.x, tag, 0x5432),
+                 __byte_perm(f.y, tag, 0x5410), __byte_perm(f.y, tag, 0x5432));
+  b = make_uint4(__byte_perm(f.z, tag, 0x5410), __byte_perm(f.z, tag, 0x5432),
+                 __byte_perm(f.w, tag, 0x5410), __byte_perm(f.w, tag, 0x5432));
+}
+// true (and the flit in f) when all eight words carry `tag`
+__device__ __forceinline__ bool tag_decode(uint4 a, uint4 b, uint32_t tag, uint4& f) {
+  const uint32_t T = tag << 16;
+  const uint32_t d = (a.x ^ T) | (a.y ^ T) | (a.z ^ T) | (a.w ^ T) | (b.x ^ T) | (b.y ^ T) |
+                     (b.z ^ T) | (b.w ^ T);
+  f = make_uint4(__byte_perm(a.x, a.y, 0x5410), __byte_perm(a.z, a.w, 0x5410),
+                 __byte_perm(b.x, b.y, 0x5410), __byte_perm(b.z, b.w, 0x5410));
+  return (d >> 16) == 0;
+}
+__device__ __forceinline__ void st_relaxed_v4(uint4* p, uint4 v) {
+  asm volatile("st.relaxed.gpu.global.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ uint4 ld_relaxed_v4(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p)
+               : "memory");
+  return v;
+}
+// store flit f to a tagged slot (two uint4)
+__device__ __forceinline__ void tag_store(uint4* slot, uint4 f, uint32_t tag) {
+  uint4 a, b;
+  tag_encode(f, tag, a, b);
+  st_relaxed_v4(slot, a);
+  st_relaxed_v4(slot + 1, b);
 }
 
 // ---------------------------------------------------------------- hashing
@@ -785,6 +833,9 @@ __device__ __forceinline__ void cswap(unsigned long long& ka, uint4& fa_, unsign
 // flit is stored straight to its output port's slot: so[p * so_stride] in
 // shared memory and, for ports in `edge` (links leaving the CTA's rectangle),
 // also go[p * go_stride] in global memory; unused ports get an empty flit.
+// With TAGGED, `go` points at tagged slots (two uint4 each, see tag_store)
+// and go_stride counts uint4.
+template <bool TAGGED = false>
 __device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint4 (&in)[4],
                                       uint32_t exists, uint4* so, int so_stride, uint4* go,
                                       size_t go_stride, uint32_t edge) {
@@ -865,7 +916,10 @@ __device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint
     freem &= ~pick;
     const int p = __ffs(pick) - 1;
     so[p * so_stride] = f;
-    if (edge & pick) __stcg(&go[p * go_stride], f);
+    if (edge & pick) {
+      if (TAGGED) tag_store(&go[p * go_stride], f, link_tag(t));
+      else __stcg(&go[p * go_stride], f);
+    }
   }
   // the ports no flit took carry nothing this cycle
   const uint4 z = make_uint4(0, 0, 0, 0);
@@ -873,7 +927,10 @@ __device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint
   for (int d = 0; d < 4; ++d)
     if (freem & (1u << d) || !(exists & (1u << d))) {
       so[d * so_stride] = z;
-      if (edge & (1u << d)) __stcg(&go[d * go_stride], z);
+      if (edge & (1u << d)) {
+        if (TAGGED) tag_store(&go[d * go_stride], z, link_tag(t));
+        else __stcg(&go[d * go_stride], z);
+      }
     }
 }
 

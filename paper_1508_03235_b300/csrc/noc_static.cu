@@ -109,14 +109,14 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
   // carve the state out of the static array
   const size_t w1 = N * P.l1_sets * P.l1_ways, w2 = N * P.l2_sets * P.l2_ways;
   const bool lspd = l2_policy != NOC_L2_INTERLEAVED, mig = l2_policy == NOC_L2_LSPD_MIGRATE;
-  const size_t n_flags = 1024;
-  size_t off[18], cur = 0;
-  const size_t sz[18] = {2 * 4 * N * 16, NCORE * N * 4, N * P.core_q * 16, N * P.svc_q * 16,
+  const size_t n_flags = 1024 * FLAG_SLOTS;
+  size_t off[19], cur = 0;
+  const size_t sz[19] = {2 * 4 * N * 16, NCORE * N * 4, N * P.core_q * 16, N * P.svc_q * 16,
                          N * P.mem_q * 16, w1 * 4, w1 * 2, w2 * 4, lspd ? w2 * 2 : 0,
                          mig ? w2 * hist_stride(P.mig_window) * 2 : 0, lspd ? (size_t)total * 4 : 0,
                          mig ? N * P.fwd_cap * 8 : 0, (size_t)NSTAT * N * 8,
-                         2 * HIST_BINS * 8, n_flags * 4, 8, 4, 64 * 8};
-  for (int k = 0; k < 18; ++k) {
+                         2 * HIST_BINS * 8, n_flags * 4, 8, 4, 64 * 8, 2 * 4 * N * 32};
+  for (int k = 0; k < 19; ++k) {
     off[k] = a256(cur);
     cur = off[k] + sz[k];
   }
@@ -151,10 +151,11 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
   P.err = reinterpret_cast<unsigned long long*>(b + off[15]);
   unsigned int* abort_flag = reinterpret_cast<unsigned int*>(b + off[16]);
   unsigned long long* totals = reinterpret_cast<unsigned long long*>(b + off[17]);
+  P.gtag = reinterpret_cast<uint4*>(b + off[18]);
 
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   // everything the simulation reads before writing starts from its reset value
-  for (int k = 0; k < 18; ++k) {
+  for (int k = 0; k < 19; ++k) {
     if (!sz[k] || k == 2 || k == 3 || k == 4) continue;  // queue slots are written before read
     int v = (k == 10 || k == 15) ? 0xFF : 0;              // directory NONE, no error
     if (cudaMemsetAsync(b + off[k], v, sz[k], st) != cudaSuccess) return NOC_ERR_CUDA;
@@ -165,7 +166,7 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
   for (int side = 16; side >= 1 && !gx; side /= 2) {
     int tx = (mesh_w + side - 1) / side, ty = (mesh_h + side - 1) / side;
     int threads = block_threads(mesh_w, mesh_h, tx, ty), cap = 0;
-    if (threads > 384 || (size_t)tx * ty > n_flags) continue;
+    if (threads > 384 || (size_t)tx * ty * FLAG_SLOTS > n_flags) continue;
     if (max_coresident_ctas(P, threads, &cap) != cudaSuccess) return NOC_ERR_CUDA;
     if (tx * ty <= cap) {
       gx = tx;

@@ -72,6 +72,18 @@ def test_tilings_hash_identically(noc, oracle_mod, tiling):
     assert g.tiling() == tiling
 
 
+@pytest.mark.parametrize("tiling", [(1, 1), (2, 2), (8, 8), (3, 5), (8, 1), (1, 8), (4, 3)])
+def test_tilings_untraced(noc, oracle_mod, tiling):
+    """The untraced cycle loop (per-warp cycle flags, no CTA barrier per cycle)
+    on every shape of rectangle, down to one tile per CTA, over several
+    launches."""
+    g, o = pair(noc, oracle_mod, I.MESH_8["params"], tiling=tiling)
+    for n in (1, 2, 700, 333):
+        g.step(n)
+        o.step(n)
+        assert_same(g, o)
+
+
 @pytest.mark.parametrize("policy", [1, 2])
 def test_lspd_policies_mesh8(noc, oracle_mod, policy):
     p = I.sim_params(8, 8, policy=policy, seed=1)
@@ -106,6 +118,9 @@ def test_ragged_meshes(noc, oracle_mod, w, h, tiling):
     g, o = pair(noc, oracle_mod, p, tiling=tiling)
     run_traced(g, o, 1200)
     assert_same(g, o)
+    g2 = noc.Sim(p, tiling=tiling)
+    g2.step(1200)
+    assert_same(g2, o)
 
 
 def test_mesh64_hotspot(noc, oracle_mod):
@@ -132,6 +147,10 @@ def test_mesh208_full_size_prefix(noc, oracle_mod, period):
     g, o = pair(noc, oracle_mod, I.mesh_208(period))
     run_traced(g, o, 160)
     assert_same(g, o)
+    g2 = noc.Sim(I.mesh_208(period))
+    g2.step(100)
+    g2.step(60)
+    assert_same(g2, o)
 
 
 def test_network_mode(noc, oracle_mod):
