@@ -473,7 +473,7 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
       if ((exists & ~boundary) & (1u << P_S)) in[P_S] = sp[P_N * nt + in_s];
       if ((exists & ~boundary) & (1u << P_E)) in[P_E] = sp[P_W * nt + in_e];
       if ((exists & ~boundary) & (1u << P_W)) in[P_W] = sp[P_E * nt + in_w];
-      route<true>(P, T, t, in, exists, sl + pout * 4 * nt + i, nt, P.gtag + pout * pstride + (size_t)r * 2,
+      route_ranked(P, T, t, in, exists, sl + pout * 4 * nt + i, nt, P.gtag + pout * pstride + (size_t)r * 2,
                   2 * N, edge_out);
     }
     // ---- publish: this warp has routed cycle t (the warp barrier orders every

@@ -67,6 +67,9 @@ struct Params {
   // multiply-high reciprocals: n / d == umul64hi(n, m) for d >= 2 (m = 2^64 / d
   // rounded up), exact for every n < 2^32; see set_divisors()
   unsigned long long mW, mN, mL1, mL2;
+  // n / W == umulhi(n, mW32) for W >= 2 (mW32 = 2^32 / W rounded up; 0 for
+  // W == 1), exact for n < 2^16: tile indices
+  uint32_t mW32;
   // device arrays
   uint4* glink;          // [2][4][N] out-links by parity, port, tile
   // out-links that cross a CTA rectangle's edge, as written during a launch of
@@ -108,6 +111,7 @@ inline unsigned long long recip64(uint32_t d) { return d <= 1 ? 0ull : (~0ull) /
 inline void set_divisors(Params& P) {
   P.hist_stride = hist_stride(P.mig_window);
   P.mW = recip64((uint32_t)P.W);
+  P.mW32 = P.W <= 1 ? 0u : (uint32_t)((0x100000000ull + (uint32_t)P.W - 1) / (uint32_t)P.W);
   P.mN = recip64((uint32_t)P.N);
   P.mL1 = recip64((uint32_t)P.l1_sets);
   P.mL2 = recip64((uint32_t)P.l2_sets);
@@ -901,7 +905,7 @@ __device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint
     const bool valid = i < 4 ? (k[i] != NOKEY) : has_inj;
     if (!valid) continue;
     const uint32_t dst = fdst(f);
-    const uint32_t dsty = qdiv(dst, P.mW);
+    const uint32_t dsty = P.mW32 ? __umulhi(dst, P.mW32) : dst;
     const int dx = (int)(dst - dsty * (uint32_t)P.W) - (int)T.x;
     const int dy = (int)dsty - (int)T.y;
     const uint32_t xb = dx > 0 ? (1u << P_E) : (dx < 0 ? (1u << P_W) : 0u);
@@ -932,6 +936,135 @@ __device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint
         else __stcg(&go[d * go_stride], z);
       }
     }
+}
+
+// The productive ports of a flit at tile (x, y): X direction in bits 0-3, Y
+// direction in bits 4-7 (one port bit each, or none when aligned).
+__device__ __forceinline__ uint32_t prod_ports(const Params& P, uint32_t dst, uint32_t x, uint32_t y) {
+  const uint32_t dy_ = P.mW32 ? __umulhi(dst, P.mW32) : dst;
+  const uint32_t dx_ = dst - dy_ * (uint32_t)P.W;
+  const uint32_t xb = dx_ > x ? (1u << P_E) : (dx_ < x ? (1u << P_W) : 0u);
+  const uint32_t yb = dy_ > y ? (1u << P_S) : (dy_ < y ? (1u << P_N) : 0u);
+  return xb | (yb << 4);
+}
+// first free port of [X-productive, Y-productive, N, S, E, W]; counts a
+// deflection when neither productive port is free
+__device__ __forceinline__ uint32_t pick_port(uint32_t prod, uint32_t freem, uint32_t& defl) {
+  const uint32_t xb = prod & 15u, yb = prod >> 4;
+  const uint32_t low = freem & (0u - freem);
+  const bool px = (freem & xb) != 0, py = (freem & yb) != 0;
+  defl += (!px && !py) ? 1u : 0u;
+  return px ? xb : (py ? yb : low);
+}
+
+// The router of Sec. 4.3 as route() computes it, for the plain cycle loop:
+// arrivals are ranked by pairwise key comparisons instead of being sorted, so
+// flits never move between registers; each flit is stored once, to its port's
+// slot, after all four slots were cleared.  Links in `edge` (leaving the CTA
+// rectangle) are then copied from the slots to tagged global slots.
+__device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t t, const uint4 (&in)[4],
+                                             uint32_t exists, uint4* so, int so_stride, uint4* go,
+                                             size_t go_stride, uint32_t edge) {
+  uint32_t vm = 0;
+  unsigned long long k[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    vm |= (ftype(in[d]) != T_NONE ? 1u : 0u) << d;
+    k[d] = fkey(in[d]);
+  }
+  const int n_arr = __popc(vm);
+  // eject the highest-priority arrival addressed to this tile
+  int ej = -1;
+  unsigned long long ejk = ~0ull;
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+    if (((vm >> d) & 1u) && fdst(in[d]) == T.r && k[d] < ejk) {
+      ejk = k[d];
+      ej = d;
+    }
+  T.ej = make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+    if (d == ej) T.ej = in[d];
+  const uint32_t rm = ej >= 0 ? vm & ~(1u << ej) : vm;
+  // rank of each remaining arrival: how many remaining arrivals are older
+  // (keys are unique: a tile injects at most one flit per cycle)
+  uint32_t rk[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = a + 1; b < 4; ++b) {
+      const bool lt = k[a] < k[b];
+      rk[b] += (((rm >> a) & 1u) && lt) ? 1u : 0u;
+      rk[a] += (((rm >> b) & 1u) && !lt) ? 1u : 0u;
+    }
+  uint32_t prod[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) prod[d] = prod_ports(P, fdst(in[d]), T.x, T.y);
+  // inject when an input port is free: service queue first, then core queue
+  uint4 inj = make_uint4(0, 0, 0, 0);
+  bool has_inj = false;
+  if (n_arr < __popc(exists)) {
+    if (T.sq_len > 0) {
+      inj = T.sq_front;
+      T.sq_head = T.sq_head + 1 == (uint32_t)P.svc_q ? 0 : T.sq_head + 1;
+      T.sq_len--;
+      if (T.sq_len > 0) T.sq_front = P.sq[(size_t)T.r * P.svc_q + T.sq_head];
+      has_inj = true;
+    } else if (T.cq_len > 0) {
+      inj = T.cq_front;
+      T.cq_head = T.cq_head + 1 == (uint32_t)P.core_q ? 0 : T.cq_head + 1;
+      T.cq_len--;
+      if (T.cq_len > 0) T.cq_front = P.cq[(size_t)T.r * P.core_q + T.cq_head];
+      has_inj = true;
+    }
+    if (has_inj) {
+      inj.x = t;
+      inj.y = (inj.y & 0xFFFF0000u) | T.r;
+      T.inj++;
+    }
+  }
+  // ports in priority order: arrivals oldest first, then the injected flit
+  uint32_t freem = exists, defl = 0;
+  uint32_t pk[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    uint32_t pr = 0;
+    bool has = false;
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+      if (((rm >> d) & 1u) && rk[d] == (uint32_t)r) {
+        pr = prod[d];
+        has = true;
+      }
+    if (has) {
+      const uint32_t pick = pick_port(pr, freem, defl);
+      freem &= ~pick;
+#pragma unroll
+      for (int d = 0; d < 4; ++d)
+        if (((rm >> d) & 1u) && rk[d] == (uint32_t)r) pk[d] = pick;
+    }
+  }
+  uint32_t pki = 0;
+  if (has_inj) {
+    pki = pick_port(prod_ports(P, fdst(inj), T.x, T.y), freem, defl);
+    freem &= ~pki;
+  }
+  T.defl += defl;
+  // every slot cleared, then each flit stored to the slot of its port
+  const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (int d = 0; d < 4; ++d) so[d * so_stride] = z;
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+    if ((rm >> d) & 1u) so[(__ffs(pk[d]) - 1) * so_stride] = in[d];
+  if (has_inj) so[(__ffs(pki) - 1) * so_stride] = inj;
+  if (edge) {
+    const uint32_t tag = link_tag(t);
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+      if ((edge >> d) & 1u) tag_store(&go[d * go_stride], so[d * so_stride], tag);
+  }
 }
 
 // ---------------------------------------------------------------- Phase 3
