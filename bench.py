@@ -111,12 +111,11 @@ def measured_peaks():
 
 
 def algorithmic_bytes(stats_delta, router_cycles, p):
-    """State bytes a cycle-stepped simulator must touch (model text, Sec. 5 of
-    the design notes): per router-cycle the four in-link and four out-link
-    slots (8 x 16 B) and the tile's 13-word core record read and written
-    (2 x 52 B); per L1 lookup or fill one L1 set read and written; per L2
-    access (lookup, install, write-through) one L2 set read and written; per
-    injected flit one 16 B queue push and pop."""
+    """State bytes a cycle-stepped simulator must touch: per router-cycle the
+    four in-link and four out-link slots (8 x 16 B) and the tile's 13-word
+    core record read and written (2 x 52 B); per L1 lookup or fill one L1 set
+    read and written; per L2 access (lookup, install, write-through) one L2
+    set read and written; per injected flit one 16 B queue push and pop."""
     l1set = 4 * p["l1_ways"]
     l2set = 4 * p["l2_ways"]
     d = stats_delta
@@ -124,6 +123,34 @@ def algorithmic_bytes(stats_delta, router_cycles, p):
     l2_ops = d["l2_hit"] + d["l2_miss"] + d["wt_hit"] + d["mem_write"] + d["mem_req"]
     return (router_cycles * (8 * 16 + 2 * 52) + l1_ops * 2 * l1set + l2_ops * 2 * l2set
             + d["injected"] * 2 * 16)
+
+
+KERNEL_SOURCES = ("noc_model.cuh", "noc_kernel.cuh", "noc_internal.h", "noc_run_variant.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "run_kernel_mesh208_traffic.md")
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1508_03235_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(cycles_per_launch):
+    """DRAM bytes (read + write) per cycle-kernel launch, scaled from the
+    committed ncu capture of the same kernel sources (by cycles per launch);
+    None when there is no capture or the kernel changed since it was taken."""
+    import re
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    text = open(TRAFFIC_FILE).read()
+    sha = re.search(r"kernel_sources_sha256:\s*([0-9a-f]{64})", text)
+    per = re.search(r"dram_bytes_per_cycle:\s*([0-9.eE+]+)", text)
+    if not sha or not per or sha.group(1) != kernel_sources_sha256():
+        return None
+    return float(per.group(1)) * cycles_per_launch
 
 
 # --------------------------------------------------------------------- GPU arm
@@ -145,17 +172,10 @@ def run_gpu(args):
     tiling = sims[0].tiling()
     cycles = args.cycles
 
-    def one_step(record=None):
+    def one_step():
         for s in sims:
             s.reset()
-            if record is not None:
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
             s.step_async(cycles)
-            if record is not None:
-                e1.record(stream)
-                record.append((e0, e1))
 
     for _ in range(args.warmup):
         one_step()
@@ -170,12 +190,13 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    records = []
+    for s in sims:
+        s.kernel_time(True)               # events around every cycle-kernel launch
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
     for _ in range(args.steps):
-        one_step(records)
+        one_step()
     t_end.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -189,12 +210,17 @@ def run_gpu(args):
     ms, value = replica_throughput(ms, rc_per_rank, world, device="cuda")
 
     # roofline of the cycle kernel: algorithmic bytes / its event-timed duration
-    launch_ms = [a.elapsed_time(b) for a, b in records]
-    stats = [s.stats() for s in sims]          # the last step's counters per period
-    alg = sum(algorithmic_bytes(st, TILES * cycles, sims[0].params) for st in stats) / len(sims)
-    avg_launch_s = statistics.mean(launch_ms) / 1e3
+    kt = [s.kernel_time(False) for s in sims]
+    kernel_ms = sum(m for m, _ in kt)
+    n_launch = sum(n for _, n in kt)
+    stats = [s.stats() for s in sims]          # every step repeats these runs exactly
+    alg_total = args.steps * sum(algorithmic_bytes(st, TILES * cycles, sims[0].params)
+                                 for st in stats)
+    alg = alg_total / n_launch                 # per launch
+    avg_launch_ms = kernel_ms / n_launch
     peak, peak_kind = measured_peaks()
-    achieved = alg / avg_launch_s / 1e9
+    achieved = alg_total / (kernel_ms / 1e3) / 1e9
+    traffic = measured_traffic(args.steps * len(PERIODS) * cycles / n_launch)
 
     # end to end through the public API: reset, run, read the counters back
     e2e_steps = max(1, min(args.steps, 3))
@@ -230,9 +256,9 @@ def run_gpu(args):
             "config": workload_config({"cycles_per_run": cycles, "tiling": list(tiling),
                                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "kernel": "noc::run_kernel",
-                         "avg_launch_ms": statistics.mean(launch_ms),
+                         "launches": n_launch, "avg_launch_ms": avg_launch_ms,
                          "alg_bytes_per_launch": alg},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -240,6 +240,15 @@ int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* cache, int l2_po
 /* Number of this library's kernels launched through this handle. */
 int64_t noc_kernel_launches(const noc_sim* sim);
 
+/* Device time of the cycle kernel alone.  With enable != 0, every later
+ * cycle-kernel launch through this handle is bracketed by a pair of CUDA
+ * events on the handle's stream (reference draws and other helper kernels
+ * are left out).  If ms_out or launches_out is non-NULL the call first waits
+ * for the recorded launches, writes their summed duration in milliseconds
+ * and their number, and forgets them.  Returns NOC_ERR_CUDA if an event call
+ * fails. */
+int noc_kernel_time(noc_sim* sim, int enable, double* ms_out, int64_t* launches_out);
+
 const char* noc_last_error(void);
 
 #ifdef __cplusplus

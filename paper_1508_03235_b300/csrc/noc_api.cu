@@ -86,6 +86,10 @@ struct noc_sim {
   long long wait_ns = 2000000000ll;
   int silent_cta = -1;
   int64_t launches = 0;
+  // cycle-kernel timing: event pairs [2k, 2k + 1] around launch k
+  bool time_kernels = false;
+  std::vector<cudaEvent_t> tev;
+  size_t tev_used = 0;
 };
 
 namespace {
@@ -331,8 +335,20 @@ int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
          "clear edge slots");
       s->gtag_clean = true;
     }
+    if (s->time_kernels) {
+      while (s->tev.size() < s->tev_used + 2) {
+        cudaEvent_t e;
+        CU(cudaEventCreate(&e), "event create");
+        s->tev.push_back(e);
+      }
+      CU(cudaEventRecord(s->tev[s->tev_used], s->stream), "event record");
+    }
     CU(launch_run(s->P, A, s->stream), "cycle kernel launch");
     s->launches++;
+    if (s->time_kernels) {
+      CU(cudaEventRecord(s->tev[s->tev_used + 1], s->stream), "event record");
+      s->tev_used += 2;
+    }
     if (plain) {
       s->gtag_clean = false;
       s->gtag_end = s->cycle + c;
@@ -440,6 +456,7 @@ void noc_destroy(noc_sim* s) {
   if (s->d_busy) cudaFree(s->d_busy);
   if (s->d_trace) cudaFree(s->d_trace);
   if (s->d_trace_off) cudaFree(s->d_trace_off);
+  for (cudaEvent_t e : s->tev) cudaEventDestroy(e);
   delete s;
 }
 
@@ -811,6 +828,24 @@ int noc_debug_wait_limit(noc_sim* s, int64_t ns, int silent_cta) {
 }
 
 int64_t noc_kernel_launches(const noc_sim* s) { return s ? s->launches : -1; }
+
+int noc_kernel_time(noc_sim* s, int enable, double* ms_out, int64_t* launches_out) {
+  if (!s) return fail(NOC_ERR_ARG, "null handle");
+  if (ms_out || launches_out) {
+    double ms = 0.0;
+    if (s->tev_used) CU(cudaEventSynchronize(s->tev[s->tev_used - 1]), "event sync");
+    for (size_t k = 0; k + 1 < s->tev_used; k += 2) {
+      float m = 0.f;
+      CU(cudaEventElapsedTime(&m, s->tev[k], s->tev[k + 1]), "event time");
+      ms += m;
+    }
+    if (ms_out) *ms_out = ms;
+    if (launches_out) *launches_out = (int64_t)(s->tev_used / 2);
+    s->tev_used = 0;
+  }
+  s->time_kernels = enable != 0;
+  return NOC_OK;
+}
 
 }  // extern "C"
 

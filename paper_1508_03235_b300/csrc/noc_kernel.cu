@@ -7,15 +7,18 @@ namespace noc {
 // ---------------------------------------------------------------- dispatch
 // Kernel variants shipped: per-cycle hash / drain records on or off, and the
 // compile-time way bounds (L1, L2) of the cache-set code: (4, 8), (4, 16) and
-// the general (16, 16).
-#define NOC_DECL_RUN(h, d, w1, w2) \
-  cudaError_t launch_run_##h##_##d##_##w1##_##w2(const Params&, const RunArgs&, cudaStream_t);
+// the general (16, 16); the plain loop also comes specialised to the
+// interleaved L2 in cache mode (the other policies' code compiled out).
+#define NOC_DECL_RUN(h, d, w1, w2, sp) \
+  cudaError_t launch_run_##h##_##d##_##w1##_##w2##_##sp(const Params&, const RunArgs&, cudaStream_t);
 #define NOC_DECL_WAYS(w1, w2)                                                   \
-  NOC_DECL_RUN(0, 0, w1, w2)                                                    \
-  NOC_DECL_RUN(1, 0, w1, w2)                                                    \
-  NOC_DECL_RUN(0, 1, w1, w2)                                                    \
-  NOC_DECL_RUN(1, 1, w1, w2)                                                    \
-  cudaError_t max_coresident_run_0_0_##w1##_##w2(int threads, int* out);       \
+  NOC_DECL_RUN(0, 0, w1, w2, gen)                                               \
+  NOC_DECL_RUN(1, 0, w1, w2, gen)                                               \
+  NOC_DECL_RUN(0, 1, w1, w2, gen)                                               \
+  NOC_DECL_RUN(1, 1, w1, w2, gen)                                               \
+  NOC_DECL_RUN(0, 0, w1, w2, il)                                                \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_gen(int threads, int* out);  \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_il(int threads, int* out);   \
   cudaError_t launch_batch_##w1##_##w2(const BatchArgs&, int, int, cudaStream_t); \
   cudaError_t max_coresident_batch_##w1##_##w2(int threads, int* out);
 NOC_DECL_WAYS(4, 8)
@@ -27,26 +30,32 @@ static int way_class(int l1_ways, int l2_ways) {
   if (l1_ways > 4) return 2;
   return l2_ways <= 8 ? 0 : 1;
 }
+// the plain loop has a variant specialised to the interleaved L2 in cache mode
+static bool interleaved_cache(const Params& P) {
+  return P.policy == POL_INTERLEAVED && P.mode == MODE_CACHE;
+}
 
-#define NOC_PICK_RUN(h, d)                                        \
+#define NOC_PICK_RUN(h, d, sp)                                    \
   switch (way_class(P.l1_ways, P.l2_ways)) {                      \
-    case 0: return launch_run_##h##_##d##_4_8(P, A, s);           \
-    case 1: return launch_run_##h##_##d##_4_16(P, A, s);          \
-    default: return launch_run_##h##_##d##_16_16(P, A, s);        \
+    case 0: return launch_run_##h##_##d##_4_8_##sp(P, A, s);      \
+    case 1: return launch_run_##h##_##d##_4_16_##sp(P, A, s);     \
+    default: return launch_run_##h##_##d##_16_16_##sp(P, A, s);   \
   }
 
 cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
-  if (A.hash_trace && A.busy) { NOC_PICK_RUN(1, 1) }
-  if (A.hash_trace) { NOC_PICK_RUN(1, 0) }
-  if (A.busy) { NOC_PICK_RUN(0, 1) }
-  NOC_PICK_RUN(0, 0)
+  if (A.hash_trace && A.busy) { NOC_PICK_RUN(1, 1, gen) }
+  if (A.hash_trace) { NOC_PICK_RUN(1, 0, gen) }
+  if (A.busy) { NOC_PICK_RUN(0, 1, gen) }
+  if (interleaved_cache(P)) { NOC_PICK_RUN(0, 0, il) }
+  NOC_PICK_RUN(0, 0, gen)
 }
 
 cudaError_t max_coresident_ctas(const Params& P, int threads, int* out) {
+  const bool il = interleaved_cache(P);
   switch (way_class(P.l1_ways, P.l2_ways)) {
-    case 0: return max_coresident_run_0_0_4_8(threads, out);
-    case 1: return max_coresident_run_0_0_4_16(threads, out);
-    default: return max_coresident_run_0_0_16_16(threads, out);
+    case 0: return il ? max_coresident_run_0_0_4_8_il(threads, out) : max_coresident_run_0_0_4_8_gen(threads, out);
+    case 1: return il ? max_coresident_run_0_0_4_16_il(threads, out) : max_coresident_run_0_0_4_16_gen(threads, out);
+    default: return il ? max_coresident_run_0_0_16_16_il(threads, out) : max_coresident_run_0_0_16_16_gen(threads, out);
   }
 }
 

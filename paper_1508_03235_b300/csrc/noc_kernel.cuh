@@ -503,7 +503,10 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
     if (sh_hist[k]) atomicAdd(&P.hist[k], (unsigned long long)sh_hist[k]);
 }
 
-template <bool HASH, bool DRAIN, int W1, int W2>
+// POLV names the device code's specialisation (-1: every policy and mode; p:
+// the L2 policy p in cache mode only), so the instantiations of translation
+// units built with different NOC_FIXED_POLICY are distinct kernels.
+template <bool HASH, bool DRAIN, int W1, int W2, int POLV>
 __global__ void __launch_bounds__(MAX_THREADS, 1)
     run_kernel(const __grid_constant__ Params P, const __grid_constant__ RunArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -513,34 +516,34 @@ __global__ void __launch_bounds__(MAX_THREADS, 1)
     run_rect<HASH, DRAIN, W1, W2>(P, A, blockIdx.x, smem_raw);
 }
 
-template <bool H, bool D, int W1, int W2>
+template <bool H, bool D, int W1, int W2, int POLV>
 static cudaError_t prepare_run() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(run_kernel<H, D, W1, W2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(run_kernel<H, D, W1, W2, POLV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)run_smem_bytes_impl(MAX_THREADS));
   if (e == cudaSuccess) done = true;
   return e;
 }
 
-template <bool H, bool D, int W1, int W2>
+template <bool H, bool D, int W1, int W2, int POLV>
 static cudaError_t launch_run_t(const Params& P, const RunArgs& A, cudaStream_t s) {
-  cudaError_t e = prepare_run<H, D, W1, W2>();
+  cudaError_t e = prepare_run<H, D, W1, W2, POLV>();
   if (e != cudaSuccess) return e;
   const int threads = block_threads_impl(P.W, P.H, A.gx, A.gy);
   void* args[] = {(void*)&P, (void*)&A};
-  return cudaLaunchCooperativeKernel((const void*)run_kernel<H, D, W1, W2>, dim3(A.gx * A.gy),
+  return cudaLaunchCooperativeKernel((const void*)run_kernel<H, D, W1, W2, POLV>, dim3(A.gx * A.gy),
                                      dim3(threads), args, run_smem_bytes_impl(threads), s);
 }
 
-template <int W1, int W2>
+template <int W1, int W2, int POLV>
 static cudaError_t max_coresident_run_t(int threads, int* out) {
-  cudaError_t e = prepare_run<false, false, W1, W2>();
+  cudaError_t e = prepare_run<false, false, W1, W2, POLV>();
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, run_kernel<false, false, W1, W2>, threads,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, run_kernel<false, false, W1, W2, POLV>, threads,
                                                     run_smem_bytes_impl(threads));
   if (e != cudaSuccess) return e;
   *out = per * sms;

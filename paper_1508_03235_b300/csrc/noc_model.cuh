@@ -11,6 +11,19 @@
 
 namespace noc {
 
+// A translation unit compiled with -DNOC_FIXED_POLICY=<p> -DNOC_FIXED_MODE=<m>
+// builds the device code for that L2 policy and traffic mode alone (the other
+// paths are compiled out); otherwise both are read from the parameters.
+#if defined(NOC_FIXED_POLICY) && defined(NOC_FIXED_MODE)
+#define POLICY(P) (NOC_FIXED_POLICY)
+#define MODE(P) (NOC_FIXED_MODE)
+#define NOC_WITH_LSPD (NOC_FIXED_POLICY != 0)
+#else
+#define POLICY(P) ((P).policy)
+#define MODE(P) ((P).mode)
+#define NOC_WITH_LSPD 1
+#endif
+
 // ---------------------------------------------------------------- constants
 enum : uint32_t {
   T_NONE = 0, T_REQ = 1, T_DATA = 2, T_WT = 3, T_DA = 4, T_DRPOS = 5, T_DRNEG = 6,
@@ -261,7 +274,7 @@ __device__ __forceinline__ uint32_t l1_set(const Params& P, uint32_t line) {
   return line - qdiv(line, P.mL1) * (uint32_t)P.l1_sets;
 }
 __device__ __forceinline__ uint32_t l2_set(const Params& P, uint32_t line) {
-  uint32_t v = P.policy == POL_INTERLEAVED ? qdiv(line, P.mN) : line;
+  uint32_t v = POLICY(P) == POL_INTERLEAVED ? qdiv(line, P.mN) : line;
   return v - qdiv(v, P.mL2) * (uint32_t)P.l2_sets;
 }
 
@@ -466,20 +479,20 @@ static __device__ int l2_install(const Params& P, Tile& T, uint32_t line, uint32
     if (old & W_VALID) {
       prev = wrank(old);
       if (old & W_DIRTY) SMALL(S_MEMWB)++;
-      if (P.policy != POL_INTERLEAVED) send_dinv(P, T, old & W_LINE, P.l2ep[base + way], t);
+      if (POLICY(P) != POL_INTERLEAVED) send_dinv(P, T, old & W_LINE, P.l2ep[base + way], t);
     } else {
       prev = set_nvalid(w, P.l2_ways);
     }
     set_put(w, way, W_VALID | line);
     set_promote(w, P.l2_ways, way, prev);
-    if (P.policy == POL_MIGRATE) {
+    if (POLICY(P) == POL_MIGRATE) {
       uint16_t* hp = hist_ptr(P, base + way);
       hp[0] = 0;
       hp[1] = 0;
     }
   }
   store_set(P.l2 + base, P.l2_ways, w);
-  if (P.policy != POL_INTERLEAVED) P.l2ep[base + way] = (uint16_t)epoch;
+  if (POLICY(P) != POL_INTERLEAVED) P.l2ep[base + way] = (uint16_t)epoch;
   return way;
 }
 
@@ -578,7 +591,7 @@ static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* s
   uint32_t set = l2_set(P, line);
   size_t base = l2_base(P, T.r, set);
 
-  if (P.policy == POL_INTERLEAVED) {
+  if (POLICY(P) == POL_INTERLEAVED) {
     uint32_t h = home_of(P, line);
     if (h == T.r) {
       uint32_t w[W2];
@@ -629,7 +642,7 @@ static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* s
     SMALL(S_L2H)++;
     set_touch(w, P.l2_ways, way);
     store_set(P.l2 + base, P.l2_ways, w);
-    if (P.policy == POL_MIGRATE) hist_push(P, base + way, T.r);
+    if (POLICY(P) == POL_MIGRATE) hist_push(P, base + way, T.r);
     l1_fill<W1>(P, T, line, T.r);
     if (write) local_wt<W2>(P, T, line);
     l2lat_sample(T, t, start, sh_hist);
@@ -713,13 +726,13 @@ __device__ __forceinline__ void mq_pop(const Params& P, Tile& T) {
 // the destination tile for network-only probes); false past a trace's end.
 // This is the definition; gen_refs_kernel and the in-place draw both use it.
 static __device__ bool draw_ref(const Params& P, uint32_t core, uint32_t k, uint32_t& raw) {
-  if (P.mode == MODE_TRACE) {
+  if (MODE(P) == MODE_TRACE) {
     uint32_t off = P.trace_off[core], n = P.trace_off[core + 1] - off;
     if (k >= n) return false;
     raw = P.trace[off + k];
     return true;
   }
-  if (P.mode == MODE_NETWORK) {
+  if (MODE(P) == MODE_NETWORK) {
     unsigned long long w[4];
     philox4x64_10(k, core, P.stream, 0, P.seed, 0x4E4F43ull, w);
     uint32_t dst = (uint32_t)__umul64hi(w[1], (unsigned long long)(P.N - 1));
@@ -790,7 +803,7 @@ static __device__ bool phase1(const Params& P, Tile& T, uint32_t t, bool drainin
   if (draining || P.period <= 0) return false;
   if ((unsigned long long)t < (unsigned long long)T.next_ref * (unsigned long long)P.period) return false;
 
-  if (P.mode == MODE_NETWORK && P.N < 2) return false;
+  if (MODE(P) == MODE_NETWORK && P.N < 2) return false;
   uint32_t raw;
   if (T.pf_ok) {
     raw = T.pf_raw;
@@ -799,7 +812,7 @@ static __device__ bool phase1(const Params& P, Tile& T, uint32_t t, bool drainin
     T.pf_raw = raw;          // kept for a retry after a full core queue
     T.pf_ok = 1;
   }
-  if (P.mode == MODE_NETWORK) {
+  if (MODE(P) == MODE_NETWORK) {
     if (cq_full(P, T)) {
       SMALL(S_CQST)++;
       return true;
@@ -1097,7 +1110,7 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
         set_touch(w, P.l2_ways, way);
         store_set(P.l2 + base, P.l2_ways, w);
         send_svc(P, T, mkflit(T_DATA, T.r, q, line, 0, 0), t);
-        if (P.policy == POL_MIGRATE) {
+        if (POLICY(P) == POL_MIGRATE) {
           hist_push(P, base + way, q);
           uint16_t* hp = hist_ptr(P, base + way);
           uint32_t n = hp[0], cnt = 0;
@@ -1111,7 +1124,7 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
         break;
       }
       SMALL(S_L2M)++;
-      if (P.policy == POL_INTERLEAVED) {
+      if (POLICY(P) == POL_INTERLEAVED) {
         if (T.mq_len >= (uint32_t)P.mem_q) {
           set_error(P, t, ERR_OVERFLOW);
           break;
@@ -1125,7 +1138,7 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
         SMALL(S_MEMREQ)++;
         break;
       }
-      if (P.policy == POL_MIGRATE) {
+      if (POLICY(P) == POL_MIGRATE) {
         // redirection (Sec. 3.3): the newest forward entry for the line
         const uint32_t* fw = P.fwd + (size_t)T.r * P.fwd_cap * 2;
         for (uint32_t i = 0; i < T.fwd_n; ++i) {
@@ -1174,6 +1187,7 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
       break;
     }
 
+#if NOC_WITH_LSPD
     case T_DA: {
       uint32_t q = fsrc(f), D = P.dir[line];
       SMALL(S_DIRS)++;
@@ -1277,6 +1291,7 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
       break;
     }
 
+#endif
     default:
       set_error(P, t, ERR_PROTOCOL);
   }

@@ -95,6 +95,7 @@ def lib():
             "noc_get_core": (i32, [vp, i32, P32]),
             "noc_debug_wait_limit": (i32, [vp, i64, i32]),
             "noc_kernel_launches": (i64, [vp]),
+            "noc_kernel_time": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)]),
             "noc_last_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -223,6 +224,13 @@ class Sim:
     @property
     def launches(self) -> int:
         return lib().noc_kernel_launches(self._h)
+
+    def kernel_time(self, enable: bool = True):
+        """(ms, launches) of the cycle-kernel launches recorded since the last
+        call (CUDA events around each launch), then keep recording iff enable."""
+        ms, n = C.c_double(), C.c_int64()
+        _check(lib().noc_kernel_time(self._h, int(enable), C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
     # --- results -----------------------------------------------------------
     def stats(self, tile: int = -1) -> dict:

@@ -58,7 +58,7 @@ def cached_tiling(params: dict):
     return tuple(t["tiling"]) if t else None
 
 
-def tune(params: dict, cycles: int = 400, warm: int = 100, max_cands: int = 10,
+def tune(params: dict, cycles: int = 2000, warm: int = 200, max_cands: int = 10,
          save: bool = True, verbose: bool = False):
     """Time candidate tilings; return (best tiling, {tiling: us per cycle})."""
     import torch
