@@ -8,7 +8,8 @@ namespace noc {
 // Kernel variants shipped: per-cycle hash / drain records on or off, and the
 // compile-time way bounds (L1, L2) of the cache-set code: (4, 8), (4, 16) and
 // the general (16, 16); the plain loop also comes specialised to the
-// interleaved L2 in cache mode (the other policies' code compiled out).
+// interleaved L2 in cache mode with the class's exact way counts (the other
+// policies' code compiled out, the way loops of fixed length).
 #define NOC_DECL_RUN(h, d, w1, w2, sp) \
   cudaError_t launch_run_##h##_##d##_##w1##_##w2##_##sp(const Params&, const RunArgs&, cudaStream_t);
 #define NOC_DECL_WAYS(w1, w2)                                                   \
@@ -31,8 +32,12 @@ static int way_class(int l1_ways, int l2_ways) {
   return l2_ways <= 8 ? 0 : 1;
 }
 // the plain loop has a variant specialised to the interleaved L2 in cache mode
+// with exactly the way counts of its class
 static bool interleaved_cache(const Params& P) {
-  return P.policy == POL_INTERLEAVED && P.mode == MODE_CACHE;
+  static const int exact[3][2] = {{4, 8}, {4, 16}, {16, 16}};
+  const int c = way_class(P.l1_ways, P.l2_ways);
+  return P.policy == POL_INTERLEAVED && P.mode == MODE_CACHE && P.l1_ways == exact[c][0] &&
+         P.l2_ways == exact[c][1];
 }
 
 #define NOC_PICK_RUN(h, d, sp)                                    \

@@ -14,6 +14,15 @@ namespace noc {
 // A translation unit compiled with -DNOC_FIXED_POLICY=<p> -DNOC_FIXED_MODE=<m>
 // builds the device code for that L2 policy and traffic mode alone (the other
 // paths are compiled out); otherwise both are read from the parameters.
+// With -DNOC_EXACT_WAYS the cache-set code takes the way counts to be exactly
+// the translation unit's compile-time bounds NOC_W1 and NOC_W2.
+#if defined(NOC_EXACT_WAYS)
+#define L1WAYS(P) (NOC_W1)
+#define L2WAYS(P) (NOC_W2)
+#else
+#define L1WAYS(P) ((P).l1_ways)
+#define L2WAYS(P) ((P).l2_ways)
+#endif
 #if defined(NOC_FIXED_POLICY) && defined(NOC_FIXED_MODE)
 #define POLICY(P) (NOC_FIXED_POLICY)
 #define MODE(P) (NOC_FIXED_MODE)
@@ -420,10 +429,10 @@ __device__ __forceinline__ void set_invalidate(uint32_t (&w)[MW], int ways, int 
 }
 
 __device__ __forceinline__ size_t l1_base(const Params& P, uint32_t r, uint32_t set) {
-  return ((size_t)r * P.l1_sets + set) * P.l1_ways;
+  return ((size_t)r * P.l1_sets + set) * L1WAYS(P);
 }
 __device__ __forceinline__ size_t l2_base(const Params& P, uint32_t r, uint32_t set) {
-  return ((size_t)r * P.l2_sets + set) * P.l2_ways;
+  return ((size_t)r * P.l2_sets + set) * L2WAYS(P);
 }
 
 // fill the L1 with `line` (insert if absent, else touch); L1 victims are clean
@@ -432,18 +441,18 @@ static __device__ void l1_fill(const Params& P, Tile& T, uint32_t line, uint32_t
   uint32_t set = l1_set(P, line);
   size_t base = l1_base(P, T.r, set);
   uint32_t w[W1];
-  load_set(P.l1 + base, P.l1_ways, w);
-  int way = set_find(w, P.l1_ways, line);
+  load_set(P.l1 + base, L1WAYS(P), w);
+  int way = set_find(w, L1WAYS(P), line);
   if (way >= 0) {
-    set_touch(w, P.l1_ways, way);
+    set_touch(w, L1WAYS(P), way);
   } else {
-    way = set_victim(w, P.l1_ways);
+    way = set_victim(w, L1WAYS(P));
     uint32_t old = set_get(w, way);
-    uint32_t prev = (old & W_VALID) ? wrank(old) : set_nvalid(w, P.l1_ways);
+    uint32_t prev = (old & W_VALID) ? wrank(old) : set_nvalid(w, L1WAYS(P));
     set_put(w, way, W_VALID | line);
-    set_promote(w, P.l1_ways, way, prev);
+    set_promote(w, L1WAYS(P), way, prev);
   }
-  store_set(P.l1 + base, P.l1_ways, w);
+  store_set(P.l1 + base, L1WAYS(P), w);
   P.l1own[base + way] = (uint16_t)owner;
 }
 
@@ -468,12 +477,12 @@ static __device__ int l2_install(const Params& P, Tile& T, uint32_t line, uint32
   uint32_t set = l2_set(P, line);
   size_t base = l2_base(P, T.r, set);
   uint32_t w[W2];
-  load_set(P.l2 + base, P.l2_ways, w);
-  int way = set_find(w, P.l2_ways, line);
+  load_set(P.l2 + base, L2WAYS(P), w);
+  int way = set_find(w, L2WAYS(P), line);
   if (way >= 0) {
-    set_touch(w, P.l2_ways, way);
+    set_touch(w, L2WAYS(P), way);
   } else {
-    way = set_victim(w, P.l2_ways);
+    way = set_victim(w, L2WAYS(P));
     uint32_t old = set_get(w, way);
     uint32_t prev;
     if (old & W_VALID) {
@@ -481,17 +490,17 @@ static __device__ int l2_install(const Params& P, Tile& T, uint32_t line, uint32
       if (old & W_DIRTY) SMALL(S_MEMWB)++;
       if (POLICY(P) != POL_INTERLEAVED) send_dinv(P, T, old & W_LINE, P.l2ep[base + way], t);
     } else {
-      prev = set_nvalid(w, P.l2_ways);
+      prev = set_nvalid(w, L2WAYS(P));
     }
     set_put(w, way, W_VALID | line);
-    set_promote(w, P.l2_ways, way, prev);
+    set_promote(w, L2WAYS(P), way, prev);
     if (POLICY(P) == POL_MIGRATE) {
       uint16_t* hp = hist_ptr(P, base + way);
       hp[0] = 0;
       hp[1] = 0;
     }
   }
-  store_set(P.l2 + base, P.l2_ways, w);
+  store_set(P.l2 + base, L2WAYS(P), w);
   if (POLICY(P) != POL_INTERLEAVED) P.l2ep[base + way] = (uint16_t)epoch;
   return way;
 }
@@ -502,12 +511,12 @@ static __device__ void local_wt(const Params& P, Tile& T, uint32_t line) {
   uint32_t set = l2_set(P, line);
   size_t base = l2_base(P, T.r, set);
   uint32_t w[W2];
-  load_set(P.l2 + base, P.l2_ways, w);
-  int way = set_find(w, P.l2_ways, line);
+  load_set(P.l2 + base, L2WAYS(P), w);
+  int way = set_find(w, L2WAYS(P), line);
   if (way >= 0) {
     set_put(w, way, set_get(w, way) | W_DIRTY);
-    set_touch(w, P.l2_ways, way);
-    store_set(P.l2 + base, P.l2_ways, w);
+    set_touch(w, L2WAYS(P), way);
+    store_set(P.l2 + base, L2WAYS(P), w);
     SMALL(S_WTH)++;
   } else {
     SMALL(S_MEMW)++;
@@ -552,8 +561,8 @@ static __device__ bool l1_step(const Params& P, Tile& T, uint32_t t, uint32_t li
   uint32_t set = l1_set(P, line);
   size_t base = l1_base(P, T.r, set);
   uint32_t w[W1];
-  load_set(P.l1 + base, P.l1_ways, w);
-  int way = set_find(w, P.l1_ways, line);
+  load_set(P.l1 + base, L1WAYS(P), w);
+  int way = set_find(w, L1WAYS(P), line);
   if (way >= 0) {
     if (write) {
       uint32_t owner = P.l1own[base + way];
@@ -569,8 +578,8 @@ static __device__ bool l1_step(const Params& P, Tile& T, uint32_t t, uint32_t li
         send_core(P, T, mkflit(T_WT, T.r, owner, line, 0, 0));
       }
     }
-    set_touch(w, P.l1_ways, way);
-    store_set(P.l1 + base, P.l1_ways, w);
+    set_touch(w, L1WAYS(P), way);
+    store_set(P.l1 + base, L1WAYS(P), w);
     SMALL(S_L1H)++;
     T.fsm = FSM_IDLE;
     return true;
@@ -595,12 +604,12 @@ static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* s
     uint32_t h = home_of(P, line);
     if (h == T.r) {
       uint32_t w[W2];
-      load_set(P.l2 + base, P.l2_ways, w);
-      int way = set_find(w, P.l2_ways, line);
+      load_set(P.l2 + base, L2WAYS(P), w);
+      int way = set_find(w, L2WAYS(P), line);
       if (way >= 0) {
         SMALL(S_L2H)++;
-        set_touch(w, P.l2_ways, way);
-        store_set(P.l2 + base, P.l2_ways, w);
+        set_touch(w, L2WAYS(P), way);
+        store_set(P.l2 + base, L2WAYS(P), w);
         l1_fill<W1>(P, T, line, T.r);
         if (write) local_wt<W2>(P, T, line);
         l2lat_sample(T, t, start, sh_hist);
@@ -636,12 +645,12 @@ static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* s
 
   // LSPD: the requester's own slice first (local placement, Sec. 3.3)
   uint32_t w[W2];
-  load_set(P.l2 + base, P.l2_ways, w);
-  int way = set_find(w, P.l2_ways, line);
+  load_set(P.l2 + base, L2WAYS(P), w);
+  int way = set_find(w, L2WAYS(P), line);
   if (way >= 0) {
     SMALL(S_L2H)++;
-    set_touch(w, P.l2_ways, way);
-    store_set(P.l2 + base, P.l2_ways, w);
+    set_touch(w, L2WAYS(P), way);
+    store_set(P.l2 + base, L2WAYS(P), w);
     if (POLICY(P) == POL_MIGRATE) hist_push(P, base + way, T.r);
     l1_fill<W1>(P, T, line, T.r);
     if (write) local_wt<W2>(P, T, line);
@@ -1103,12 +1112,12 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
       uint32_t q = fa(f);
       SMALL(S_REQR)++;
       uint32_t w[W2];
-      load_set(P.l2 + base, P.l2_ways, w);
-      int way = set_find(w, P.l2_ways, line);
+      load_set(P.l2 + base, L2WAYS(P), w);
+      int way = set_find(w, L2WAYS(P), line);
       if (way >= 0) {
         SMALL(S_L2H)++;
-        set_touch(w, P.l2_ways, way);
-        store_set(P.l2 + base, P.l2_ways, w);
+        set_touch(w, L2WAYS(P), way);
+        store_set(P.l2 + base, L2WAYS(P), w);
         send_svc(P, T, mkflit(T_DATA, T.r, q, line, 0, 0), t);
         if (POLICY(P) == POL_MIGRATE) {
           hist_push(P, base + way, q);
@@ -1174,12 +1183,12 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
 
     case T_WT: {
       uint32_t w[W2];
-      load_set(P.l2 + base, P.l2_ways, w);
-      int way = set_find(w, P.l2_ways, line);
+      load_set(P.l2 + base, L2WAYS(P), w);
+      int way = set_find(w, L2WAYS(P), line);
       if (way >= 0) {
         set_put(w, way, set_get(w, way) | W_DIRTY);
-        set_touch(w, P.l2_ways, way);
-        store_set(P.l2 + base, P.l2_ways, w);
+        set_touch(w, L2WAYS(P), way);
+        store_set(P.l2 + base, L2WAYS(P), w);
         SMALL(S_WTH)++;
       } else {
         SMALL(S_MEMW)++;
@@ -1272,12 +1281,12 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
       }
       // invalidate the source copy and remember where the block went
       uint32_t w[W2];
-      load_set(P.l2 + base, P.l2_ways, w);
-      int way = set_find(w, P.l2_ways, line);
+      load_set(P.l2 + base, L2WAYS(P), w);
+      int way = set_find(w, L2WAYS(P), line);
       if (way >= 0) {
         if (set_get(w, way) & W_DIRTY) SMALL(S_MEMWB)++;
-        set_invalidate(w, P.l2_ways, way);
-        store_set(P.l2 + base, P.l2_ways, w);
+        set_invalidate(w, L2WAYS(P), way);
+        store_set(P.l2 + base, L2WAYS(P), w);
         P.l2ep[base + way] = 0;
         uint16_t* hp = hist_ptr(P, base + way);
         hp[0] = 0;

@@ -1,8 +1,9 @@
 // noc_run_variant.cu -- one variant of the cycle kernel per compilation: the
 // build compiles this file once for each (per-cycle hash record, drain record,
 // L1 way bound, L2 way bound) combination it ships, and the plain loop once
-// more per way bound specialised to the interleaved L2 in cache mode
-// (-DNOC_FIXED_POLICY=0 -DNOC_FIXED_MODE=0).
+// more per way bound specialised to the interleaved L2 in cache mode with
+// exactly those way counts (-DNOC_FIXED_POLICY=0 -DNOC_FIXED_MODE=0
+// -DNOC_EXACT_WAYS=1).
 #include "noc_kernel.cuh"
 
 #if !defined(NOC_HASH) || !defined(NOC_DRAIN) || !defined(NOC_W1) || !defined(NOC_W2)
