@@ -175,9 +175,13 @@ int noc_debug_wait_limit(noc_sim* sim, int64_t ns, int silent_cta);
  * Batch engine: many independent simulations of uneven size, seed and L2
  * policy in one persistent cooperative launch per memory wave.  CTAs pop
  * (instance, rectangle) items from a device work queue; each instance's
- * rectangles run together with the neighbour-flag barrier of noc_step.  Each
- * instance's results are bit-identical to running it alone through
- * noc_create / noc_step (trace mode is not supported in a batch).
+ * rectangles run together with the neighbour waits of noc_step.  Instances
+ * are first grouped by the kernel variant that serves them (the interleaved
+ * L2 in cache mode with the exact way counts of a variant's class runs on
+ * that specialised kernel; all other instances share the general one), and
+ * each group runs in its own waves.  Each instance's results are
+ * bit-identical to running it alone through noc_create / noc_step (trace
+ * mode is not supported in a batch).
  * ------------------------------------------------------------------------ */
 typedef struct {
   int32_t mesh_w, mesh_h, l2_policy, reserved;
@@ -207,6 +211,8 @@ int noc_batch_set_collect_hash(noc_batch* batch, int enable);
 /* Run every instance to its cycle count.  Synchronous.  Returns the first
  * instance error (see noc_batch_error for each). */
 int noc_batch_run(noc_batch* batch);
+/* Work-queue launches of the last run: at least one per kernel-variant group
+ * (at most four groups), more when a group's state exceeds the pool. */
 int noc_batch_waves(const noc_batch* batch);
 int noc_batch_error(const noc_batch* batch, int i, int64_t* err_cycle);
 int noc_batch_stats(const noc_batch* batch, int i, noc_stats_t* out);

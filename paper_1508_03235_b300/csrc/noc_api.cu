@@ -959,36 +959,15 @@ int noc_batch_set_collect_hash(noc_batch* b, int enable) {
   return NOC_OK;
 }
 
-int noc_batch_run(noc_batch* b) {
-  if (!b) return fail(NOC_ERR_ARG, "null handle");
-  const int n = (int)b->sims.size();
-  if (!b->pool) {
-    size_t fr = 0, tot = 0;
-    CU(cudaMemGetInfo(&fr, &tot), "memory info");
-    size_t want = std::min(noc_batch_total_bytes(b), (size_t)(fr * 0.8));
-    want = std::max(want, noc_batch_min_bytes(b));
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, want);
-    if (e != cudaSuccess) return fail(NOC_ERR_OOM, "batch pool of %zu bytes: %s", want, cudaGetErrorString(e));
-    b->pool = static_cast<unsigned char*>(p);
-    b->pool_bytes = want;
-    b->pool_owned = true;
-  }
-  if (noc_batch_min_bytes(b) > b->pool_bytes)
-    return fail(NOC_ERR_OOM, "pool of %zu bytes is below the largest instance (%zu)", b->pool_bytes,
-                noc_batch_min_bytes(b));
+// run one kernel-variant group of a batch: memory waves over the pool, one
+// work-queue launch per wave, results read back per instance
+static int run_batch_group(noc_batch* b, const std::vector<int>& members, int threads, int w1, int w2,
+                           bool il, int* first_err) {
   const int side = b->rect;
-  const int threads = ((side * side + 31) / 32) * 32;
-  int w1 = 1, w2 = 1;  // one kernel variant serves all instances: the largest way bounds
-  for (noc_sim* s : b->sims) {
-    w1 = std::max(w1, s->P.l1_ways);
-    w2 = std::max(w2, s->P.l2_ways);
-  }
   int cap = 0;
-  CU(max_coresident_batch(w1, w2, threads, &cap), "occupancy");
+  CU(max_coresident_batch(w1, w2, il, threads, &cap), "occupancy");
   // largest first, so the tail of each wave holds the small instances
-  std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
+  std::vector<int> order = members;
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
     return (double)b->sims[a]->P.N * b->cycles[a] > (double)b->sims[c]->P.N * b->cycles[c];
   });
@@ -1000,8 +979,6 @@ int noc_batch_run(noc_batch* b) {
     s->run_gx = gx;
     s->run_gy = gy;
   }
-  b->waves = 0;
-  int first_err = NOC_OK;
   size_t pos = 0;
   while (pos < order.size()) {
     // admit instances in order while their state fits the pool
@@ -1078,7 +1055,7 @@ int noc_batch_run(noc_batch* b) {
     B.n_items = ni;
     B.gang_ns = 300ll * 1000000000ll;
     if (ni) {
-      CU(launch_batch(B, std::min(cap, ni), threads, w1, w2, st), "batch kernel launch");
+      CU(launch_batch(B, std::min(cap, ni), threads, w1, w2, il, st), "batch kernel launch");
       b->launches++;
     }
     CU(cudaStreamSynchronize(st), "batch wave");
@@ -1091,7 +1068,7 @@ int noc_batch_run(noc_batch* b) {
       int rc = read_error(s, &ec);
       b->err[i] = rc;
       b->err_cycle[i] = ec;
-      if (rc && !first_err) first_err = rc;
+      if (rc && !*first_err) *first_err = rc;
       rc = noc_stats(s, -1, &b->stats[i]);
       if (rc) return rc;
       b->launches++;
@@ -1108,6 +1085,50 @@ int noc_batch_run(noc_batch* b) {
       s->ready = false;
       s->base = nullptr;
     }
+  }
+  return NOC_OK;
+}
+
+int noc_batch_run(noc_batch* b) {
+  if (!b) return fail(NOC_ERR_ARG, "null handle");
+  const int n = (int)b->sims.size();
+  if (!b->pool) {
+    size_t fr = 0, tot = 0;
+    CU(cudaMemGetInfo(&fr, &tot), "memory info");
+    size_t want = std::min(noc_batch_total_bytes(b), (size_t)(fr * 0.8));
+    want = std::max(want, noc_batch_min_bytes(b));
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) return fail(NOC_ERR_OOM, "batch pool of %zu bytes: %s", want, cudaGetErrorString(e));
+    b->pool = static_cast<unsigned char*>(p);
+    b->pool_bytes = want;
+    b->pool_owned = true;
+  }
+  if (noc_batch_min_bytes(b) > b->pool_bytes)
+    return fail(NOC_ERR_OOM, "pool of %zu bytes is below the largest instance (%zu)", b->pool_bytes,
+                noc_batch_min_bytes(b));
+  const int side = b->rect;
+  const int threads = ((side * side + 31) / 32) * 32;
+  // kernel-variant groups: the instances the specialised kernel of way class
+  // 0, 1, 2 serves (interleaved L2, cache mode, exact ways), then the rest on
+  // the general kernel with the largest way bounds among them
+  std::vector<int> group[4];
+  for (int i = 0; i < n; ++i) {
+    const Params& P = b->sims[i]->P;
+    group[batch_specialised(P) ? batch_way_class(P.l1_ways, P.l2_ways) : 3].push_back(i);
+  }
+  b->waves = 0;
+  int first_err = NOC_OK;
+  for (int g = 0; g < 4; ++g) {
+    if (group[g].empty()) continue;
+    const bool il = g < 3;
+    int w1 = 1, w2 = 1;
+    for (int i : group[g]) {
+      w1 = std::max(w1, b->sims[i]->P.l1_ways);
+      w2 = std::max(w2, b->sims[i]->P.l2_ways);
+    }
+    int rc = run_batch_group(b, group[g], threads, w1, w2, il, &first_err);
+    if (rc) return rc;
   }
   b->done = true;
   if (first_err) return fail(first_err, "an instance ended with error %d", first_err);

@@ -1,12 +1,20 @@
 // noc_batch.cu -- the batch engine's persistent work-queue kernel (compiled once
-// per L1/L2 way bound)
+// per L1/L2 way bound, and once more per bound specialised like the plain
+// cycle loop: -DNOC_FIXED_POLICY=0 -DNOC_FIXED_MODE=0 -DNOC_EXACT_WAYS=1)
 #include "noc_kernel.cuh"
 
 #if !defined(NOC_W1) || !defined(NOC_W2)
 #error "compile with -DNOC_W1= -DNOC_W2="
 #endif
-#define NOC_PASTE3(a, b, c) a##_##b##_##c
-#define NOC_NAME(a, b, c) NOC_PASTE3(a, b, c)
+#if defined(NOC_FIXED_POLICY)
+#define NOC_POLV NOC_FIXED_POLICY
+#define NOC_SPEC il
+#else
+#define NOC_POLV (-1)
+#define NOC_SPEC gen
+#endif
+#define NOC_PASTE4(a, b, c, d) a##_##b##_##c##_##d
+#define NOC_NAME(a, b, c, d) NOC_PASTE4(a, b, c, d)
 
 namespace noc {
 
@@ -17,7 +25,7 @@ namespace noc {
 // (so the instance's neighbour waits start together), then runs it to the end
 // of the instance's cycles.  Items are popped in order, so every instance
 // before the current one is already running to completion: the waits end.
-template <int W1, int W2>
+template <int W1, int W2, int POLV>
 __global__ void __launch_bounds__(MAX_THREADS, 1) batch_kernel(const __grid_constant__ BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Params sP;
@@ -53,24 +61,26 @@ __global__ void __launch_bounds__(MAX_THREADS, 1) batch_kernel(const __grid_cons
   }
 }
 
-cudaError_t NOC_NAME(launch_batch, NOC_W1, NOC_W2)(const BatchArgs& B, int grid, int threads,
-                                                  cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(batch_kernel<NOC_W1, NOC_W2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+#define NOC_BATCH_KERNEL batch_kernel<NOC_W1, NOC_W2, NOC_POLV>
+
+cudaError_t NOC_NAME(launch_batch, NOC_W1, NOC_W2, NOC_SPEC)(const BatchArgs& B, int grid, int threads,
+                                                            cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(NOC_BATCH_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)run_smem_bytes_impl(MAX_THREADS));
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&B};
-  return cudaLaunchCooperativeKernel((const void*)batch_kernel<NOC_W1, NOC_W2>, dim3(grid), dim3(threads), args,
+  return cudaLaunchCooperativeKernel((const void*)NOC_BATCH_KERNEL, dim3(grid), dim3(threads), args,
                                      run_smem_bytes_impl(threads), s);
 }
 
-cudaError_t NOC_NAME(max_coresident_batch, NOC_W1, NOC_W2)(int threads, int* out) {
-  cudaError_t e = cudaFuncSetAttribute(batch_kernel<NOC_W1, NOC_W2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+cudaError_t NOC_NAME(max_coresident_batch, NOC_W1, NOC_W2, NOC_SPEC)(int threads, int* out) {
+  cudaError_t e = cudaFuncSetAttribute(NOC_BATCH_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)run_smem_bytes_impl(MAX_THREADS));
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<NOC_W1, NOC_W2>, threads, run_smem_bytes_impl(threads));
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, NOC_BATCH_KERNEL, threads, run_smem_bytes_impl(threads));
   if (e != cudaSuccess) return e;
   *out = per * sms;
   return cudaSuccess;

@@ -36,9 +36,14 @@ struct BatchArgs {
   int n_items;
   long long gang_ns;        // limit of the wait for an instance's rectangles
 };
-cudaError_t launch_batch(const BatchArgs& B, int grid, int threads, int l1_ways, int l2_ways,
+// il: the variant specialised to the interleaved L2 in cache mode with exactly
+// the way counts of the class of (l1_ways, l2_ways); batch_specialised(P)
+// says whether an instance may run on it
+cudaError_t launch_batch(const BatchArgs& B, int grid, int threads, int l1_ways, int l2_ways, bool il,
                          cudaStream_t s);
-cudaError_t max_coresident_batch(int l1_ways, int l2_ways, int threads, int* out);
+cudaError_t max_coresident_batch(int l1_ways, int l2_ways, bool il, int threads, int* out);
+bool batch_specialised(const Params& P);
+int batch_way_class(int l1_ways, int l2_ways);
 
 // geometry of the launch for a gx x gy rectangle grid
 int block_threads(int W, int H, int gx, int gy);

@@ -20,8 +20,10 @@ namespace noc {
   NOC_DECL_RUN(0, 0, w1, w2, il)                                                \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_gen(int threads, int* out);  \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_il(int threads, int* out);   \
-  cudaError_t launch_batch_##w1##_##w2(const BatchArgs&, int, int, cudaStream_t); \
-  cudaError_t max_coresident_batch_##w1##_##w2(int threads, int* out);
+  cudaError_t launch_batch_##w1##_##w2##_gen(const BatchArgs&, int, int, cudaStream_t); \
+  cudaError_t launch_batch_##w1##_##w2##_il(const BatchArgs&, int, int, cudaStream_t);  \
+  cudaError_t max_coresident_batch_##w1##_##w2##_gen(int threads, int* out);             \
+  cudaError_t max_coresident_batch_##w1##_##w2##_il(int threads, int* out);
 NOC_DECL_WAYS(4, 8)
 NOC_DECL_WAYS(4, 16)
 NOC_DECL_WAYS(16, 16)
@@ -64,20 +66,23 @@ cudaError_t max_coresident_ctas(const Params& P, int threads, int* out) {
   }
 }
 
-cudaError_t launch_batch(const BatchArgs& B, int grid, int threads, int l1_ways, int l2_ways,
+bool batch_specialised(const Params& P) { return interleaved_cache(P); }
+int batch_way_class(int l1_ways, int l2_ways) { return way_class(l1_ways, l2_ways); }
+
+cudaError_t launch_batch(const BatchArgs& B, int grid, int threads, int l1_ways, int l2_ways, bool il,
                          cudaStream_t s) {
   switch (way_class(l1_ways, l2_ways)) {
-    case 0: return launch_batch_4_8(B, grid, threads, s);
-    case 1: return launch_batch_4_16(B, grid, threads, s);
-    default: return launch_batch_16_16(B, grid, threads, s);
+    case 0: return il ? launch_batch_4_8_il(B, grid, threads, s) : launch_batch_4_8_gen(B, grid, threads, s);
+    case 1: return il ? launch_batch_4_16_il(B, grid, threads, s) : launch_batch_4_16_gen(B, grid, threads, s);
+    default: return il ? launch_batch_16_16_il(B, grid, threads, s) : launch_batch_16_16_gen(B, grid, threads, s);
   }
 }
 
-cudaError_t max_coresident_batch(int l1_ways, int l2_ways, int threads, int* out) {
+cudaError_t max_coresident_batch(int l1_ways, int l2_ways, bool il, int threads, int* out) {
   switch (way_class(l1_ways, l2_ways)) {
-    case 0: return max_coresident_batch_4_8(threads, out);
-    case 1: return max_coresident_batch_4_16(threads, out);
-    default: return max_coresident_batch_16_16(threads, out);
+    case 0: return il ? max_coresident_batch_4_8_il(threads, out) : max_coresident_batch_4_8_gen(threads, out);
+    case 1: return il ? max_coresident_batch_4_16_il(threads, out) : max_coresident_batch_4_16_gen(threads, out);
+    default: return il ? max_coresident_batch_16_16_il(threads, out) : max_coresident_batch_16_16_gen(threads, out);
   }
 }
 
