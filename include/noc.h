@@ -138,8 +138,16 @@ int noc_stats(noc_sim* sim, int tile, noc_stats_t* out);
 /* which: 0 = flit latency, 1 = L2 access latency; bins: nbins >= NOC_HIST_BINS */
 int noc_latency_hist(noc_sim* sim, int which, uint64_t* bins, int nbins);
 
-/* Order-free hashes of the simulation state (definitions in the model text):
- * the dynamic state after the last cycle, and the full state. */
+/* Order-free hashes of the simulation state, with mix64 the splitmix64
+ * finaliser and fold(w0, w1, ...) = h <- mix64(w0 + 0x9E3779B97F4A7C15), then
+ * h <- mix64(h ^ wi) per further word:
+ *   dynamic hash = sum over tiles r (mod 2^64) of fold(r, the four output
+ *     flits of the last cycle, the core record words, injected, ejected,
+ *     deflections) -- the state a cycle carries to the next;
+ *   full hash = dynamic hash + fold(0x18, cycle) + sums of folds over every
+ *     valid L1 and L2 way, queue and memory-FIFO entry, directory and forward
+ *     entry (each tagged 0x11..0x17).
+ * Both are independent of how the state is laid out or ordered in memory. */
 int noc_dyn_hash(noc_sim* sim, uint64_t* out);
 int noc_state_hash(noc_sim* sim, uint64_t* out);
 /* Record the dynamic hash after every cycle of the following noc_step calls

@@ -156,7 +156,10 @@ __device__ __forceinline__ void flit_words(uint4 f, unsigned long long& w0, unsi
   w2 = fe(f);
 }
 
-// full-state terms other than the dynamic hash (model text, "full state hash")
+// full-state terms other than the dynamic hash: fold(0x18, cycle) plus one fold
+// per valid L1 way (0x11), valid L2 way (0x12), core / service queue entry
+// (0x13 / 0x14), memory-FIFO entry (0x15), directory entry (0x16) and
+// forward entry (0x17)
 __global__ void state_terms_kernel(const Params P, uint32_t cycle, unsigned long long* out) {
   __shared__ unsigned long long red[32];
   unsigned long long acc = 0;

@@ -1307,7 +1307,9 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
 }
 
 // ---------------------------------------------------------------- hash
-// dynamic hash of one tile after a cycle (model text, "dynamic hash")
+// dynamic hash of one tile after a cycle: fold(r, its four output flits, its
+// core record words C0..C6, injected, ejected, deflections); fields that mean
+// nothing in the current FSM / outstanding-miss state hash as 0
 static __device__ unsigned long long tile_hash(const Tile& T, const uint4 (&out)[4]) {
   unsigned long long h = hstart(T.r);
 #pragma unroll

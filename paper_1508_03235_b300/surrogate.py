@@ -4,15 +4,16 @@ Inputs (10, padded to 16): mesh side, injection period, private / shared /
 remote address fractions, write fraction, private working set (KB), L2 policy
 one-hot (interleaved, LSPD-local, LSPD-migrate).  Outputs (3, padded to 16):
 log mean L2 access latency, deflections per flit, accepted flits per node per
-cycle -- each computed from a simulation's counters (metric definitions in
-the model text).  Network: 16 -> 256 -> 256 -> 256 -> 256 -> 16, GELU,
+cycle -- each computed from a simulation's counters (mean L2 access latency =
+l2lat_sum / l2lat_cnt, deflections / ejected flits, ejected / (tiles x cycles)).
+Network: 16 -> 256 -> 256 -> 256 -> 256 -> 16, GELU,
 trained with AdamW on the standardised outputs by the library's own tensor-core
 forward / backward kernels (include/mlp.h); torch only holds the buffers.
 
-The exact simulator is both the training-data source and the judge: the
-relative error of each output against fresh simulations is reported with the
-epsilon floors of the model text (0.01 deflections/flit, 1e-3 flits/node/cycle,
-latency on its natural scale).
+The exact simulator is both the training-data source and the reference the
+surrogate is scored against: the relative error of each output against fresh
+simulations is reported with epsilon floors in the denominators (0.01
+deflections/flit, 1e-3 flits/node/cycle; latency on its natural scale).
 """
 from __future__ import annotations
 
@@ -187,8 +188,9 @@ def make_dataset(n, cycles, seed=0, **kw):
 
 
 def relative_errors(pred, true):
-    """Per-output relative error with the model text's epsilon floors; latency
-    is compared on its natural (not log) scale."""
+    """Per-output relative error, |pred - true| / max(|true|, floor) with floors
+    0.01 deflections/flit and 1e-3 flits/node/cycle; latency is compared on its
+    natural (not log) scale."""
     err = np.empty_like(true)
     lp, lt = np.exp(pred[:, 0]), np.exp(true[:, 0])
     err[:, 0] = np.abs(lp - lt) / np.abs(lt)
@@ -246,7 +248,7 @@ class Surrogate:
 def run(points=50_000, holdout=5_000, cycles=20_000, chunk=2_000, epochs=300, batch=1024,
         lr=2e-3, data_path=None, seed=0, log=print):
     """Simulate `points` design points with the batch engine, train on all but
-    `holdout`, judge the held-out ones against their exact simulations, and time
+    `holdout`, score the held-out ones against their exact simulations, and time
     batch-4096 inference against the batched simulator."""
     import json
     import time
@@ -303,7 +305,7 @@ if __name__ == "__main__":
     import os
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
-    ap = argparse.ArgumentParser(description="simulate, train and judge the surrogate")
+    ap = argparse.ArgumentParser(description="simulate, train and score the surrogate")
     ap.add_argument("--points", type=int, default=50_000)
     ap.add_argument("--holdout", type=int, default=5_000)
     ap.add_argument("--cycles", type=int, default=20_000)

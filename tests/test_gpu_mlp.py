@@ -92,7 +92,7 @@ def test_training_fits_a_smooth_function(sur):
 
 
 def test_small_surrogate_of_the_simulator_and_screening(sur):
-    """Train on simulated design points, judge on fresh simulations, and show
+    """Train on simulated design points, score on fresh simulations, and show
     what screening with the network gains over random screening at the same
     simulation budget (the lowest mean L2 access latency found)."""
     kw = dict(sides=(8, 16, 24), period_lo=2, period_hi=40)
