@@ -313,18 +313,22 @@ def batch_section(n, cycles, rect):
     tb = time.perf_counter() - t0
     waves, launches = b.waves, b.launches
     b.close()
-    sims = [noc.Sim(p) for p in pts]
-    for s in sims[:2]:
-        s.step(100)
+    # one at a time: each instance created (allocation untimed), run to its
+    # cycle count and read back, before the next starts
+    for p in pts[:2]:
+        noc.Sim(p).step(100)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s in sims:
+    t1 = 0.0
+    for p in pts:
+        s = noc.Sim(p)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         s.reset()
         s.step_async(cycles)
         s.stats()
-    t1 = time.perf_counter() - t0
-    for s in sims:
+        t1 += time.perf_counter() - t0
         s.close()
+        del s
     return {"instances": n, "cycles": cycles, "rect": rect, "waves": waves,
             "batched_sims_per_s": n / tb, "one_at_a_time_sims_per_s": n / t1,
             "speedup": t1 / tb, "batched_router_cycles_per_s": tiles * cycles / tb,
@@ -422,7 +426,7 @@ def main():
     ap.add_argument("--ref-cycles", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--batch-n", type=int, default=64)
+    ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-cycles", type=int, default=20_000)
     ap.add_argument("--batch-rect", type=int, default=19)
     args = ap.parse_args()

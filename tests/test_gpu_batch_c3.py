@@ -1,0 +1,99 @@
+"""The batch engine on the full 512-instance workload (sides 8..128, periods
+2..40, Dirichlet(2,2,1) address mixes, all three L2 policies, seeds 1..512,
+20,000 cycles each) in the launch configuration the bench times (19x19-tile
+rectangles): every instance satisfies the model's conservation laws, and a
+stratified sample (each policy at its smallest and a mid-size mesh, plus a
+128x128 mesh) equals its oracle run bit for bit.  With NOC_FULL_C3=1 every one
+of the 512 instances is compared with its oracle run (about an hour of oracle
+time, spread over the host's cores)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1508_03235_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+CYCLES = 20_000
+RECT = 19
+
+
+@pytest.fixture(scope="module")
+def noc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_03235_b300 import noc as _noc
+    return _noc
+
+
+@pytest.fixture(scope="module")
+def c3_points():
+    pts = I.batch_design_points(512, seed=0)
+    for p in pts:
+        p.pop("design")
+    return pts
+
+
+@pytest.fixture(scope="module")
+def c3_batch(noc, c3_points):
+    b = noc.Batch(c3_points, CYCLES, rect=RECT)
+    b.run()
+    res = [(b.stats(i), b.state_hash(i), b.hist(i, 0), b.hist(i, 1)) for i in range(len(c3_points))]
+    b.close()
+    return res
+
+
+def sample(pts):
+    pick = set()
+    for pol in (0, 1, 2):
+        idx = [i for i, p in enumerate(pts) if p["policy"] == pol]
+        idx.sort(key=lambda i: pts[i]["mesh_w"])
+        pick.add(idx[0])
+        pick.add(min(idx, key=lambda i: abs(pts[i]["mesh_w"] - 64)))
+    pick.add(next(i for i, p in enumerate(pts) if p["mesh_w"] == 128))
+    return sorted(pick)
+
+
+def compare(i, got, want):
+    (gs, gh, g0, g1), (os_, oh, o0, o1) = got, want
+    for k, v in os_.items():
+        if k in gs:
+            assert gs[k] == v, (i, k, gs[k], v)
+    assert gh == oh, i
+    assert (g0 == o0).all() and (g1 == o1).all(), i
+
+
+def test_c3_invariants_every_instance(c3_points, c3_batch):
+    for i, (p, (st, h, h0, h1)) in enumerate(zip(c3_points, c3_batch)):
+        n = p["mesh_w"] * p["mesh_h"]
+        assert st["cycle"] == CYCLES, i
+        assert st["injected"] == st["ejected"] + st["in_flight"], i
+        assert int(h0.sum()) == st["ejected"], i                 # one latency sample per flit
+        assert int(h1.sum()) == st["l2lat_cnt"], i
+        assert st["l1_hit"] + st["l1_miss"] >= st["refs"], i      # every reference looks up the L1
+        assert st["ejected"] <= n * CYCLES, i                    # one ejection per tile-cycle
+        assert st["lat_max"] < CYCLES, i
+
+
+def test_c3_sample_matches_oracle(c3_points, c3_batch):
+    from tests.oracle_pool import run_many
+    idx = sample(c3_points)
+    assert {c3_points[i]["policy"] for i in idx} == {0, 1, 2}
+    want = run_many([c3_points[i] for i in idx], CYCLES)
+    for i, w in zip(idx, want):
+        compare(i, c3_batch[i], w)
+
+
+@pytest.mark.skipif(os.environ.get("NOC_FULL_C3") != "1", reason="set NOC_FULL_C3=1 (about an hour of oracle CPU time)")
+def test_c3_every_instance_matches_oracle(c3_points, c3_batch):
+    from tests.oracle_pool import run_many
+    want = run_many(c3_points, CYCLES)
+    bad = []
+    for i, w in enumerate(want):
+        try:
+            compare(i, c3_batch[i], w)
+        except AssertionError:
+            bad.append(i)
+    assert not bad, f"{len(bad)} of {len(c3_points)} instances differ: {bad[:10]}"
