@@ -1046,27 +1046,25 @@ __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t 
       T.inj++;
     }
   }
-  // ports in priority order: arrivals oldest first, then the injected flit
-  uint32_t freem = exists, defl = 0;
-  uint32_t pk[4] = {0, 0, 0, 0};
+  // ports in priority order: arrivals oldest first, then the injected flit.
+  // The productive-port bytes are packed in rank order (byte r = the flit of
+  // rank r), the grants come back packed by rank (nibble r), then by flit.
+  uint32_t rp = 0;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    uint32_t pr = 0;
-    bool has = false;
+  for (int d = 0; d < 4; ++d)
+    if ((rm >> d) & 1u) rp |= prod[d] << (8u * rk[d]);
+  const uint32_t n_rem = __popc(rm);
+  uint32_t freem = exists, defl = 0, pkp = 0;
 #pragma unroll
-    for (int d = 0; d < 4; ++d)
-      if (((rm >> d) & 1u) && rk[d] == (uint32_t)r) {
-        pr = prod[d];
-        has = true;
-      }
-    if (has) {
-      const uint32_t pick = pick_port(pr, freem, defl);
+  for (int r = 0; r < 4; ++r)
+    if ((uint32_t)r < n_rem) {
+      const uint32_t pick = pick_port((rp >> (8 * r)) & 0xFFu, freem, defl);
       freem &= ~pick;
-#pragma unroll
-      for (int d = 0; d < 4; ++d)
-        if (((rm >> d) & 1u) && rk[d] == (uint32_t)r) pk[d] = pick;
+      pkp |= pick << (4 * r);
     }
-  }
+  uint32_t pk[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) pk[d] = (pkp >> (4u * rk[d])) & 15u;
   uint32_t pki = 0;
   if (has_inj) {
     pki = pick_port(prod_ports(P, fdst(inj), T.x, T.y), freem, defl);
