@@ -101,28 +101,42 @@ static int grid_for(size_t n, int threads) {
 // [t0, t0 + n): those eligible by cycle t0 + n - 1 from its next_ref on, at most
 // refcap.  One thread per (tile, slot), so the Philox work runs at full width
 // instead of on the cycle kernel's serial path.
+// One warp per tile: the window of references the tile's core may issue in
+// cycles [t0, t0 + n), at most refcap, and no more than twice what the core
+// took from its previous window plus 32 (a core that runs behind schedule
+// takes far fewer than the schedule allows; past the window the cycle kernel
+// draws in place, so the window's size never changes a result).  Lanes draw
+// consecutive references, so the window's stores are coalesced.
 __global__ void gen_refs_kernel(const Params P, uint32_t t0, uint32_t n) {
-  const size_t N = (size_t)P.N, total = N * P.refcap;
-  for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < total;
-       it += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t c = (uint32_t)(it / P.refcap), j = (uint32_t)(it % P.refcap);
+  const size_t N = (size_t)P.N;
+  const uint32_t lane = threadIdx.x & 31u;
+  const size_t warps = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t c = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < N; c += warps) {
     const uint32_t k0 = P.core[C_NEXT * N + c];
     uint32_t cnt = 0;
     if (P.period > 0 && P.mode != MODE_TRACE) {
       const unsigned long long last = (unsigned long long)(t0 + n - 1) / (unsigned)P.period;
       if (last + 1 > k0) cnt = (uint32_t)min(last + 1 - k0, (unsigned long long)P.refcap);
+      const uint32_t prev_cnt = P.refcnt[c], prev_k0 = P.refk0[c];
+      if (prev_cnt > 0 && k0 >= prev_k0) {
+        const unsigned long long used = k0 - prev_k0;
+        cnt = (uint32_t)min((unsigned long long)cnt, 2 * used + 32);
+      }
     }
-    if (j == 0) {
+    __syncwarp();
+    if (lane == 0) {
       P.refk0[c] = k0;
       P.refcnt[c] = cnt;
     }
-    uint32_t raw;
-    if (j < cnt && draw_ref(P, c, k0 + j, raw)) P.refbuf[c * (size_t)P.refcap + j] = raw;
+    for (uint32_t j = lane; j < cnt; j += 32) {
+      uint32_t raw;
+      if (draw_ref(P, (uint32_t)c, k0 + j, raw)) P.refbuf[c * (size_t)P.refcap + j] = raw;
+    }
   }
 }
 
 cudaError_t launch_gen_refs(const Params& P, uint32_t t0, uint32_t n, cudaStream_t s) {
-  gen_refs_kernel<<<grid_for((size_t)P.N * P.refcap, 256), 256, 0, s>>>(P, t0, n);
+  gen_refs_kernel<<<grid_for((size_t)P.N * 32, 256), 256, 0, s>>>(P, t0, n);
   return cudaGetLastError();
 }
 
