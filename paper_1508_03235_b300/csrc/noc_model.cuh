@@ -358,26 +358,42 @@ __device__ __forceinline__ uint32_t wrank(uint32_t v) { return (v >> W_RANK_SHIF
 __device__ __forceinline__ uint32_t wset_rank(uint32_t v, uint32_t r) {
   return (v & ~(15u << W_RANK_SHIFT)) | (r << W_RANK_SHIFT);
 }
+// the way holding `line` and its word, or -1 (lines are below 2^26, so the
+// valid bit and the line compare as one masked word)
 template <int MW>
-__device__ __forceinline__ int set_find(const uint32_t (&w)[MW], int ways, uint32_t line) {
+__device__ __forceinline__ int set_find(const uint32_t (&w)[MW], int ways, uint32_t line,
+                                        uint32_t& word) {
   int found = -1;
+  word = 0;
+  const uint32_t key = W_VALID | line;
 #pragma unroll
   for (int i = MW - 1; i >= 0; --i)
-    if (i < ways && (w[i] & W_VALID) && (w[i] & W_LINE) == line) found = i;
+    if (i < ways && (w[i] & (W_VALID | W_LINE)) == key) {
+      found = i;
+      word = w[i];
+    }
   return found;
 }
-// make way `way` the most recently used; `prev_rank` is its rank before (the
-// number of valid ways for a way that was invalid)
 template <int MW>
-__device__ __forceinline__ void set_promote(uint32_t (&w)[MW], int ways, int way,
-                                            uint32_t prev_rank) {
+__device__ __forceinline__ int set_find(const uint32_t (&w)[MW], int ways, uint32_t line) {
+  uint32_t word;
+  return set_find(w, ways, line, word);
+}
+// make way `way` the most recently used (and OR `bits` into its word);
+// `prev_rank` is its rank before (the number of valid ways for a way that was
+// invalid).  The valid ways more recent than it age by one: with the valid bit
+// and the 4-bit rank in the word's top five bits, "valid and rank < prev" is
+// one unsigned compare.  The way itself may age here; its rank is reset after.
+template <int MW>
+__device__ __forceinline__ void set_promote(uint32_t (&w)[MW], int ways, int way, uint32_t prev_rank,
+                                            uint32_t bits = 0) {
+  const uint32_t lim = prev_rank << W_RANK_SHIFT;
 #pragma unroll
   for (int i = 0; i < MW; ++i)
-    if (i < ways && i != way && (w[i] & W_VALID) && wrank(w[i]) < prev_rank)
-      w[i] = wset_rank(w[i], wrank(w[i]) + 1);
+    if (i < ways && (w[i] & 0xF8000000u) - W_VALID < lim) w[i] += 1u << W_RANK_SHIFT;
 #pragma unroll
   for (int i = 0; i < MW; ++i)
-    if (i == way) w[i] = wset_rank(w[i], 0);
+    if (i == way) w[i] = (w[i] & ~(15u << W_RANK_SHIFT)) | bits;
 }
 template <int MW>
 __device__ __forceinline__ uint32_t set_get(const uint32_t (&w)[MW], int way) {
@@ -393,9 +409,11 @@ __device__ __forceinline__ void set_put(uint32_t (&w)[MW], int way, uint32_t v) 
   for (int i = 0; i < MW; ++i)
     if (i == way) w[i] = v;
 }
+// promote a way found holding `word`
 template <int MW>
-__device__ __forceinline__ void set_touch(uint32_t (&w)[MW], int ways, int way) {
-  set_promote(w, ways, way, wrank(set_get(w, way)));
+__device__ __forceinline__ void set_touch(uint32_t (&w)[MW], int ways, int way, uint32_t word,
+                                          uint32_t bits = 0) {
+  set_promote(w, ways, way, wrank(word), bits);
 }
 // victim: lowest-index invalid way, else the least recently used way
 template <int MW>
@@ -442,9 +460,10 @@ static __device__ void l1_fill(const Params& P, Tile& T, uint32_t line, uint32_t
   size_t base = l1_base(P, T.r, set);
   uint32_t w[W1];
   load_set(P.l1 + base, L1WAYS(P), w);
-  int way = set_find(w, L1WAYS(P), line);
+  uint32_t fword;
+  int way = set_find(w, L1WAYS(P), line, fword);
   if (way >= 0) {
-    set_touch(w, L1WAYS(P), way);
+    set_touch(w, L1WAYS(P), way, fword);
   } else {
     way = set_victim(w, L1WAYS(P));
     uint32_t old = set_get(w, way);
@@ -478,9 +497,10 @@ static __device__ int l2_install(const Params& P, Tile& T, uint32_t line, uint32
   size_t base = l2_base(P, T.r, set);
   uint32_t w[W2];
   load_set(P.l2 + base, L2WAYS(P), w);
-  int way = set_find(w, L2WAYS(P), line);
+  uint32_t fword;
+  int way = set_find(w, L2WAYS(P), line, fword);
   if (way >= 0) {
-    set_touch(w, L2WAYS(P), way);
+    set_touch(w, L2WAYS(P), way, fword);
   } else {
     way = set_victim(w, L2WAYS(P));
     uint32_t old = set_get(w, way);
@@ -512,10 +532,10 @@ static __device__ void local_wt(const Params& P, Tile& T, uint32_t line) {
   size_t base = l2_base(P, T.r, set);
   uint32_t w[W2];
   load_set(P.l2 + base, L2WAYS(P), w);
-  int way = set_find(w, L2WAYS(P), line);
+  uint32_t fword;
+  int way = set_find(w, L2WAYS(P), line, fword);
   if (way >= 0) {
-    set_put(w, way, set_get(w, way) | W_DIRTY);
-    set_touch(w, L2WAYS(P), way);
+    set_touch(w, L2WAYS(P), way, fword, W_DIRTY);
     store_set(P.l2 + base, L2WAYS(P), w);
     SMALL(S_WTH)++;
   } else {
@@ -562,7 +582,8 @@ static __device__ bool l1_step(const Params& P, Tile& T, uint32_t t, uint32_t li
   size_t base = l1_base(P, T.r, set);
   uint32_t w[W1];
   load_set(P.l1 + base, L1WAYS(P), w);
-  int way = set_find(w, L1WAYS(P), line);
+  uint32_t fword;
+  int way = set_find(w, L1WAYS(P), line, fword);
   if (way >= 0) {
     if (write) {
       uint32_t owner = P.l1own[base + way];
@@ -578,7 +599,7 @@ static __device__ bool l1_step(const Params& P, Tile& T, uint32_t t, uint32_t li
         send_core(P, T, mkflit(T_WT, T.r, owner, line, 0, 0));
       }
     }
-    set_touch(w, L1WAYS(P), way);
+    set_touch(w, L1WAYS(P), way, fword);
     store_set(P.l1 + base, L1WAYS(P), w);
     SMALL(S_L1H)++;
     T.fsm = FSM_IDLE;
@@ -605,10 +626,11 @@ static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* s
     if (h == T.r) {
       uint32_t w[W2];
       load_set(P.l2 + base, L2WAYS(P), w);
-      int way = set_find(w, L2WAYS(P), line);
+      uint32_t fword;
+      int way = set_find(w, L2WAYS(P), line, fword);
       if (way >= 0) {
         SMALL(S_L2H)++;
-        set_touch(w, L2WAYS(P), way);
+        set_touch(w, L2WAYS(P), way, fword);
         store_set(P.l2 + base, L2WAYS(P), w);
         l1_fill<W1>(P, T, line, T.r);
         if (write) local_wt<W2>(P, T, line);
@@ -646,10 +668,11 @@ static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* s
   // LSPD: the requester's own slice first (local placement, Sec. 3.3)
   uint32_t w[W2];
   load_set(P.l2 + base, L2WAYS(P), w);
-  int way = set_find(w, L2WAYS(P), line);
+  uint32_t fword;
+  int way = set_find(w, L2WAYS(P), line, fword);
   if (way >= 0) {
     SMALL(S_L2H)++;
-    set_touch(w, L2WAYS(P), way);
+    set_touch(w, L2WAYS(P), way, fword);
     store_set(P.l2 + base, L2WAYS(P), w);
     if (POLICY(P) == POL_MIGRATE) hist_push(P, base + way, T.r);
     l1_fill<W1>(P, T, line, T.r);
@@ -1111,10 +1134,11 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
       SMALL(S_REQR)++;
       uint32_t w[W2];
       load_set(P.l2 + base, L2WAYS(P), w);
-      int way = set_find(w, L2WAYS(P), line);
+      uint32_t fword;
+      int way = set_find(w, L2WAYS(P), line, fword);
       if (way >= 0) {
         SMALL(S_L2H)++;
-        set_touch(w, L2WAYS(P), way);
+        set_touch(w, L2WAYS(P), way, fword);
         store_set(P.l2 + base, L2WAYS(P), w);
         send_svc(P, T, mkflit(T_DATA, T.r, q, line, 0, 0), t);
         if (POLICY(P) == POL_MIGRATE) {
@@ -1182,10 +1206,10 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
     case T_WT: {
       uint32_t w[W2];
       load_set(P.l2 + base, L2WAYS(P), w);
-      int way = set_find(w, L2WAYS(P), line);
+      uint32_t fword;
+      int way = set_find(w, L2WAYS(P), line, fword);
       if (way >= 0) {
-        set_put(w, way, set_get(w, way) | W_DIRTY);
-        set_touch(w, L2WAYS(P), way);
+        set_touch(w, L2WAYS(P), way, fword, W_DIRTY);
         store_set(P.l2 + base, L2WAYS(P), w);
         SMALL(S_WTH)++;
       } else {
@@ -1280,9 +1304,10 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
       // invalidate the source copy and remember where the block went
       uint32_t w[W2];
       load_set(P.l2 + base, L2WAYS(P), w);
-      int way = set_find(w, L2WAYS(P), line);
+      uint32_t fword;
+      int way = set_find(w, L2WAYS(P), line, fword);
       if (way >= 0) {
-        if (set_get(w, way) & W_DIRTY) SMALL(S_MEMWB)++;
+        if (fword & W_DIRTY) SMALL(S_MEMWB)++;
         set_invalidate(w, L2WAYS(P), way);
         store_set(P.l2 + base, L2WAYS(P), w);
         P.l2ep[base + way] = 0;
