@@ -435,6 +435,47 @@ __device__ __forceinline__ uint32_t set_nvalid(const uint32_t (&w)[MW], int ways
     if (i < ways && (w[i] & W_VALID)) n++;
   return n;
 }
+// choose the way to fill: the lowest invalid way, else the least recently
+// used; returns it with its old word and its rank before (for an invalid way,
+// the number of valid ways), in one pass over the set
+template <int MW>
+__device__ __forceinline__ int set_choose(const uint32_t (&w)[MW], int ways, uint32_t& old,
+                                          uint32_t& prev_rank) {
+  uint32_t minv = 0, nvalid = 0, lruw = 0;
+  int lru = 0;
+  const uint32_t lru_top = W_VALID | ((uint32_t)(ways - 1) << W_RANK_SHIFT);
+#pragma unroll
+  for (int i = 0; i < MW; ++i)
+    if (i < ways) {
+      const uint32_t v = w[i] >> 31;
+      minv |= (v ^ 1u) << i;
+      nvalid += v;
+      if ((w[i] & 0xF8000000u) == lru_top) {
+        lru = i;
+        lruw = w[i];
+      }
+    }
+  if (minv) {
+    old = 0;
+    prev_rank = nvalid;
+    return __ffs(minv) - 1;
+  }
+  old = lruw;
+  prev_rank = (uint32_t)(ways - 1);
+  return lru;
+}
+// make way `way` the most recently used, replacing its word by `word`
+template <int MW>
+__device__ __forceinline__ void set_replace(uint32_t (&w)[MW], int ways, int way, uint32_t prev_rank,
+                                            uint32_t word) {
+  const uint32_t lim = prev_rank << W_RANK_SHIFT;
+#pragma unroll
+  for (int i = 0; i < MW; ++i)
+    if (i < ways && (w[i] & 0xF8000000u) - W_VALID < lim) w[i] += 1u << W_RANK_SHIFT;
+#pragma unroll
+  for (int i = 0; i < MW; ++i)
+    if (i == way) w[i] = word;
+}
 // remove way `way`; the ways it was more recent than move up one rank
 template <int MW>
 __device__ __forceinline__ void set_invalidate(uint32_t (&w)[MW], int ways, int way) {
@@ -465,11 +506,9 @@ static __device__ void l1_fill(const Params& P, Tile& T, uint32_t line, uint32_t
   if (way >= 0) {
     set_touch(w, L1WAYS(P), way, fword);
   } else {
-    way = set_victim(w, L1WAYS(P));
-    uint32_t old = set_get(w, way);
-    uint32_t prev = (old & W_VALID) ? wrank(old) : set_nvalid(w, L1WAYS(P));
-    set_put(w, way, W_VALID | line);
-    set_promote(w, L1WAYS(P), way, prev);
+    uint32_t old, prev;
+    way = set_choose(w, L1WAYS(P), old, prev);
+    set_replace(w, L1WAYS(P), way, prev, W_VALID | line);
   }
   store_set(P.l1 + base, L1WAYS(P), w);
   P.l1own[base + way] = (uint16_t)owner;
@@ -502,18 +541,13 @@ static __device__ int l2_install(const Params& P, Tile& T, uint32_t line, uint32
   if (way >= 0) {
     set_touch(w, L2WAYS(P), way, fword);
   } else {
-    way = set_victim(w, L2WAYS(P));
-    uint32_t old = set_get(w, way);
-    uint32_t prev;
+    uint32_t old, prev;
+    way = set_choose(w, L2WAYS(P), old, prev);
     if (old & W_VALID) {
-      prev = wrank(old);
       if (old & W_DIRTY) SMALL(S_MEMWB)++;
       if (POLICY(P) != POL_INTERLEAVED) send_dinv(P, T, old & W_LINE, P.l2ep[base + way], t);
-    } else {
-      prev = set_nvalid(w, L2WAYS(P));
     }
-    set_put(w, way, W_VALID | line);
-    set_promote(w, L2WAYS(P), way, prev);
+    set_replace(w, L2WAYS(P), way, prev, W_VALID | line);
     if (POLICY(P) == POL_MIGRATE) {
       uint16_t* hp = hist_ptr(P, base + way);
       hp[0] = 0;
