@@ -379,6 +379,52 @@ def cpu_baseline(cycles_per_period=400):
                       f"of the 208x208 workload ({rc} router-cycles, {t:.1f} s)"}
 
 
+def _oracle_instance(job):
+    """One oracle run (a spawn-pool worker): router-cycles and seconds."""
+    params, cycles = job
+    sys.path.insert(0, ROOT)
+    from oracle import oracle
+    o = oracle.OracleSim(params)
+    t0 = time.perf_counter()
+    o.step(cycles)
+    dt = time.perf_counter() - t0
+    o.close()
+    return params["mesh_w"] * params["mesh_h"] * cycles, dt
+
+
+def oracle_configs(c3_sample=64):
+    """The oracle as it stands on the other workloads, on the host cores: the
+    8x8 mesh in full (20,000 cycles), the 64x64 hotspot mesh (seed 1, 100,000
+    cycles), and a sample of the 512-instance batch (every 8th instance,
+    20,000 cycles each) one core at a time and over all cores."""
+    import multiprocessing as mp
+    from oracle import oracle
+    oracle.build()
+    out = {}
+    for name, params, cycles in (("mesh8_full", I.MESH_8["params"], I.MESH_8["cycles"]),
+                                 ("mesh64_hotspot_seed1", I.mesh_64(1), 100_000)):
+        rc, dt = _oracle_instance((params, cycles))
+        out[name] = {"router_cycles_per_s": rc / dt, "seconds": dt, "cores": 1}
+    pts = I.batch_design_points(512, seed=0)[::512 // c3_sample]
+    for p in pts:
+        p.pop("design")
+    jobs = [(p, 20_000) for p in pts]
+    t0 = time.perf_counter()
+    one = [_oracle_instance(j) for j in jobs[: max(1, len(jobs) // 8)]]
+    t1 = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_instance, sorted(jobs, key=lambda j: -j[0]["mesh_w"]), chunksize=1)
+    t2 = time.perf_counter() - t0
+    out["batch_sample_1core"] = {"instances": len(one), "sims_per_s": len(one) / t1,
+                                 "router_cycles_per_s": sum(r for r, _ in one) / t1, "cores": 1}
+    out["batch_sample_all_cores"] = {"instances": len(jobs), "sims_per_s": len(jobs) / t2,
+                                     "router_cycles_per_s": sum(r for r, _ in res) / t2,
+                                     "cores": cores}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -429,8 +475,12 @@ def main():
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-cycles", type=int, default=20_000)
     ap.add_argument("--batch-rect", type=int, default=19)
+    ap.add_argument("--oracle-configs", action="store_true",
+                    help="time the oracle on the 8x8, 64x64 and batch workloads (host cores) and exit")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.oracle_configs:
+        print(json.dumps({"oracle_configs": oracle_configs()}), flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
