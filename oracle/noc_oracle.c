@@ -93,6 +93,11 @@ typedef struct {
   int64_t trace_n;
   /* ejected flit handed from Phase 2 to Phase 3 */
   Flit ejected;
+  /* reorder buffer (packet mode): packets with some but not all flits here */
+  struct {
+    uint32_t src, type, line, count;
+    int valid;
+  } * rob;
   uint64_t st[ORC_NSTAT];
 } Tile;
 
@@ -272,6 +277,15 @@ static Flit q_pop(FlitQ* q) {
   return f;
 }
 
+/* flits of a message: 1, or in packet mode the Table 1 sizes of a data reply
+ * (remote L2 access, 4) and of a block migration (16) */
+static uint32_t packet_flits(const orc_sim* s, uint32_t type) {
+  if (!s->p.packet_mode) return 1;
+  if (type == T_DATA) return 4;
+  if (type == T_MIG) return 16;
+  return 1;
+}
+
 /* service-queue messages are never refused: exceeding the capacity is an error */
 static void send_svc(orc_sim* s, int r, Flit f) {
   Tile* T = &s->tiles[r];
@@ -283,7 +297,22 @@ static void send_svc(orc_sim* s, int r, Flit f) {
   if (f.type == T_REQ) T->st[ORC_ST_REQ_MADE]++;
   if (f.type == T_DATA || f.type == T_DRPOS || f.type == T_DRNEG || f.type == T_NACK)
     T->st[ORC_ST_REPLY_SENT]++;
-  q_push(&T->sq, f);
+  uint32_t n = packet_flits(s, f.type);
+  if (n == 1) {
+    q_push(&T->sq, f);
+    return;
+  }
+  /* a multi-flit packet: n flits queued together, flit i carries a = i, e = n */
+  if (T->sq.cap - T->sq.len < (int)n) {
+    set_error(s, ORC_ERR_QUEUE_OVERFLOW);
+    return;
+  }
+  for (uint32_t i = 0; i < n; i++) {
+    Flit g = f;
+    g.a = i;
+    g.e = n;
+    q_push(&T->sq, g);
+  }
 }
 /* core-queue messages: caller has checked for space */
 static void send_core(orc_sim* s, int r, Flit f) {
@@ -737,6 +766,32 @@ static void phase3(orc_sim* s, int r, uint32_t t) {
   if (lat > T->st[ORC_ST_LAT_MAX]) T->st[ORC_ST_LAT_MAX] = lat;
   hist_add(s, 0, lat);
 
+  /* packet mode: the handler runs once, when the last flit of a packet is in */
+  if (f.e > 1 && packet_flits(s, f.type) > 1) {
+    int hit = -1, free_slot = -1;
+    for (int i = 0; i < s->p.rob_entries; i++) {
+      if (T->rob[i].valid && T->rob[i].src == f.src && T->rob[i].type == f.type &&
+          T->rob[i].line == f.line)
+        hit = i;
+      else if (!T->rob[i].valid && free_slot < 0)
+        free_slot = i;
+    }
+    if (hit < 0) {
+      if (free_slot < 0) {
+        set_error(s, ORC_ERR_QUEUE_OVERFLOW);
+        return;
+      }
+      hit = free_slot;
+      T->rob[hit].valid = 1;
+      T->rob[hit].src = f.src;
+      T->rob[hit].type = f.type;
+      T->rob[hit].line = f.line;
+      T->rob[hit].count = 0;
+    }
+    if (++T->rob[hit].count < f.e) return;
+    T->rob[hit].valid = 0;
+  }
+
   Cache* c2 = &T->l2;
   int set2 = l2_set(s, f.line);
   int policy = s->p.policy;
@@ -983,7 +1038,16 @@ static uint64_t tile_hash(const orc_sim* s, int r) {
 
 uint64_t orc_dyn_hash(const orc_sim* s) {
   uint64_t H = 0;
-  for (int r = 0; r < s->N; r++) H += tile_hash(s, r);
+  for (int r = 0; r < s->N; r++) {
+    H += tile_hash(s, r);
+    /* packet mode: one term per partly received packet (none otherwise) */
+    const Tile* T = &s->tiles[r];
+    for (int i = 0; i < s->p.rob_entries && s->p.packet_mode; i++)
+      if (T->rob[i].valid)
+        H += fold(fold(fold(fold_start(0x1A), (uint64_t)r),
+                       (uint64_t)T->rob[i].line | ((uint64_t)T->rob[i].type << 26)),
+                  (uint64_t)T->rob[i].src | ((uint64_t)T->rob[i].count << 16));
+  }
   return H;
 }
 
@@ -1094,6 +1158,8 @@ static int check_params(const orc_params* p) {
   uint64_t total = (uint64_t)p->remote_lines + p->shared_lines +
                    (uint64_t)p->priv_lines * (uint64_t)p->mesh_w * p->mesh_h;
   if (total >= (1ull << 26)) return 0;
+  if (p->packet_mode < 0 || p->packet_mode > 1) return 0;
+  if (p->packet_mode && (p->rob_entries < 1 || p->rob_entries > 64 || p->svc_q < 16)) return 0;
   return 1;
 }
 
@@ -1138,6 +1204,10 @@ int orc_create(const orc_params* p, orc_sim** out) {
     if (!T->l1.w || !T->l2.w || !T->cq.buf || !T->sq.buf || !T->mq || !T->fwd_line ||
         !T->fwd_tile)
       goto oom;
+    if (p->packet_mode) {
+      T->rob = calloc((size_t)p->rob_entries, sizeof *T->rob);
+      if (!T->rob) goto oom;
+    }
   }
   *out = s;
   return ORC_OK;
@@ -1159,6 +1229,7 @@ void orc_destroy(orc_sim* s) {
       free(T->mq);
       free(T->fwd_line);
       free(T->fwd_tile);
+      free(T->rob);
       free(T->trace);
     }
   free(s->tiles);
@@ -1196,6 +1267,8 @@ static int quiescent(const orc_sim* s) {
     const Tile* T = &s->tiles[r];
     if (T->cq.len || T->sq.len || T->mq_len || T->fsm != FSM_IDLE || T->om_kind != OM_NONE)
       return 0;
+    for (int i = 0; i < s->p.rob_entries && s->p.packet_mode; i++)
+      if (T->rob[i].valid) return 0;
   }
   /* flits are counted at the injecting and at the ejecting tile */
   uint64_t inj = 0, ej = 0;

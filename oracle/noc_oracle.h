@@ -52,6 +52,10 @@ typedef struct {
   uint32_t priv_lines, shared_lines, remote_lines;
   uint64_t seed;
   uint32_t stream;
+  /* packets (Table 1, Sec. 2.3): 0 = every message is one flit; 1 = a DATA
+   * reply (remote L2 access, RA) is 4 flits and a migration (B2) 16 flits,
+   * reassembled in a per-tile reorder buffer of rob_entries packets */
+  int32_t packet_mode, rob_entries;
 } orc_params;
 
 /* statistic indices (order fixed by the written model) */

@@ -59,6 +59,8 @@ def cache_cfg(l1_kb=32, l1_ways=4, l2_kb=256, l2_ways=8, **over):
         svc_q=256,
         mem_q=128,
         fwd_entries=4,
+        packet_mode=0,
+        rob_entries=8,
     )
     cfg.update(over)
     return cfg

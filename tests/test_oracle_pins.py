@@ -469,3 +469,68 @@ def test_reference_stream_distribution(oracle_mod):
     f_hot = 0.4 + 0.6 * 16 / N
     sd = np.sqrt(f_hot * (1 - f_hot) / shared)
     assert abs(hot / shared - f_hot) < 5 * sd
+
+
+# --------------------------------------------------------------------------
+# packet mode (Table 1): a data reply is 4 flits, reassembled in a reorder
+# buffer; its handler runs once, when the last flit is in
+def test_packet_remote_read_timeline(oracle_mod):
+    s = oracle_mod.OracleSim(trace_params(3, 3, packet_mode=1, rob_entries=4))
+    s.set_trace(0, [8])            # as the one-flit timeline: home 8, 4 hops
+    s.step(113)                                          # cycles 0..112
+    assert s.core(0)["om_kind"] == 2          # first flit in at 112, three to go
+    s.step(2)                                            # cycles 113, 114
+    assert s.core(0)["om_kind"] == 2
+    s.step(1)                                            # cycle 115: the 4th flit
+    st = s.stats()
+    assert s.core(0)["om_kind"] == 0
+    # the four flits leave home at 108..111 and arrive at 112..115
+    assert st["l2lat_sum"] == 115 and st["l2lat_cnt"] == 1
+    assert st["injected"] == st["ejected"] == 5
+    assert st["lat_sum"] == 4 + 4 * 4
+    assert st["reply_sent"] == st["reply_rcvd"] == 1
+
+
+def test_packet_handler_runs_on_the_last_flit_in_any_order(oracle_mod):
+    s = oracle_mod.OracleSim(quiet_params(3, 3, packet_mode=1, rob_entries=4))
+    s.step(10)
+    h = s.dyn_hash()
+    for k, idx in enumerate((2, 0, 3, 1)):       # out of order, one per cycle
+        s.debug_link(4, W_, dict(type="DATA", src=3, dst=4, inject=9 + k, line=11, a=idx, e=4))
+        s.step(1, check=False)
+        if k < 3:
+            assert s.error()[0] == 0
+            assert s.dyn_hash() != h             # the partial packet is state
+            h = s.dyn_hash()
+    # no miss is outstanding at tile 4, so the completed reply is a protocol
+    # error -- raised exactly at the cycle the fourth flit was ejected
+    assert s.error() == (6, 13)
+    assert s.stats()["reply_rcvd"] == 1
+
+
+def test_packet_reorder_buffer_overflow(oracle_mod):
+    s = oracle_mod.OracleSim(quiet_params(3, 3, packet_mode=1, rob_entries=1))
+    s.step(10)
+    s.debug_link(4, W_, dict(type="DATA", src=3, dst=4, inject=5, line=11, a=0, e=4))
+    s.debug_link(4, N_, dict(type="DATA", src=1, dst=4, inject=7, line=13, a=0, e=4))
+    s.step(5, check=False)
+    # the older flit takes the only entry at cycle 10; the younger, deflected
+    # north and back, needs a second entry when it is ejected at cycle 12
+    assert s.error() == (3, 12)
+
+
+def test_packet_mode_conservation_after_drain(oracle_mod):
+    cache = I.cache_cfg(l1_kb=2, l1_ways=2, l2_kb=4, l2_ways=4, svc_q=512, packet_mode=1,
+                        rob_entries=8)
+    traf = I.traffic(period=3, write=0.3, priv=0.3, shared=0.6, priv_kb=4, shared_mb=0)
+    traf.update(shared_lines=300)
+    s = oracle_mod.OracleSim(I.sim_params(6, 6, policy=0, cache=cache, traf=traf, seed=9))
+    s.step(4000)
+    s.drain(100_000)
+    st = s.stats()
+    assert st["injected"] == st["ejected"]
+    assert st["req_made"] == st["req_rcvd"] > 0
+    assert st["reply_sent"] == st["reply_rcvd"] > 0
+    # interleaved L2: requests and write-throughs are one flit, every reply a
+    # 4-flit data packet
+    assert st["injected"] == st["req_made"] + st["wt_sent"] + 4 * st["reply_sent"]
