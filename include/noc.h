@@ -69,6 +69,13 @@ typedef struct {
   int32_t svc_q;              /* service-queue capacity (overflow = error)   */
   int32_t mem_q;              /* memory-return FIFO capacity (overflow = error) */
   int32_t fwd_entries;        /* redirection forward-table entries per tile  */
+  /* Packets (Table 1, Sec. 2.3).  0: every message is one flit.  1: a data
+   * reply (remote L2 access) is 4 flits and a block migration 16, queued
+   * together, routed independently and reassembled at the receiver in a
+   * reorder buffer of rob_entries packets (1..64; a full buffer is
+   * NOC_ERR_QUEUE_OVERFLOW); the message's handler runs in the cycle its last
+   * flit is ejected.  Needs svc_q >= 16. */
+  int32_t packet_mode, rob_entries;
 } noc_cache_cfg;
 
 /* Reference stream.  Fractions are q16 fixed point (65536 = 1).  Reference k

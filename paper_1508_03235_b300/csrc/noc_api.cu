@@ -52,7 +52,7 @@ struct noc_sim {
   noc_traffic traf;
   uint64_t seed;
   // arena layout (byte offsets)
-  size_t o_glink, o_gtag, o_core, o_cq, o_sq, o_mq, o_l1, o_l1own, o_l2, o_l2ep, o_l2hist, o_dir, o_fwd,
+  size_t o_rob, o_glink, o_gtag, o_core, o_cq, o_sq, o_mq, o_l1, o_l1own, o_l2, o_l2ep, o_l2hist, o_dir, o_fwd,
       o_stats, o_hist, o_flags, o_err, o_abort, o_scratch, o_refbuf, o_refk0, o_refcnt, bytes;
   int refcap = 512;              // references drawn ahead per tile (0 = draw in place)
   size_t n_flags;
@@ -119,6 +119,7 @@ void layout(noc_sim* s) {
   s->o_l2hist = take(mig ? w2 * hist_stride(P.mig_window) * sizeof(uint16_t) : 0);
   s->o_dir = take(lspd ? (size_t)P.total_lines * sizeof(uint32_t) : 0);
   s->o_fwd = take(mig ? N * P.fwd_cap * 2 * sizeof(uint32_t) : 0);
+  s->o_rob = take(N * P.rob_entries * 2 * sizeof(uint32_t));
   s->o_stats = take((size_t)NSTAT * N * sizeof(unsigned long long));
   s->o_hist = take(2 * HIST_BINS * sizeof(unsigned long long));
   s->o_flags = take(s->n_flags * sizeof(unsigned int));
@@ -148,6 +149,7 @@ void set_pointers(noc_sim* s) {
   P.l2hist = mig ? reinterpret_cast<uint16_t*>(b + s->o_l2hist) : nullptr;
   P.dir = lspd ? reinterpret_cast<uint32_t*>(b + s->o_dir) : nullptr;
   P.fwd = mig ? reinterpret_cast<uint32_t*>(b + s->o_fwd) : nullptr;
+  P.rob = P.rob_entries ? reinterpret_cast<uint32_t*>(b + s->o_rob) : nullptr;
   P.stats = reinterpret_cast<unsigned long long*>(b + s->o_stats);
   P.hist = reinterpret_cast<unsigned long long*>(b + s->o_hist);
   P.flags = reinterpret_cast<unsigned int*>(b + s->o_flags);
@@ -180,6 +182,7 @@ int do_reset(noc_sim* s) {
     CU(cudaMemsetAsync(P.l2hist, 0, w2 * hist_stride(P.mig_window) * sizeof(uint16_t), st), "reset history");
   if (P.dir) CU(cudaMemsetAsync(P.dir, 0xFF, (size_t)P.total_lines * 4, st), "reset directory");
   if (P.fwd) CU(cudaMemsetAsync(P.fwd, 0, N * P.fwd_cap * 8, st), "reset forward tables");
+  if (P.rob) CU(cudaMemsetAsync(P.rob, 0, N * P.rob_entries * 8, st), "reset reorder buffers");
   CU(cudaMemsetAsync(P.stats, 0, (size_t)NSTAT * N * 8, st), "reset counters");
   CU(cudaMemsetAsync(P.hist, 0, 2 * HIST_BINS * 8, st), "reset histograms");
   CU(cudaMemsetAsync(P.flags, 0, s->n_flags * 4, st), "reset flags");
@@ -389,6 +392,9 @@ int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, co
       (c->mig_window < 1 || c->mig_window > HIST_MAX || c->mig_threshold < 1 ||
        c->fwd_entries < 1 || c->fwd_entries > 65535))
     return fail(NOC_ERR_ARG, "migration: window 1..30, threshold >= 1, forward entries >= 1");
+  if (c->packet_mode < 0 || c->packet_mode > 1 ||
+      (c->packet_mode && (c->rob_entries < 1 || c->rob_entries > 64 || c->svc_q < 16)))
+    return fail(NOC_ERR_ARG, "packets: mode 0/1, reorder entries 1..64, svc_q >= 16");
   if (tr->mode < 0 || tr->mode > 2 || tr->period < 0) return fail(NOC_ERR_ARG, "traffic mode/period");
   if (tr->write_q16 > 65536 || tr->priv_q16 + (uint64_t)tr->shared_q16 > 65536 || tr->hot_q16 > 65536)
     return fail(NOC_ERR_ARG, "q16 fractions out of range");
@@ -429,6 +435,8 @@ int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, co
   P.svc_q = c->svc_q;
   P.mem_q = c->mem_q;
   P.fwd_cap = c->fwd_entries > 0 ? c->fwd_entries : 1;
+  P.packet_mode = c->packet_mode;
+  P.rob_entries = c->packet_mode ? c->rob_entries : 0;
   P.write_q16 = tr->write_q16;
   P.priv_q16 = tr->priv_q16;
   P.shared_q16 = tr->shared_q16;

@@ -38,8 +38,8 @@ static int way_class(int l1_ways, int l2_ways) {
 static bool interleaved_cache(const Params& P) {
   static const int exact[3][2] = {{4, 8}, {4, 16}, {16, 16}};
   const int c = way_class(P.l1_ways, P.l2_ways);
-  return P.policy == POL_INTERLEAVED && P.mode == MODE_CACHE && P.l1_ways == exact[c][0] &&
-         P.l2_ways == exact[c][1];
+  return P.policy == POL_INTERLEAVED && P.mode == MODE_CACHE && !P.packet_mode &&
+         P.l1_ways == exact[c][0] && P.l2_ways == exact[c][1];
 }
 
 #define NOC_PICK_RUN(h, d, sp)                                    \
@@ -153,7 +153,7 @@ __global__ void dyn_hash_kernel(const Params P, uint32_t cycle, unsigned long lo
     uint4 o[4];
 #pragma unroll
     for (int d = 0; d < 4; ++d) o[d] = P.glink[((size_t)par * 4 + d) * N + r];
-    acc += tile_hash(T, o);
+    acc += tile_hash(T, o) + rob_hash(P, r);
   }
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) atomicAdd(out, acc);

@@ -294,12 +294,12 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
       for (int d = 0; d < 4; ++d) out[d] = sl[(pout * 4 + d) * nt + i];
     }
     if (HASH) {
-      unsigned long long h = active ? tile_hash(T, out) : 0ull;
+      unsigned long long h = active ? tile_hash(T, out) + rob_hash(P, r) : 0ull;
       h = block_sum(h, sh_red);
       if (i == 0) atomicAdd(&A.hash_trace[t - t0], h);
     }
     if (DRAIN) {
-      unsigned long long q = (active && !tile_quiet(T, out)) ? 1ull : 0ull;
+      unsigned long long q = (active && (!tile_quiet(T, out) || !rob_empty(P, r))) ? 1ull : 0ull;
       q = block_sum(q, sh_red);
       if (i == 0 && q) atomicAdd(&A.busy[t - t0], (unsigned)q);
     }

@@ -27,10 +27,12 @@ namespace noc {
 #define POLICY(P) (NOC_FIXED_POLICY)
 #define MODE(P) (NOC_FIXED_MODE)
 #define NOC_WITH_LSPD (NOC_FIXED_POLICY != 0)
+#define PACKETS(P) 0
 #else
 #define POLICY(P) ((P).policy)
 #define MODE(P) ((P).mode)
 #define NOC_WITH_LSPD 1
+#define PACKETS(P) ((P).packet_mode)
 #endif
 
 // ---------------------------------------------------------------- constants
@@ -81,6 +83,7 @@ struct Params {
   int l1_sets, l1_ways, l2_sets, l2_ways;
   int l1_miss, mem_lat, mig_window, mig_threshold, hist_stride;
   int core_q, svc_q, mem_q, fwd_cap;
+  int packet_mode, rob_entries;  // Table 1 packets; reorder-buffer entries per tile
   uint32_t write_q16, priv_q16, shared_q16, hot_q16;
   int hot_side, hot_x0, hot_y0;
   uint32_t priv_lines, shared_lines, remote_lines, total_lines;
@@ -109,6 +112,9 @@ struct Params {
   uint16_t* l2hist;      // [N][l2_sets][l2_ways][hist_stride] (migrate)
   uint32_t* dir;         // [total_lines]            (LSPD)
   uint32_t* fwd;         // [N][fwd_cap][2]          (migrate)
+  // packet mode: per tile, rob_entries partly received packets, two words
+  // each: line | type << 26 | valid << 31, and src | flits received << 16
+  uint32_t* rob;         // [N][rob_entries][2]
   uint32_t* trace_off;   // [N+1]                    (trace mode)
   uint32_t* trace;       // refs                     (trace mode)
   // references drawn ahead by gen_refs_kernel: refbuf[tile][j] is reference
@@ -293,17 +299,34 @@ __device__ __forceinline__ void count_sent(Tile& T, uint32_t ty) {
   if (ty == T_REQ) SMALL(S_REQM)++;
   if (ty == T_DATA || ty == T_DRPOS || ty == T_DRNEG || ty == T_NACK) SMALL(S_REPS)++;
 }
+// flits of a message: 1, or in packet mode the Table 1 sizes of a data reply
+// (remote L2 access, 4) and of a block migration (16)
+__device__ __forceinline__ uint32_t packet_flits(const Params& P, uint32_t ty) {
+  if (!PACKETS(P)) return 1;
+  return ty == T_DATA ? 4u : (ty == T_MIG ? 16u : 1u);
+}
+// service-queue messages are never refused: exceeding the capacity is an
+// error.  A multi-flit packet is queued whole, flit i carrying a = i, e = n.
 __device__ __forceinline__ void send_svc(const Params& P, Tile& T, uint4 f, uint32_t t) {
   if (T.sq_len >= (uint32_t)P.svc_q) {
     set_error(P, t, ERR_OVERFLOW);
     return;
   }
   count_sent(T, ftype(f));
-  uint32_t slot = T.sq_head + T.sq_len;
-  if (slot >= (uint32_t)P.svc_q) slot -= P.svc_q;
-  P.sq[(size_t)T.r * P.svc_q + slot] = f;
-  if (T.sq_len == 0) T.sq_front = f;
-  T.sq_len++;
+  const uint32_t n = packet_flits(P, ftype(f));
+  if (n > 1 && T.sq_len + n > (uint32_t)P.svc_q) {
+    set_error(P, t, ERR_OVERFLOW);
+    return;
+  }
+  for (uint32_t i = 0; i < n; ++i) {
+    uint4 g = f;
+    if (n > 1) g.w = i | (n << 16);
+    uint32_t slot = T.sq_head + T.sq_len;
+    if (slot >= (uint32_t)P.svc_q) slot -= P.svc_q;
+    P.sq[(size_t)T.r * P.svc_q + slot] = g;
+    if (T.sq_len == 0) T.sq_front = g;
+    T.sq_len++;
+  }
 }
 __device__ __forceinline__ void send_core(const Params& P, Tile& T, uint4 f) {
   count_sent(T, ftype(f));
@@ -1156,6 +1179,34 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
   if (lat > T.latmax) T.latmax = lat;
   atomicAdd(&sh_hist[lat < HIST_BINS - 1 ? lat : HIST_BINS - 1], 1u);
 
+  // packet mode: the handler runs once, when the last flit of a packet is in
+  if (PACKETS(P) && fe(f) > 1 && packet_flits(P, ty) > 1) {
+    uint32_t* rb = P.rob + (size_t)T.r * P.rob_entries * 2;
+    const uint32_t key = W_VALID | fline(f) | (ty << 26), src = fsrc(f);
+    int hit = -1, free_slot = -1;
+    for (int i = 0; i < P.rob_entries; ++i) {
+      const uint32_t w0 = rb[2 * i];
+      if (w0 == key && (rb[2 * i + 1] & 0xFFFFu) == src) hit = i;
+      else if (!(w0 & W_VALID) && free_slot < 0) free_slot = i;
+    }
+    if (hit < 0) {
+      if (free_slot < 0) {
+        set_error(P, t, ERR_OVERFLOW);
+        return;
+      }
+      hit = free_slot;
+      rb[2 * hit] = key;
+      rb[2 * hit + 1] = src;
+    }
+    const uint32_t cnt = (rb[2 * hit + 1] >> 16) + 1;
+    if (cnt < fe(f)) {
+      rb[2 * hit + 1] = src | (cnt << 16);
+      return;
+    }
+    rb[2 * hit] = 0;
+    rb[2 * hit + 1] = 0;
+  }
+
   const uint32_t line = fline(f);
   const uint32_t set = l2_set(P, line);
   const size_t base = l2_base(P, T.r, set);
@@ -1364,6 +1415,25 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
 }
 
 // ---------------------------------------------------------------- hash
+// the dynamic-hash terms of a tile's partly received packets (packet mode):
+// one fold(0x1A, r, line | type << 26, src | count << 16) per entry, summed
+static __device__ unsigned long long rob_hash(const Params& P, uint32_t r) {
+  unsigned long long h = 0;
+  if (!PACKETS(P)) return 0;
+  const uint32_t* rb = P.rob + (size_t)r * P.rob_entries * 2;
+  for (int i = 0; i < P.rob_entries; ++i)
+    if (rb[2 * i] & W_VALID)
+      h += hfold(hfold(hfold(hstart(0x1A), r), rb[2 * i] & ~W_VALID), rb[2 * i + 1]);
+  return h;
+}
+// whether a tile has no partly received packet
+static __device__ bool rob_empty(const Params& P, uint32_t r) {
+  if (!PACKETS(P)) return true;
+  const uint32_t* rb = P.rob + (size_t)r * P.rob_entries * 2;
+  for (int i = 0; i < P.rob_entries; ++i)
+    if (rb[2 * i] & W_VALID) return false;
+  return true;
+}
 // dynamic hash of one tile after a cycle: fold(r, its four output flits, its
 // core record words C0..C6, injected, ejected, deflections); fields that mean
 // nothing in the current FSM / outstanding-miss state hash as 0

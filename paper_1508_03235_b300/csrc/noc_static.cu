@@ -62,6 +62,9 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
       (c->mig_window < 1 || c->mig_window > HIST_MAX || c->mig_threshold < 1 ||
        c->fwd_entries < 1))
     return NOC_ERR_ARG;
+  if (c->packet_mode < 0 || c->packet_mode > 1 ||
+      (c->packet_mode && (c->rob_entries < 1 || c->rob_entries > 64 || c->svc_q < 16)))
+    return NOC_ERR_ARG;
   // trace mode needs per-core reference lists, which live outside the array
   if (tr->mode < 0 || tr->mode > 1 || tr->period < 0 || tr->write_q16 > 65536 ||
       tr->priv_q16 + (uint64_t)tr->shared_q16 > 65536 || tr->hot_q16 > 65536 ||
@@ -91,6 +94,8 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
   P.svc_q = c->svc_q;
   P.mem_q = c->mem_q;
   P.fwd_cap = c->fwd_entries > 0 ? c->fwd_entries : 1;
+  P.packet_mode = c->packet_mode;
+  P.rob_entries = c->packet_mode ? c->rob_entries : 0;
   P.write_q16 = tr->write_q16;
   P.priv_q16 = tr->priv_q16;
   P.shared_q16 = tr->shared_q16;
@@ -110,13 +115,14 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
   const size_t w1 = N * P.l1_sets * P.l1_ways, w2 = N * P.l2_sets * P.l2_ways;
   const bool lspd = l2_policy != NOC_L2_INTERLEAVED, mig = l2_policy == NOC_L2_LSPD_MIGRATE;
   const size_t n_flags = 1024 * FLAG_SLOTS;
-  size_t off[19], cur = 0;
-  const size_t sz[19] = {2 * 4 * N * 16, NCORE * N * 4, N * P.core_q * 16, N * P.svc_q * 16,
+  size_t off[20], cur = 0;
+  const size_t sz[20] = {2 * 4 * N * 16, NCORE * N * 4, N * P.core_q * 16, N * P.svc_q * 16,
                          N * P.mem_q * 16, w1 * 4, w1 * 2, w2 * 4, lspd ? w2 * 2 : 0,
                          mig ? w2 * hist_stride(P.mig_window) * 2 : 0, lspd ? (size_t)total * 4 : 0,
                          mig ? N * P.fwd_cap * 8 : 0, (size_t)NSTAT * N * 8,
-                         2 * HIST_BINS * 8, n_flags * 4, 8, 4, 64 * 8, 2 * 4 * N * 32};
-  for (int k = 0; k < 19; ++k) {
+                         2 * HIST_BINS * 8, n_flags * 4, 8, 4, 64 * 8, 2 * 4 * N * 32,
+                         N * (size_t)P.rob_entries * 8};
+  for (int k = 0; k < 20; ++k) {
     off[k] = a256(cur);
     cur = off[k] + sz[k];
   }
@@ -152,10 +158,11 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
   unsigned int* abort_flag = reinterpret_cast<unsigned int*>(b + off[16]);
   unsigned long long* totals = reinterpret_cast<unsigned long long*>(b + off[17]);
   P.gtag = reinterpret_cast<uint4*>(b + off[18]);
+  P.rob = P.rob_entries ? reinterpret_cast<uint32_t*>(b + off[19]) : nullptr;
 
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   // everything the simulation reads before writing starts from its reset value
-  for (int k = 0; k < 19; ++k) {
+  for (int k = 0; k < 20; ++k) {
     if (!sz[k] || k == 2 || k == 3 || k == 4) continue;  // queue slots are written before read
     int v = (k == 10 || k == 15) ? 0xFF : 0;              // directory NONE, no error
     if (cudaMemsetAsync(b + off[k], v, sz[k], st) != cudaSuccess) return NOC_ERR_CUDA;

@@ -26,7 +26,8 @@ FLIT_TYPES = dict(NONE=0, REQ=1, DATA=2, WT=3, DA=4, DRPOS=5, DRNEG=6, NACK=7, D
 class CacheCfg(C.Structure):
     _fields_ = [(n, C.c_int32) for n in (
         "l1_sets", "l1_ways", "l2_sets", "l2_ways", "l1_miss_cycles", "mem_latency",
-        "mig_window", "mig_threshold", "core_q", "svc_q", "mem_q", "fwd_entries")]
+        "mig_window", "mig_threshold", "core_q", "svc_q", "mem_q", "fwd_entries",
+        "packet_mode", "rob_entries")]
 
 
 class Traffic(C.Structure):
