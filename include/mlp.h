@@ -28,6 +28,7 @@ extern "C" {
 
 #define MLP_OK 0
 #define MLP_ERR_ARG 1
+#define MLP_ERR_TIMEOUT 4
 #define MLP_ERR_CUDA 5
 #define MLP_MAX_LAYERS 8
 
@@ -60,6 +61,19 @@ int mlp_adamw(size_t n, float* params, uint16_t* params_bf16, const float* grads
               void* stream);
 /* FP32 -> BF16 (round to nearest even). */
 int mlp_to_bf16(const float* src, uint16_t* dst, size_t n, void* stream);
+
+/* GEMM engine of the layers.  path 0 (default): the 5th-generation tensor
+ * cores (tcgen05.mma, FP32 accumulator in tensor memory) for every GEMM whose
+ * rows are a multiple of 128, inner dimension 16..256 and output width up to
+ * 256, both multiples of 16, with unit-stride operands (every layer of the
+ * forward pass at batch sizes that are multiples of 128), warp-level mma.sync
+ * for the others (the backward pass's transposed products); path 1: mma.sync
+ * for all.
+ * Returns the previous path, or -1 for an invalid one. */
+int mlp_set_gemm_path(int path);
+/* Waits for the device; MLP_ERR_TIMEOUT if a tcgen05 GEMM since the last call
+ * gave up waiting for its MMAs (its output is then incomplete), else MLP_OK. */
+int mlp_gemm_status(void);
 
 #ifdef __cplusplus
 }

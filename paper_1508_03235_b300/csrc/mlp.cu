@@ -8,6 +8,7 @@
 #include <cmath>
 
 #include "mlp.h"
+#include "mlp_tc.cuh"
 
 namespace mlpk {
 
@@ -112,7 +113,68 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const Gemm g) {
         }
 }
 
+// epilogue of the tcgen05 GEMM: W (16 or 32) consecutive columns of one row
+// per thread
+struct TcEpi {
+  const __nv_bfloat16* bias;
+  float* Cf;
+  __nv_bfloat16* Cb;
+  long long ldc;
+  int gelu;
+  template <int W>
+  __device__ void operator()(int row, int col, const float (&v)[W]) const {
+    float o[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) o[j] = v[j] + (bias ? __bfloat162float(bias[col + j]) : 0.0f);
+    if (Cf) {
+      float4* p = reinterpret_cast<float4*>(Cf + row * ldc + col);
+#pragma unroll
+      for (int q = 0; q < W / 4; ++q) p[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    }
+    if (Cb) {
+      uint32_t w[W / 2];
+#pragma unroll
+      for (int j = 0; j < W / 2; ++j) {
+        const float a = gelu ? mlpk::gelu(o[2 * j]) : o[2 * j];
+        const float b = gelu ? mlpk::gelu(o[2 * j + 1]) : o[2 * j + 1];
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        w[j] = *reinterpret_cast<const uint32_t*>(&h);
+      }
+      uint4* p = reinterpret_cast<uint4*>(Cb + row * ldc + col);
+#pragma unroll
+      for (int q = 0; q < W / 8; ++q) p[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    }
+  }
+};
+
+int g_path = 0;  // 0: tcgen05 where it applies, 1: mma.sync for every GEMM
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+bool tc_applies(const Gemm& g) {
+  return g_path == 0 && g.sAk == 1 && g.sAm == g.K && g.sBk == 1 && g.sBn == g.K && g.K >= 16 &&
+         g.K <= tc::MAXK && g.K % 16 == 0 && g.M % tc::TM == 0 && g.N % 16 == 0 && g.N <= tc::MAXN &&
+         aligned16(g.A) && aligned16(g.B) && (!g.Cf || (aligned16(g.Cf) && g.ldc % 4 == 0)) &&
+         (!g.Cb || (aligned16(g.Cb) && g.ldc % 8 == 0));
+}
+
 cudaError_t gemm(const Gemm& g, cudaStream_t s) {
+  if (tc_applies(g)) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(tc::gemm_kernel<TcEpi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)tc::smem_bytes(tc::MAXN, tc::MAXK));
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    const TcEpi epi{g.bias, g.Cf, g.Cb, g.ldc, g.gelu};
+    // column tiles of 64 (or the whole width if narrower) so that a layer
+    // spreads over (M / 128) x (N / 64) CTAs
+    const int nt = g.N % 64 == 0 ? 64 : (g.N % 32 == 0 ? 32 : 16);
+    const dim3 grid(g.M / tc::TM, g.N / nt);
+    tc::gemm_kernel<TcEpi><<<grid, tc::THREADS, tc::smem_bytes(nt, g.K), s>>>(g.A, g.B, g.M, nt, g.K, epi);
+    return cudaGetLastError();
+  }
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
   gemm_kernel<<<grid, THREADS, 0, s>>>(g);
   return cudaGetLastError();
@@ -368,6 +430,22 @@ int mlp_to_bf16(const float* src, uint16_t* dst, size_t n, void* stream) {
   to_bf16_kernel<<<grid_1d(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
       src, reinterpret_cast<__nv_bfloat16*>(dst), n);
   return cudaGetLastError() == cudaSuccess ? MLP_OK : MLP_ERR_CUDA;
+}
+
+int mlp_set_gemm_path(int path) {
+  if (path != 0 && path != 1) return -1;
+  const int old = mlpk::g_path;
+  mlpk::g_path = path;
+  return old;
+}
+
+int mlp_gemm_status(void) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return MLP_ERR_CUDA;
+  unsigned int v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, mlpk::tc::g_tc_status, sizeof v) != cudaSuccess) return MLP_ERR_CUDA;
+  if (v && cudaMemcpyToSymbol(mlpk::tc::g_tc_status, &zero, sizeof zero) != cudaSuccess)
+    return MLP_ERR_CUDA;
+  return v ? MLP_ERR_TIMEOUT : MLP_OK;
 }
 
 }  // extern "C"

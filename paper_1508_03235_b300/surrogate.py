@@ -48,12 +48,25 @@ def _mlp_lib():
             ("mlp_mse", i32, [vp, vp, i32, i32, i32, vp, vp, vp]),
             ("mlp_adamw", i32, [sz, vp, vp, vp, vp, vp, f, f, f, f, f, i32, vp]),
             ("mlp_to_bf16", i32, [vp, vp, sz, vp]),
+            ("mlp_set_gemm_path", i32, [i32]),
+            ("mlp_gemm_status", i32, []),
         ):
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
         L._mlp_sigs = True
     return L
+
+
+def set_gemm_path(path: int) -> int:
+    """0: tcgen05 tensor cores where they apply (default), 1: mma.sync for
+    every GEMM; returns the previous setting."""
+    return _mlp_lib().mlp_set_gemm_path(path)
+
+
+def gemm_status() -> int:
+    """0, or MLP_ERR_TIMEOUT if a tcgen05 GEMM gave up waiting for its MMAs."""
+    return _mlp_lib().mlp_gemm_status()
 
 
 def _ok(rc, what):

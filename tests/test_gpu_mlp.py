@@ -110,3 +110,48 @@ def test_small_surrogate_of_the_simulator_and_screening(sur):
     y_top = sur.simulate([pc[i] for i in top], 3000)
     y_rnd = sur.simulate([pc[i] for i in rnd], 3000)
     assert y_top[:, 0].min() < y_rnd[:, 0].min()
+
+
+@pytest.mark.parametrize("B", [128, 1024])
+def test_tcgen05_layer_exact_sum(sur, B):
+    """One 256 -> 256 layer at a batch the tcgen05 path takes: the result is
+    the fp64 sum of the BF16 products to FP32 accuracy, on both GEMM engines."""
+    import torch
+    net = sur.MLP(dims=(256, 256), seed=11, max_batch=B)
+    rng = np.random.default_rng(B)
+    x = rng.normal(size=(B, 256)).astype(np.float32)
+    xb = torch.as_tensor(x).cuda().to(torch.bfloat16)
+    p = M.bf16_round(net.params.double().cpu().numpy())
+    W, b = p[:256 * 256].reshape(256, 256), p[256 * 256:]
+    want = M.bf16_round(x) @ W.T + b
+    out = {}
+    for path in (0, 1):
+        old = sur.set_gemm_path(path)
+        out[path] = net.forward(xb).double().cpu().numpy()
+        sur.set_gemm_path(old)
+    assert sur.gemm_status() == 0
+    scale = np.abs(want).max()
+    for path in (0, 1):
+        assert np.abs(out[path] - want).max() < 2e-5 * scale, path
+    assert np.abs(out[0] - out[1]).max() < 2e-5 * scale
+
+
+@pytest.mark.parametrize("B", [128, 4096])
+def test_tcgen05_network_matches_mma_sync_and_oracle(sur, B):
+    """The full network (three 256 x 256 hidden layers on tcgen05 at these
+    batches) against the mma.sync engine and the fp64 oracle."""
+    import torch
+    net = sur.MLP(seed=7, max_batch=B)
+    rng = np.random.default_rng(B + 1)
+    x = rng.normal(size=(B, 16)).astype(np.float32)
+    xb = torch.as_tensor(x).cuda().to(torch.bfloat16)
+    old = sur.set_gemm_path(1)
+    y1 = net.forward(xb).double().cpu().numpy()
+    sur.set_gemm_path(0)
+    y0 = net.forward(xb).double().cpu().numpy()
+    sur.set_gemm_path(old)
+    assert sur.gemm_status() == 0
+    want, _ = M.forward(list(sur.DIMS), net.params.double().cpu().numpy(), x)
+    assert rel(y0, want) < 1e-2
+    assert np.allclose(y0, want, rtol=3e-2, atol=3e-2 * np.abs(want).max())
+    assert rel(y0, y1) < 5e-3
