@@ -259,10 +259,13 @@ class Surrogate:
 
 # ----------------------------------------------------------------- full run
 def run(points=50_000, holdout=5_000, cycles=20_000, chunk=2_000, epochs=300, batch=1024,
-        lr=2e-3, data_path=None, seed=0, log=print):
+        lr=2e-3, data_path=None, seed=0, log=print, from_data=None, time_points=2_000):
     """Simulate `points` design points with the batch engine, train on all but
     `holdout`, score the held-out ones against their exact simulations, and time
-    batch-4096 inference against the batched simulator."""
+    batch-4096 inference against the batched simulator.  With `from_data`, the
+    design points' exact outputs come from a dataset this function saved
+    before (same points, seed and cycles), and the simulator's rate is timed on
+    the first `time_points` of them."""
     import json
     import time
 
@@ -272,14 +275,27 @@ def run(points=50_000, holdout=5_000, cycles=20_000, chunk=2_000, epochs=300, ba
     Xs, Ys = [], []
     pts_all = I.batch_design_points(points, seed=seed)
     sim_s = 0.0
-    for s in range(0, points, chunk):
-        pts = pts_all[s:s + chunk]
+    if from_data:
+        z = np.load(from_data)
+        if int(z["cycles"]) != cycles or int(z["seed"]) != seed or len(z["X"]) != points:
+            raise ValueError(f"{from_data} holds other design points")
+        X, Y = z["X"], z["Y"]
+        n = min(time_points, points)
         a = time.perf_counter()
-        Ys.append(simulate(pts, cycles))
-        sim_s += time.perf_counter() - a
-        Xs.append(np.stack([features(p["design"]) for p in pts]))
-        log(f"simulated {min(s + chunk, points)}/{points} design points ({sim_s:.0f} s)")
-    X, Y = np.concatenate(Xs), np.concatenate(Ys)
+        Yt = simulate(pts_all[:n], cycles)
+        sim_s = (time.perf_counter() - a) * points / n     # the rate, scaled to all points
+        if not np.array_equal(Yt, Y[:n]):
+            raise ValueError("the simulator no longer reproduces the saved outputs")
+        log(f"loaded {points} design points; simulator timed on {n} ({sim_s * n / points:.0f} s)")
+    else:
+        for s in range(0, points, chunk):
+            pts = pts_all[s:s + chunk]
+            a = time.perf_counter()
+            Ys.append(simulate(pts, cycles))
+            sim_s += time.perf_counter() - a
+            Xs.append(np.stack([features(p["design"]) for p in pts]))
+            log(f"simulated {min(s + chunk, points)}/{points} design points ({sim_s:.0f} s)")
+        X, Y = np.concatenate(Xs), np.concatenate(Ys)
     if data_path:
         np.savez_compressed(data_path, X=X, Y=Y, cycles=cycles, seed=seed)
     ntr = points - holdout
@@ -324,11 +340,15 @@ if __name__ == "__main__":
     ap.add_argument("--cycles", type=int, default=20_000)
     ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--data", default=None, help="save the simulated dataset (.npz)")
+    ap.add_argument("--from-data", default=None,
+                    help="reuse a saved dataset; time the simulator on --time-points of it")
+    ap.add_argument("--time-points", type=int, default=2_000)
     ap.add_argument("--out", default=None, help="write the result JSON here")
     a = ap.parse_args()
     from paper_1508_03235_b300 import surrogate as S
     res, _ = S.run(points=a.points, holdout=a.holdout, cycles=a.cycles, epochs=a.epochs,
-                   data_path=a.data, log=lambda m: print(m, flush=True))
+                   data_path=a.data, log=lambda m: print(m, flush=True), from_data=a.from_data,
+                   time_points=a.time_points)
     if a.out:
         with open(a.out, "w") as f:
             json.dump(res, f, indent=1)
