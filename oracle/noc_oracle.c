@@ -193,6 +193,11 @@ static int neighbour(const orc_sim* s, int r, int d) {
 static int opposite(int d) { return d ^ 1; }
 
 static uint32_t home_of(const orc_sim* s, uint32_t line) { return line % (uint32_t)s->N; }
+/* the tile holding a line's directory entry (LSPD): its home, or the one
+ * directory node of the centralized variant */
+static uint32_t dir_home(const orc_sim* s, uint32_t line) {
+  return s->p.dir_central ? (uint32_t)s->p.dir_tile : home_of(s, line);
+}
 
 /* ------------------------------------------------------------------------ */
 /* errors: the first cycle with an error wins, smaller code on ties          */
@@ -341,7 +346,7 @@ static uint32_t dir_entry(uint32_t tile, uint32_t epoch) { return tile | (epoch 
 /* victim's directory entry delete (Sec. 3.4): at the home, the entry is
  * cleared only if it still names this copy */
 static void send_dinv(orc_sim* s, int r, uint32_t vline, uint32_t vepoch) {
-  uint32_t h = home_of(s, vline);
+  uint32_t h = dir_home(s, vline);
   if ((int)h == r) {
     if (s->dir[vline] == dir_entry((uint32_t)r, vepoch)) s->dir[vline] = DIR_NONE;
   } else {
@@ -560,7 +565,7 @@ static void l2_step(orc_sim* s, int r, uint32_t t) {
     T->fsm = FSM_STALL;
     return;
   }
-  uint32_t h = home_of(s, line);
+  uint32_t h = dir_home(s, line);
   if (h == (uint32_t)r) {
     /* the directory entry is at this tile: no flit for the lookup */
     uint32_t D = s->dir[line];
@@ -938,7 +943,7 @@ static void phase3(orc_sim* s, int r, uint32_t t) {
       Way* x = way_at(c2, set2, w);
       x->hist_n = 0;
       x->migrating = 0;
-      uint32_t h = home_of(s, f.line);
+      uint32_t h = dir_home(s, f.line);
       if (h == (uint32_t)r) {
         /* the directory update happens here: same as a DIRUPD handler */
         s->dir[f.line] = dir_entry((uint32_t)r, T->epoch);
@@ -1160,6 +1165,8 @@ static int check_params(const orc_params* p) {
   if (total >= (1ull << 26)) return 0;
   if (p->packet_mode < 0 || p->packet_mode > 1) return 0;
   if (p->packet_mode && (p->rob_entries < 1 || p->rob_entries > 64 || p->svc_q < 16)) return 0;
+  if (p->dir_central < 0 || p->dir_central > 1) return 0;
+  if (p->dir_central && (p->dir_tile < 0 || p->dir_tile >= p->mesh_w * p->mesh_h)) return 0;
   return 1;
 }
 

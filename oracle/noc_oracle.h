@@ -56,6 +56,9 @@ typedef struct {
    * reply (remote L2 access, RA) is 4 flits and a migration (B2) 16 flits,
    * reassembled in a per-tile reorder buffer of rob_entries packets */
   int32_t packet_mode, rob_entries;
+  /* directory placement (LSPD policies, Sec. 3.2): 0 = each line's entry at
+   * its home tile; 1 = every entry at one directory node, tile dir_tile */
+  int32_t dir_central, dir_tile;
 } orc_params;
 
 /* statistic indices (order fixed by the written model) */

@@ -61,6 +61,8 @@ def cache_cfg(l1_kb=32, l1_ways=4, l2_kb=256, l2_ways=8, **over):
         fwd_entries=4,
         packet_mode=0,
         rob_entries=8,
+        dir_central=0,
+        dir_tile=0,
     )
     cfg.update(over)
     return cfg

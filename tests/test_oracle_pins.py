@@ -534,3 +534,38 @@ def test_packet_mode_conservation_after_drain(oracle_mod):
     # interleaved L2: requests and write-throughs are one flit, every reply a
     # 4-flit data packet
     assert st["injected"] == st["req_made"] + st["wt_sent"] + 4 * st["reply_sent"]
+
+
+# --------------------------------------------------------------------------
+# centralized directory node (Sec. 3.2's alternative): every directory message
+# goes to one tile instead of the line's home
+def test_central_directory_timeline(oracle_mod):
+    dist = oracle_mod.OracleSim(trace_params(3, 3, policy=I.POLICY_LSPD_LOCAL))
+    cent = oracle_mod.OracleSim(trace_params(3, 3, policy=I.POLICY_LSPD_LOCAL, dir_central=1,
+                                             dir_tile=1))
+    for s in (dist, cent):
+        s.set_trace(0, [8])        # home 8 is 4 hops from tile 0; tile 1 is 1 hop
+        s.step(150)
+    a, b = dist.stats(), cent.stats()
+    # DA out and DR_NEG back each travel 3 hops fewer
+    assert a["l2lat_sum"] == 113 and b["l2lat_sum"] == 113 - 2 * 3
+    assert a["dir_search"] == b["dir_search"] == 1
+    assert cent.stats(1)["dir_search"] == 1 and dist.stats(8)["dir_search"] == 1
+    assert cent.dir_get(8) == dist.dir_get(8) == (0 | (1 << 16))
+
+
+@pytest.mark.parametrize("policy", [1, 2])
+def test_central_directory_takes_every_lookup(oracle_mod, policy):
+    cache = I.cache_cfg(l1_kb=2, l1_ways=2, l2_kb=4, l2_ways=4, mig_window=4, mig_threshold=2,
+                        svc_q=512, dir_central=1, dir_tile=14)
+    traf = I.traffic(period=3, write=0.3, priv=0.3, shared=0.6, priv_kb=4, shared_mb=0)
+    traf.update(shared_lines=300)
+    s = oracle_mod.OracleSim(I.sim_params(6, 6, policy=policy, cache=cache, traf=traf, seed=9))
+    s.step(4000)
+    s.drain(100_000)
+    st = s.stats()
+    assert st["dir_search"] > 0 and s.stats(14)["dir_search"] == st["dir_search"]
+    assert st["injected"] == st["ejected"]
+    assert st["req_made"] == st["req_rcvd"] and st["reply_sent"] == st["reply_rcvd"]
+    if policy == 2:
+        assert st["migrations"] > 0 and s.stats(14)["migrations"] == st["migrations"]
