@@ -76,6 +76,11 @@ typedef struct {
    * NOC_ERR_QUEUE_OVERFLOW); the message's handler runs in the cycle its last
    * flit is ejected.  Needs svc_q >= 16. */
   int32_t packet_mode, rob_entries;
+  /* Directory placement (LSPD policies, Sec. 3.2): dir_central 0 keeps each
+   * line's entry at its home tile (line mod N); 1 keeps every entry at one
+   * directory node, tile dir_tile (0..N-1) -- the centralized organisation
+   * whose node becomes a hot spot.  Ignored by the interleaved policy. */
+  int32_t dir_central, dir_tile;
 } noc_cache_cfg;
 
 /* Reference stream.  Fractions are q16 fixed point (65536 = 1).  Reference k

@@ -395,6 +395,9 @@ int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, co
   if (c->packet_mode < 0 || c->packet_mode > 1 ||
       (c->packet_mode && (c->rob_entries < 1 || c->rob_entries > 64 || c->svc_q < 16)))
     return fail(NOC_ERR_ARG, "packets: mode 0/1, reorder entries 1..64, svc_q >= 16");
+  if (c->dir_central < 0 || c->dir_central > 1 ||
+      (c->dir_central && (c->dir_tile < 0 || (long)c->dir_tile >= (long)mesh_w * mesh_h)))
+    return fail(NOC_ERR_ARG, "directory node: dir_central 0/1, dir_tile a tile of the mesh");
   if (tr->mode < 0 || tr->mode > 2 || tr->period < 0) return fail(NOC_ERR_ARG, "traffic mode/period");
   if (tr->write_q16 > 65536 || tr->priv_q16 + (uint64_t)tr->shared_q16 > 65536 || tr->hot_q16 > 65536)
     return fail(NOC_ERR_ARG, "q16 fractions out of range");
@@ -437,6 +440,8 @@ int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, co
   P.fwd_cap = c->fwd_entries > 0 ? c->fwd_entries : 1;
   P.packet_mode = c->packet_mode;
   P.rob_entries = c->packet_mode ? c->rob_entries : 0;
+  P.dir_central = c->dir_central;
+  P.dir_tile = c->dir_central ? c->dir_tile : 0;
   P.write_q16 = tr->write_q16;
   P.priv_q16 = tr->priv_q16;
   P.shared_q16 = tr->shared_q16;

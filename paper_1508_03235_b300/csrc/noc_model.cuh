@@ -84,6 +84,7 @@ struct Params {
   int l1_miss, mem_lat, mig_window, mig_threshold, hist_stride;
   int core_q, svc_q, mem_q, fwd_cap;
   int packet_mode, rob_entries;  // Table 1 packets; reorder-buffer entries per tile
+  int dir_central, dir_tile;     // directory entries at each line's home, or all at dir_tile
   uint32_t write_q16, priv_q16, shared_q16, hot_q16;
   int hot_side, hot_x0, hot_y0;
   uint32_t priv_lines, shared_lines, remote_lines, total_lines;
@@ -284,6 +285,11 @@ __device__ __forceinline__ void set_error(const Params& P, uint32_t t, int code)
 
 __device__ __forceinline__ uint32_t home_of(const Params& P, uint32_t line) {
   return line - qdiv(line, P.mN) * (uint32_t)P.N;
+}
+// the tile holding a line's directory entry (LSPD): its home, or the one
+// directory node of the centralized variant
+__device__ __forceinline__ uint32_t dir_home(const Params& P, uint32_t line) {
+  return P.dir_central ? (uint32_t)P.dir_tile : home_of(P, line);
 }
 __device__ __forceinline__ uint32_t l1_set(const Params& P, uint32_t line) {
   return line - qdiv(line, P.mL1) * (uint32_t)P.l1_sets;
@@ -543,7 +549,7 @@ __device__ __forceinline__ uint16_t* hist_ptr(const Params& P, size_t way_index)
 
 // directory entry delete for an evicted L2 victim (Sec. 3.4)
 static __device__ void send_dinv(const Params& P, Tile& T, uint32_t vline, uint32_t vepoch, uint32_t t) {
-  uint32_t h = home_of(P, vline);
+  uint32_t h = dir_home(P, vline);
   if (h == T.r) {
     if (P.dir[vline] == (T.r | (vepoch << 16))) P.dir[vline] = DIR_NONE;
   } else {
@@ -743,7 +749,7 @@ static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* s
     T.fsm = FSM_STALL;
     return;
   }
-  uint32_t h = home_of(P, line);
+  uint32_t h = dir_home(P, line);
   if (h == T.r) {
     uint32_t D = P.dir[line];
     if (D == DIR_NONE || (D & 0xFFFFu) == T.r) {
@@ -1360,7 +1366,7 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
       uint16_t* hp = hist_ptr(P, base + way);
       hp[0] = 0;
       hp[1] = 0;
-      uint32_t h = home_of(P, line);
+      uint32_t h = dir_home(P, line);
       if (h == T.r) {
         P.dir[line] = T.r | (T.epoch << 16);
         SMALL(S_MIGR)++;
