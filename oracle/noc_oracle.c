@@ -356,20 +356,6 @@ static void send_dinv(orc_sim* s, int r, uint32_t vline, uint32_t vepoch) {
 
 /* ------------------------------------------------------------------------ */
 /* cache operations                                                          */
-static void l1_fill(orc_sim* s, int r, uint32_t line, uint32_t owner) {
-  Cache* c = &s->tiles[r].l1;
-  int set = l1_set(s, line);
-  int w = cache_find(c, set, line);
-  if (w < 0) {
-    w = cache_victim(c, set); /* L1 victims are clean (write-through): dropped */
-    Way* x = way_at(c, set, w);
-    way_clear(x);
-    x->valid = 1;
-    x->line = line;
-  }
-  way_at(c, set, w)->owner = owner;
-  cache_touch(c, set, w);
-}
 
 /* install a block in r's L2 slice: insert if absent, else touch (Sec. 3.4) */
 static void l2_install(orc_sim* s, int r, uint32_t line, uint32_t epoch) {
@@ -414,6 +400,45 @@ static void local_wt(orc_sim* s, int r, uint32_t line) {
     s->tiles[r].st[ORC_ST_WT_HIT]++;
   } else {
     s->tiles[r].st[ORC_ST_MEM_WRITE]++;
+  }
+}
+
+/* a write of `line` reaching the L2 that holds it: the owner recorded with
+ * the L1 copy (this tile's own slice, another tile through a WT message, or
+ * memory when no slice holds it) */
+static void write_to_owner(orc_sim* s, int r, uint32_t line, uint32_t owner) {
+  if (owner == (uint32_t)r)
+    local_wt(s, r, line);
+  else if (owner == NO_TILE)
+    s->tiles[r].st[ORC_ST_MEM_WRITE]++;
+  else
+    send_svc(s, r, make_flit(T_WT, (uint32_t)r, owner, line, 0, 0));
+}
+
+/* fill r's L1 with `line` (insert if absent, else touch); `owner` is the tile
+ * whose L2 supplied it.  Write-through: a write is passed on to the owner
+ * after the fill and victims are clean.  Write-back: a write dirties the L1
+ * copy, and a dirty victim is written to its owner first. */
+static void l1_fill(orc_sim* s, int r, uint32_t line, uint32_t owner, int write) {
+  Cache* c = &s->tiles[r].l1;
+  int set = l1_set(s, line);
+  int w = cache_find(c, set, line);
+  if (w < 0) {
+    w = cache_victim(c, set);
+    Way* x = way_at(c, set, w);
+    if (s->p.l1_write_back && x->valid && x->dirty) write_to_owner(s, r, x->line, x->owner);
+    way_clear(x);
+    x->valid = 1;
+    x->line = line;
+  }
+  Way* x = way_at(c, set, w);
+  x->owner = owner;
+  cache_touch(c, set, w);
+  if (write) {
+    if (s->p.l1_write_back)
+      x->dirty = 1;
+    else
+      write_to_owner(s, r, line, owner);
   }
 }
 
@@ -462,7 +487,9 @@ static int l1_step(orc_sim* s, int r, uint32_t t, uint32_t line, int write) {
   int set = l1_set(s, line);
   int w = cache_find(c, set, line);
   if (w >= 0) {
-    if (write) {
+    if (write && s->p.l1_write_back) {
+      way_at(c, set, w)->dirty = 1;
+    } else if (write) {
       uint32_t owner = way_at(c, set, w)->owner;
       if (owner == (uint32_t)r) {
         local_wt(s, r, line);
@@ -515,8 +542,7 @@ static void l2_step(orc_sim* s, int r, uint32_t t) {
       if (w >= 0) {
         T->st[ORC_ST_L2_HIT]++;
         cache_touch(c2, set2, w);
-        l1_fill(s, r, line, (uint32_t)r);
-        if (write) local_wt(s, r, line);
+        l1_fill(s, r, line, (uint32_t)r, write);
         l2lat_sample(s, r, t, start);
         T->fsm = FSM_IDLE;
         return;
@@ -554,8 +580,7 @@ static void l2_step(orc_sim* s, int r, uint32_t t) {
     T->st[ORC_ST_L2_HIT]++;
     cache_touch(c2, set2, w);
     if (s->p.policy == ORC_L2_LSPD_MIGRATE) hist_push(s, way_at(c2, set2, w), (uint32_t)r);
-    l1_fill(s, r, line, (uint32_t)r);
-    if (write) local_wt(s, r, line);
+    l1_fill(s, r, line, (uint32_t)r, write);
     l2lat_sample(s, r, t, start);
     T->fsm = FSM_IDLE;
     return;
@@ -619,11 +644,9 @@ static void phase1(orc_sim* s, int r, uint32_t t) {
   if ((T->om_kind == OM_MEM_L2 || T->om_kind == OM_MEM_L1) && T->om_timer <= t) {
     if (T->om_kind == OM_MEM_L2) {
       l2_install(s, r, T->om_line, T->om_epoch);
-      l1_fill(s, r, T->om_line, (uint32_t)r);
-      if (T->om_write) local_wt(s, r, T->om_line);
+      l1_fill(s, r, T->om_line, (uint32_t)r, T->om_write);
     } else {
-      l1_fill(s, r, T->om_line, NO_TILE);
-      if (T->om_write) T->st[ORC_ST_MEM_WRITE]++;
+      l1_fill(s, r, T->om_line, NO_TILE, T->om_write);
     }
     l2lat_sample(s, r, t, T->om_start);
     set_om(T, OM_NONE, 0, 0, 0);
@@ -867,8 +890,7 @@ static void phase3(orc_sim* s, int r, uint32_t t) {
         protocol_error(s);
         break;
       }
-      l1_fill(s, r, f.line, f.src);
-      if (T->om_write) send_svc(s, r, make_flit(T_WT, (uint32_t)r, f.src, f.line, 0, 0));
+      l1_fill(s, r, f.line, f.src, T->om_write);
       l2lat_sample(s, r, t, T->om_start);
       set_om(T, OM_NONE, 0, 0, 0);
       break;
@@ -1070,7 +1092,7 @@ uint64_t orc_state_hash(const orc_sim* s) {
         h = fold(h, (uint64_t)r);
         h = fold(h, (uint64_t)set);
         h = fold(h, (uint64_t)w);
-        h = fold(h, x->line);
+        h = fold(h, (uint64_t)x->line | ((uint64_t)x->dirty << 31));
         h = fold(h, x->owner);
         h = fold(h, (uint64_t)cache_rank(c1, set, w));
         H += h;
@@ -1166,6 +1188,7 @@ static int check_params(const orc_params* p) {
   if (p->packet_mode < 0 || p->packet_mode > 1) return 0;
   if (p->packet_mode && (p->rob_entries < 1 || p->rob_entries > 64 || p->svc_q < 16)) return 0;
   if (p->dir_central < 0 || p->dir_central > 1) return 0;
+  if (p->l1_write_back < 0 || p->l1_write_back > 1) return 0;
   if (p->dir_central && (p->dir_tile < 0 || p->dir_tile >= p->mesh_w * p->mesh_h)) return 0;
   return 1;
 }

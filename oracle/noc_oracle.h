@@ -59,6 +59,9 @@ typedef struct {
   /* directory placement (LSPD policies, Sec. 3.2): 0 = each line's entry at
    * its home tile; 1 = every entry at one directory node, tile dir_tile */
   int32_t dir_central, dir_tile;
+  /* L1 write policy: 0 = write-through (Sec. 3.1, 3.2); 1 = write-back, a dirty
+   * victim written back to the L2 that supplied it (Sec. 3.4, 7.1) */
+  int32_t l1_write_back;
 } orc_params;
 
 /* statistic indices (order fixed by the written model) */

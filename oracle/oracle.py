@@ -41,7 +41,7 @@ class _Params(C.Structure):
         (n, C.c_uint32) for n in ("priv_lines", "shared_lines", "remote_lines")] + [
         ("seed", C.c_uint64), ("stream", C.c_uint32),
         ("packet_mode", C.c_int32), ("rob_entries", C.c_int32),
-        ("dir_central", C.c_int32), ("dir_tile", C.c_int32)]
+        ("dir_central", C.c_int32), ("dir_tile", C.c_int32), ("l1_write_back", C.c_int32)]
 
 
 def build(force: bool = False) -> str:

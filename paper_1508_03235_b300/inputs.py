@@ -63,6 +63,7 @@ def cache_cfg(l1_kb=32, l1_ways=4, l2_kb=256, l2_ways=8, **over):
         rob_entries=8,
         dir_central=0,
         dir_tile=0,
+        l1_write_back=0,
     )
     cfg.update(over)
     return cfg

@@ -569,3 +569,88 @@ def test_central_directory_takes_every_lookup(oracle_mod, policy):
     assert st["req_made"] == st["req_rcvd"] and st["reply_sent"] == st["reply_rcvd"]
     if policy == 2:
         assert st["migrations"] > 0 and s.stats(14)["migrations"] == st["migrations"]
+
+
+# --------------------------------------------------------------------------
+# L1 write-back option: a write dirties the L1 copy; a dirty victim is written
+# to the L2 that supplied it (local slice, another tile, or memory)
+def lru_model_write_back(refs, l1_sets, l1_ways, l2_sets, l2_ways):
+    l1 = [OrderedDict() for _ in range(l1_sets)]      # line -> dirty
+    l2 = [OrderedDict() for _ in range(l2_sets)]
+    c = Counter()
+
+    def to_l2(line):
+        s2 = l2[line % l2_sets]
+        if line in s2:
+            s2[line] = 1
+            s2.move_to_end(line)
+            c["wt_hit"] += 1
+        else:
+            c["mem_write"] += 1
+
+    for line, write in refs:
+        s1 = l1[line % l1_sets]
+        if line in s1:
+            c["l1_hit"] += 1
+            if write:
+                s1[line] = 1
+            s1.move_to_end(line)
+            continue
+        c["l1_miss"] += 1
+        s2 = l2[line % l2_sets]
+        if line in s2:
+            c["l2_hit"] += 1
+            s2.move_to_end(line)
+        else:
+            c["l2_miss"] += 1
+            if len(s2) == l2_ways:
+                _, dirty = s2.popitem(last=False)
+                c["mem_wb"] += dirty
+            s2[line] = 0
+        if len(s1) == l1_ways:
+            victim, vdirty = s1.popitem(last=False)
+            if vdirty:
+                to_l2(victim)
+        s1[line] = 1 if write else 0
+    return c
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_l1_write_back_brute_force(oracle_mod, seed):
+    rng = np.random.default_rng(seed)
+    cache = I.cache_cfg(l1_write_back=1)
+    cache.update(l1_sets=2, l1_ways=2, l2_sets=4, l2_ways=3)
+    p = trace_params(1, 1, period=200, cache=cache)
+    lines = rng.integers(0, 40, size=400)
+    writes = rng.random(400) < 0.3
+    refs = [(int(a), bool(b)) for a, b in zip(lines, writes)]
+    s = oracle_mod.OracleSim(p)
+    s.set_trace(0, [a | (int(b) << 31) for a, b in refs])
+    s.step(400 * 200 + 200)
+    st = s.stats()
+    want = lru_model_write_back(refs, 2, 2, 4, 3)
+    for k in ("l1_hit", "l1_miss", "l2_hit", "l2_miss", "wt_hit", "mem_write", "mem_wb"):
+        assert st[k] == want[k], k
+    # write-back generates fewer L2 writes than write-through on the same refs
+    wt = lru_model(refs, 2, 2, 4, 3)
+    assert want["wt_hit"] + want["mem_write"] <= wt["wt_hit"] + wt["mem_write"]
+
+
+def test_l1_write_back_timeline(oracle_mod):
+    # core 0 reads line 8 (home 8, remote), writes it (an L1 hit), then four
+    # more lines of the same L1 set evict it: only then does a WT go home
+    l1_sets = I.cache_cfg()["l1_sets"]
+    refs = [8, 8 | (1 << 31)] + [8 + k * l1_sets for k in range(1, 5)]
+    s = oracle_mod.OracleSim(trace_params(3, 3, l1_write_back=1))
+    s.set_trace(0, refs)
+    s.step(2 * 200 + 50)
+    assert s.stats()["wt_sent"] == 0 and s.stats()["l1_hit"] == 1
+    s.step(6 * 200)
+    st = s.stats()
+    assert st["wt_sent"] == 1 and st["wt_hit"] == 1 and st["l1_miss"] == 5
+    l2 = s.cache(8, 2)
+    assert any(l2[0, w, 0] and l2[0, w, 1] == 8 and (l2[0, w, 2] & 1) for w in range(l2.shape[1]))
+    wt = oracle_mod.OracleSim(trace_params(3, 3))
+    wt.set_trace(0, refs)
+    wt.step(2 * 200 + 50)
+    assert wt.stats()["wt_sent"] == 1                  # write-through: at the write
