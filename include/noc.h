@@ -81,6 +81,11 @@ typedef struct {
    * directory node, tile dir_tile (0..N-1) -- the centralized organisation
    * whose node becomes a hot spot.  Ignored by the interleaved policy. */
   int32_t dir_central, dir_tile;
+  /* L1 write policy: 0 = write-through (Sec. 3.1, 3.2: every write goes to
+   * the L2 that supplied the line); 1 = write-back (Sec. 3.4, 7.1: a write
+   * dirties the L1 copy; a dirty victim is written to that L2, or to memory
+   * if none holds it, when it is evicted). */
+  int32_t l1_write_back;
 } noc_cache_cfg;
 
 /* Reference stream.  Fractions are q16 fixed point (65536 = 1).  Reference k

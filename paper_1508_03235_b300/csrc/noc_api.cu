@@ -398,6 +398,7 @@ int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, co
   if (c->dir_central < 0 || c->dir_central > 1 ||
       (c->dir_central && (c->dir_tile < 0 || (long)c->dir_tile >= (long)mesh_w * mesh_h)))
     return fail(NOC_ERR_ARG, "directory node: dir_central 0/1, dir_tile a tile of the mesh");
+  if (c->l1_write_back < 0 || c->l1_write_back > 1) return fail(NOC_ERR_ARG, "l1_write_back 0/1");
   if (tr->mode < 0 || tr->mode > 2 || tr->period < 0) return fail(NOC_ERR_ARG, "traffic mode/period");
   if (tr->write_q16 > 65536 || tr->priv_q16 + (uint64_t)tr->shared_q16 > 65536 || tr->hot_q16 > 65536)
     return fail(NOC_ERR_ARG, "q16 fractions out of range");
@@ -442,6 +443,7 @@ int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, co
   P.rob_entries = c->packet_mode ? c->rob_entries : 0;
   P.dir_central = c->dir_central;
   P.dir_tile = c->dir_central ? c->dir_tile : 0;
+  P.l1_write_back = c->l1_write_back;
   P.write_q16 = tr->write_q16;
   P.priv_q16 = tr->priv_q16;
   P.shared_q16 = tr->shared_q16;

@@ -39,7 +39,7 @@ static bool interleaved_cache(const Params& P) {
   static const int exact[3][2] = {{4, 8}, {4, 16}, {16, 16}};
   const int c = way_class(P.l1_ways, P.l2_ways);
   return P.policy == POL_INTERLEAVED && P.mode == MODE_CACHE && !P.packet_mode &&
-         P.l1_ways == exact[c][0] && P.l2_ways == exact[c][1];
+         !P.l1_write_back && P.l1_ways == exact[c][0] && P.l2_ways == exact[c][1];
 }
 
 #define NOC_PICK_RUN(h, d, sp)                                    \
@@ -191,7 +191,7 @@ __global__ void state_terms_kernel(const Params P, uint32_t cycle, unsigned long
     h = hfold(h, r);
     h = hfold(h, set);
     h = hfold(h, way);
-    h = hfold(h, v & W_LINE);
+    h = hfold(h, (v & W_LINE) | ((unsigned long long)((v & W_DIRTY) ? 1 : 0) << 31));
     h = hfold(h, P.l1own[k]);
     h = hfold(h, wrank(v));
     acc += h;

@@ -28,11 +28,13 @@ namespace noc {
 #define MODE(P) (NOC_FIXED_MODE)
 #define NOC_WITH_LSPD (NOC_FIXED_POLICY != 0)
 #define PACKETS(P) 0
+#define L1WB(P) 0
 #else
 #define POLICY(P) ((P).policy)
 #define MODE(P) ((P).mode)
 #define NOC_WITH_LSPD 1
 #define PACKETS(P) ((P).packet_mode)
+#define L1WB(P) ((P).l1_write_back)
 #endif
 
 // ---------------------------------------------------------------- constants
@@ -85,6 +87,7 @@ struct Params {
   int core_q, svc_q, mem_q, fwd_cap;
   int packet_mode, rob_entries;  // Table 1 packets; reorder-buffer entries per tile
   int dir_central, dir_tile;     // directory entries at each line's home, or all at dir_tile
+  int l1_write_back;             // 0: write-through L1; 1: write-back L1
   uint32_t write_q16, priv_q16, shared_q16, hot_q16;
   int hot_side, hot_x0, hot_y0;
   uint32_t priv_lines, shared_lines, remote_lines, total_lines;
@@ -523,25 +526,6 @@ __device__ __forceinline__ size_t l2_base(const Params& P, uint32_t r, uint32_t 
   return ((size_t)r * P.l2_sets + set) * L2WAYS(P);
 }
 
-// fill the L1 with `line` (insert if absent, else touch); L1 victims are clean
-template <int W1>
-static __device__ void l1_fill(const Params& P, Tile& T, uint32_t line, uint32_t owner) {
-  uint32_t set = l1_set(P, line);
-  size_t base = l1_base(P, T.r, set);
-  uint32_t w[W1];
-  load_set(P.l1 + base, L1WAYS(P), w);
-  uint32_t fword;
-  int way = set_find(w, L1WAYS(P), line, fword);
-  if (way >= 0) {
-    set_touch(w, L1WAYS(P), way, fword);
-  } else {
-    uint32_t old, prev;
-    way = set_choose(w, L1WAYS(P), old, prev);
-    set_replace(w, L1WAYS(P), way, prev, W_VALID | line);
-  }
-  store_set(P.l1 + base, L1WAYS(P), w);
-  P.l1own[base + way] = (uint16_t)owner;
-}
 
 __device__ __forceinline__ uint16_t* hist_ptr(const Params& P, size_t way_index) {
   return P.l2hist + way_index * (size_t)P.hist_stride;
@@ -606,6 +590,45 @@ static __device__ void local_wt(const Params& P, Tile& T, uint32_t line) {
   }
 }
 
+// a write of `line` reaching the L2 that holds it: the owner recorded with the
+// L1 copy (this tile's own slice, another tile through a WT message, or
+// memory when no slice holds it)
+template <int W2>
+__device__ __forceinline__ void write_to_owner(const Params& P, Tile& T, uint32_t line, uint32_t owner,
+                                               uint32_t t) {
+  if (owner == T.r) local_wt<W2>(P, T, line);
+  else if (owner == NO_TILE) SMALL(S_MEMW)++;
+  else send_svc(P, T, mkflit(T_WT, T.r, owner, line, 0, 0), t);
+}
+
+// fill the L1 with `line` (insert if absent, else touch); `owner` is the tile
+// whose L2 supplied it.  Write-through: a write is passed on to the owner
+// after the fill and victims are clean.  Write-back: a write dirties the L1
+// copy, and a dirty victim is written to its owner first.
+template <int W1, int W2>
+static __device__ void l1_fill(const Params& P, Tile& T, uint32_t line, uint32_t owner, uint32_t write,
+                               uint32_t t) {
+  uint32_t set = l1_set(P, line);
+  size_t base = l1_base(P, T.r, set);
+  uint32_t w[W1];
+  load_set(P.l1 + base, L1WAYS(P), w);
+  const uint32_t dirty = (L1WB(P) && write) ? W_DIRTY : 0u;
+  uint32_t fword;
+  int way = set_find(w, L1WAYS(P), line, fword);
+  if (way >= 0) {
+    set_touch(w, L1WAYS(P), way, fword, dirty);
+  } else {
+    uint32_t old, prev;
+    way = set_choose(w, L1WAYS(P), old, prev);
+    if (L1WB(P) && (old & W_VALID) && (old & W_DIRTY))
+      write_to_owner<W2>(P, T, old & W_LINE, P.l1own[base + way], t);
+    set_replace(w, L1WAYS(P), way, prev, W_VALID | line | dirty);
+  }
+  store_set(P.l1 + base, L1WAYS(P), w);
+  P.l1own[base + way] = (uint16_t)owner;
+  if (write && !L1WB(P)) write_to_owner<W2>(P, T, line, owner, t);
+}
+
 // record accessor `who` in the block's history of the last mig_window accessors
 static __device__ void hist_push(const Params& P, size_t way_index, uint32_t who) {
   uint16_t* hp = hist_ptr(P, way_index);
@@ -648,7 +671,7 @@ static __device__ bool l1_step(const Params& P, Tile& T, uint32_t t, uint32_t li
   uint32_t fword;
   int way = set_find(w, L1WAYS(P), line, fword);
   if (way >= 0) {
-    if (write) {
+    if (write && !L1WB(P)) {
       uint32_t owner = P.l1own[base + way];
       if (owner == T.r) {
         local_wt<W2>(P, T, line);
@@ -662,7 +685,8 @@ static __device__ bool l1_step(const Params& P, Tile& T, uint32_t t, uint32_t li
         send_core(P, T, mkflit(T_WT, T.r, owner, line, 0, 0));
       }
     }
-    set_touch(w, L1WAYS(P), way, fword);
+    // write-back: the write dirties the L1 copy, nothing leaves the tile
+    set_touch(w, L1WAYS(P), way, fword, (write && L1WB(P)) ? W_DIRTY : 0u);
     store_set(P.l1 + base, L1WAYS(P), w);
     SMALL(S_L1H)++;
     T.fsm = FSM_IDLE;
@@ -695,8 +719,7 @@ static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* s
         SMALL(S_L2H)++;
         set_touch(w, L2WAYS(P), way, fword);
         store_set(P.l2 + base, L2WAYS(P), w);
-        l1_fill<W1>(P, T, line, T.r);
-        if (write) local_wt<W2>(P, T, line);
+        l1_fill<W1, W2>(P, T, line, T.r, write, t);
         l2lat_sample(T, t, start, sh_hist);
         T.fsm = FSM_IDLE;
         return;
@@ -738,8 +761,7 @@ static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* s
     set_touch(w, L2WAYS(P), way, fword);
     store_set(P.l2 + base, L2WAYS(P), w);
     if (POLICY(P) == POL_MIGRATE) hist_push(P, base + way, T.r);
-    l1_fill<W1>(P, T, line, T.r);
-    if (write) local_wt<W2>(P, T, line);
+    l1_fill<W1, W2>(P, T, line, T.r, write, t);
     l2lat_sample(T, t, start, sh_hist);
     T.fsm = FSM_IDLE;
     return;
@@ -875,11 +897,9 @@ static __device__ bool phase1(const Params& P, Tile& T, uint32_t t, bool drainin
   if ((T.om_kind == OM_MEM_L2 || T.om_kind == OM_MEM_L1) && T.om_timer <= t) {
     if (T.om_kind == OM_MEM_L2) {
       l2_install<W2>(P, T, T.om_line, T.om_epoch, t);
-      l1_fill<W1>(P, T, T.om_line, T.r);
-      if (T.om_write) local_wt<W2>(P, T, T.om_line);
+      l1_fill<W1, W2>(P, T, T.om_line, T.r, T.om_write, t);
     } else {
-      l1_fill<W1>(P, T, T.om_line, NO_TILE);
-      if (T.om_write) SMALL(S_MEMW)++;
+      l1_fill<W1, W2>(P, T, T.om_line, NO_TILE, T.om_write, t);
     }
     l2lat_sample(T, t, T.om_start, sh_hist);
     set_om(T, OM_NONE, 0, 0, 0);
@@ -1288,8 +1308,7 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
         set_error(P, t, ERR_PROTOCOL);
         break;
       }
-      l1_fill<W1>(P, T, line, fsrc(f));
-      if (T.om_write) send_svc(P, T, mkflit(T_WT, T.r, fsrc(f), line, 0, 0), t);
+      l1_fill<W1, W2>(P, T, line, fsrc(f), T.om_write, t);
       l2lat_sample(T, t, T.om_start, sh_hist);
       set_om(T, OM_NONE, 0, 0, 0);
       break;

@@ -68,6 +68,7 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
   if (c->dir_central < 0 || c->dir_central > 1 ||
       (c->dir_central && (c->dir_tile < 0 || (long)c->dir_tile >= (long)mesh_w * mesh_h)))
     return NOC_ERR_ARG;
+  if (c->l1_write_back < 0 || c->l1_write_back > 1) return NOC_ERR_ARG;
   // trace mode needs per-core reference lists, which live outside the array
   if (tr->mode < 0 || tr->mode > 1 || tr->period < 0 || tr->write_q16 > 65536 ||
       tr->priv_q16 + (uint64_t)tr->shared_q16 > 65536 || tr->hot_q16 > 65536 ||
@@ -101,6 +102,7 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
   P.rob_entries = c->packet_mode ? c->rob_entries : 0;
   P.dir_central = c->dir_central;
   P.dir_tile = c->dir_central ? c->dir_tile : 0;
+  P.l1_write_back = c->l1_write_back;
   P.write_q16 = tr->write_q16;
   P.priv_q16 = tr->priv_q16;
   P.shared_q16 = tr->shared_q16;

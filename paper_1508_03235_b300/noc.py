@@ -27,7 +27,7 @@ class CacheCfg(C.Structure):
     _fields_ = [(n, C.c_int32) for n in (
         "l1_sets", "l1_ways", "l2_sets", "l2_ways", "l1_miss_cycles", "mem_latency",
         "mig_window", "mig_threshold", "core_q", "svc_q", "mem_q", "fwd_entries",
-        "packet_mode", "rob_entries", "dir_central", "dir_tile")]
+        "packet_mode", "rob_entries", "dir_central", "dir_tile", "l1_write_back")]
 
 
 class Traffic(C.Structure):
