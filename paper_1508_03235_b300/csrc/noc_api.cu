@@ -977,10 +977,10 @@ int noc_batch_set_collect_hash(noc_batch* b, int enable) {
 // run one kernel-variant group of a batch: memory waves over the pool, one
 // work-queue launch per wave, results read back per instance
 static int run_batch_group(noc_batch* b, const std::vector<int>& members, int threads, int w1, int w2,
-                           bool il, int* first_err) {
+                           int kind, int* first_err) {
   const int side = b->rect;
   int cap = 0;
-  CU(max_coresident_batch(w1, w2, il, threads, &cap), "occupancy");
+  CU(max_coresident_batch(w1, w2, kind, threads, &cap), "occupancy");
   // largest first, so the tail of each wave holds the small instances
   std::vector<int> order = members;
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
@@ -1070,7 +1070,7 @@ static int run_batch_group(noc_batch* b, const std::vector<int>& members, int th
     B.n_items = ni;
     B.gang_ns = 300ll * 1000000000ll;
     if (ni) {
-      CU(launch_batch(B, std::min(cap, ni), threads, w1, w2, il, st), "batch kernel launch");
+      CU(launch_batch(B, std::min(cap, ni), threads, w1, w2, kind, st), "batch kernel launch");
       b->launches++;
     }
     CU(cudaStreamSynchronize(st), "batch wave");
@@ -1125,24 +1125,27 @@ int noc_batch_run(noc_batch* b) {
   const int side = b->rect;
   const int threads = ((side * side + 31) / 32) * 32;
   // kernel-variant groups: the instances the specialised kernel of way class
-  // 0, 1, 2 serves (interleaved L2, cache mode, exact ways), then the rest on
-  // the general kernel with the largest way bounds among them
-  std::vector<int> group[4];
+  // 0, 1, 2 serves (interleaved L2, cache mode, exact ways), those without the
+  // packet, write-back and directory-node options on the base kernel, then the
+  // rest on the general kernel; the last two with the largest way bounds among
+  // their instances
+  std::vector<int> group[5];
   for (int i = 0; i < n; ++i) {
     const Params& P = b->sims[i]->P;
-    group[batch_specialised(P) ? batch_way_class(P.l1_ways, P.l2_ways) : 3].push_back(i);
+    const int kind = variant_kind(P);
+    group[kind == KIND_IL ? batch_way_class(P.l1_ways, P.l2_ways) : kind == KIND_BASE ? 3 : 4].push_back(i);
   }
   b->waves = 0;
   int first_err = NOC_OK;
-  for (int g = 0; g < 4; ++g) {
+  for (int g = 0; g < 5; ++g) {
     if (group[g].empty()) continue;
-    const bool il = g < 3;
+    const int kind = g < 3 ? KIND_IL : g == 3 ? KIND_BASE : KIND_GEN;
     int w1 = 1, w2 = 1;
     for (int i : group[g]) {
       w1 = std::max(w1, b->sims[i]->P.l1_ways);
       w2 = std::max(w2, b->sims[i]->P.l2_ways);
     }
-    int rc = run_batch_group(b, group[g], threads, w1, w2, il, &first_err);
+    int rc = run_batch_group(b, group[g], threads, w1, w2, kind, &first_err);
     if (rc) return rc;
   }
   b->done = true;

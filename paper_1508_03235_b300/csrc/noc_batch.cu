@@ -1,6 +1,7 @@
 // noc_batch.cu -- the batch engine's persistent work-queue kernel (compiled once
-// per L1/L2 way bound, and once more per bound specialised like the plain
-// cycle loop: -DNOC_FIXED_POLICY=0 -DNOC_FIXED_MODE=0 -DNOC_EXACT_WAYS=1)
+// per L1/L2 way bound, and twice more per bound specialised like the plain
+// cycle loop: -DNOC_BASE=1, and -DNOC_FIXED_POLICY=0 -DNOC_FIXED_MODE=0
+// -DNOC_EXACT_WAYS=1)
 #include "noc_kernel.cuh"
 
 #if !defined(NOC_W1) || !defined(NOC_W2)
@@ -9,6 +10,9 @@
 #if defined(NOC_FIXED_POLICY)
 #define NOC_POLV NOC_FIXED_POLICY
 #define NOC_SPEC il
+#elif defined(NOC_BASE)
+#define NOC_POLV (-2)
+#define NOC_SPEC base
 #else
 #define NOC_POLV (-1)
 #define NOC_SPEC gen

@@ -36,13 +36,16 @@ struct BatchArgs {
   int n_items;
   long long gang_ns;        // limit of the wait for an instance's rectangles
 };
-// il: the variant specialised to the interleaved L2 in cache mode with exactly
-// the way counts of the class of (l1_ways, l2_ways); batch_specialised(P)
-// says whether an instance may run on it
-cudaError_t launch_batch(const BatchArgs& B, int grid, int threads, int l1_ways, int l2_ways, bool il,
+// kind: which specialisation of the device code runs -- KIND_IL (interleaved
+// L2 in cache mode with exactly the way counts of the class of (l1_ways,
+// l2_ways)), KIND_BASE (every policy and mode, none of the packet, write-back
+// or directory-node options) or KIND_GEN (everything); variant_kind(P) is the
+// narrowest one a configuration may run on
+enum { KIND_GEN = 0, KIND_BASE = 1, KIND_IL = 2 };
+int variant_kind(const Params& P);
+cudaError_t launch_batch(const BatchArgs& B, int grid, int threads, int l1_ways, int l2_ways, int kind,
                          cudaStream_t s);
-cudaError_t max_coresident_batch(int l1_ways, int l2_ways, bool il, int threads, int* out);
-bool batch_specialised(const Params& P);
+cudaError_t max_coresident_batch(int l1_ways, int l2_ways, int kind, int threads, int* out);
 int batch_way_class(int l1_ways, int l2_ways);
 
 // geometry of the launch for a gx x gy rectangle grid

@@ -7,9 +7,11 @@ namespace noc {
 // ---------------------------------------------------------------- dispatch
 // Kernel variants shipped: per-cycle hash / drain records on or off, and the
 // compile-time way bounds (L1, L2) of the cache-set code: (4, 8), (4, 16) and
-// the general (16, 16); the plain loop also comes specialised to the
-// interleaved L2 in cache mode with the class's exact way counts (the other
-// policies' code compiled out, the way loops of fixed length).
+// the general (16, 16).  The plain loop also comes as "base" (every policy and
+// mode, the packet, write-back and directory-node options compiled out) and as
+// "il", specialised to the interleaved L2 in cache mode with the class's exact
+// way counts (the other policies' code compiled out, the way loops of fixed
+// length).
 #define NOC_DECL_RUN(h, d, w1, w2, sp) \
   cudaError_t launch_run_##h##_##d##_##w1##_##w2##_##sp(const Params&, const RunArgs&, cudaStream_t);
 #define NOC_DECL_WAYS(w1, w2)                                                   \
@@ -18,12 +20,16 @@ namespace noc {
   NOC_DECL_RUN(0, 1, w1, w2, gen)                                               \
   NOC_DECL_RUN(1, 1, w1, w2, gen)                                               \
   NOC_DECL_RUN(0, 0, w1, w2, il)                                                \
+  NOC_DECL_RUN(0, 0, w1, w2, base)                                              \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_gen(int threads, int* out);  \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_il(int threads, int* out);   \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_base(int threads, int* out); \
   cudaError_t launch_batch_##w1##_##w2##_gen(const BatchArgs&, int, int, cudaStream_t); \
   cudaError_t launch_batch_##w1##_##w2##_il(const BatchArgs&, int, int, cudaStream_t);  \
+  cudaError_t launch_batch_##w1##_##w2##_base(const BatchArgs&, int, int, cudaStream_t); \
   cudaError_t max_coresident_batch_##w1##_##w2##_gen(int threads, int* out);             \
-  cudaError_t max_coresident_batch_##w1##_##w2##_il(int threads, int* out);
+  cudaError_t max_coresident_batch_##w1##_##w2##_il(int threads, int* out);              \
+  cudaError_t max_coresident_batch_##w1##_##w2##_base(int threads, int* out);
 NOC_DECL_WAYS(4, 8)
 NOC_DECL_WAYS(4, 16)
 NOC_DECL_WAYS(16, 16)
@@ -41,6 +47,12 @@ static bool interleaved_cache(const Params& P) {
   return P.policy == POL_INTERLEAVED && P.mode == MODE_CACHE && !P.packet_mode &&
          !P.l1_write_back && P.l1_ways == exact[c][0] && P.l2_ways == exact[c][1];
 }
+// the plain-loop variant a configuration runs on
+int variant_kind(const Params& P) {
+  if (interleaved_cache(P)) return KIND_IL;
+  if (!P.packet_mode && !P.l1_write_back && !P.dir_central) return KIND_BASE;
+  return KIND_GEN;
+}
 
 #define NOC_PICK_RUN(h, d, sp)                                    \
   switch (way_class(P.l1_ways, P.l2_ways)) {                      \
@@ -53,36 +65,45 @@ cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
   if (A.hash_trace && A.busy) { NOC_PICK_RUN(1, 1, gen) }
   if (A.hash_trace) { NOC_PICK_RUN(1, 0, gen) }
   if (A.busy) { NOC_PICK_RUN(0, 1, gen) }
-  if (interleaved_cache(P)) { NOC_PICK_RUN(0, 0, il) }
-  NOC_PICK_RUN(0, 0, gen)
+  switch (variant_kind(P)) {
+    case KIND_IL: NOC_PICK_RUN(0, 0, il)
+    case KIND_BASE: NOC_PICK_RUN(0, 0, base)
+    default: NOC_PICK_RUN(0, 0, gen)
+  }
 }
+
+#define NOC_PICK_KIND(fn, kind, w1, w2, ...)                                    \
+  switch (kind) {                                                                \
+    case KIND_IL: return fn##_##w1##_##w2##_il(__VA_ARGS__);                     \
+    case KIND_BASE: return fn##_##w1##_##w2##_base(__VA_ARGS__);                 \
+    default: return fn##_##w1##_##w2##_gen(__VA_ARGS__);                        \
+  }
 
 cudaError_t max_coresident_ctas(const Params& P, int threads, int* out) {
-  const bool il = interleaved_cache(P);
+  const int kind = variant_kind(P);
   switch (way_class(P.l1_ways, P.l2_ways)) {
-    case 0: return il ? max_coresident_run_0_0_4_8_il(threads, out) : max_coresident_run_0_0_4_8_gen(threads, out);
-    case 1: return il ? max_coresident_run_0_0_4_16_il(threads, out) : max_coresident_run_0_0_4_16_gen(threads, out);
-    default: return il ? max_coresident_run_0_0_16_16_il(threads, out) : max_coresident_run_0_0_16_16_gen(threads, out);
+    case 0: NOC_PICK_KIND(max_coresident_run_0_0, kind, 4, 8, threads, out)
+    case 1: NOC_PICK_KIND(max_coresident_run_0_0, kind, 4, 16, threads, out)
+    default: NOC_PICK_KIND(max_coresident_run_0_0, kind, 16, 16, threads, out)
   }
 }
 
-bool batch_specialised(const Params& P) { return interleaved_cache(P); }
 int batch_way_class(int l1_ways, int l2_ways) { return way_class(l1_ways, l2_ways); }
 
-cudaError_t launch_batch(const BatchArgs& B, int grid, int threads, int l1_ways, int l2_ways, bool il,
+cudaError_t launch_batch(const BatchArgs& B, int grid, int threads, int l1_ways, int l2_ways, int kind,
                          cudaStream_t s) {
   switch (way_class(l1_ways, l2_ways)) {
-    case 0: return il ? launch_batch_4_8_il(B, grid, threads, s) : launch_batch_4_8_gen(B, grid, threads, s);
-    case 1: return il ? launch_batch_4_16_il(B, grid, threads, s) : launch_batch_4_16_gen(B, grid, threads, s);
-    default: return il ? launch_batch_16_16_il(B, grid, threads, s) : launch_batch_16_16_gen(B, grid, threads, s);
+    case 0: NOC_PICK_KIND(launch_batch, kind, 4, 8, B, grid, threads, s)
+    case 1: NOC_PICK_KIND(launch_batch, kind, 4, 16, B, grid, threads, s)
+    default: NOC_PICK_KIND(launch_batch, kind, 16, 16, B, grid, threads, s)
   }
 }
 
-cudaError_t max_coresident_batch(int l1_ways, int l2_ways, bool il, int threads, int* out) {
+cudaError_t max_coresident_batch(int l1_ways, int l2_ways, int kind, int threads, int* out) {
   switch (way_class(l1_ways, l2_ways)) {
-    case 0: return il ? max_coresident_batch_4_8_il(threads, out) : max_coresident_batch_4_8_gen(threads, out);
-    case 1: return il ? max_coresident_batch_4_16_il(threads, out) : max_coresident_batch_4_16_gen(threads, out);
-    default: return il ? max_coresident_batch_16_16_il(threads, out) : max_coresident_batch_16_16_gen(threads, out);
+    case 0: NOC_PICK_KIND(max_coresident_batch, kind, 4, 8, threads, out)
+    case 1: NOC_PICK_KIND(max_coresident_batch, kind, 4, 16, threads, out)
+    default: NOC_PICK_KIND(max_coresident_batch, kind, 16, 16, threads, out)
   }
 }
 

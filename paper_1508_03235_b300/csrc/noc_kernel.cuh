@@ -503,9 +503,11 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
     if (sh_hist[k]) atomicAdd(&P.hist[k], (unsigned long long)sh_hist[k]);
 }
 
-// POLV names the device code's specialisation (-1: every policy and mode; p:
-// the L2 policy p in cache mode only), so the instantiations of translation
-// units built with different NOC_FIXED_POLICY are distinct kernels.
+// POLV names the device code's specialisation (-1: every policy, mode and
+// option; -2: every policy and mode without the packet, write-back and
+// directory-node options; p: the L2 policy p in cache mode only), so the
+// instantiations of translation units built with different specialisation
+// flags are distinct kernels.
 template <bool HASH, bool DRAIN, int W1, int W2, int POLV>
 __global__ void __launch_bounds__(MAX_THREADS, 1)
     run_kernel(const __grid_constant__ Params P, const __grid_constant__ RunArgs A) {

@@ -14,8 +14,11 @@ namespace noc {
 // A translation unit compiled with -DNOC_FIXED_POLICY=<p> -DNOC_FIXED_MODE=<m>
 // builds the device code for that L2 policy and traffic mode alone (the other
 // paths are compiled out); otherwise both are read from the parameters.
-// With -DNOC_EXACT_WAYS the cache-set code takes the way counts to be exactly
-// the translation unit's compile-time bounds NOC_W1 and NOC_W2.
+// With -DNOC_BASE every policy and mode stays, but the options beyond the
+// paper's workloads (multi-flit packets, L1 write-back, the centralized
+// directory node) are compiled out.  With -DNOC_EXACT_WAYS the cache-set code
+// takes the way counts to be exactly the translation unit's compile-time
+// bounds NOC_W1 and NOC_W2.
 #if defined(NOC_EXACT_WAYS)
 #define L1WAYS(P) (NOC_W1)
 #define L2WAYS(P) (NOC_W2)
@@ -27,14 +30,25 @@ namespace noc {
 #define POLICY(P) (NOC_FIXED_POLICY)
 #define MODE(P) (NOC_FIXED_MODE)
 #define NOC_WITH_LSPD (NOC_FIXED_POLICY != 0)
-#define PACKETS(P) 0
-#define L1WB(P) 0
+#define NOC_EXTENSIONS 0
 #else
 #define POLICY(P) ((P).policy)
 #define MODE(P) ((P).mode)
 #define NOC_WITH_LSPD 1
+#if defined(NOC_BASE)
+#define NOC_EXTENSIONS 0
+#else
+#define NOC_EXTENSIONS 1
+#endif
+#endif
+#if NOC_EXTENSIONS
 #define PACKETS(P) ((P).packet_mode)
 #define L1WB(P) ((P).l1_write_back)
+#define DIRC(P) ((P).dir_central)
+#else
+#define PACKETS(P) 0
+#define L1WB(P) 0
+#define DIRC(P) 0
 #endif
 
 // ---------------------------------------------------------------- constants
@@ -292,7 +306,7 @@ __device__ __forceinline__ uint32_t home_of(const Params& P, uint32_t line) {
 // the tile holding a line's directory entry (LSPD): its home, or the one
 // directory node of the centralized variant
 __device__ __forceinline__ uint32_t dir_home(const Params& P, uint32_t line) {
-  return P.dir_central ? (uint32_t)P.dir_tile : home_of(P, line);
+  return DIRC(P) ? (uint32_t)P.dir_tile : home_of(P, line);
 }
 __device__ __forceinline__ uint32_t l1_set(const Params& P, uint32_t line) {
   return line - qdiv(line, P.mL1) * (uint32_t)P.l1_sets;

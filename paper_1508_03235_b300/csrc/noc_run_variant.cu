@@ -1,7 +1,8 @@
 // noc_run_variant.cu -- one variant of the cycle kernel per compilation: the
 // build compiles this file once for each (per-cycle hash record, drain record,
-// L1 way bound, L2 way bound) combination it ships, and the plain loop once
-// more per way bound specialised to the interleaved L2 in cache mode with
+// L1 way bound, L2 way bound) combination it ships, and the plain loop twice
+// more per way bound: without the options beyond the paper's workloads
+// (-DNOC_BASE=1), and specialised to the interleaved L2 in cache mode with
 // exactly those way counts (-DNOC_FIXED_POLICY=0 -DNOC_FIXED_MODE=0
 // -DNOC_EXACT_WAYS=1).
 #include "noc_kernel.cuh"
@@ -12,6 +13,9 @@
 #if defined(NOC_FIXED_POLICY)
 #define NOC_POLV NOC_FIXED_POLICY
 #define NOC_SPEC il
+#elif defined(NOC_BASE)
+#define NOC_POLV (-2)
+#define NOC_SPEC base
 #else
 #define NOC_POLV (-1)
 #define NOC_SPEC gen
