@@ -41,6 +41,7 @@ enum { PN = 0, PS = 1, PE = 2, PW = 3 };
 
 typedef struct {
   uint32_t type, src, dst, inject, line, a, e;
+  uint32_t age; /* deflections so far (age_mode 1; always 0 under age_mode 0) */
 } Flit;
 
 typedef struct {
@@ -268,6 +269,7 @@ static Flit make_flit(uint32_t type, uint32_t src, uint32_t dst, uint32_t line, 
   f.line = line;
   f.a = a;
   f.e = e;
+  f.age = 0;
   return f;
 }
 static int q_full(const FlitQ* q) { return q->len >= q->cap; }
@@ -699,8 +701,12 @@ static void phase1(orc_sim* s, int r, uint32_t t) {
 /* ------------------------------------------------------------------------ */
 /* Phase 2 (Sec. 4.3, Sec. 7.1 "Work in phase two"): one bufferless router   */
 
-/* priority: older (smaller inject cycle) first, then smaller source tile */
-static int older(const Flit* a, const Flit* b) {
+/* priority (Sec. 4.2, 4.3).  age_mode 0: older (smaller inject cycle) first,
+ * then smaller source tile.  age_mode 1: the age the paper's flit carries --
+ * its count of deflections (Sec. 4.2, 6.2.1, 7.1) -- highest first, ties by
+ * the same (inject cycle, source tile) order. */
+static int older(const orc_sim* s, const Flit* a, const Flit* b) {
+  if (s->p.age_mode && a->age != b->age) return a->age > b->age;
   if (a->inject != b->inject) return a->inject < b->inject;
   return a->src < b->src;
 }
@@ -723,7 +729,7 @@ static void phase2(orc_sim* s, int r, uint32_t t) {
   /* eject: the highest-priority arrival addressed to this tile */
   int ej = -1;
   for (int i = 0; i < n; i++)
-    if (arr[i].dst == (uint32_t)r && (ej < 0 || older(&arr[i], &arr[ej]))) ej = i;
+    if (arr[i].dst == (uint32_t)r && (ej < 0 || older(s, &arr[i], &arr[ej]))) ej = i;
   T->ejected.type = T_NONE;
   if (ej >= 0) {
     T->ejected = arr[ej];
@@ -735,7 +741,7 @@ static void phase2(orc_sim* s, int r, uint32_t t) {
   for (int i = 1; i < n; i++) {
     Flit k = arr[i];
     int j = i - 1;
-    while (j >= 0 && older(&k, &arr[j])) {
+    while (j >= 0 && older(s, &k, &arr[j])) {
       arr[j + 1] = arr[j];
       j--;
     }
@@ -750,6 +756,7 @@ static void phase2(orc_sim* s, int r, uint32_t t) {
       Flit f = q_pop(q);
       f.inject = t;
       f.src = (uint32_t)r;
+      f.age = 0; /* a new flit has age zero (Sec. 7.1) */
       arr[n++] = f;
       T->st[ORC_ST_INJECTED]++;
     }
@@ -774,7 +781,13 @@ static void phase2(orc_sim* s, int r, uint32_t t) {
     /* a free existing port always remains: arrivals + injected <= degree */
     taken[port] = 1;
     out[port] = arr[i];
-    if (port != xp && port != yp) T->st[ORC_ST_DEFLECTIONS]++;
+    if (port != xp && port != yp) {
+      T->st[ORC_ST_DEFLECTIONS]++;
+      if (s->p.age_mode) { /* a deflection ages the flit (Sec. 4.2) */
+        if (out[port].age == ORC_AGE_MAX) set_error(s, ORC_ERR_RANGE);
+        else out[port].age++;
+      }
+    }
   }
 }
 
@@ -1029,7 +1042,7 @@ static void flit_words(const Flit* f, uint64_t w[3]) {
   w[0] = (uint64_t)f->type | ((uint64_t)f->src << 16) | ((uint64_t)f->dst << 32) |
          ((uint64_t)f->a << 48);
   w[1] = (uint64_t)f->line | ((uint64_t)f->inject << 32);
-  w[2] = (uint64_t)f->e;
+  w[2] = (uint64_t)f->e | ((uint64_t)f->age << 32);
 }
 
 static uint64_t tile_hash(const orc_sim* s, int r) {
@@ -1189,6 +1202,7 @@ static int check_params(const orc_params* p) {
   if (p->packet_mode && (p->rob_entries < 1 || p->rob_entries > 64 || p->svc_q < 16)) return 0;
   if (p->dir_central < 0 || p->dir_central > 1) return 0;
   if (p->l1_write_back < 0 || p->l1_write_back > 1) return 0;
+  if (p->age_mode < 0 || p->age_mode > 1) return 0;
   if (p->dir_central && (p->dir_tile < 0 || p->dir_tile >= p->mesh_w * p->mesh_h)) return 0;
   return 1;
 }
@@ -1284,6 +1298,7 @@ static void one_cycle(orc_sim* s) {
 int orc_step(orc_sim* s, int64_t n, uint64_t* trace) {
   if (!s || n < 0) return ORC_ERR_ARG;
   if (s->err) return s->err;
+  if (s->p.age_mode && (int64_t)s->cycle + n > ORC_AGE_CYCLES) return ORC_ERR_ARG;
   for (int64_t i = 0; i < n; i++) {
     one_cycle(s);
     if (trace) trace[i] = orc_dyn_hash(s);
@@ -1312,6 +1327,7 @@ static int quiescent(const orc_sim* s) {
 int orc_drain(orc_sim* s, int64_t max_cycles, int64_t* taken) {
   if (!s || max_cycles < 0) return ORC_ERR_ARG;
   if (s->err) return s->err;
+  if (s->p.age_mode && (int64_t)s->cycle + max_cycles > ORC_AGE_CYCLES) return ORC_ERR_ARG;
   s->draining = 1;
   int64_t i = 0;
   while (!quiescent(s) && i < max_cycles) {
@@ -1371,7 +1387,7 @@ int orc_set_trace(orc_sim* s, int core, int64_t n, const uint32_t* refs) {
   return ORC_OK;
 }
 
-static Flit flit_from7(const uint32_t* w) {
+static Flit flit_from8(const uint32_t* w) {
   Flit f;
   f.type = w[0];
   f.src = w[1];
@@ -1380,12 +1396,14 @@ static Flit flit_from7(const uint32_t* w) {
   f.line = w[4];
   f.a = w[5];
   f.e = w[6];
+  f.age = w[7];
   return f;
 }
 
-int orc_debug_enqueue(orc_sim* s, int tile, int queue, const uint32_t* flit7) {
-  if (!s || !flit7 || tile < 0 || tile >= s->N || queue < 0 || queue > 1) return ORC_ERR_ARG;
-  Flit f = flit_from7(flit7);
+int orc_debug_enqueue(orc_sim* s, int tile, int queue, const uint32_t* flit8) {
+  if (!s || !flit8 || tile < 0 || tile >= s->N || queue < 0 || queue > 1) return ORC_ERR_ARG;
+  Flit f = flit_from8(flit8);
+  f.age = 0;
   if (f.type == T_NONE || f.type > T_PROBE || f.dst >= (uint32_t)s->N || f.dst == (uint32_t)tile)
     return ORC_ERR_ARG;
   f.src = (uint32_t)tile;
@@ -1395,12 +1413,13 @@ int orc_debug_enqueue(orc_sim* s, int tile, int queue, const uint32_t* flit7) {
   return ORC_OK;
 }
 
-int orc_debug_link(orc_sim* s, int tile, int dir, const uint32_t* flit7) {
-  if (!s || !flit7 || tile < 0 || tile >= s->N || dir < 0 || dir > 3) return ORC_ERR_ARG;
+int orc_debug_link(orc_sim* s, int tile, int dir, const uint32_t* flit8) {
+  if (!s || !flit8 || tile < 0 || tile >= s->N || dir < 0 || dir > 3) return ORC_ERR_ARG;
   int nb = neighbour(s, tile, dir);
   if (nb < 0) return ORC_ERR_ARG;
-  Flit f = flit_from7(flit7);
+  Flit f = flit_from8(flit8);
   if (f.type == T_NONE || f.type > T_PROBE || f.dst >= (uint32_t)s->N) return ORC_ERR_ARG;
+  if (f.age && !s->p.age_mode) return ORC_ERR_ARG;
   /* counted as injected so that conservation holds */
   s->tiles[f.src < (uint32_t)s->N ? f.src : (uint32_t)nb].st[ORC_ST_INJECTED]++;
   s->out_prev[(size_t)nb * 4 + opposite(dir)] = f;
@@ -1411,7 +1430,7 @@ int orc_get_links(const orc_sim* s, uint32_t* out) {
   if (!s || !out) return ORC_ERR_ARG;
   for (int i = 0; i < s->N * 4; i++) {
     const Flit* f = &s->out_prev[i];
-    uint32_t* o = &out[(size_t)i * 7];
+    uint32_t* o = &out[(size_t)i * 8];
     o[0] = f->type;
     o[1] = f->type ? f->src : 0;
     o[2] = f->type ? f->dst : 0;
@@ -1419,6 +1438,7 @@ int orc_get_links(const orc_sim* s, uint32_t* out) {
     o[4] = f->type ? f->line : 0;
     o[5] = f->type ? f->a : 0;
     o[6] = f->type ? f->e : 0;
+    o[7] = f->type ? f->age : 0;
   }
   return ORC_OK;
 }

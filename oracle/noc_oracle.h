@@ -30,6 +30,12 @@ extern "C" {
 #define ORC_ERR_CUDA 5
 #define ORC_ERR_PROTOCOL 6
 #define ORC_ERR_STATE 7
+#define ORC_ERR_RANGE 8 /* age_mode 1: a flit deflected with age ORC_AGE_MAX */
+
+/* age_mode 1 limits: a flit's age counts at most ORC_AGE_MAX deflections, and
+ * a run (steps and drains) ends at or before cycle ORC_AGE_CYCLES */
+#define ORC_AGE_MAX 4095u
+#define ORC_AGE_CYCLES (1ll << 20)
 
 /* L2 placement policies (Sec. 3) */
 #define ORC_L2_INTERLEAVED 0   /* home = line mod N holds the only L2 copy      */
@@ -62,6 +68,9 @@ typedef struct {
   /* L1 write policy: 0 = write-through (Sec. 3.1, 3.2); 1 = write-back, a dirty
    * victim written back to the L2 that supplied it (Sec. 3.4, 7.1) */
   int32_t l1_write_back;
+  /* router priority: 0 = oldest first (inject cycle, then source tile);
+   * 1 = most deflections first (the paper's age field), then the same order */
+  int32_t age_mode;
 } orc_params;
 
 /* statistic indices (order fixed by the written model) */
@@ -97,13 +106,14 @@ uint64_t orc_state_hash(const orc_sim* s);
 /* trace mode: per-core reference lists, ref = line | write << 31 */
 int orc_set_trace(orc_sim* s, int core, int64_t n, const uint32_t* refs);
 
-/* flits as 7 words: type, src, dst, inject_cycle, line, a, e */
+/* flits as 8 words: type, src, dst, inject_cycle, line, a, e, age (the
+ * deflection count of age_mode 1; an enqueued flit's age is ignored) */
 int orc_debug_enqueue(orc_sim* s, int tile, int queue /*0 core, 1 service*/,
-                      const uint32_t* flit7);
+                      const uint32_t* flit8);
 /* place a flit so that it arrives at `tile` from direction dir (0 N,1 S,2 E,3 W)
- * in the next cycle */
-int orc_debug_link(orc_sim* s, int tile, int dir, const uint32_t* flit7);
-/* out-links written in the last cycle: N*4 flits of 7 words */
+ * in the next cycle; a non-zero age needs age_mode 1 */
+int orc_debug_link(orc_sim* s, int tile, int dir, const uint32_t* flit8);
+/* out-links written in the last cycle: N*4 flits of 8 words */
 int orc_get_links(const orc_sim* s, uint32_t* out);
 /* cache contents of one tile: per (set, way) 4 words: valid, line, aux, rank;
  * aux = owner for L1, dirty | epoch << 16 for L2 */

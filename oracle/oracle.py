@@ -41,7 +41,8 @@ class _Params(C.Structure):
         (n, C.c_uint32) for n in ("priv_lines", "shared_lines", "remote_lines")] + [
         ("seed", C.c_uint64), ("stream", C.c_uint32),
         ("packet_mode", C.c_int32), ("rob_entries", C.c_int32),
-        ("dir_central", C.c_int32), ("dir_tile", C.c_int32), ("l1_write_back", C.c_int32)]
+        ("dir_central", C.c_int32), ("dir_tile", C.c_int32), ("l1_write_back", C.c_int32),
+        ("age_mode", C.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -203,7 +204,7 @@ class OracleSim:
         if isinstance(f, dict):
             f = [FLIT_TYPES[f["type"]] if isinstance(f["type"], str) else f["type"],
                  f.get("src", 0), f["dst"], f.get("inject", 0), f.get("line", 0),
-                 f.get("a", 0), f.get("e", 0)]
+                 f.get("a", 0), f.get("e", 0), f.get("age", 0)]
         return np.ascontiguousarray(f, dtype=np.uint32)
 
     def debug_enqueue(self, tile: int, queue: int, flit):
@@ -219,9 +220,9 @@ class OracleSim:
             raise ValueError(f"orc_debug_link status {rc}")
 
     def links(self) -> np.ndarray:
-        out = np.zeros(self.N * 4 * 7, dtype=np.uint32)
+        out = np.zeros(self.N * 4 * 8, dtype=np.uint32)
         lib().orc_get_links(self._h, _p32(out))
-        return out.reshape(self.N, 4, 7)
+        return out.reshape(self.N, 4, 8)
 
     def cache(self, tile: int, which: int) -> np.ndarray:
         p = self.params

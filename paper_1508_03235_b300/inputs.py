@@ -64,6 +64,7 @@ def cache_cfg(l1_kb=32, l1_ways=4, l2_kb=256, l2_ways=8, **over):
         dir_central=0,
         dir_tile=0,
         l1_write_back=0,
+        age_mode=0,
     )
     cfg.update(over)
     return cfg

@@ -654,3 +654,162 @@ def test_l1_write_back_timeline(oracle_mod):
     wt.set_trace(0, refs)
     wt.step(2 * 200 + 50)
     assert wt.stats()["wt_sent"] == 1                  # write-through: at the write
+
+
+# --------------------------------------------------------------------------
+# age_mode 1: the paper's age field, a count of deflections (Sec. 4.2, 6.2.1,
+# 7.1) -- most deflections first, ties by inject cycle, then source tile
+def one_router_model(arrivals, queued, here, W, H, t, age_mode):
+    """An independent model of one router's cycle (Sec. 4.3): arrivals is a
+    list of (input port, flit dict); returns (ejected flit, {out port: flit},
+    deflections).  Written from the rules, not from either simulator."""
+    x, y = here % W, here // W
+    exists = [y > 0, y < H - 1, x < W - 1, x > 0]           # N, S, E, W
+    def key(f):
+        return ((-f["age"] if age_mode else 0), f["inject"], f["src"])
+    flits = [dict(f) for _, f in arrivals]
+    mine = [f for f in flits if f["dst"] == here]
+    ej = min(mine, key=key) if mine else None
+    rest = sorted((f for f in flits if f is not ej), key=key)
+    if len(arrivals) < sum(exists) and queued is not None:
+        rest.append(dict(queued, inject=t, src=here, age=0))
+    out, defl = {}, 0
+    for f in rest:
+        dx, dy = f["dst"] % W - x, f["dst"] // W - y
+        xp = E_ if dx > 0 else (W_ if dx < 0 else None)
+        yp = S_ if dy > 0 else (N_ if dy < 0 else None)
+        port = next(p for p in (xp, yp, N_, S_, E_, W_)
+                    if p is not None and exists[p] and p not in out)
+        if port not in (xp, yp):
+            defl += 1
+            if age_mode:
+                f["age"] += 1
+        out[port] = f
+    return ej, out, defl
+
+
+@pytest.mark.parametrize("age_mode", [0, 1])
+@pytest.mark.parametrize("here", [4, 1, 0])
+def test_one_router_brute_force(oracle_mod, age_mode, here):
+    W = H = 3
+    rng = np.random.default_rng(100 + 10 * here + age_mode)
+    x, y = here % W, here // W
+    ports = [p for p, ok in zip((N_, S_, E_, W_), (y > 0, y < H - 1, x < W - 1, x > 0)) if ok]
+    for trial in range(120):
+        s = oracle_mod.OracleSim(quiet_params(W, H, age_mode=age_mode))
+        s.step(10)
+        k = int(rng.integers(0, len(ports) + 1))
+        used = rng.choice(ports, size=k, replace=False)
+        srcs = rng.choice([r for r in range(9) if r != here], size=k, replace=False)
+        arrivals = []
+        for p, src in zip(used, srcs):
+            f = dict(type="PROBE", src=int(src), dst=int(rng.integers(0, 9)),
+                     inject=int(rng.integers(0, 4)), age=int(rng.integers(0, 3)) if age_mode else 0)
+            s.debug_link(here, int(p), f)
+            arrivals.append((int(p), f))
+        queued = None
+        if rng.random() < 0.6:
+            queued = dict(type="PROBE", dst=int(rng.choice([r for r in range(9) if r != here])))
+            s.debug_enqueue(here, 0, queued)
+        ej, out, defl = one_router_model(arrivals, queued, here, W, H, 10, age_mode)
+        s.step(1)
+        st = s.stats()
+        assert st["deflections"] == defl, trial
+        assert st["ejected"] == (1 if ej else 0), trial
+        if ej:
+            assert st["lat_sum"] == 10 - ej["inject"], trial
+        lk = s.links()[here]
+        for p in range(4):
+            if p in out:
+                f = out[p]
+                assert (lk[p, 1], lk[p, 2], lk[p, 3], lk[p, 7]) == \
+                    (f["src"], f["dst"], f["inject"], f["age"]), (trial, p)
+            else:
+                assert lk[p, 0] == 0, (trial, p)
+
+
+def test_deflection_age_conflict(oracle_mod):
+    """The conflict of test_two_flit_conflict under age_mode 1: the younger
+    flit B has been deflected twice, so it takes port E and the older A is
+    deflected north and ages by one; with equal ages the older one wins."""
+    s = oracle_mod.OracleSim(quiet_params(3, 3, age_mode=1))
+    s.step(10)
+    s.debug_link(4, W_, dict(type="PROBE", src=3, dst=5, inject=5, age=0))
+    s.debug_link(4, N_, dict(type="PROBE", src=1, dst=5, inject=7, age=2))
+    s.step(1)
+    lk = s.links()
+    assert lk[4, E_][1] == 1 and lk[4, E_][7] == 2
+    assert lk[4, N_][1] == 3 and lk[4, N_][7] == 1
+    s.step(5)
+    st = s.stats()
+    # B: one hop (cycle 11); A: N, then E, then S (cycle 13)
+    assert st["ejected"] == 2 and st["lat_sum"] == (11 - 7) + (13 - 5)
+    t = oracle_mod.OracleSim(quiet_params(3, 3, age_mode=1))
+    t.step(10)
+    t.debug_link(4, W_, dict(type="PROBE", src=3, dst=5, inject=5, age=1))
+    t.debug_link(4, N_, dict(type="PROBE", src=1, dst=5, inject=7, age=1))
+    t.step(1)
+    lk = t.links()
+    assert lk[4, E_][1] == 3 and lk[4, N_][1] == 1 and lk[4, N_][7] == 2
+    # age_mode 0 ignores the age field: a planted age is refused there
+    u = oracle_mod.OracleSim(quiet_params(3, 3))
+    with pytest.raises(ValueError):
+        u.debug_link(4, W_, dict(type="PROBE", src=3, dst=5, inject=5, age=1))
+
+
+def test_deflection_age_top_flit_never_deflected(oracle_mod):
+    """Under load with age_mode 1 the flit of highest priority in the whole
+    network (most deflections, then oldest, then lowest source) is never
+    deflected: it ejects or moves one hop closer every cycle; flits do age."""
+    W = H = 6
+    p = net_params(W, H, period=2)
+    p["age_mode"] = 1
+    s = oracle_mod.OracleSim(p)
+    nbr = {N_: -W, S_: W, E_: 1, W_: -1}
+    top_age = 0
+    for _ in range(400):
+        lk = s.links()
+        valid = np.argwhere(lk[:, :, 0] != 0)
+        st = s.stats()
+        assert len(valid) == st["injected"] - st["ejected"]
+        if not len(valid):
+            s.step(1)
+            continue
+        keys = [(-int(lk[t, p, 7]), int(lk[t, p, 3]), int(lk[t, p, 1]), t, p) for t, p in valid]
+        nage, inj, src, t, p = min(keys)
+        top_age = max(top_age, -nage)
+        at, dst = t + nbr[p], int(lk[t, p, 2])
+        s.step(1)
+        lk2 = s.links()
+        hit = [(t2, p2) for t2, p2 in np.argwhere(lk2[:, :, 0] != 0)
+               if int(lk2[t2, p2, 3]) == inj and int(lk2[t2, p2, 1]) == src]
+        if at == dst:
+            assert not hit
+            continue
+        assert len(hit) == 1
+        t2, p2 = hit[0]
+        assert int(lk2[t2, p2, 7]) == -nage                          # not aged
+        d0 = abs(at % W - dst % W) + abs(at // W - dst // W)
+        nxt = t2 + nbr[p2]
+        assert abs(nxt % W - dst % W) + abs(nxt // W - dst // W) == d0 - 1
+    assert top_age >= 2 and s.stats()["deflections"] > 0
+
+
+def test_deflection_age_limits(oracle_mod):
+    """age_mode 1 counts at most 4095 deflections per flit (one more is error
+    8 in that cycle) and runs at most 2^20 cycles (a longer step or drain is
+    refused as an argument error before it runs)."""
+    s = oracle_mod.OracleSim(quiet_params(3, 3, age_mode=1))
+    s.step(10)
+    s.debug_link(4, W_, dict(type="PROBE", src=3, dst=5, inject=5, age=4095))
+    s.debug_link(4, N_, dict(type="PROBE", src=1, dst=5, inject=7, age=4095))
+    assert s.step(1, check=False) == 8
+    assert s.error() == (8, 10)
+    t = oracle_mod.OracleSim(quiet_params(3, 3, age_mode=1))
+    assert t.step((1 << 20) + 1, check=False) == 1 and t.cycle == 0
+    with pytest.raises(Exception):
+        t.drain((1 << 20) + 1)
+    t.step(1000)
+    assert t.step((1 << 20) - 999, check=False) == 1 and t.cycle == 1000
+    u = oracle_mod.OracleSim(quiet_params(3, 3))                   # age_mode 0: no limit
+    assert u.step((1 << 20) + 1, check=False) == 0
