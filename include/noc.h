@@ -41,6 +41,7 @@ extern "C" {
 #define NOC_ERR_CUDA 5           /* a CUDA runtime call failed                   */
 #define NOC_ERR_PROTOCOL 6       /* a reply arrived that matches no request      */
 #define NOC_ERR_STATE 7          /* call not valid in the handle's current state */
+#define NOC_ERR_RANGE 8          /* age_mode 1: a flit deflected with age 4095   */
 
 /* L2 placement (Sec. 3): interleaved homes; LSPD with local placement and a
  * home-tile directory (Sec. 3.2, Sec. 6.2.2); LSPD plus migration and
@@ -86,6 +87,14 @@ typedef struct {
    * dirties the L1 copy; a dirty victim is written to that L2, or to memory
    * if none holds it, when it is evicted). */
   int32_t l1_write_back;
+  /* Router priority (Sec. 4.2, 4.3).  0: oldest first -- smaller inject
+   * cycle, then smaller source tile.  1: the paper's age field, a flit's
+   * count of deflections (Sec. 6.2.1, 7.1): more deflections first, ties by
+   * the age_mode 0 order; a new flit has age 0.  Under age_mode 1 a flit
+   * counts at most 4095 deflections (one more ends the step with
+   * NOC_ERR_RANGE) and a run ends at or before cycle 2^20 (a step, drain or
+   * batch that would pass it is NOC_ERR_ARG). */
+  int32_t age_mode;
 } noc_cache_cfg;
 
 /* Reference stream.  Fractions are q16 fixed point (65536 = 1).  Reference k
@@ -181,12 +190,14 @@ int noc_get_tiling(const noc_sim* sim, int* gx, int* gy);
 int noc_set_trace(noc_sim* sim, int core, int64_t n, const uint32_t* refs);
 
 /* Test and inspection entry points (synchronous, between steps).
- * Flits are 7 host words: type, src, dst, inject_cycle, line, a, e. */
+ * Flits are 8 host words: type, src, dst, inject_cycle, line, a, e, age (the
+ * deflection count of age_mode 1; ignored when enqueued, and a non-zero age
+ * on a link needs age_mode 1 and at most 4095). */
 int noc_debug_enqueue(noc_sim* sim, int tile, int queue /*0 core,1 service*/,
-                      const uint32_t* flit7);
+                      const uint32_t* flit8);
 int noc_debug_link(noc_sim* sim, int tile, int dir /*0 N,1 S,2 E,3 W*/,
-                   const uint32_t* flit7);
-int noc_get_links(noc_sim* sim, uint32_t* out /* N*4*7 */);
+                   const uint32_t* flit8);
+int noc_get_links(noc_sim* sim, uint32_t* out /* N*4*8 */);
 int noc_get_cache(noc_sim* sim, int tile, int which /*1 L1, 2 L2*/,
                   uint32_t* out /* sets*ways*4: valid, line, aux, rank */);
 int noc_dir_get(noc_sim* sim, uint32_t line, uint32_t* out);

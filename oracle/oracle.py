@@ -205,7 +205,9 @@ class OracleSim:
             f = [FLIT_TYPES[f["type"]] if isinstance(f["type"], str) else f["type"],
                  f.get("src", 0), f["dst"], f.get("inject", 0), f.get("line", 0),
                  f.get("a", 0), f.get("e", 0), f.get("age", 0)]
-        return np.ascontiguousarray(f, dtype=np.uint32)
+        a = np.zeros(8, dtype=np.uint32)
+        a[:len(f)] = f          # 7 words (no age) or 8
+        return a
 
     def debug_enqueue(self, tile: int, queue: int, flit):
         a = self._flit(flit)

@@ -362,9 +362,12 @@ int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
   return NOC_OK;
 }
 
-uint4 pack_flit(const uint32_t* f7, uint32_t src) {
-  return make_uint4(f7[3], (src & 0xFFFFu) | (f7[2] << 16), (f7[4] & W_LINE) | (f7[0] << 26),
-                    (f7[5] & 0xFFFFu) | (f7[6] << 16));
+// a host flit of 8 words (type, src, dst, inject, line, a, e, age) in the
+// device layout; under age_mode 1 the age goes above the inject cycle
+uint4 pack_flit(const Params& P, const uint32_t* f8, uint32_t src) {
+  const uint32_t x = P.age_mode ? (f8[3] & (AGE_ONE - 1u)) | (f8[7] << AGE_SHIFT) : f8[3];
+  return make_uint4(x, (src & 0xFFFFu) | (f8[2] << 16), (f8[4] & W_LINE) | (f8[0] << 26),
+                    (f8[5] & 0xFFFFu) | (f8[6] << 16));
 }
 
 }  // namespace
@@ -399,6 +402,7 @@ int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, co
       (c->dir_central && (c->dir_tile < 0 || (long)c->dir_tile >= (long)mesh_w * mesh_h)))
     return fail(NOC_ERR_ARG, "directory node: dir_central 0/1, dir_tile a tile of the mesh");
   if (c->l1_write_back < 0 || c->l1_write_back > 1) return fail(NOC_ERR_ARG, "l1_write_back 0/1");
+  if (c->age_mode < 0 || c->age_mode > 1) return fail(NOC_ERR_ARG, "age_mode 0/1");
   if (tr->mode < 0 || tr->mode > 2 || tr->period < 0) return fail(NOC_ERR_ARG, "traffic mode/period");
   if (tr->write_q16 > 65536 || tr->priv_q16 + (uint64_t)tr->shared_q16 > 65536 || tr->hot_q16 > 65536)
     return fail(NOC_ERR_ARG, "q16 fractions out of range");
@@ -444,6 +448,7 @@ int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, co
   P.dir_central = c->dir_central;
   P.dir_tile = c->dir_central ? c->dir_tile : 0;
   P.l1_write_back = c->l1_write_back;
+  P.age_mode = c->age_mode;
   P.write_q16 = tr->write_q16;
   P.priv_q16 = tr->priv_q16;
   P.shared_q16 = tr->shared_q16;
@@ -505,6 +510,8 @@ int noc_step(noc_sim* s, int64_t n) {
   if (rc) return rc;
   if (n == 0) return NOC_OK;
   if ((uint64_t)s->cycle + (uint64_t)n >= (1ull << 32) - 2) return fail(NOC_ERR_ARG, "cycle count above 2^32");
+  if (s->P.age_mode && (uint64_t)s->cycle + (uint64_t)n > (1ull << AGE_SHIFT))
+    return fail(NOC_ERR_ARG, "age_mode 1 runs end at or before cycle 2^20");
   if (s->hash_on) {
     if ((size_t)n > s->hash_cap) {
       if (s->d_hash) cudaFree(s->d_hash);
@@ -533,6 +540,8 @@ int noc_drain(noc_sim* s, int64_t max_cycles, int64_t* taken) {
   if (rc) return rc;
   rc = noc_sync(s, nullptr);
   if (rc) return rc;
+  if (s->P.age_mode && (uint64_t)s->cycle + (uint64_t)max_cycles > (1ull << AGE_SHIFT))
+    return fail(NOC_ERR_ARG, "age_mode 1 runs end at or before cycle 2^20");
   s->draining = true;
   unsigned int busy0 = 0;
   unsigned int* d_b0 = reinterpret_cast<unsigned int*>(scratch_ptr(s));
@@ -695,9 +704,9 @@ int noc_set_trace(noc_sim* s, int core, int64_t n, const uint32_t* refs) {
   return NOC_OK;
 }
 
-int noc_debug_enqueue(noc_sim* s, int tile, int queue, const uint32_t* f7) {
-  if (!s || !f7 || tile < 0 || tile >= s->P.N || queue < 0 || queue > 1) return fail(NOC_ERR_ARG, "bad argument");
-  if (f7[0] == 0 || f7[0] > T_PROBE || f7[2] >= (uint32_t)s->P.N || f7[2] == (uint32_t)tile)
+int noc_debug_enqueue(noc_sim* s, int tile, int queue, const uint32_t* f8) {
+  if (!s || !f8 || tile < 0 || tile >= s->P.N || queue < 0 || queue > 1) return fail(NOC_ERR_ARG, "bad argument");
+  if (f8[0] == 0 || f8[0] > T_PROBE || f8[2] >= (uint32_t)s->P.N || f8[2] == (uint32_t)tile)
     return fail(NOC_ERR_ARG, "bad flit");
   int rc = ensure_memory(s);
   if (rc) return rc;
@@ -708,7 +717,7 @@ int noc_debug_enqueue(noc_sim* s, int tile, int queue, const uint32_t* f7) {
   CU(cudaMemcpy(&q, fld, 4, cudaMemcpyDeviceToHost), "queue read");
   const uint32_t cap = queue == 0 ? s->P.core_q : s->P.svc_q, head = q & 0xFFFFu, len = q >> 16;
   if (len >= cap) return fail(NOC_ERR_QUEUE_OVERFLOW, "queue full");
-  uint4 f = pack_flit(f7, (uint32_t)tile);
+  uint4 f = pack_flit(s->P, f8, (uint32_t)tile);
   f.x = 0;
   uint4* buf = (queue == 0 ? s->P.cq : s->P.sq) + (size_t)tile * cap + (head + len) % cap;
   CU(cudaMemcpy(buf, &f, sizeof f, cudaMemcpyHostToDevice), "queue write");
@@ -717,8 +726,8 @@ int noc_debug_enqueue(noc_sim* s, int tile, int queue, const uint32_t* f7) {
   return NOC_OK;
 }
 
-int noc_debug_link(noc_sim* s, int tile, int dir, const uint32_t* f7) {
-  if (!s || !f7 || tile < 0 || tile >= s->P.N || dir < 0 || dir > 3) return fail(NOC_ERR_ARG, "bad argument");
+int noc_debug_link(noc_sim* s, int tile, int dir, const uint32_t* f8) {
+  if (!s || !f8 || tile < 0 || tile >= s->P.N || dir < 0 || dir > 3) return fail(NOC_ERR_ARG, "bad argument");
   const int W = s->P.W, H = s->P.H, x = tile % W, y = tile / W;
   int nb = -1;
   if (dir == P_N && y > 0) nb = tile - W;
@@ -726,17 +735,19 @@ int noc_debug_link(noc_sim* s, int tile, int dir, const uint32_t* f7) {
   if (dir == P_E && x < W - 1) nb = tile + 1;
   if (dir == P_W && x > 0) nb = tile - 1;
   if (nb < 0) return fail(NOC_ERR_ARG, "no neighbour in that direction");
-  if (f7[0] == 0 || f7[0] > T_PROBE || f7[2] >= (uint32_t)s->P.N) return fail(NOC_ERR_ARG, "bad flit");
+  if (f8[0] == 0 || f8[0] > T_PROBE || f8[2] >= (uint32_t)s->P.N) return fail(NOC_ERR_ARG, "bad flit");
+  if (f8[7] && (!s->P.age_mode || f8[7] > AGE_MAX || f8[3] >= AGE_ONE))
+    return fail(NOC_ERR_ARG, "a flit's age needs age_mode 1, at most 4095, and an inject cycle below 2^20");
   int rc = ensure_memory(s);
   if (rc) return rc;
   CU(cudaStreamSynchronize(s->stream), "sync");
   const size_t N = (size_t)s->P.N;
   const uint32_t par = (s->cycle - 1u) & 1u;
-  uint4 f = pack_flit(f7, f7[1]);
+  uint4 f = pack_flit(s->P, f8, f8[1]);
   CU(cudaMemcpy(s->P.glink + ((size_t)par * 4 + (dir ^ 1)) * N + nb, &f, sizeof f, cudaMemcpyHostToDevice),
      "link write");
   // counted as injected at its source so that conservation holds
-  const uint32_t src = f7[1] < N ? f7[1] : (uint32_t)nb;
+  const uint32_t src = f8[1] < N ? f8[1] : (uint32_t)nb;
   unsigned long long v;
   CU(cudaMemcpy(&v, s->P.stats + S_INJ * N + src, 8, cudaMemcpyDeviceToHost), "counter read");
   v++;
@@ -757,15 +768,16 @@ int noc_get_links(noc_sim* s, uint32_t* out) {
   for (size_t r = 0; r < N; ++r)
     for (int d = 0; d < 4; ++d) {
       uint4 f = h[d * N + r];
-      uint32_t* o = out + (r * 4 + d) * 7;
+      uint32_t* o = out + (r * 4 + d) * 8;
       uint32_t ty = f.z >> 26;
       o[0] = ty;
       o[1] = ty ? (f.y & 0xFFFFu) : 0;
       o[2] = ty ? (f.y >> 16) : 0;
-      o[3] = ty ? f.x : 0;
+      o[3] = ty ? (s->P.age_mode ? f.x & (AGE_ONE - 1u) : f.x) : 0;
       o[4] = ty ? (f.z & W_LINE) : 0;
       o[5] = ty ? (f.w & 0xFFFFu) : 0;
       o[6] = ty ? (f.w >> 16) : 0;
+      o[7] = ty && s->P.age_mode ? f.x >> AGE_SHIFT : 0;
     }
   return NOC_OK;
 }
@@ -1126,7 +1138,7 @@ int noc_batch_run(noc_batch* b) {
   const int threads = ((side * side + 31) / 32) * 32;
   // kernel-variant groups: the instances the specialised kernel of way class
   // 0, 1, 2 serves (interleaved L2, cache mode, exact ways), those without the
-  // packet, write-back and directory-node options on the base kernel, then the
+  // packet, write-back, directory-node and age options on the base kernel, then the
   // rest on the general kernel; the last two with the largest way bounds among
   // their instances
   std::vector<int> group[5];

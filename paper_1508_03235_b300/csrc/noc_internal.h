@@ -38,8 +38,8 @@ struct BatchArgs {
 };
 // kind: which specialisation of the device code runs -- KIND_IL (interleaved
 // L2 in cache mode with exactly the way counts of the class of (l1_ways,
-// l2_ways)), KIND_BASE (every policy and mode, none of the packet, write-back
-// or directory-node options) or KIND_GEN (everything); variant_kind(P) is the
+// l2_ways)), KIND_BASE (every policy and mode, none of the packet, write-back,
+// directory-node or age options) or KIND_GEN (everything); variant_kind(P) is the
 // narrowest one a configuration may run on
 enum { KIND_GEN = 0, KIND_BASE = 1, KIND_IL = 2 };
 int variant_kind(const Params& P);

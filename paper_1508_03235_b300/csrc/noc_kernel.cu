@@ -8,7 +8,7 @@ namespace noc {
 // Kernel variants shipped: per-cycle hash / drain records on or off, and the
 // compile-time way bounds (L1, L2) of the cache-set code: (4, 8), (4, 16) and
 // the general (16, 16).  The plain loop also comes as "base" (every policy and
-// mode, the packet, write-back and directory-node options compiled out) and as
+// mode, the packet, write-back, directory-node and age options compiled out) and as
 // "il", specialised to the interleaved L2 in cache mode with the class's exact
 // way counts (the other policies' code compiled out, the way loops of fixed
 // length).
@@ -45,12 +45,12 @@ static bool interleaved_cache(const Params& P) {
   static const int exact[3][2] = {{4, 8}, {4, 16}, {16, 16}};
   const int c = way_class(P.l1_ways, P.l2_ways);
   return P.policy == POL_INTERLEAVED && P.mode == MODE_CACHE && !P.packet_mode &&
-         !P.l1_write_back && P.l1_ways == exact[c][0] && P.l2_ways == exact[c][1];
+         !P.l1_write_back && !P.age_mode && P.l1_ways == exact[c][0] && P.l2_ways == exact[c][1];
 }
 // the plain-loop variant a configuration runs on
 int variant_kind(const Params& P) {
   if (interleaved_cache(P)) return KIND_IL;
-  if (!P.packet_mode && !P.l1_write_back && !P.dir_central) return KIND_BASE;
+  if (!P.packet_mode && !P.l1_write_back && !P.dir_central && !P.age_mode) return KIND_BASE;
   return KIND_GEN;
 }
 
@@ -174,21 +174,21 @@ __global__ void dyn_hash_kernel(const Params P, uint32_t cycle, unsigned long lo
     uint4 o[4];
 #pragma unroll
     for (int d = 0; d < 4; ++d) o[d] = P.glink[((size_t)par * 4 + d) * N + r];
-    acc += tile_hash(T, o) + rob_hash(P, r);
+    acc += tile_hash(P, T, o) + rob_hash(P, r);
   }
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) atomicAdd(out, acc);
 }
 
-__device__ __forceinline__ void flit_words(uint4 f, unsigned long long& w0, unsigned long long& w1,
-                                           unsigned long long& w2) {
+__device__ __forceinline__ void flit_words(const Params& P, uint4 f, unsigned long long& w0,
+                                           unsigned long long& w1, unsigned long long& w2) {
   uint32_t ty = ftype(f);
   w0 = w1 = w2 = 0;
   if (!ty) return;
   w0 = (unsigned long long)ty | ((unsigned long long)fsrc(f) << 16) |
        ((unsigned long long)fdst(f) << 32) | ((unsigned long long)fa(f) << 48);
-  w1 = (unsigned long long)fline(f) | ((unsigned long long)f.x << 32);
-  w2 = fe(f);
+  w1 = (unsigned long long)fline(f) | ((unsigned long long)finject(P, f) << 32);
+  w2 = (unsigned long long)fe(f) | ((unsigned long long)fage(P, f) << 32);
 }
 
 // full-state terms other than the dynamic hash: fold(0x18, cycle) plus one fold
@@ -255,7 +255,7 @@ __global__ void state_terms_kernel(const Params P, uint32_t cycle, unsigned long
       uint32_t pos = (uint32_t)((slot + cap - head) % cap);
       if (pos >= len) continue;
       unsigned long long w0, w1, w2;
-      flit_words(buf[k], w0, w1, w2);
+      flit_words(P, buf[k], w0, w1, w2);
       unsigned long long h = hstart(0x13 + qi);
       h = hfold(h, r);
       h = hfold(h, pos);

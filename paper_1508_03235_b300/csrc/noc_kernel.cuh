@@ -294,7 +294,7 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
       for (int d = 0; d < 4; ++d) out[d] = sl[(pout * 4 + d) * nt + i];
     }
     if (HASH) {
-      unsigned long long h = active ? tile_hash(T, out) + rob_hash(P, r) : 0ull;
+      unsigned long long h = active ? tile_hash(P, T, out) + rob_hash(P, r) : 0ull;
       h = block_sum(h, sh_red);
       if (i == 0) atomicAdd(&A.hash_trace[t - t0], h);
     }
@@ -504,8 +504,8 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
 }
 
 // POLV names the device code's specialisation (-1: every policy, mode and
-// option; -2: every policy and mode without the packet, write-back and
-// directory-node options; p: the L2 policy p in cache mode only), so the
+// option; -2: every policy and mode without the packet, write-back,
+// directory-node and age options; p: the L2 policy p in cache mode only), so the
 // instantiations of translation units built with different specialisation
 // flags are distinct kernels.
 template <bool HASH, bool DRAIN, int W1, int W2, int POLV>

@@ -16,7 +16,7 @@ namespace noc {
 // paths are compiled out); otherwise both are read from the parameters.
 // With -DNOC_BASE every policy and mode stays, but the options beyond the
 // paper's workloads (multi-flit packets, L1 write-back, the centralized
-// directory node) are compiled out.  With -DNOC_EXACT_WAYS the cache-set code
+// directory node, the deflection-count age) are compiled out.  With -DNOC_EXACT_WAYS the cache-set code
 // takes the way counts to be exactly the translation unit's compile-time
 // bounds NOC_W1 and NOC_W2.
 #if defined(NOC_EXACT_WAYS)
@@ -45,10 +45,12 @@ namespace noc {
 #define PACKETS(P) ((P).packet_mode)
 #define L1WB(P) ((P).l1_write_back)
 #define DIRC(P) ((P).dir_central)
+#define AGE1(P) ((P).age_mode)
 #else
 #define PACKETS(P) 0
 #define L1WB(P) 0
 #define DIRC(P) 0
+#define AGE1(P) 0
 #endif
 
 // ---------------------------------------------------------------- constants
@@ -61,7 +63,7 @@ enum : uint32_t { OM_NONE = 0, OM_WAIT_DR = 1, OM_WAIT_DATA = 2, OM_MEM_L2 = 3, 
 enum : int { P_N = 0, P_S = 1, P_E = 2, P_W = 3 };
 enum : int { POL_INTERLEAVED = 0, POL_LOCAL = 1, POL_MIGRATE = 2 };
 enum : int { MODE_CACHE = 0, MODE_NETWORK = 1, MODE_TRACE = 2 };
-enum : int { ERR_OVERFLOW = 3, ERR_TIMEOUT = 4, ERR_PROTOCOL = 6 };
+enum : int { ERR_OVERFLOW = 3, ERR_TIMEOUT = 4, ERR_PROTOCOL = 6, ERR_RANGE = 8 };
 
 constexpr uint32_t NO_TILE = 0xFFFFu;
 constexpr uint32_t DIR_NONE = 0xFFFFFFFFu;
@@ -102,6 +104,7 @@ struct Params {
   int packet_mode, rob_entries;  // Table 1 packets; reorder-buffer entries per tile
   int dir_central, dir_tile;     // directory entries at each line's home, or all at dir_tile
   int l1_write_back;             // 0: write-through L1; 1: write-back L1
+  int age_mode;                  // 0: oldest first; 1: most deflections first
   uint32_t write_q16, priv_q16, shared_q16, hot_q16;
   int hot_side, hot_x0, hot_y0;
   uint32_t priv_lines, shared_lines, remote_lines, total_lines;
@@ -165,7 +168,12 @@ inline void set_divisors(Params& P) {
 
 // ---------------------------------------------------------------- flits
 // uint4 flit: x = inject cycle, y = src | dst << 16, z = line | type << 26,
-// w = a | e << 16.  All-zero = empty link.
+// w = a | e << 16.  All-zero = empty link.  Under age_mode 1, x holds the
+// inject cycle in its low AGE_SHIFT bits (runs end before cycle 2^AGE_SHIFT)
+// and the flit's deflection count (its age, at most AGE_MAX) above them.
+constexpr uint32_t AGE_SHIFT = 20;
+constexpr uint32_t AGE_MAX = 4095;
+constexpr uint32_t AGE_ONE = 1u << AGE_SHIFT;
 __device__ __forceinline__ uint4 mkflit(uint32_t type, uint32_t src, uint32_t dst, uint32_t line,
                                         uint32_t a, uint32_t e) {
   return make_uint4(0u, src | (dst << 16), line | (type << 26), a | (e << 16));
@@ -176,9 +184,19 @@ __device__ __forceinline__ uint32_t fsrc(uint4 f) { return f.y & 0xFFFFu; }
 __device__ __forceinline__ uint32_t fdst(uint4 f) { return f.y >> 16; }
 __device__ __forceinline__ uint32_t fa(uint4 f) { return f.w & 0xFFFFu; }
 __device__ __forceinline__ uint32_t fe(uint4 f) { return f.w >> 16; }
-// priority key: older (smaller inject cycle) first, then smaller source
-__device__ __forceinline__ unsigned long long fkey(uint4 f) {
-  return ((unsigned long long)f.x << 16) | (f.y & 0xFFFFu);
+// inject cycle and age of a flit (the age is 0 under age_mode 0)
+__device__ __forceinline__ uint32_t finject(const Params& P, uint4 f) {
+  return AGE1(P) ? f.x & (AGE_ONE - 1u) : f.x;
+}
+__device__ __forceinline__ uint32_t fage(const Params& P, uint4 f) {
+  return AGE1(P) ? f.x >> AGE_SHIFT : 0u;
+}
+// priority key, smaller first: older (smaller inject cycle), then smaller
+// source; under age_mode 1 more deflections before both (the age bits of x
+// inverted, so that a larger age gives a smaller key)
+__device__ __forceinline__ unsigned long long fkey(const Params& P, uint4 f) {
+  const uint32_t flip = AGE1(P) ? (AGE_MAX << AGE_SHIFT) : 0u;
+  return ((unsigned long long)(f.x ^ flip) << 16) | (f.y & 0xFFFFu);
 }
 
 // Tagged link slots (cross-rectangle links of the plain cycle loop).  Every
@@ -238,14 +256,14 @@ __device__ __forceinline__ unsigned long long hstart(unsigned long long w) {
 __device__ __forceinline__ unsigned long long hfold(unsigned long long h, unsigned long long w) {
   return mix64(h ^ w);
 }
-__device__ __forceinline__ unsigned long long hflit(unsigned long long h, uint4 f) {
+__device__ __forceinline__ unsigned long long hflit(const Params& P, unsigned long long h, uint4 f) {
   uint32_t ty = ftype(f);
   unsigned long long w0 = 0, w1 = 0, w2 = 0;
   if (ty) {
     w0 = (unsigned long long)ty | ((unsigned long long)fsrc(f) << 16) |
          ((unsigned long long)fdst(f) << 32) | ((unsigned long long)fa(f) << 48);
-    w1 = (unsigned long long)fline(f) | ((unsigned long long)f.x << 32);
-    w2 = fe(f);
+    w1 = (unsigned long long)fline(f) | ((unsigned long long)finject(P, f) << 32);
+    w2 = (unsigned long long)fe(f) | ((unsigned long long)fage(P, f) << 32);
   }
   h = hfold(h, w0);
   h = hfold(h, w1);
@@ -298,6 +316,13 @@ struct Tile {
 
 __device__ __forceinline__ void set_error(const Params& P, uint32_t t, int code) {
   atomicMin(P.err, ((unsigned long long)t << 8) | (unsigned long long)code);
+}
+// one more deflection of flit f under age_mode 1 (Sec. 4.2: a deflection ages
+// the flit); a flit already at AGE_MAX is left as it is and the cycle's error
+// is raised
+__device__ __forceinline__ void age_deflected(const Params& P, uint4& f, uint32_t t) {
+  if ((f.x >> AGE_SHIFT) == AGE_MAX) set_error(P, t, ERR_RANGE);
+  else f.x += AGE_ONE;
 }
 
 __device__ __forceinline__ uint32_t home_of(const Params& P, uint32_t line) {
@@ -992,7 +1017,7 @@ __device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint
   for (int d = 0; d < 4; ++d) {
     bool v = ftype(in[d]) != T_NONE;
     n_arr += v;
-    k[d] = v ? fkey(in[d]) : NOKEY;
+    k[d] = v ? fkey(P, in[d]) : NOKEY;
   }
   // eject the highest-priority arrival addressed to this tile
   int ej = -1;
@@ -1043,7 +1068,7 @@ __device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint
   uint32_t freem = exists;
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    const uint4 f = i < 4 ? in[i] : inj;
+    uint4 f = i < 4 ? in[i] : inj;
     const bool valid = i < 4 ? (k[i] != NOKEY) : has_inj;
     if (!valid) continue;
     const uint32_t dst = fdst(f);
@@ -1058,6 +1083,7 @@ __device__ __forceinline__ void route(const Params& P, Tile& T, uint32_t t, uint
     else {
       pick = freem & (0u - freem);  // lowest free port: N, S, E, W order
       T.defl++;
+      if (AGE1(P)) age_deflected(P, f, t);
     }
     freem &= ~pick;
     const int p = __ffs(pick) - 1;
@@ -1112,7 +1138,7 @@ __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t 
 #pragma unroll
   for (int d = 0; d < 4; ++d) {
     vm |= (ftype(in[d]) != T_NONE ? 1u : 0u) << d;
-    k[d] = fkey(in[d]);
+    k[d] = fkey(P, in[d]);
   }
   const int n_arr = __popc(vm);
   // eject the highest-priority arrival addressed to this tile
@@ -1185,9 +1211,10 @@ __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t 
   uint32_t pk[4];
 #pragma unroll
   for (int d = 0; d < 4; ++d) pk[d] = (pkp >> (4u * rk[d])) & 15u;
-  uint32_t pki = 0;
+  uint32_t pki = 0, prodi = 0;
   if (has_inj) {
-    pki = pick_port(prod_ports(P, fdst(inj), T.x, T.y), freem, defl);
+    prodi = prod_ports(P, fdst(inj), T.x, T.y);
+    pki = pick_port(prodi, freem, defl);
     freem &= ~pki;
   }
   T.defl += defl;
@@ -1195,9 +1222,21 @@ __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t 
   const uint4 z = make_uint4(0, 0, 0, 0);
 #pragma unroll
   for (int d = 0; d < 4; ++d) so[d * so_stride] = z;
+  if (AGE1(P)) {
+    // age_mode 1: a flit whose port is neither productive one ages by one
 #pragma unroll
-  for (int d = 0; d < 4; ++d)
-    if ((rm >> d) & 1u) so[(__ffs(pk[d]) - 1) * so_stride] = in[d];
+    for (int d = 0; d < 4; ++d)
+      if ((rm >> d) & 1u) {
+        uint4 f = in[d];
+        if (!(pk[d] & (prod[d] | (prod[d] >> 4)))) age_deflected(P, f, t);
+        so[(__ffs(pk[d]) - 1) * so_stride] = f;
+      }
+    if (has_inj && !(pki & (prodi | (prodi >> 4)))) age_deflected(P, inj, t);
+  } else {
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+      if ((rm >> d) & 1u) so[(__ffs(pk[d]) - 1) * so_stride] = in[d];
+  }
   if (has_inj) so[(__ffs(pki) - 1) * so_stride] = inj;
   if (edge) {
     const uint32_t tag = link_tag(t);
@@ -1213,7 +1252,7 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
   uint4 f = T.ej;
   uint32_t ty = ftype(f);
   if (ty == T_NONE) return;
-  uint32_t lat = t - f.x;
+  uint32_t lat = t - finject(P, f);
   T.ejc++;
   T.latsum += lat;
   if (lat > T.latmax) T.latmax = lat;
@@ -1476,10 +1515,10 @@ static __device__ bool rob_empty(const Params& P, uint32_t r) {
 // dynamic hash of one tile after a cycle: fold(r, its four output flits, its
 // core record words C0..C6, injected, ejected, deflections); fields that mean
 // nothing in the current FSM / outstanding-miss state hash as 0
-static __device__ unsigned long long tile_hash(const Tile& T, const uint4 (&out)[4]) {
+static __device__ unsigned long long tile_hash(const Params& P, const Tile& T, const uint4 (&out)[4]) {
   unsigned long long h = hstart(T.r);
 #pragma unroll
-  for (int d = 0; d < 4; ++d) h = hflit(h, out[d]);
+  for (int d = 0; d < 4; ++d) h = hflit(P, h, out[d]);
   bool busy = T.fsm != FSM_IDLE, wait = T.fsm == FSM_L2WAIT, om = T.om_kind != OM_NONE;
   bool mem = T.om_kind == OM_MEM_L2 || T.om_kind == OM_MEM_L1;
   h = hfold(h, T.next_ref);

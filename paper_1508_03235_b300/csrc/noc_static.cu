@@ -69,6 +69,7 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
       (c->dir_central && (c->dir_tile < 0 || (long)c->dir_tile >= (long)mesh_w * mesh_h)))
     return NOC_ERR_ARG;
   if (c->l1_write_back < 0 || c->l1_write_back > 1) return NOC_ERR_ARG;
+  if (c->age_mode < 0 || c->age_mode > 1 || (c->age_mode && n_cycles > (1ll << AGE_SHIFT))) return NOC_ERR_ARG;
   // trace mode needs per-core reference lists, which live outside the array
   if (tr->mode < 0 || tr->mode > 1 || tr->period < 0 || tr->write_q16 > 65536 ||
       tr->priv_q16 + (uint64_t)tr->shared_q16 > 65536 || tr->hot_q16 > 65536 ||
@@ -103,6 +104,7 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
   P.dir_central = c->dir_central;
   P.dir_tile = c->dir_central ? c->dir_tile : 0;
   P.l1_write_back = c->l1_write_back;
+  P.age_mode = c->age_mode;
   P.write_q16 = tr->write_q16;
   P.priv_q16 = tr->priv_q16;
   P.shared_q16 = tr->shared_q16;

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libnoc.so")
 
 NOC_OK = 0
 ERR_NAMES = {1: "NOC_ERR_ARG", 2: "NOC_ERR_OOM", 3: "NOC_ERR_QUEUE_OVERFLOW", 4: "NOC_ERR_TIMEOUT",
-             5: "NOC_ERR_CUDA", 6: "NOC_ERR_PROTOCOL", 7: "NOC_ERR_STATE"}
+             5: "NOC_ERR_CUDA", 6: "NOC_ERR_PROTOCOL", 7: "NOC_ERR_STATE", 8: "NOC_ERR_RANGE"}
 HIST_BINS = 1025
 FLIT_TYPES = dict(NONE=0, REQ=1, DATA=2, WT=3, DA=4, DRPOS=5, DRNEG=6, NACK=7, DINV=8, MIG=9,
                   DIRUPD=10, INV=11, PROBE=12)
@@ -27,7 +27,7 @@ class CacheCfg(C.Structure):
     _fields_ = [(n, C.c_int32) for n in (
         "l1_sets", "l1_ways", "l2_sets", "l2_ways", "l1_miss_cycles", "mem_latency",
         "mig_window", "mig_threshold", "core_q", "svc_q", "mem_q", "fwd_entries",
-        "packet_mode", "rob_entries", "dir_central", "dir_tile", "l1_write_back")]
+        "packet_mode", "rob_entries", "dir_central", "dir_tile", "l1_write_back", "age_mode")]
 
 
 class Traffic(C.Structure):
@@ -268,8 +268,10 @@ class Sim:
         if isinstance(f, dict):
             f = [FLIT_TYPES[f["type"]] if isinstance(f["type"], str) else f["type"],
                  f.get("src", 0), f["dst"], f.get("inject", 0), f.get("line", 0),
-                 f.get("a", 0), f.get("e", 0)]
-        return np.ascontiguousarray(f, dtype=np.uint32)
+                 f.get("a", 0), f.get("e", 0), f.get("age", 0)]
+        a = np.zeros(8, dtype=np.uint32)
+        a[:len(f)] = f          # 7 words (no age) or 8
+        return a
 
     def debug_enqueue(self, tile: int, queue: int, flit):
         a = self._flit(flit)
@@ -280,9 +282,9 @@ class Sim:
         _check(lib().noc_debug_link(self._h, tile, direction, _p32(a)))
 
     def links(self) -> np.ndarray:
-        out = np.zeros(self.N * 4 * 7, dtype=np.uint32)
+        out = np.zeros(self.N * 4 * 8, dtype=np.uint32)
         _check(lib().noc_get_links(self._h, _p32(out)))
-        return out.reshape(self.N, 4, 7)
+        return out.reshape(self.N, 4, 8)
 
     def cache(self, tile: int, which: int) -> np.ndarray:
         p = self.params

@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(libnoc):
 
 def test_struct_layouts_match_header(libnoc):
     from paper_1508_03235_b300 import noc
-    assert C.sizeof(noc.CacheCfg) == 17 * 4
+    assert C.sizeof(noc.CacheCfg) == 18 * 4
     assert C.sizeof(noc.Traffic) == 11 * 4
     assert C.sizeof(noc.Stats) == 30 * 8
     hdr = open(os.path.join(ROOT, "include", "noc.h")).read()
