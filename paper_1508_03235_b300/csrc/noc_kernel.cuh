@@ -420,6 +420,8 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
   uint32_t t = t0;
   for (; t < tend; ++t) {
     const uint32_t pin = (t - 1u) & 1u, pout = t & 1u;
+    // the injection candidate needs only this tile's state: taken before the wait
+    const InjCand ic = active ? inj_candidate(P, T) : InjCand{make_uint4(0, 0, 0, 0), 0u, 0};
     uint4 in[4];
     const uint4 z = make_uint4(0, 0, 0, 0);
 #pragma unroll
@@ -474,7 +476,7 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
       if ((exists & ~boundary) & (1u << P_E)) in[P_E] = sp[P_W * nt + in_e];
       if ((exists & ~boundary) & (1u << P_W)) in[P_W] = sp[P_E * nt + in_w];
       route_ranked(P, T, t, in, exists, sl + pout * 4 * nt + i, nt, P.gtag + pout * pstride + (size_t)r * 2,
-                  2 * N, edge_out);
+                  2 * N, edge_out, ic);
     }
     // ---- publish: this warp has routed cycle t (the warp barrier orders every
     // lane's shared link stores before lane 0's flag store)

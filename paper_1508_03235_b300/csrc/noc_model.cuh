@@ -1125,14 +1125,33 @@ __device__ __forceinline__ uint32_t pick_port(uint32_t prod, uint32_t freem, uin
   return px ? xb : (py ? yb : low);
 }
 
+// The flit a tile would inject this cycle if an input port is free (the
+// service-queue head, else the core-queue head) with its productive ports.
+// It depends on the tile's own state only, so the plain cycle loop takes it
+// before waiting for the neighbours' outputs.
+struct InjCand {
+  uint4 f;
+  uint32_t prod;  // prod_ports() of its destination
+  int q;          // 0: none, 1: service queue, 2: core queue
+};
+__device__ __forceinline__ InjCand inj_candidate(const Params& P, const Tile& T) {
+  InjCand c;
+  c.q = T.sq_len > 0 ? 1 : (T.cq_len > 0 ? 2 : 0);
+  c.f = c.q == 1 ? T.sq_front : T.cq_front;
+  c.prod = c.q ? prod_ports(P, fdst(c.f), T.x, T.y) : 0u;
+  return c;
+}
+
 // The router of Sec. 4.3 as route() computes it, for the plain cycle loop:
 // arrivals are ranked by pairwise key comparisons instead of being sorted, so
-// flits never move between registers; each flit is stored once, to its port's
-// slot, after all four slots were cleared.  Links in `edge` (leaving the CTA
-// rectangle) are then copied from the slots to tagged global slots.
+// flits never move between registers; the ejected flit is the lowest-ranked
+// arrival addressed here, and the others' ranks close up behind it.  Each flit
+// is stored once, to its port's slot, after all four slots were cleared.
+// Links in `edge` (leaving the CTA rectangle) are then copied from the slots
+// to tagged global slots.  `ic` is inj_candidate() of the tile's state.
 __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t t, const uint4 (&in)[4],
                                              uint32_t exists, uint4* so, int so_stride, uint4* go,
-                                             size_t go_stride, uint32_t edge) {
+                                             size_t go_stride, uint32_t edge, const InjCand& ic) {
   uint32_t vm = 0;
   unsigned long long k[4];
 #pragma unroll
@@ -1141,56 +1160,54 @@ __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t 
     k[d] = fkey(P, in[d]);
   }
   const int n_arr = __popc(vm);
-  // eject the highest-priority arrival addressed to this tile
-  int ej = -1;
-  unsigned long long ejk = ~0ull;
-#pragma unroll
-  for (int d = 0; d < 4; ++d)
-    if (((vm >> d) & 1u) && fdst(in[d]) == T.r && k[d] < ejk) {
-      ejk = k[d];
-      ej = d;
-    }
-  T.ej = make_uint4(0, 0, 0, 0);
-#pragma unroll
-  for (int d = 0; d < 4; ++d)
-    if (d == ej) T.ej = in[d];
-  const uint32_t rm = ej >= 0 ? vm & ~(1u << ej) : vm;
-  // rank of each remaining arrival: how many remaining arrivals are older
-  // (keys are unique: a tile injects at most one flit per cycle)
+  // rank of each arrival among the valid ones: how many are older (keys are
+  // unique: a tile injects at most one flit per cycle)
   uint32_t rk[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = a + 1; b < 4; ++b) {
       const bool lt = k[a] < k[b];
-      rk[b] += (((rm >> a) & 1u) && lt) ? 1u : 0u;
-      rk[a] += (((rm >> b) & 1u) && !lt) ? 1u : 0u;
+      rk[b] += (((vm >> a) & 1u) && lt) ? 1u : 0u;
+      rk[a] += (((vm >> b) & 1u) && !lt) ? 1u : 0u;
     }
   uint32_t prod[4];
 #pragma unroll
   for (int d = 0; d < 4; ++d) prod[d] = prod_ports(P, fdst(in[d]), T.x, T.y);
-  // inject when an input port is free: service queue first, then core queue
+  // eject the highest-priority arrival addressed to this tile: bit r of emr
+  // is set when the arrival of rank r is addressed here
+  uint32_t emr = 0;
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+    if (((vm >> d) & 1u) && fdst(in[d]) == T.r) emr |= 1u << rk[d];
+  const uint32_t rej = emr ? (uint32_t)(__ffs(emr) - 1) : 4u;
+  T.ej = make_uint4(0, 0, 0, 0);
+  uint32_t rm = vm;
+#pragma unroll
+  for (int d = 0; d < 4; ++d)
+    if (((vm >> d) & 1u) && rk[d] == rej) {
+      T.ej = in[d];
+      rm &= ~(1u << d);
+    }
+#pragma unroll
+  for (int d = 0; d < 4; ++d) rk[d] -= rk[d] > rej ? 1u : 0u;
+  // inject when an input port is free: the candidate taken off its queue
   uint4 inj = make_uint4(0, 0, 0, 0);
-  bool has_inj = false;
-  if (n_arr < __popc(exists)) {
-    if (T.sq_len > 0) {
-      inj = T.sq_front;
+  const bool has_inj = ic.q != 0 && n_arr < __popc(exists);
+  if (has_inj) {
+    inj = ic.f;
+    if (ic.q == 1) {
       T.sq_head = T.sq_head + 1 == (uint32_t)P.svc_q ? 0 : T.sq_head + 1;
       T.sq_len--;
       if (T.sq_len > 0) T.sq_front = P.sq[(size_t)T.r * P.svc_q + T.sq_head];
-      has_inj = true;
-    } else if (T.cq_len > 0) {
-      inj = T.cq_front;
+    } else {
       T.cq_head = T.cq_head + 1 == (uint32_t)P.core_q ? 0 : T.cq_head + 1;
       T.cq_len--;
       if (T.cq_len > 0) T.cq_front = P.cq[(size_t)T.r * P.core_q + T.cq_head];
-      has_inj = true;
     }
-    if (has_inj) {
-      inj.x = t;
-      inj.y = (inj.y & 0xFFFF0000u) | T.r;
-      T.inj++;
-    }
+    inj.x = t;
+    inj.y = (inj.y & 0xFFFF0000u) | T.r;
+    T.inj++;
   }
   // ports in priority order: arrivals oldest first, then the injected flit.
   // The productive-port bytes are packed in rank order (byte r = the flit of
@@ -1211,10 +1228,9 @@ __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t 
   uint32_t pk[4];
 #pragma unroll
   for (int d = 0; d < 4; ++d) pk[d] = (pkp >> (4u * rk[d])) & 15u;
-  uint32_t pki = 0, prodi = 0;
+  uint32_t pki = 0;
   if (has_inj) {
-    prodi = prod_ports(P, fdst(inj), T.x, T.y);
-    pki = pick_port(prodi, freem, defl);
+    pki = pick_port(ic.prod, freem, defl);
     freem &= ~pki;
   }
   T.defl += defl;
@@ -1231,7 +1247,7 @@ __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t 
         if (!(pk[d] & (prod[d] | (prod[d] >> 4)))) age_deflected(P, f, t);
         so[(__ffs(pk[d]) - 1) * so_stride] = f;
       }
-    if (has_inj && !(pki & (prodi | (prodi >> 4)))) age_deflected(P, inj, t);
+    if (has_inj && !(pki & (ic.prod | (ic.prod >> 4)))) age_deflected(P, inj, t);
   } else {
 #pragma unroll
     for (int d = 0; d < 4; ++d)
