@@ -221,6 +221,9 @@ def run_gpu(args):
     kernel_ms = sum(m for m, _ in kt)
     n_launch = sum(n for _, n in kt)
     stats = [s.stats() for s in sims]          # every step repeats these runs exactly
+    # the period runs' end states: on this mesh every core is held up by its
+    # miss latency, never by its period, so the five runs can coincide
+    end_hashes = [s.state_hash() for s in sims]
     alg_total = args.steps * sum(algorithmic_bytes(st, TILES * cycles, sims[0].params)
                                  for st in stats)
     alg = alg_total / n_launch                 # per launch
@@ -271,6 +274,8 @@ def run_gpu(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": gpu_launches,
             "clocks": clk,
+            "period_runs": {"periods": list(PERIODS), "refs": [st["refs"] for st in stats],
+                            "distinct_end_states": len(set(end_hashes))},
             "batch": batch,
             "surrogate": surrogate,
             "cpu_baseline": cpu,
