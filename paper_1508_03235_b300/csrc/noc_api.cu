@@ -993,12 +993,8 @@ static int run_batch_group(noc_batch* b, const std::vector<int>& members, int th
   const int side = b->rect;
   int cap = 0;
   CU(max_coresident_batch(w1, w2, kind, threads, &cap), "occupancy");
-  // largest first, so the tail of each wave holds the small instances
-  std::vector<int> order = members;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-    return (double)b->sims[a]->P.N * b->cycles[a] > (double)b->sims[c]->P.N * b->cycles[c];
-  });
-  for (int i : order) {
+  std::vector<int> by_size = members;
+  for (int i : by_size) {
     noc_sim* s = b->sims[i];
     int gx = (s->P.W + side - 1) / side, gy = (s->P.H + side - 1) / side;
     if (gx * gy > cap || gx * gy * FLAG_SLOTS > (int)s->n_flags)
@@ -1006,6 +1002,31 @@ static int run_batch_group(noc_batch* b, const std::vector<int>& members, int th
     s->run_gx = gx;
     s->run_gy = gy;
   }
+  // Queue order.  An instance runs once all its rectangles are popped, so the
+  // CTAs are handed out in rounds of `cap`: instances are packed first-fit
+  // decreasing by CTA count (then by work) into rounds that fill the
+  // co-resident CTAs, and the rounds are queued one after another.  Instances
+  // of equal length then start together each round instead of leaving part
+  // of the GPU waiting for a gang that does not fit.
+  auto ctas = [&](int i) { return b->sims[i]->run_gx * b->sims[i]->run_gy; };
+  std::stable_sort(by_size.begin(), by_size.end(), [&](int a, int c) {
+    if (ctas(a) != ctas(c)) return ctas(a) > ctas(c);
+    return (double)b->sims[a]->P.N * b->cycles[a] > (double)b->sims[c]->P.N * b->cycles[c];
+  });
+  std::vector<std::vector<int>> rounds;
+  std::vector<int> room;
+  for (int i : by_size) {
+    size_t k = 0;
+    while (k < rounds.size() && room[k] < ctas(i)) ++k;
+    if (k == rounds.size()) {
+      rounds.emplace_back();
+      room.push_back(cap);
+    }
+    rounds[k].push_back(i);
+    room[k] -= ctas(i);
+  }
+  std::vector<int> order;
+  for (const auto& r : rounds) order.insert(order.end(), r.begin(), r.end());
   size_t pos = 0;
   while (pos < order.size()) {
     // admit instances in order while their state fits the pool
