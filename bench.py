@@ -174,7 +174,8 @@ def run_gpu(args):
     from paper_1508_03235_b300 import tune
     stream = torch.cuda.current_stream()
     # tiling: the autotuner's cached choice for this configuration, if any
-    sims = [noc.Sim(I.mesh_208(P), stream=stream, tiling=tune.cached_tiling(I.mesh_208(P)))
+    sims = [noc.Sim(I.mesh_208(P), stream=stream, tiling=tune.cached_tiling(I.mesh_208(P)),
+                    thread_map=tune.cached_thread_map(I.mesh_208(P)))
             for P in PERIODS]
     tiling = sims[0].tiling()
     cycles = args.cycles
@@ -264,6 +265,7 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic (seeded Philox reference streams; the paper's traces are unavailable)",
             "config": workload_config({"cycles_per_run": cycles, "tiling": list(tiling),
+                                       "thread_map": noc.THREAD_MAPS[sims[0].thread_map()],
                                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -298,7 +300,7 @@ def replica_throughput(ms, units_per_rank, world, device="cpu"):
 
 
 # --------------------------------------------------------------------- batch + surrogate
-def batch_section(n, cycles, rect):
+def batch_section(n, cycles, rect, thread_map=2):
     """The batched-engine half of the metric: n independent design points
     (mixed sizes, loads, mixes and L2 policies) in one persistent launch per
     memory wave, against the same instances run one at a time through the
@@ -310,7 +312,7 @@ def batch_section(n, cycles, rect):
     for p in pts:
         p.pop("design")
     tiles = sum(p["mesh_w"] * p["mesh_h"] for p in pts)
-    b = noc.Batch(pts, cycles, rect=rect, collect_hash=False)
+    b = noc.Batch(pts, cycles, rect=rect, collect_hash=False, thread_map=thread_map)
     b.run()                                   # warm-up (also checks every instance)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -325,7 +327,7 @@ def batch_section(n, cycles, rect):
     torch.cuda.synchronize()
     t1 = 0.0
     for p in pts:
-        s = noc.Sim(p)
+        s = noc.Sim(p, thread_map=thread_map)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s.reset()
@@ -334,7 +336,8 @@ def batch_section(n, cycles, rect):
         t1 += time.perf_counter() - t0
         s.close()
         del s
-    return {"instances": n, "cycles": cycles, "rect": rect, "waves": waves,
+    return {"instances": n, "cycles": cycles, "rect": rect,
+            "thread_map": noc.THREAD_MAPS[thread_map], "waves": waves,
             "batched_sims_per_s": n / tb, "one_at_a_time_sims_per_s": n / t1,
             "speedup": t1 / tb, "batched_router_cycles_per_s": tiles * cycles / tb,
             "one_at_a_time_router_cycles_per_s": tiles * cycles / t1,
@@ -479,7 +482,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-cycles", type=int, default=20_000)
-    ap.add_argument("--batch-rect", type=int, default=19)
+    ap.add_argument("--batch-rect", type=int, default=8)
     ap.add_argument("--oracle-configs", action="store_true",
                     help="time the oracle on the 8x8, 64x64 and batch workloads (host cores) and exit")
     args = ap.parse_args()

@@ -186,6 +186,13 @@ int noc_hash_trace(noc_sim* sim, uint64_t* buf, int64_t n);
 int noc_set_tiling(noc_sim* sim, int gx, int gy);
 int noc_get_tiling(const noc_sim* sim, int* gx, int* gy);
 
+/* Tile-to-thread order inside each CTA rectangle: 0 = perimeter tiles first
+ * (the default), 1 = row-major, 2 = column-major.  Results never depend on
+ * it; the autotuner picks it with the tiling.  noc_get_thread_map returns the
+ * current order, or -1 for a null handle. */
+int noc_set_thread_map(noc_sim* sim, int map);
+int noc_get_thread_map(const noc_sim* sim);
+
 /* Trace mode: reference list of one core (line | write << 31), copied. */
 int noc_set_trace(noc_sim* sim, int core, int64_t n, const uint32_t* refs);
 
@@ -242,6 +249,9 @@ int noc_batch_bind_memory(noc_batch* batch, void* dev_ptr, size_t bytes);
 int noc_batch_set_stream(noc_batch* batch, void* cuda_stream);
 /* CTA rectangle side in tiles (1..19; default 8): a tuning knob only. */
 int noc_batch_set_rect(noc_batch* batch, int side);
+/* Tile-to-thread order of every instance (as noc_set_thread_map; default 0):
+ * a tuning knob only. */
+int noc_batch_set_thread_map(noc_batch* batch, int map);
 /* Collect each instance's full state hash after its wave (default on). */
 int noc_batch_set_collect_hash(noc_batch* batch, int enable);
 /* Run every instance to its cycle count.  Synchronous.  Returns the first

@@ -85,6 +85,7 @@ struct noc_sim {
   // debug knobs
   long long wait_ns = 2000000000ll;
   int silent_cta = -1;
+  int thread_map = 0;     // tile-to-thread order inside a CTA rectangle
   int64_t launches = 0;
   // cycle-kernel timing: event pairs [2k, 2k + 1] around launch k
   bool time_kernels = false;
@@ -332,6 +333,7 @@ int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
     A.abort_flag = abort_ptr(s);
     A.wait_ns = s->wait_ns;
     A.silent_cta = s->silent_cta;
+    A.thread_map = s->thread_map;
     const bool plain = !A.hash_trace && !A.busy;
     if (plain && !s->gtag_clean && s->gtag_end != s->cycle) {
       CU(cudaMemsetAsync(s->P.gtag, 0, 2 * 4 * (size_t)s->P.N * 2 * sizeof(uint4), s->stream),
@@ -673,6 +675,15 @@ int noc_hash_trace(noc_sim* s, uint64_t* buf, int64_t n) {
   return NOC_OK;
 }
 
+int noc_set_thread_map(noc_sim* s, int map) {
+  if (!s) return fail(NOC_ERR_ARG, "null handle");
+  if (map < 0 || map > 2) return fail(NOC_ERR_ARG, "thread map 0 (perimeter first), 1 (rows) or 2 (columns)");
+  s->thread_map = map;
+  return NOC_OK;
+}
+
+int noc_get_thread_map(const noc_sim* s) { return s ? s->thread_map : -1; }
+
 int noc_set_tiling(noc_sim* s, int gx, int gy) {
   if (!s) return fail(NOC_ERR_ARG, "null handle");
   if (gx == 0 && gy == 0) {
@@ -980,6 +991,12 @@ int noc_batch_set_rect(noc_batch* b, int side) {
   return NOC_OK;
 }
 
+int noc_batch_set_thread_map(noc_batch* b, int map) {
+  if (!b || map < 0 || map > 2) return fail(NOC_ERR_ARG, "thread map 0, 1 or 2");
+  for (noc_sim* s : b->sims) s->thread_map = map;
+  return NOC_OK;
+}
+
 int noc_batch_set_collect_hash(noc_batch* b, int enable) {
   if (!b) return fail(NOC_ERR_ARG, "null handle");
   b->collect_hash = enable != 0;
@@ -1061,6 +1078,7 @@ static int run_batch_group(noc_batch* b, const std::vector<int>& members, int th
       A.abort_flag = abort_ptr(s);
       A.wait_ns = s->wait_ns;
       A.silent_cta = -1;
+      A.thread_map = s->thread_map;
       hp.push_back(s->P);
       ha.push_back(A);
       const int G = s->run_gx * s->run_gy;

@@ -21,6 +21,7 @@ struct RunArgs {
   unsigned int* abort_flag;        // set when a wait ran out; all CTAs stop
   long long wait_ns;               // limit of each device-side wait
   int silent_cta;                  // test fault: this CTA never publishes
+  int thread_map;                  // tile-to-thread order inside a rectangle (MAP_*)
 };
 
 // batch work queue: per-instance parameters, and items (instance, rectangle)

@@ -163,23 +163,33 @@ inline int block_threads_impl(int W, int H, int gx, int gy) {
   return ((a + 31) / 32) * 32;
 }
 
-// Thread order inside a rectangle: the perimeter tiles first (row-major), then
-// the interior (row-major).  Only perimeter tiles have links that leave the
-// rectangle, so the first warps alone hold everything the neighbouring CTAs
-// wait for.  Rectangles with a side <= 2 are all perimeter.
+// Tiles on the perimeter of a bw x bh rectangle (only they have links that
+// leave it); rectangles with a side <= 2 are all perimeter.
 __device__ __forceinline__ int perim_count(int bw, int bh) {
   return (bw <= 2 || bh <= 2) ? bw * bh : 2 * bw + 2 * (bh - 2);
 }
-__device__ __forceinline__ int tile_index(int lx, int ly, int bw, int bh) {
-  if (bw <= 2 || bh <= 2) return ly * bw + lx;
+// Tile-to-thread order inside a bw x bh rectangle (thread i runs tile
+// (lx, ly)): perimeter first (the top row, the side columns pairwise, the
+// bottom row, then the interior row by row, so the few warps that touch the
+// links leaving the rectangle are the first ones), row-major, or
+// column-major.  Rectangles two tiles thin or less are row-major in all three.
+enum : int { MAP_PERIMETER = 0, MAP_ROWS = 1, MAP_COLUMNS = 2 };
+__device__ __forceinline__ int tile_index(int lx, int ly, int bw, int bh, int map) {
+  if (map == MAP_COLUMNS && bw > 2 && bh > 2) return lx * bh + ly;
+  if (map == MAP_ROWS || bw <= 2 || bh <= 2) return ly * bw + lx;
   if (ly == 0) return lx;
   if (ly == bh - 1) return bw + 2 * (bh - 2) + lx;
   if (lx == 0) return bw + 2 * (ly - 1);
   if (lx == bw - 1) return bw + 2 * (ly - 1) + 1;
   return perim_count(bw, bh) + (ly - 1) * (bw - 2) + (lx - 1);
 }
-__device__ __forceinline__ void tile_of(int i, int bw, int bh, int& lx, int& ly) {
-  if (bw <= 2 || bh <= 2) {
+__device__ __forceinline__ void tile_of(int i, int bw, int bh, int map, int& lx, int& ly) {
+  if (map == MAP_COLUMNS && bw > 2 && bh > 2) {
+    lx = i / bh;
+    ly = i % bh;
+    return;
+  }
+  if (map == MAP_ROWS || bw <= 2 || bh <= 2) {
     lx = i % bw;
     ly = i / bw;
     return;
@@ -219,14 +229,16 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
   const int i = threadIdx.x;
   const bool active = i < bw * bh;
   int lx = 0, ly = 0;
-  if (active) tile_of(i, bw, bh, lx, ly);
+  if (active) tile_of(i, bw, bh, A.thread_map, lx, ly);
   // shared-memory slots (thread indices) of the in-rectangle neighbours
-  const int in_n = ly > 0 ? tile_index(lx, ly - 1, bw, bh) : 0;
-  const int in_s = ly < bh - 1 ? tile_index(lx, ly + 1, bw, bh) : 0;
-  const int in_e = lx < bw - 1 ? tile_index(lx + 1, ly, bw, bh) : 0;
-  const int in_w = lx > 0 ? tile_index(lx - 1, ly, bw, bh) : 0;
+  const int in_n = ly > 0 ? tile_index(lx, ly - 1, bw, bh, A.thread_map) : 0;
+  const int in_s = ly < bh - 1 ? tile_index(lx, ly + 1, bw, bh, A.thread_map) : 0;
+  const int in_e = lx < bw - 1 ? tile_index(lx + 1, ly, bw, bh, A.thread_map) : 0;
+  const int in_w = lx > 0 ? tile_index(lx - 1, ly, bw, bh, A.thread_map) : 0;
   // the warps that hold the perimeter, which publish the cycle on their own
-  const int edge_threads = ((perim_count(bw, bh) + 31) / 32) * 32;
+  // the warps holding perimeter tiles: the first ones in perimeter-first
+  // order, any of them otherwise
+  const int edge_threads = A.thread_map == MAP_PERIMETER ? ((perim_count(bw, bh) + 31) / 32) * 32 : nt;
   const bool edge_warp = i < edge_threads;
   const uint32_t x = X0 + lx, y = Y0 + ly, r = y * P.W + x;
   const size_t N = (size_t)P.N;
@@ -366,11 +378,11 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
   const int i = threadIdx.x, lane = i & 31, warp = i >> 5;
   const bool active = i < bw * bh;
   int lx = 0, ly = 0;
-  if (active) tile_of(i, bw, bh, lx, ly);
-  const int in_n = ly > 0 ? tile_index(lx, ly - 1, bw, bh) : 0;
-  const int in_s = ly < bh - 1 ? tile_index(lx, ly + 1, bw, bh) : 0;
-  const int in_e = lx < bw - 1 ? tile_index(lx + 1, ly, bw, bh) : 0;
-  const int in_w = lx > 0 ? tile_index(lx - 1, ly, bw, bh) : 0;
+  if (active) tile_of(i, bw, bh, A.thread_map, lx, ly);
+  const int in_n = ly > 0 ? tile_index(lx, ly - 1, bw, bh, A.thread_map) : 0;
+  const int in_s = ly < bh - 1 ? tile_index(lx, ly + 1, bw, bh, A.thread_map) : 0;
+  const int in_e = lx < bw - 1 ? tile_index(lx + 1, ly, bw, bh, A.thread_map) : 0;
+  const int in_w = lx > 0 ? tile_index(lx - 1, ly, bw, bh, A.thread_map) : 0;
   const uint32_t x = X0 + lx, y = Y0 + ly, r = y * P.W + x;
   const size_t N = (size_t)P.N;
   const bool draining = A.draining != 0;

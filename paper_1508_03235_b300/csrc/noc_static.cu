@@ -205,6 +205,7 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
     A.abort_flag = abort_flag;
     A.wait_ns = 2000000000ll;
     A.silent_cta = -1;
+    A.thread_map = 0;
     if (launch_run(P, A, st) != cudaSuccess) return NOC_ERR_CUDA;
     done += n;
   }

@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnoc.so")
 
 NOC_OK = 0
+THREAD_MAPS = ("perimeter first", "rows", "columns")
 ERR_NAMES = {1: "NOC_ERR_ARG", 2: "NOC_ERR_OOM", 3: "NOC_ERR_QUEUE_OVERFLOW", 4: "NOC_ERR_TIMEOUT",
              5: "NOC_ERR_CUDA", 6: "NOC_ERR_PROTOCOL", 7: "NOC_ERR_STATE", 8: "NOC_ERR_RANGE"}
 HIST_BINS = 1025
@@ -87,6 +88,8 @@ def lib():
             "noc_hash_trace": (i32, [vp, P64, i64]),
             "noc_set_tiling": (i32, [vp, i32, i32]),
             "noc_get_tiling": (i32, [vp, C.POINTER(i32), C.POINTER(i32)]),
+            "noc_set_thread_map": (i32, [vp, i32]),
+            "noc_get_thread_map": (i32, [vp]),
             "noc_set_trace": (i32, [vp, i32, i64, P32]),
             "noc_debug_enqueue": (i32, [vp, i32, i32, P32]),
             "noc_debug_link": (i32, [vp, i32, i32, P32]),
@@ -138,7 +141,7 @@ class Sim:
     """One simulation on the current CUDA device.  `params` is a flat dict from
     paper_1508_03235_b300.inputs.sim_params()."""
 
-    def __init__(self, params: dict, stream=None, tiling=None):
+    def __init__(self, params: dict, stream=None, tiling=None, thread_map=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the simulator needs a CUDA device")
@@ -160,6 +163,8 @@ class Sim:
         _check(lib().noc_set_stream(h, C.c_void_p(st.cuda_stream)))
         if tiling is not None:
             self.set_tiling(*tiling)
+        if thread_map is not None:
+            self.set_thread_map(thread_map)
         _check(lib().noc_reset(h))
 
     def close(self):
@@ -218,6 +223,13 @@ class Sim:
         gx, gy = C.c_int(), C.c_int()
         _check(lib().noc_get_tiling(self._h, C.byref(gx), C.byref(gy)))
         return gx.value, gy.value
+
+    def set_thread_map(self, m: int):
+        """Tile-to-thread order inside each CTA rectangle: THREAD_MAPS[m]."""
+        _check(lib().noc_set_thread_map(self._h, m))
+
+    def thread_map(self) -> int:
+        return lib().noc_get_thread_map(self._h)
 
     def wait_limit(self, ns: int, silent_cta: int = -1):
         _check(lib().noc_debug_wait_limit(self._h, ns, silent_cta))
@@ -325,6 +337,7 @@ def _batch_sigs(L):
         "noc_batch_bind_memory": (i32, [vp, vp, C.c_size_t]),
         "noc_batch_set_stream": (i32, [vp, vp]),
         "noc_batch_set_rect": (i32, [vp, i32]),
+        "noc_batch_set_thread_map": (i32, [vp, i32]),
         "noc_batch_set_collect_hash": (i32, [vp, i32]),
         "noc_batch_run": (i32, [vp]),
         "noc_batch_waves": (i32, [vp]),
@@ -348,7 +361,7 @@ class Batch:
     that do not fit run in later waves."""
 
     def __init__(self, params_list, cycles, stream=None, rect=8, collect_hash=True,
-                 pool_bytes=None):
+                 pool_bytes=None, thread_map=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the batch engine needs a CUDA device")
@@ -379,6 +392,7 @@ class Batch:
         st = stream if stream is not None else torch.cuda.current_stream()
         _check(L.noc_batch_set_stream(h, C.c_void_p(st.cuda_stream)))
         _check(L.noc_batch_set_rect(h, rect))
+        _check(L.noc_batch_set_thread_map(h, thread_map))
         _check(L.noc_batch_set_collect_hash(h, 1 if collect_hash else 0))
 
     def close(self):

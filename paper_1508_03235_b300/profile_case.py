@@ -27,7 +27,7 @@ def main(argv=None):
     from paper_1508_03235_b300 import inputs as I
     from paper_1508_03235_b300 import noc, tune
     p = {8: I.MESH_8["params"], 64: I.mesh_64(1), 208: I.mesh_208(a.period)}[a.mesh]
-    s = noc.Sim(p, tiling=tune.cached_tiling(p))
+    s = noc.Sim(p, tiling=tune.cached_tiling(p), thread_map=tune.cached_thread_map(p))
     s.kernel_time(True)
     s.step(a.warm)
     _, warm_launches = s.kernel_time(True)

@@ -1,10 +1,13 @@
-"""Autotuner for the CTA tiling of the cycle kernel.
+"""Autotuner for the CTA tiling and the router-to-thread mapping of the cycle
+kernel.
 
-The mesh is cut into gx x gy rectangles, one CTA each (one thread per tile).
-Simulation results never depend on the tiling (the GPU tests check every
-tiling against the oracle); only the time per simulated cycle does.  The
-tuner times a handful of candidate tilings on a short run of the actual
-configuration and keeps the fastest in a JSON cache next to this file.
+The mesh is cut into gx x gy rectangles, one CTA each (one thread per tile),
+and the tiles of a rectangle are handed to its threads in one of three orders
+(perimeter first, rows, columns).  Simulation results depend on neither (the
+GPU tests check every tiling and order against the oracle); only the time per
+simulated cycle does.  The tuner times a handful of candidate tilings in
+every order on a short run of the actual configuration and keeps the fastest
+pair in a JSON cache next to this file.
 """
 from __future__ import annotations
 
@@ -58,9 +61,17 @@ def cached_tiling(params: dict):
     return tuple(t["tiling"]) if t else None
 
 
+def cached_thread_map(params: dict):
+    """The tuned tile-to-thread order, or None (the library default)."""
+    t = load_cache().get(key(params))
+    return t.get("thread_map", 0) if t else None
+
+
 def tune(params: dict, cycles: int = 2000, warm: int = 200, max_cands: int = 10,
-         save: bool = True, verbose: bool = False):
-    """Time candidate tilings; return (best tiling, {tiling: us per cycle})."""
+         maps=(0, 1, 2), reps: int = 2, save: bool = True, verbose: bool = False):
+    """Time candidate tilings in each tile-to-thread order (the best of `reps`
+    timed runs each); return (best (gx, gy, order), {(gx, gy, order): us per
+    cycle})."""
     import torch
 
     from . import noc
@@ -68,25 +79,32 @@ def tune(params: dict, cycles: int = 2000, warm: int = 200, max_cands: int = 10,
     sim = noc.Sim(params)
     timings = {}
     for gx, gy in candidates(params["mesh_w"], params["mesh_h"])[:max_cands]:
-        try:
-            sim.set_tiling(gx, gy)
-            sim.reset()
-            sim.step(warm)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            sim.step(cycles)
-            dt = time.perf_counter() - t0
-        except noc.NocError:
-            continue                       # not co-resident on this GPU
-        timings[(gx, gy)] = 1e6 * dt / cycles
-        if verbose:
-            print(f"  tiling {gx}x{gy}: {timings[(gx, gy)]:.2f} us/cycle", flush=True)
+        for m in maps:
+            try:
+                sim.set_tiling(gx, gy)
+                sim.set_thread_map(m)
+                dt = float("inf")
+                for _ in range(reps):
+                    sim.reset()
+                    sim.step(warm)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    sim.step(cycles)
+                    dt = min(dt, time.perf_counter() - t0)
+            except noc.NocError:
+                break                      # not co-resident on this GPU
+            timings[(gx, gy, m)] = 1e6 * dt / cycles
+            if verbose:
+                print(f"  tiling {gx}x{gy} {noc.THREAD_MAPS[m]}: {timings[(gx, gy, m)]:.2f} us/cycle",
+                      flush=True)
     sim.close()
     best = min(timings, key=timings.get)
     if save:
         cache = load_cache()
-        cache[key(params)] = {"tiling": list(best), "us_per_cycle": timings[best],
-                              "timings": {f"{a}x{b}": v for (a, b), v in timings.items()},
+        cache[key(params)] = {"tiling": list(best[:2]), "thread_map": best[2],
+                              "us_per_cycle": timings[best],
+                              "timings": {f"{a}x{b}/{noc.THREAD_MAPS[m]}": v
+                                          for (a, b, m), v in timings.items()},
                               "device": torch.cuda.get_device_name()}
         with open(CACHE, "w") as f:
             json.dump(cache, f, indent=1, sort_keys=True)

@@ -1,7 +1,7 @@
 """The batch engine on the full 512-instance workload (sides 8..128, periods
 2..40, Dirichlet(2,2,1) address mixes, all three L2 policies, seeds 1..512,
-20,000 cycles each) in the launch configuration the bench times (19x19-tile
-rectangles): every instance satisfies the model's conservation laws, and a
+20,000 cycles each) in the launch configuration the bench times (8x8-tile
+rectangles, column-major thread order): every instance satisfies the model's conservation laws, and a
 stratified sample (each policy at its smallest and a mid-size mesh, plus a
 128x128 mesh) equals its oracle run bit for bit.  With NOC_FULL_C3=1 every one
 of the 512 instances is compared with its oracle run (about an hour of oracle
@@ -16,7 +16,8 @@ from paper_1508_03235_b300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 CYCLES = 20_000
-RECT = 19
+RECT = 8
+THREAD_MAP = 2
 
 
 @pytest.fixture(scope="module")
@@ -38,7 +39,7 @@ def c3_points():
 
 @pytest.fixture(scope="module")
 def c3_batch(noc, c3_points):
-    b = noc.Batch(c3_points, CYCLES, rect=RECT)
+    b = noc.Batch(c3_points, CYCLES, rect=RECT, thread_map=THREAD_MAP)
     b.run()
     res = [(b.stats(i), b.state_hash(i), b.hist(i, 0), b.hist(i, 1)) for i in range(len(c3_points))]
     b.close()

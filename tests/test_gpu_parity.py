@@ -72,6 +72,28 @@ def test_tilings_hash_identically(noc, oracle_mod, tiling):
     assert g.tiling() == tiling
 
 
+@pytest.mark.parametrize("thread_map", [1, 2])
+@pytest.mark.parametrize("tiling", [(1, 1), (3, 2), (2, 5), (13, 1)])
+def test_thread_maps(noc, oracle_mod, thread_map, tiling):
+    """Row-major and column-major tile-to-thread orders (the autotuner's other
+    choices) on square, ragged and thin rectangles: the traced loop (its
+    perimeter-warp barrier then spans every warp), the plain loop and a
+    drain."""
+    cache = I.cache_cfg(l2_kb=64, svc_q=512)
+    p = I.sim_params(13, 11, policy=2 if tiling[0] % 2 else 0, seed=4, cache=cache,
+                     traf=I.traffic(period=3, priv=0.4, shared=0.5, shared_mb=1))
+    g = noc.Sim(p, tiling=tiling, thread_map=thread_map)
+    o = oracle_mod.OracleSim(p)
+    assert g.thread_map() == thread_map
+    run_traced(g, o, 600)
+    assert_same(g, o)
+    g.step(900)
+    o.step(900)
+    assert_same(g, o)
+    assert g.drain(100_000) == o.drain(100_000)
+    assert_same(g, o)
+
+
 @pytest.mark.parametrize("tiling", [(1, 1), (2, 2), (8, 8), (3, 5), (8, 1), (1, 8), (4, 3)])
 def test_tilings_untraced(noc, oracle_mod, tiling):
     """The untraced cycle loop (per-warp cycle flags, no CTA barrier per cycle)
@@ -142,12 +164,17 @@ def test_mesh64_seeds_prefix(noc, oracle_mod, seed):
 
 @pytest.mark.parametrize("period", [10, 2])
 def test_mesh208_full_size_prefix(noc, oracle_mod, period):
-    """The 208x208 mesh in the bench's launch configuration (default tiling):
-    every cycle of a prefix, then the full state."""
-    g, o = pair(noc, oracle_mod, I.mesh_208(period))
+    """The 208x208 mesh in the bench's launch configuration (the tuned tiling
+    and tile-to-thread order): every cycle of a prefix, then the full state
+    after the plain cycle loop."""
+    from paper_1508_03235_b300 import tune
+    p = I.mesh_208(period)
+    tiling, tmap = tune.cached_tiling(p), tune.cached_thread_map(p)
+    g = noc.Sim(p, tiling=tiling, thread_map=tmap)
+    o = oracle_mod.OracleSim(p)
     run_traced(g, o, 160)
     assert_same(g, o)
-    g2 = noc.Sim(I.mesh_208(period))
+    g2 = noc.Sim(p, tiling=tiling, thread_map=tmap)
     g2.step(100)
     g2.step(60)
     assert_same(g2, o)
