@@ -1,7 +1,8 @@
 // mlp.cu -- the surrogate network's kernels (include/mlp.h): tensor-core GEMMs
-// in BF16 with FP32 accumulation (mma.sync m16n8k16), with the bias, GELU and
-// pre-activation store fused into the GEMM epilogue, plus the GELU backward,
-// bias-gradient, MSE and AdamW element kernels.
+// in BF16 with FP32 accumulation -- tcgen05 (mlp_tc.cuh) for the forward and
+// backward GEMMs whose shapes it takes, mma.sync m16n8k16 for the rest -- with
+// the bias, GELU and pre-activation store fused into the GEMM epilogue, plus
+// the transpose, GELU backward, bias-gradient, MSE and AdamW kernels.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -151,9 +152,13 @@ int g_path = 0;  // 0: tcgen05 where it applies, 1: mma.sync for every GEMM
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// the GEMM shapes the tcgen05 kernel takes (both operands K-major)
+bool tc_shape(int M, int N, int K) {
+  return g_path == 0 && K >= 16 && K % 16 == 0 && M % tc::TM == 0 && N % 16 == 0 && N <= tc::MAXN;
+}
+
 bool tc_applies(const Gemm& g) {
-  return g_path == 0 && g.sAk == 1 && g.sAm == g.K && g.sBk == 1 && g.sBn == g.K && g.K >= 16 &&
-         g.K <= tc::MAXK && g.K % 16 == 0 && g.M % tc::TM == 0 && g.N % 16 == 0 && g.N <= tc::MAXN &&
+  return g_path == 0 && g.sAk == 1 && g.sAm == g.K && g.sBk == 1 && g.sBn == g.K && tc_shape(g.M, g.N, g.K) &&
          aligned16(g.A) && aligned16(g.B) && (!g.Cf || (aligned16(g.Cf) && g.ldc % 4 == 0)) &&
          (!g.Cb || (aligned16(g.Cb) && g.ldc % 8 == 0));
 }
@@ -172,11 +177,33 @@ cudaError_t gemm(const Gemm& g, cudaStream_t s) {
     // spreads over (M / 128) x (N / 64) CTAs
     const int nt = g.N % 64 == 0 ? 64 : (g.N % 32 == 0 ? 32 : 16);
     const dim3 grid(g.M / tc::TM, g.N / nt);
-    tc::gemm_kernel<TcEpi><<<grid, tc::THREADS, tc::smem_bytes(nt, g.K), s>>>(g.A, g.B, g.M, nt, g.K, epi);
+    const int kc = g.K < tc::MAXK ? g.K : tc::MAXK;
+    tc::gemm_kernel<TcEpi><<<grid, tc::THREADS, tc::smem_bytes(nt, kc), s>>>(g.A, g.B, g.M, nt, g.K, epi);
     return cudaGetLastError();
   }
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
   gemm_kernel<<<grid, THREADS, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+// dst[c][r] = src[r][c] for a rows x cols BF16 matrix (32 x 32 tiles through
+// shared memory, so that both the reads and the writes are coalesced)
+__global__ void transpose_kernel(const __nv_bfloat16* src, int rows, int cols, __nv_bfloat16* dst) {
+  __shared__ __nv_bfloat16 t[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
+  for (int j = ty; j < 32; j += 8) {
+    const int r = r0 + j, c = c0 + tx;
+    if (r < rows && c < cols) t[j][tx] = src[(size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int c = c0 + j, r = r0 + tx;
+    if (r < rows && c < cols) dst[(size_t)c * rows + r] = t[tx][j];
+  }
+}
+
+cudaError_t transpose(const __nv_bfloat16* src, int rows, int cols, __nv_bfloat16* dst, cudaStream_t s) {
+  transpose_kernel<<<dim3((cols + 31) / 32, (rows + 31) / 32), dim3(32, 8), 0, s>>>(src, rows, cols, dst);
   return cudaGetLastError();
 }
 
@@ -274,6 +301,9 @@ struct Workspace {
   __nv_bfloat16* A[MLP_MAX_LAYERS];   // activations of hidden layers [B][dims[l+1]]
   float *dAf, *dZf;
   __nv_bfloat16* dZb;
+  // K-major copies for the tcgen05 backward GEMMs: dZ^T [N][B], the layer
+  // input transposed [K][B], W^T [K][N]
+  __nv_bfloat16 *dZt, *inT, *Wt;
   size_t bytes;
 };
 
@@ -297,6 +327,12 @@ Workspace carve(const mlp_shape* s, int B, void* base) {
   o = a256(o + (size_t)B * maxd * 4);
   w.dZb = reinterpret_cast<__nv_bfloat16*>(p + o);
   o = a256(o + (size_t)B * maxd * 2);
+  w.dZt = reinterpret_cast<__nv_bfloat16*>(p + o);
+  o = a256(o + (size_t)B * maxd * 2);
+  w.inT = reinterpret_cast<__nv_bfloat16*>(p + o);
+  o = a256(o + (size_t)B * maxd * 2);
+  w.Wt = reinterpret_cast<__nv_bfloat16*>(p + o);
+  o = a256(o + (size_t)maxd * maxd * 2);
   w.bytes = o;
   return w;
 }
@@ -365,17 +401,29 @@ int mlp_backward(const mlp_shape* s, const uint16_t* params_bf16, const uint16_t
     float* gb = gW + (size_t)N * K;
     colsum_kernel<<<(N + 31) / 32, 256, 0, st>>>(dZf, B, N, gb);
     const __nv_bfloat16* prev = l == 0 ? reinterpret_cast<const __nv_bfloat16*>(x) : w.A[l - 1];
-    // dW_l[n][k] = sum_m dZ[m][n] * prev[m][k]
+    // dW_l[n][k] = sum_m dZ[m][n] * prev[m][k]: a contraction over the batch;
+    // on the tensor-core path both operands are first transposed to K-major
     Gemm g;
     g.M = N;
     g.N = K;
     g.K = B;
-    g.A = w.dZb;                   // A[n][m] = dZ[m][n]
-    g.sAm = 1;
-    g.sAk = N;
-    g.B = prev;                    // B[m][k] = prev[m][k]
-    g.sBn = 1;
-    g.sBk = K;
+    if (tc_shape(N, K, B)) {
+      if (transpose(w.dZb, B, N, w.dZt, st) != cudaSuccess) return MLP_ERR_CUDA;
+      if (transpose(prev, B, K, w.inT, st) != cudaSuccess) return MLP_ERR_CUDA;
+      g.A = w.dZt;                 // A[n][m] = dZ^T[n][m]
+      g.sAm = B;
+      g.sAk = 1;
+      g.B = w.inT;                 // B[m][k] = prev^T[k][m]
+      g.sBn = B;
+      g.sBk = 1;
+    } else {
+      g.A = w.dZb;                 // A[n][m] = dZ[m][n]
+      g.sAm = 1;
+      g.sAk = N;
+      g.B = prev;                  // B[m][k] = prev[m][k]
+      g.sBn = 1;
+      g.sBk = K;
+    }
     g.bias = nullptr;
     g.Cf = gW;
     g.Cb = nullptr;
@@ -391,9 +439,16 @@ int mlp_backward(const mlp_shape* s, const uint16_t* params_bf16, const uint16_t
     h.A = w.dZb;
     h.sAm = N;
     h.sAk = 1;
-    h.B = P + w_off(s, l);         // B[n][k] = W[n][k]
-    h.sBn = 1;
-    h.sBk = K;
+    if (tc_shape(B, K, N)) {
+      if (transpose(P + w_off(s, l), N, K, w.Wt, st) != cudaSuccess) return MLP_ERR_CUDA;
+      h.B = w.Wt;                  // B[n][k] = W^T[k][n]
+      h.sBn = N;
+      h.sBk = 1;
+    } else {
+      h.B = P + w_off(s, l);       // B[n][k] = W[n][k]
+      h.sBn = 1;
+      h.sBk = K;
+    }
     h.bias = nullptr;
     h.Cf = w.dAf;
     h.Cb = nullptr;

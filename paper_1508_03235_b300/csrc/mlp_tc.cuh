@@ -6,12 +6,13 @@
 //
 // One CTA of 128 threads computes a 128 x NT tile of C = A * B^T (+ bias):
 // A is [M][K] and B is [N][K], both K-major (row-major with unit stride in K),
-// 16 <= K <= 256 with K % 16 == 0, M % 128 == 0, and the CTA grid is
-// (M / 128) x (N / NT) with NT in {16, 32, 64, 128, 256} dividing N.  The
-// whole K extent of both operand tiles is staged in shared memory at once (at
-// most 192 KB), so one commit covers all K / 16 MMA steps.  K is stored in
-// 128-byte rows of 64 elements; a last partial row block holds only the
-// chunks the MMA steps read.
+// K >= 16 with K % 16 == 0, M % 128 == 0, and the CTA grid is (M / 128) x
+// (N / NT) with NT in {16, 32, 64, 128, 256} dividing N.  K is taken in chunks
+// of at most MAXK: each chunk of both operand tiles is staged in shared memory
+// (at most 192 KB), its K / 16 MMA steps accumulate into the same TMEM tile
+// under one commit, and the next chunk is staged once that commit's mbarrier
+// phase completes.  A chunk is stored in 128-byte rows of 64 elements; a last
+// partial row block holds only the 16-byte pieces the MMA steps read.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -153,10 +154,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   // operand tiles start on a 1024-byte boundary (the swizzle pattern's period)
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const int kblocks = kblocks_of(K);
+  const int KC = K < MAXK ? K : MAXK;                         // K of one chunk
+  const int kblocks_max = kblocks_of(KC);
   unsigned char* As = base;                                   // [kblocks][128 rows][128 B]
-  unsigned char* Bs = base + (size_t)TM * kblocks * 128;      // [kblocks][NT rows][128 B]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + (size_t)NT * kblocks * 128);
+  unsigned char* Bs = base + (size_t)TM * kblocks_max * 128;  // [kblocks][NT rows][128 B]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + (size_t)NT * kblocks_max * 128);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -169,47 +171,54 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
 
-  // operands into shared memory in the canonical 128-byte-swizzled K-major
-  // layout: 16-byte chunk c of row r goes to chunk c ^ (r & 7); chunks past
-  // K are neither loaded nor read
-  for (int e = tid; e < TM * kblocks * 8; e += THREADS) {
-    const int c = e & 7, r = (e >> 3) % TM, kb = (e >> 3) / TM;
-    if (kb * KATOM + c * 8 >= K) continue;
-    cp_async16(As + (size_t)kb * TM * 128 + r * 128 + ((c ^ (r & 7)) << 4),
-               A + (size_t)(m0 + r) * K + kb * KATOM + c * 8);
-  }
-  for (int e = tid; e < NT * kblocks * 8; e += THREADS) {
-    const int c = e & 7, n = (e >> 3) % NT, kb = (e >> 3) / NT;
-    if (kb * KATOM + c * 8 >= K) continue;
-    cp_async16(Bs + (size_t)kb * NT * 128 + n * 128 + ((c ^ (n & 7)) << 4),
-               B + (size_t)(n0 + n) * K + kb * KATOM + c * 8);
-  }
-  cp_async_wait_all();
-  // the copies must be visible to the tensor core's async proxy
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  fence_before_sync();
-  __syncthreads();
-  fence_after_sync();
-  const uint32_t tmem = *tslot;
+  bool done = true;
+  uint32_t tmem = 0;
+  for (int k0 = 0, chunk = 0; k0 < K && done; k0 += KC, ++chunk) {
+    const int kc = K - k0 < KC ? K - k0 : KC;
+    const int kblocks = kblocks_of(kc);
+    // operands into shared memory in the canonical 128-byte-swizzled K-major
+    // layout: 16-byte piece c of row r goes to piece c ^ (r & 7); pieces past
+    // the chunk are neither loaded nor read
+    for (int e = tid; e < TM * kblocks * 8; e += THREADS) {
+      const int c = e & 7, r = (e >> 3) % TM, kb = (e >> 3) / TM;
+      if (kb * KATOM + c * 8 >= kc) continue;
+      cp_async16(As + (size_t)kb * TM * 128 + r * 128 + ((c ^ (r & 7)) << 4),
+                 A + (size_t)(m0 + r) * K + k0 + kb * KATOM + c * 8);
+    }
+    for (int e = tid; e < NT * kblocks * 8; e += THREADS) {
+      const int c = e & 7, n = (e >> 3) % NT, kb = (e >> 3) / NT;
+      if (kb * KATOM + c * 8 >= kc) continue;
+      cp_async16(Bs + (size_t)kb * NT * 128 + n * 128 + ((c ^ (n & 7)) << 4),
+                 B + (size_t)(n0 + n) * K + k0 + kb * KATOM + c * 8);
+    }
+    cp_async_wait_all();
+    // the copies must be visible to the tensor core's async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    tmem = *tslot;
 
-  if (tid == 0) {
-    const uint32_t idesc = instr_desc(TM, NT);
-    const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
-    for (int kb = 0; kb < kblocks; ++kb)
-      for (int ks = 0; ks < KATOM / 16 && kb * KATOM + ks * 16 < K; ++ks)
-        mma(tmem, smem_desc(a0 + kb * TM * 128 + ks * 32), smem_desc(b0 + kb * NT * 128 + ks * 32),
-            idesc, (kb | ks) != 0);
-    commit(bar);
+    if (tid == 0) {
+      const uint32_t idesc = instr_desc(TM, NT);
+      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+      for (int kb = 0; kb < kblocks; ++kb)
+        for (int ks = 0; ks < KATOM / 16 && kb * KATOM + ks * 16 < kc; ++ks)
+          mma(tmem, smem_desc(a0 + kb * TM * 128 + ks * 32), smem_desc(b0 + kb * NT * 128 + ks * 32),
+              idesc, (k0 | kb | ks) != 0);
+      commit(bar);
+    }
+    // wait for this chunk's MMAs (bounded: about a second of polling at
+    // most); the mbarrier's phase parity alternates chunk by chunk
+    bool ok = false;
+    for (uint32_t it = 0; it < (1u << 22) && !ok; ++it) {
+      ok = mbar_try_wait(bar, (uint32_t)(chunk & 1));
+      if (!ok && it > 64) __nanosleep(200);
+    }
+    done = __syncthreads_and(ok);           // every thread saw the phase complete
+    if (!done && tid == 0) atomicCAS(&g_tc_status, 0u, 1u);
+    fence_after_sync();
   }
-  // wait for the accumulator (bounded: about a second of polling at most)
-  bool done = false;
-  for (uint32_t it = 0; it < (1u << 22) && !done; ++it) {
-    done = mbar_try_wait(bar, 0);
-    if (!done && it > 64) __nanosleep(200);
-  }
-  done = __any_sync(0xFFFFFFFFu, done);   // the phase completed for every lane
-  if (!done && lane == 0) atomicCAS(&g_tc_status, 0u, 1u);
-  fence_after_sync();
 
   // epilogue: warp w holds rows 32w .. 32w + 31 of the tile, one per lane
   if (done) {

@@ -344,8 +344,11 @@ if __name__ == "__main__":
                     help="reuse a saved dataset; time the simulator on --time-points of it")
     ap.add_argument("--time-points", type=int, default=2_000)
     ap.add_argument("--out", default=None, help="write the result JSON here")
+    ap.add_argument("--gemm-path", type=int, default=0,
+                    help="0: tcgen05 where it applies (default), 1: mma.sync for every GEMM")
     a = ap.parse_args()
     from paper_1508_03235_b300 import surrogate as S
+    S.set_gemm_path(a.gemm_path)
     res, _ = S.run(points=a.points, holdout=a.holdout, cycles=a.cycles, epochs=a.epochs,
                    data_path=a.data, log=lambda m: print(m, flush=True), from_data=a.from_data,
                    time_points=a.time_points)

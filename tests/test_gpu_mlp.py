@@ -155,3 +155,72 @@ def test_tcgen05_network_matches_mma_sync_and_oracle(sur, B):
     assert rel(y0, want) < 1e-2
     assert np.allclose(y0, want, rtol=3e-2, atol=3e-2 * np.abs(want).max())
     assert rel(y0, y1) < 5e-3
+
+
+def _grads_both_paths(sur, net, xb, dy):
+    import torch
+    out = {}
+    for path in (0, 1):
+        old = sur.set_gemm_path(path)
+        net.forward(xb)
+        out[path] = net.backward(xb, torch.as_tensor(dy).cuda()).double().cpu().numpy()
+        sur.set_gemm_path(old)
+    assert sur.gemm_status() == 0
+    return out
+
+
+@pytest.mark.parametrize("B", [1024, 256])
+def test_tcgen05_backward_matches_mma_sync_and_oracle(sur, B):
+    """At training batches the tcgen05 path takes the backward GEMMs too: the
+    weight gradients (a contraction over the batch, in chunks of 256) on K-major
+    transposes of dZ and the layer input, the input gradients on W^T.  Both
+    engines accumulate in FP32, so they agree to FP32 rounding; both match the
+    fp64 oracle to BF16 accuracy."""
+    import torch
+    net = sur.MLP(seed=13, max_batch=B)
+    rng = np.random.default_rng(B + 5)
+    x = rng.normal(size=(B, 16)).astype(np.float32)
+    xb = torch.as_tensor(x).cuda().to(torch.bfloat16)
+    dy = rng.normal(size=(B, 16)).astype(np.float32)
+    g = _grads_both_paths(sur, net, xb, dy)
+    p = net.params.double().cpu().numpy()
+    gw = M.backward(list(sur.DIMS), p, x, dy.astype(np.float64))
+    off = 0
+    for l in range(len(sur.DIMS) - 1):
+        n, k = sur.DIMS[l + 1], sur.DIMS[l]
+        for size in (n * k, n):
+            a0, a1, want = g[0][off:off + size], g[1][off:off + size], gw[off:off + size]
+            assert rel(a0, a1) < 1e-4, (l, size)
+            assert rel(a0, want) < 2e-2, (l, size)
+            off += size
+
+
+def test_tcgen05_long_contraction(sur):
+    """A 512 -> 256 layer at batch 512: the forward GEMM (K = 512, two chunks
+    of the tcgen05 kernel's K loop) against the mma.sync engine and the exact
+    fp64 sum of the BF16 products; its weight gradient (512 columns, wider
+    than the tcgen05 tile allows, so on mma.sync under either setting) against
+    the same sum."""
+    import torch
+    B = 512
+    net = sur.MLP(dims=(512, 256), seed=17, max_batch=B)
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(B, 512)).astype(np.float32)
+    xb = torch.as_tensor(x).cuda().to(torch.bfloat16)
+    p = M.bf16_round(net.params.double().cpu().numpy())
+    W, b = p[:512 * 256].reshape(256, 512), p[512 * 256:]
+    want = M.bf16_round(x) @ W.T + b
+    ys = {}
+    for path in (0, 1):
+        old = sur.set_gemm_path(path)
+        ys[path] = net.forward(xb).double().cpu().numpy()
+        sur.set_gemm_path(old)
+    scale = np.abs(want).max()
+    for path in (0, 1):
+        assert np.abs(ys[path] - want).max() < 2e-5 * scale, path
+    dy = rng.normal(size=(B, 256)).astype(np.float32)
+    g = _grads_both_paths(sur, net, xb, dy)
+    gW = M.bf16_round(dy.astype(np.float64)).T @ M.bf16_round(x)
+    for path in (0, 1):
+        got = g[path][:512 * 256].reshape(256, 512)
+        assert np.abs(got - gW).max() < 2e-5 * np.abs(gW).max(), path
