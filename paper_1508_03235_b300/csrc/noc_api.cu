@@ -43,6 +43,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr uint32_t kMaxChunk = 1u << 20;  // cycles per launch (32-bit counter deltas)
+constexpr int kBatchRefcap = 256;          // references drawn ahead per tile of a batch instance
 
 }  // namespace
 
@@ -929,7 +930,9 @@ int noc_batch_create(int n, const noc_instance_desc* d, noc_batch** out) {
       noc_batch_destroy(b);
       return rc;
     }
-    s->refcap = 0;  // batch instances draw their references in place
+    // one window of references per tile, drawn before the wave's launch;
+    // past it an instance draws in place
+    s->refcap = kBatchRefcap;
     layout(s);
     b->sims.push_back(s);
     b->cycles.push_back(d[i].cycles);
@@ -1069,6 +1072,10 @@ static int run_batch_group(noc_batch* b, const std::vector<int>& members, int th
       noc_sim* s = b->sims[wave[k]];
       int rc = ensure_memory(s);
       if (rc) return rc;
+      if (s->P.refcap && b->cycles[wave[k]] > 0) {
+        CU(launch_gen_refs(s->P, 0, (uint32_t)b->cycles[wave[k]], b->stream), "reference draw launch");
+        b->launches++;
+      }
       RunArgs A;
       memset(&A, 0, sizeof A);
       A.t0 = 0;
