@@ -62,13 +62,30 @@ int mlp_adamw(size_t n, float* params, uint16_t* params_bf16, const float* grads
 /* FP32 -> BF16 (round to nearest even). */
 int mlp_to_bf16(const float* src, uint16_t* dst, size_t n, void* stream);
 
+/* Whole-network inference in one kernel (the network's weights packed once
+ * into the tensor cores' shared-memory operand layout; activations never leave
+ * the SM).  For shapes whose every width is a multiple of 16 in 16..256.
+ * mlp_packed_bytes: device bytes of the packed image (0: shape not taken).
+ * mlp_pack: write the image from the BF16 parameters (again after every
+ * parameter update).  mlp_infer: y[batch][dims[L]] (FP32) = network(x), x
+ * BF16 [batch][dims[0]], batch a positive multiple of 128; packed, x and y
+ * 16-byte aligned; results equal mlp_forward's on the tensor-core path.
+ * MLP_ERR_ARG for a shape, batch or alignment it does not take. */
+size_t mlp_packed_bytes(const mlp_shape* shape);
+int mlp_pack(const mlp_shape* shape, const uint16_t* params_bf16, void* packed, void* stream);
+int mlp_infer(const mlp_shape* shape, const void* packed, const uint16_t* x, int batch, float* y,
+              void* stream);
+
 /* GEMM engine of the layers.  path 0 (default): the 5th-generation tensor
  * cores (tcgen05.mma, FP32 accumulator in tensor memory) for every GEMM whose
- * rows are a multiple of 128, inner dimension 16..256 and output width up to
- * 256, both multiples of 16, with unit-stride operands (every layer of the
- * forward pass at batch sizes that are multiples of 128), warp-level mma.sync
- * for the others (the backward pass's transposed products); path 1: mma.sync
- * for all.
+ * rows are a multiple of 128, output width up to 256 and inner dimension at
+ * least 16, both multiples of 16 -- every forward layer at batches that are
+ * multiples of 128, and in the backward pass the input gradients (batches
+ * that are multiples of 128) and the weight gradients of layers whose output
+ * width is a multiple of 128 (batches that are multiples of 16), on K-major
+ * transposes the library makes; warp-level mma.sync for the others; path 1:
+ * mma.sync for all.
+ * mlp_infer is not affected.
  * Returns the previous path, or -1 for an invalid one. */
 int mlp_set_gemm_path(int path);
 /* Waits for the device; MLP_ERR_TIMEOUT if a tcgen05 GEMM since the last call

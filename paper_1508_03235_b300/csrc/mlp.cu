@@ -148,6 +148,10 @@ struct TcEpi {
   }
 };
 
+}  // namespace mlpk
+#include "mlp_fused.cuh"
+namespace mlpk {
+
 int g_path = 0;  // 0: tcgen05 where it applies, 1: mma.sync for every GEMM
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
@@ -484,6 +488,46 @@ int mlp_to_bf16(const float* src, uint16_t* dst, size_t n, void* stream) {
   if (!src || !dst) return MLP_ERR_ARG;
   to_bf16_kernel<<<grid_1d(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
       src, reinterpret_cast<__nv_bfloat16*>(dst), n);
+  return cudaGetLastError() == cudaSuccess ? MLP_OK : MLP_ERR_CUDA;
+}
+
+size_t mlp_packed_bytes(const mlp_shape* s) {
+  mlpk::fused::Plan p;
+  if (!shape_ok(s) || !mlpk::fused::plan_of(s->n_layers, s->dims, p)) return 0;
+  return p.bytes;
+}
+
+int mlp_pack(const mlp_shape* s, const uint16_t* params_bf16, void* packed, void* stream) {
+  mlpk::fused::Plan p;
+  if (!shape_ok(s) || !params_bf16 || !packed || !mlpk::fused::plan_of(s->n_layers, s->dims, p) ||
+      (reinterpret_cast<uintptr_t>(packed) & 15))
+    return MLP_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int l = 0; l < p.n_layers; ++l) {
+    const size_t work = (size_t)mlpk::tc::kblocks_of(p.l[l].K) * p.l[l].N * 8 + p.l[l].N;
+    mlpk::fused::pack_kernel<<<grid_1d(work), 256, 0, st>>>(
+        reinterpret_cast<const __nv_bfloat16*>(params_bf16), w_off(s, l), p.l[l],
+        static_cast<unsigned char*>(packed));
+  }
+  return cudaGetLastError() == cudaSuccess ? MLP_OK : MLP_ERR_CUDA;
+}
+
+int mlp_infer(const mlp_shape* s, const void* packed, const uint16_t* x, int B, float* y, void* stream) {
+  mlpk::fused::Plan p;
+  if (!shape_ok(s) || !packed || !x || !y || B < mlpk::tc::TM || B % mlpk::tc::TM ||
+      !mlpk::fused::plan_of(s->n_layers, s->dims, p) || (reinterpret_cast<uintptr_t>(packed) & 15) ||
+      (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(y) & 15))
+    return MLP_ERR_ARG;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(mlpk::fused::infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)mlpk::fused::smem_bytes()) != cudaSuccess)
+      return MLP_ERR_CUDA;
+    attr = true;
+  }
+  mlpk::fused::infer_kernel<<<B / mlpk::tc::TM, mlpk::fused::FT, mlpk::fused::smem_bytes(),
+                              static_cast<cudaStream_t>(stream)>>>(
+      p, static_cast<const unsigned char*>(packed), reinterpret_cast<const __nv_bfloat16*>(x), y);
   return cudaGetLastError() == cudaSuccess ? MLP_OK : MLP_ERR_CUDA;
 }
 

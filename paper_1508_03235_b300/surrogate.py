@@ -50,6 +50,9 @@ def _mlp_lib():
             ("mlp_to_bf16", i32, [vp, vp, sz, vp]),
             ("mlp_set_gemm_path", i32, [i32]),
             ("mlp_gemm_status", i32, []),
+            ("mlp_packed_bytes", sz, [C.POINTER(Shape)]),
+            ("mlp_pack", i32, [C.POINTER(Shape), vp, vp, vp]),
+            ("mlp_infer", i32, [C.POINTER(Shape), vp, vp, i32, vp, vp]),
         ):
             fn = getattr(L, name)
             fn.restype = res
@@ -109,6 +112,9 @@ class MLP:
         self.ws = torch.empty(L.mlp_workspace_bytes(C.byref(self.shape), max_batch) + 256,
                               dtype=torch.uint8, device="cuda")
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        nb = L.mlp_packed_bytes(C.byref(self.shape))
+        self.packed = torch.empty(nb + 16, dtype=torch.uint8, device="cuda") if nb else None
+        self._packed_step = None               # parameter version the image holds
         self.sync_bf16()
 
     def _stream(self):
@@ -121,6 +127,27 @@ class MLP:
     def sync_bf16(self):
         _ok(_mlp_lib().mlp_to_bf16(_p(self.params), _p(self.params_bf16), self.n, self._stream()),
             "mlp_to_bf16")
+        self._packed_step = None
+
+    def _packed(self):
+        p = self.packed.data_ptr()
+        return C.c_void_p(p + (-p) % 16)
+
+    def infer(self, xb):
+        """The whole network in one fused tcgen05 kernel (mlp_infer): xb BF16
+        [B, dims[0]] with B a multiple of 128 -> FP32 [B, dims[-1]], equal to
+        forward() on the tensor-core path."""
+        B = xb.shape[0]
+        if self.packed is None or B < 128 or B % 128 or xb.dtype != self.torch.bfloat16:
+            raise ValueError("mlp_infer takes BF16 batches of a multiple of 128 rows of a packable shape")
+        if self._packed_step != self.step:
+            _ok(_mlp_lib().mlp_pack(C.byref(self.shape), _p(self.params_bf16), self._packed(),
+                                    self._stream()), "mlp_pack")
+            self._packed_step = self.step
+        y = self.torch.empty(B, self.dims[-1], dtype=self.torch.float32, device="cuda")
+        _ok(_mlp_lib().mlp_infer(C.byref(self.shape), self._packed(), _p(xb), B, _p(y),
+                                 self._stream()), "mlp_infer")
+        return y
 
     def load_params(self, flat):
         self.params.copy_(self.torch.as_tensor(flat, dtype=self.torch.float32))
@@ -249,9 +276,18 @@ class Surrogate:
         return float(loss.item())
 
     def predict(self, X):
+        """Network outputs for design-point features X, through the fused
+        inference kernel (each chunk padded to a multiple of 128 rows)."""
         out = []
         for s in range(0, len(X), self.net.max_batch):
-            y = self.net.forward(self._x(X[s:s + self.net.max_batch]))
+            chunk = X[s:s + self.net.max_batch]
+            n = len(chunk)
+            if self.net.packed is not None:
+                pad = (-n) % 128
+                xb = self._x(np.concatenate([chunk, np.repeat(chunk[-1:], pad, axis=0)]) if pad else chunk)
+                y = self.net.infer(xb)[:n]
+            else:
+                y = self.net.forward(self._x(chunk))
             out.append(y[:, :N_OUT].double().cpu().numpy())
         Z = np.concatenate(out)
         return Z * self.sd + self.mu

@@ -224,3 +224,35 @@ def test_tcgen05_long_contraction(sur):
     for path in (0, 1):
         got = g[path][:512 * 256].reshape(256, 512)
         assert np.abs(got - gW).max() < 2e-5 * np.abs(gW).max(), path
+
+
+@pytest.mark.parametrize("dims,B", [(None, 4096), (None, 128), ((64, 128, 256, 32), 384)])
+def test_fused_inference_equals_layered_forward(sur, dims, B):
+    """The one-kernel inference (weights packed into the operand layout and
+    brought in by bulk copies, activations kept on chip, TMEM accumulators
+    chained layer to layer) gives exactly the layered tensor-core forward's
+    outputs, which the tests above tie to the fp64 oracle; the image is
+    repacked after a parameter update."""
+    import torch
+    net = sur.MLP(dims=dims or sur.DIMS, seed=21, max_batch=B)
+    rng = np.random.default_rng(B)
+    x = rng.normal(size=(B, net.dims[0])).astype(np.float32)
+    xb = torch.as_tensor(x).cuda().to(torch.bfloat16)
+    old = sur.set_gemm_path(0)
+    y_layered = net.forward(xb).cpu().numpy()
+    y_fused = net.infer(xb).cpu().numpy()
+    assert sur.gemm_status() == 0
+    assert np.array_equal(y_fused, y_layered)
+    want, _ = M.forward(list(net.dims), net.params.double().cpu().numpy(), x)
+    assert rel(y_fused.astype(np.float64), want) < 1e-2
+    net.grads.copy_(torch.as_tensor(rng.normal(size=net.n).astype(np.float32)))
+    net.adamw(1e-2)
+    assert np.array_equal(net.infer(xb).cpu().numpy(), net.forward(xb).cpu().numpy())
+    sur.set_gemm_path(old)
+    with pytest.raises(ValueError):
+        net.infer(xb[:64])
+    # the C ABI refuses a batch that is not a multiple of 128 (MLP_ERR_ARG)
+    import ctypes as C
+    y = torch.empty(64, net.dims[-1], device="cuda")
+    L = sur._mlp_lib()
+    assert L.mlp_infer(C.byref(net.shape), net._packed(), sur._p(xb), 64, sur._p(y), net._stream()) == 1
