@@ -451,7 +451,9 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
       const uint32_t tag = link_tag(t - 1);
       const uint4* gt = P.gtag + pin * pstride;
       uint32_t need = boundary;
-      const unsigned long long start = global_ns();
+      // the clock is read at the first periodic check, not on every cycle's
+      // entry: the wait's limit then runs from that check
+      unsigned long long start = 0;
       bool aborted = false;
       for (unsigned it = 0;; ++it) {
 #pragma unroll
@@ -464,6 +466,7 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
         if (__all_sync(0xFFFFFFFFu, ok)) break;
         if ((it & 31u) == 31u) {
           bool stop = ld_acquire_u32(A.abort_flag) != 0 || it >= (1u << 28);
+          if (start == 0) start = global_ns();
           if (!stop && (long long)(global_ns() - start) > A.wait_ns) {
             stop = true;
             if (lane == 0) {
