@@ -1185,7 +1185,7 @@ static int check_params(const orc_params* p) {
   if (p->l1_miss_cycles < 0 || p->mem_latency < 1) return 0;
   if (p->core_q < 1 || p->svc_q < 1 || p->mem_q < 1) return 0;
   if (p->policy == ORC_L2_LSPD_MIGRATE &&
-      (p->mig_window < 1 || p->mig_window > 64 || p->mig_threshold < 1 || p->fwd_entries < 1))
+      (p->mig_window < 1 || p->mig_window > 30 || p->mig_threshold < 1 || p->fwd_entries < 1))
     return 0;
   if (p->mode < 0 || p->mode > 2 || p->period < 0) return 0;
   if (p->write_q16 > 65536 || p->priv_q16 + p->shared_q16 > 65536 || p->hot_q16 > 65536) return 0;

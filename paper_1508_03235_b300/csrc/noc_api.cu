@@ -387,9 +387,9 @@ int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, co
   if (mesh_w < 1 || mesh_h < 1 || (long)mesh_w * mesh_h > 65535)
     return fail(NOC_ERR_ARG, "mesh %dx%d: need 1..65535 tiles", mesh_w, mesh_h);
   if (l2_policy < 0 || l2_policy > 2) return fail(NOC_ERR_ARG, "l2_policy %d", l2_policy);
-  auto pow2_ways = [](int w) { return w == 1 || w == 2 || w == 4 || w == 8 || w == 16; };
-  if (c->l1_sets < 1 || !pow2_ways(c->l1_ways) || c->l2_sets < 1 || !pow2_ways(c->l2_ways))
-    return fail(NOC_ERR_ARG, "cache geometry: sets >= 1, ways in {1,2,4,8,16}");
+  if (c->l1_sets < 1 || c->l1_ways < 1 || c->l1_ways > MAX_WAYS || c->l2_sets < 1 || c->l2_ways < 1 ||
+      c->l2_ways > MAX_WAYS)
+    return fail(NOC_ERR_ARG, "cache geometry: sets >= 1, ways 1..16");
   if (c->l1_miss_cycles < 0 || c->mem_latency < 1) return fail(NOC_ERR_ARG, "latencies");
   if (c->core_q < 1 || c->svc_q < 1 || c->mem_q < 1 || c->core_q > 65535 || c->svc_q > 65535 ||
       c->mem_q > 65535)

@@ -53,7 +53,7 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
     return NOC_ERR_ARG;
   if (mesh_w < 1 || mesh_h < 1 || (long)mesh_w * mesh_h > 65535 || l2_policy < 0 || l2_policy > 2)
     return NOC_ERR_ARG;
-  auto ways_ok = [](int w) { return w == 1 || w == 2 || w == 4 || w == 8 || w == 16; };
+  auto ways_ok = [](int w) { return w >= 1 && w <= MAX_WAYS; };
   if (c->l1_sets < 1 || !ways_ok(c->l1_ways) || c->l2_sets < 1 || !ways_ok(c->l2_ways) ||
       c->l1_miss_cycles < 0 || c->mem_latency < 1 || c->core_q < 1 || c->svc_q < 1 ||
       c->mem_q < 1 || c->core_q > 65535 || c->svc_q > 65535 || c->mem_q > 65535)

@@ -54,7 +54,7 @@ def test_no_gpu_calls_fail_cleanly_without_device(libnoc):
                               C.byref(noc.traffic_struct(p)), 1, C.byref(h))
     assert rc == 0
     assert noc.lib().noc_required_bytes(h) > 8 * 8 * 512 * 8 * 4
-    bad = noc.cache_struct(dict(p, l1_ways=3))
+    bad = noc.cache_struct(dict(p, l1_ways=17))
     h2 = C.c_void_p()
     assert noc.lib().noc_create(8, 8, C.byref(bad), 0, C.byref(noc.traffic_struct(p)), 1,
                                 C.byref(h2)) == 1
@@ -65,3 +65,49 @@ def test_no_gpu_calls_fail_cleanly_without_device(libnoc):
 def test_stat_names_agree_with_oracle(oracle_mod):
     from paper_1508_03235_b300 import noc
     assert set(oracle_mod.STAT_NAMES) | {"cycle", "in_flight"} == set(noc.STATS_FIELDS)
+
+
+INVALID = {
+    "l2_ways32": dict(l2_ways=32), "l1_sets0": dict(l1_sets=0), "mesh0": dict(mesh_w=0),
+    "mesh_too_big": dict(mesh_w=300, mesh_h=300), "policy3": dict(policy=3),
+    "mem_latency0": dict(mem_latency=0), "svc_q0": dict(svc_q=0), "core_q0": dict(core_q=0),
+    "mem_q0": dict(mem_q=0), "l1_miss_neg": dict(l1_miss_cycles=-1), "packet2": dict(packet_mode=2),
+    "rob0": dict(packet_mode=1, rob_entries=0), "rob65": dict(packet_mode=1, rob_entries=65),
+    "packets_small_svc_q": dict(packet_mode=1, svc_q=8), "dir_tile_off_mesh": dict(dir_central=1, dir_tile=64),
+    "dir2": dict(dir_central=2), "write_back2": dict(l1_write_back=2), "age2": dict(age_mode=2),
+    "period_neg": dict(period=-1), "write_frac_big": dict(write_q16=70000),
+    "mig_window31": dict(policy=2, mig_window=31), "mig_threshold0": dict(policy=2, mig_threshold=0),
+    "fwd0": dict(policy=2, fwd_entries=0), "hot_side_big": dict(hot_side=9), "mode3": dict(mode=3),
+    "priv_lines0": dict(priv_lines=0),
+}
+VALID = {
+    "mesh8": {}, "odd_ways": dict(l1_ways=3, l2_ways=6), "ways16": dict(l1_ways=16, l2_ways=16),
+    "packets": dict(packet_mode=1), "dir_node": dict(policy=1, dir_central=1, dir_tile=63),
+    "every_option": dict(policy=2, packet_mode=1, dir_central=1, dir_tile=5, l1_write_back=1,
+                         age_mode=1),
+    "window_unused": dict(policy=0, mig_window=31),
+}
+
+
+@pytest.mark.parametrize("name", sorted(INVALID) + sorted(VALID))
+def test_library_and_oracle_accept_the_same_configurations(libnoc, oracle_mod, name):
+    """noc_create (host-only, no GPU needed) and the oracle agree on which
+    configurations are valid; a rejected one is NOC_ERR_ARG with a message."""
+    from paper_1508_03235_b300 import inputs as I
+    from paper_1508_03235_b300 import noc
+    p = dict(I.MESH_8["params"])
+    p.update(INVALID.get(name) or VALID.get(name))
+    h = C.c_void_p()
+    rc = noc.lib().noc_create(p["mesh_w"], p["mesh_h"], C.byref(noc.cache_struct(p)), p["policy"],
+                              C.byref(noc.traffic_struct(p)), 1, C.byref(h))
+    if rc == 0:
+        noc.lib().noc_destroy(h)
+    try:
+        oracle_mod.OracleSim(p).close()
+        oracle_ok = True
+    except ValueError:
+        oracle_ok = False
+    want = name in VALID
+    assert (rc == 0) == want and oracle_ok == want, (rc, oracle_ok)
+    if not want:
+        assert rc == 1 and noc.lib().noc_last_error()

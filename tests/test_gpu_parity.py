@@ -294,3 +294,22 @@ def test_general_way_bounds(noc, oracle_mod):
         g, o = pair(noc, oracle_mod, p, tiling=(2, 2))
         run_traced(g, o, 1500)
         assert_same(g, o)
+
+
+@pytest.mark.parametrize("policy,l1_ways,l2_ways", [(0, 3, 6), (2, 5, 12), (1, 1, 7)])
+def test_ways_that_are_not_powers_of_two(noc, oracle_mod, policy, l1_ways, l2_ways):
+    """Any way count 1..16 (the cache-set code ranks ways up to ways - 1, so
+    nothing assumes a power of two); these run on the general and base kernels
+    and their way-bound classes."""
+    cache = I.cache_cfg(l1_kb=3 * l1_ways, l1_ways=l1_ways, l2_kb=6 * l2_ways, l2_ways=l2_ways,
+                        mig_window=4, mig_threshold=2, svc_q=512)
+    traf = I.traffic(period=3, priv=0.4, shared=0.5, priv_kb=4, shared_mb=0)
+    traf.update(shared_lines=400)
+    p = I.sim_params(9, 7, policy=policy, cache=cache, traf=traf, seed=3)
+    g, o = pair(noc, oracle_mod, p, tiling=(3, 2))
+    run_traced(g, o, 2000)
+    assert_same(g, o)
+    g.step(1500)
+    o.step(1500)
+    assert_same(g, o)
+    assert g.stats()["l1_hit"] > 0 and g.stats()["l2_hit"] > 0
