@@ -1217,14 +1217,20 @@ __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t 
   for (int d = 0; d < 4; ++d)
     if ((rm >> d) & 1u) rp |= prod[d] << (8u * rk[d]);
   const uint32_t n_rem = __popc(rm);
+  // branch-free over the four ranks: a rank past the remaining arrivals picks
+  // nothing and counts no deflection (lanes differ in how many they have)
   uint32_t freem = exists, defl = 0, pkp = 0;
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
-    if ((uint32_t)r < n_rem) {
-      const uint32_t pick = pick_port((rp >> (8 * r)) & 0xFFu, freem, defl);
-      freem &= ~pick;
-      pkp |= pick << (4 * r);
-    }
+  for (int r = 0; r < 4; ++r) {
+    const uint32_t on = (uint32_t)r < n_rem ? ~0u : 0u;
+    const uint32_t prod_r = (rp >> (8 * r)) & 0xFFu, xb = prod_r & 15u, yb = prod_r >> 4;
+    const uint32_t low = freem & (0u - freem);
+    const bool px = (freem & xb) != 0, py = (freem & yb) != 0;
+    const uint32_t pick = (px ? xb : (py ? yb : low)) & on;
+    defl += (!px && !py) ? (on & 1u) : 0u;
+    freem &= ~pick;
+    pkp |= pick << (4 * r);
+  }
   uint32_t pk[4];
 #pragma unroll
   for (int d = 0; d < 4; ++d) pk[d] = (pkp >> (4u * rk[d])) & 15u;
