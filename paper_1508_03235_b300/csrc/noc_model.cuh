@@ -1234,9 +1234,12 @@ __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t 
   uint32_t pk[4];
 #pragma unroll
   for (int d = 0; d < 4; ++d) pk[d] = (pkp >> (4u * rk[d])) & 15u;
-  uint32_t pki = 0;
-  if (has_inj) {
-    pki = pick_port(ic.prod, freem, defl);
+  uint32_t pki;
+  {
+    const uint32_t on = has_inj ? ~0u : 0u, xb = ic.prod & 15u, yb = ic.prod >> 4;
+    const bool px = (freem & xb) != 0, py = (freem & yb) != 0;
+    pki = (px ? xb : (py ? yb : freem & (0u - freem))) & on;
+    defl += (!px && !py) ? (on & 1u) : 0u;
     freem &= ~pki;
   }
   T.defl += defl;
