@@ -1115,14 +1115,16 @@ __device__ __forceinline__ uint32_t prod_ports(const Params& P, uint32_t dst, ui
   const uint32_t yb = dy_ > y ? (1u << P_S) : (dy_ < y ? (1u << P_N) : 0u);
   return xb | (yb << 4);
 }
-// first free port of [X-productive, Y-productive, N, S, E, W]; counts a
-// deflection when neither productive port is free
-__device__ __forceinline__ uint32_t pick_port(uint32_t prod, uint32_t freem, uint32_t& defl) {
+// first free port of [X-productive, Y-productive, N, S, E, W] for a flit
+// whose productive ports are `prod` (prod_ports), counting a deflection when
+// neither productive port is free; with `on` = 0 (no such flit) nothing is
+// picked or counted.  Branch-free: lanes differ in how many flits they place.
+__device__ __forceinline__ uint32_t pick_port(uint32_t prod, uint32_t freem, uint32_t on, uint32_t& defl) {
   const uint32_t xb = prod & 15u, yb = prod >> 4;
   const uint32_t low = freem & (0u - freem);
   const bool px = (freem & xb) != 0, py = (freem & yb) != 0;
-  defl += (!px && !py) ? 1u : 0u;
-  return px ? xb : (py ? yb : low);
+  defl += (!px && !py) ? (on & 1u) : 0u;
+  return (px ? xb : (py ? yb : low)) & on;
 }
 
 // The flit a tile would inject this cycle if an input port is free (the
@@ -1217,31 +1219,19 @@ __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t 
   for (int d = 0; d < 4; ++d)
     if ((rm >> d) & 1u) rp |= prod[d] << (8u * rk[d]);
   const uint32_t n_rem = __popc(rm);
-  // branch-free over the four ranks: a rank past the remaining arrivals picks
-  // nothing and counts no deflection (lanes differ in how many they have)
+  // over all four ranks: a rank past the remaining arrivals picks nothing
   uint32_t freem = exists, defl = 0, pkp = 0;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    const uint32_t on = (uint32_t)r < n_rem ? ~0u : 0u;
-    const uint32_t prod_r = (rp >> (8 * r)) & 0xFFu, xb = prod_r & 15u, yb = prod_r >> 4;
-    const uint32_t low = freem & (0u - freem);
-    const bool px = (freem & xb) != 0, py = (freem & yb) != 0;
-    const uint32_t pick = (px ? xb : (py ? yb : low)) & on;
-    defl += (!px && !py) ? (on & 1u) : 0u;
+    const uint32_t pick = pick_port((rp >> (8 * r)) & 0xFFu, freem, (uint32_t)r < n_rem ? ~0u : 0u, defl);
     freem &= ~pick;
     pkp |= pick << (4 * r);
   }
   uint32_t pk[4];
 #pragma unroll
   for (int d = 0; d < 4; ++d) pk[d] = (pkp >> (4u * rk[d])) & 15u;
-  uint32_t pki;
-  {
-    const uint32_t on = has_inj ? ~0u : 0u, xb = ic.prod & 15u, yb = ic.prod >> 4;
-    const bool px = (freem & xb) != 0, py = (freem & yb) != 0;
-    pki = (px ? xb : (py ? yb : freem & (0u - freem))) & on;
-    defl += (!px && !py) ? (on & 1u) : 0u;
-    freem &= ~pki;
-  }
+  const uint32_t pki = pick_port(ic.prod, freem, has_inj ? ~0u : 0u, defl);
+  freem &= ~pki;
   T.defl += defl;
   // every slot cleared, then each flit stored to the slot of its port
   const uint4 z = make_uint4(0, 0, 0, 0);
