@@ -49,6 +49,20 @@ def candidates(W: int, H: int, targets=(384, 320, 256, 192, 160, 128, 96, 64, 32
     return out
 
 
+def broad_candidates(W: int, H: int, lo: int = 48, hi: int = MAX_THREADS):
+    """Every rectangle shape of lo..hi tiles the mesh can be cut into, each
+    with the fewest CTAs that give it, largest rectangles first."""
+    best = {}
+    for gy in range(1, H + 1):
+        for gx in range(1, W + 1):
+            bw, bh = -(-W // gx), -(-H // gy)
+            if not lo <= bw * bh <= hi:
+                continue
+            if (bw, bh) not in best or gx * gy < best[(bw, bh)][0] * best[(bw, bh)][1]:
+                best[(bw, bh)] = (gx, gy)
+    return sorted(best.values(), key=lambda g: (-(-(-W // g[0]) * -(-H // g[1])), g))
+
+
 def load_cache() -> dict:
     if os.path.exists(CACHE):
         with open(CACHE) as f:
@@ -68,17 +82,21 @@ def cached_thread_map(params: dict):
 
 
 def tune(params: dict, cycles: int = 2000, warm: int = 200, max_cands: int = 10,
-         maps=(0, 1, 2), reps: int = 2, save: bool = True, verbose: bool = False):
+         maps=(0, 1, 2), reps: int = 2, broad: bool = False, save: bool = True,
+         verbose: bool = False):
     """Time candidate tilings in each tile-to-thread order (the best of `reps`
     timed runs each); return (best (gx, gy, order), {(gx, gy, order): us per
-    cycle})."""
+    cycle}).  With `broad`, every rectangle shape of broad_candidates() is
+    tried instead of one grid per size target."""
     import torch
 
     from . import noc
 
     sim = noc.Sim(params)
     timings = {}
-    for gx, gy in candidates(params["mesh_w"], params["mesh_h"])[:max_cands]:
+    cands = (broad_candidates(params["mesh_w"], params["mesh_h"]) if broad
+             else candidates(params["mesh_w"], params["mesh_h"])[:max_cands])
+    for gx, gy in cands:
         for m in maps:
             try:
                 sim.set_tiling(gx, gy)
@@ -116,8 +134,12 @@ if __name__ == "__main__":
     sys.path.insert(0, os.path.dirname(HERE))
     from paper_1508_03235_b300 import inputs as I
     from paper_1508_03235_b300.tune import tune as _tune
+    broad = "--broad" in sys.argv
     for name, p in (("mesh208", I.mesh_208(10)), ("mesh64", I.mesh_64(1)),
                     ("mesh8", I.MESH_8["params"])):
         print(name, flush=True)
-        b, _ = _tune(p, verbose=True)
+        b, t = _tune(p, broad=broad, verbose=not broad)
+        if broad:
+            for k in sorted(t, key=t.get)[:10]:
+                print(f"  {k[0]}x{k[1]} order {k[2]}: {t[k]:.3f} us/cycle", flush=True)
         print(f"  best {b}", flush=True)
