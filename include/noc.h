@@ -252,6 +252,11 @@ int noc_batch_set_rect(noc_batch* batch, int side);
 /* Tile-to-thread order of every instance (as noc_set_thread_map; default 0):
  * a tuning knob only. */
 int noc_batch_set_thread_map(noc_batch* batch, int map);
+/* enable != 0: cut each instance into strips of at most side * side tiles --
+ * as wide as the mesh (or side * side) with as many rows as then fit --
+ * instead of side x side squares, so that east-west links stay inside a CTA.
+ * A tuning knob only (default 0). */
+int noc_batch_set_strips(noc_batch* batch, int enable);
 /* Collect each instance's full state hash after its wave (default on). */
 int noc_batch_set_collect_hash(noc_batch* batch, int enable);
 /* Run every instance to its cycle count.  Synchronous.  Returns the first

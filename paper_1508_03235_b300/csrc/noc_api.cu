@@ -897,6 +897,7 @@ struct noc_batch {
   bool pool_owned = false;
   cudaStream_t stream = nullptr;
   int rect = 8;
+  bool strips = false;   // cut instances into strips of rect * rect tiles, not squares
   bool collect_hash = true;
   int waves = 0;
   int64_t launches = 0;
@@ -994,6 +995,12 @@ int noc_batch_set_rect(noc_batch* b, int side) {
   return NOC_OK;
 }
 
+int noc_batch_set_strips(noc_batch* b, int enable) {
+  if (!b) return fail(NOC_ERR_ARG, "null handle");
+  b->strips = enable != 0;
+  return NOC_OK;
+}
+
 int noc_batch_set_thread_map(noc_batch* b, int map) {
   if (!b || map < 0 || map > 2) return fail(NOC_ERR_ARG, "thread map 0, 1 or 2");
   for (noc_sim* s : b->sims) s->thread_map = map;
@@ -1016,7 +1023,14 @@ static int run_batch_group(noc_batch* b, const std::vector<int>& members, int th
   std::vector<int> by_size = members;
   for (int i : by_size) {
     noc_sim* s = b->sims[i];
-    int gx = (s->P.W + side - 1) / side, gy = (s->P.H + side - 1) / side;
+    // squares of side x side tiles, or strips of the same capacity: as wide as
+    // the mesh (or the capacity) and as many rows as then fit
+    int bw = side, bh = side;
+    if (b->strips) {
+      bw = std::min(s->P.W, side * side);
+      bh = std::max(1, side * side / bw);
+    }
+    int gx = (s->P.W + bw - 1) / bw, gy = (s->P.H + bh - 1) / bh;
     if (gx * gy > cap || gx * gy * FLAG_SLOTS > (int)s->n_flags)
       return fail(NOC_ERR_ARG, "instance %d needs %d CTAs, %d fit co-resident", i, gx * gy, cap);
     s->run_gx = gx;

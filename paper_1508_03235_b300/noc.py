@@ -338,6 +338,7 @@ def _batch_sigs(L):
         "noc_batch_set_stream": (i32, [vp, vp]),
         "noc_batch_set_rect": (i32, [vp, i32]),
         "noc_batch_set_thread_map": (i32, [vp, i32]),
+        "noc_batch_set_strips": (i32, [vp, i32]),
         "noc_batch_set_collect_hash": (i32, [vp, i32]),
         "noc_batch_run": (i32, [vp]),
         "noc_batch_waves": (i32, [vp]),
@@ -361,7 +362,7 @@ class Batch:
     that do not fit run in later waves."""
 
     def __init__(self, params_list, cycles, stream=None, rect=8, collect_hash=True,
-                 pool_bytes=None, thread_map=0):
+                 pool_bytes=None, thread_map=0, strips=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the batch engine needs a CUDA device")
@@ -393,6 +394,7 @@ class Batch:
         _check(L.noc_batch_set_stream(h, C.c_void_p(st.cuda_stream)))
         _check(L.noc_batch_set_rect(h, rect))
         _check(L.noc_batch_set_thread_map(h, thread_map))
+        _check(L.noc_batch_set_strips(h, 1 if strips else 0))
         _check(L.noc_batch_set_collect_hash(h, 1 if collect_hash else 0))
 
     def close(self):
