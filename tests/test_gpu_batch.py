@@ -56,10 +56,11 @@ def oracle_results(oracle_mod):
     return pts, cycles, res
 
 
-@pytest.mark.parametrize("rect", [8, 5, 19])
-def test_batch_matches_oracle(noc, oracle_results, rect):
+@pytest.mark.parametrize("rect,strips,tmap", [(8, False, 0), (5, False, 1), (19, False, 2),
+                                               (8, True, 2), (11, True, 0)])
+def test_batch_matches_oracle(noc, oracle_results, rect, strips, tmap):
     pts, cycles, res = oracle_results
-    b = noc.Batch(pts, cycles, rect=rect)
+    b = noc.Batch(pts, cycles, rect=rect, strips=strips, thread_map=tmap)
     b.run()
     assert b.waves == n_variant_groups(pts)     # the pool holds every group at once
     for i, (st, h, h0, h1) in enumerate(res):
