@@ -133,10 +133,10 @@ class MLP:
         p = self.packed.data_ptr()
         return C.c_void_p(p + (-p) % 16)
 
-    def infer(self, xb):
+    def infer(self, xb, out=None):
         """The whole network in one fused tcgen05 kernel (mlp_infer): xb BF16
-        [B, dims[0]] with B a multiple of 128 -> FP32 [B, dims[-1]], equal to
-        forward() on the tensor-core path."""
+        [B, dims[0]] with B a multiple of 128 -> FP32 [B, dims[-1]] (into `out`
+        if given), equal to forward() on the tensor-core path."""
         B = xb.shape[0]
         if self.packed is None or B < 128 or B % 128 or xb.dtype != self.torch.bfloat16:
             raise ValueError("mlp_infer takes BF16 batches of a multiple of 128 rows of a packable shape")
@@ -144,7 +144,8 @@ class MLP:
             _ok(_mlp_lib().mlp_pack(C.byref(self.shape), _p(self.params_bf16), self._packed(),
                                     self._stream()), "mlp_pack")
             self._packed_step = self.step
-        y = self.torch.empty(B, self.dims[-1], dtype=self.torch.float32, device="cuda")
+        y = out if out is not None else self.torch.empty(B, self.dims[-1], dtype=self.torch.float32,
+                                                         device="cuda")
         _ok(_mlp_lib().mlp_infer(C.byref(self.shape), self._packed(), _p(xb), B, _p(y),
                                  self._stream()), "mlp_infer")
         return y

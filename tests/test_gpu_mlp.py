@@ -226,7 +226,8 @@ def test_tcgen05_long_contraction(sur):
         assert np.abs(got - gW).max() < 2e-5 * np.abs(gW).max(), path
 
 
-@pytest.mark.parametrize("dims,B", [(None, 4096), (None, 128), ((64, 128, 256, 32), 384)])
+@pytest.mark.parametrize("dims,B", [(None, 4096), (None, 128), ((64, 128, 256, 32), 384),
+                                    ((16, 192, 64), 256)])
 def test_fused_inference_equals_layered_forward(sur, dims, B):
     """The one-kernel inference (weights packed into the operand layout and
     brought in by bulk copies, activations kept on chip, TMEM accumulators
