@@ -212,9 +212,19 @@ __global__ void __launch_bounds__(FT, 1)
         for (int j = 0; j < 16; ++j) v[j] = h[j];
         w = 16;
       }
+      // the biases of these columns in 16-byte pieces (the packed image puts
+      // each layer's biases on a 16-byte boundary and col is a multiple of 16)
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < w) v[j] += __bfloat162float(bias[col + j]);
+      for (int q = 0; q < 4; ++q) {
+        if (8 * q >= w) continue;
+        const uint4 b8 = *reinterpret_cast<const uint4*>(bias + col + 8 * q);
+        const uint32_t bw[4] = {b8.x, b8.y, b8.z, b8.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          v[8 * q + 2 * j] += __uint_as_float(bw[j] << 16);
+          v[8 * q + 2 * j + 1] += __uint_as_float(bw[j] & 0xFFFF0000u);
+        }
+      }
       if (last) {
         float4* p = reinterpret_cast<float4*>(y + (size_t)(m0 + r) * Ly.N + col);
 #pragma unroll

@@ -257,3 +257,32 @@ def test_fused_inference_equals_layered_forward(sur, dims, B):
     y = torch.empty(64, net.dims[-1], device="cuda")
     L = sur._mlp_lib()
     assert L.mlp_infer(C.byref(net.shape), net._packed(), sur._p(xb), 64, sur._p(y), net._stream()) == 1
+
+
+def test_fused_inference_replays_in_a_cuda_graph(sur):
+    """mlp_infer launched on the caller's stream captures into a CUDA graph:
+    a replay writes into the captured output buffer exactly what a direct
+    call gives, and a replay after the input buffer changes follows it."""
+    import torch
+    net = sur.MLP(seed=5, max_batch=4096)
+    xb = torch.rand(4096, sur.DIMS[0], device="cuda").to(torch.bfloat16)
+    y = torch.empty(4096, sur.DIMS[-1], device="cuda")
+    net.infer(xb, out=y)                       # packs the weights outside the capture
+    want = net.infer(xb).clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        net.infer(xb, out=y)
+        with torch.cuda.graph(g, stream=s):
+            net.infer(xb, out=y)
+    torch.cuda.current_stream().wait_stream(s)
+    y.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y, want)
+    xb.copy_(torch.rand(4096, sur.DIMS[0], device="cuda").to(torch.bfloat16))
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y, net.infer(xb))
+    assert sur.gemm_status() == 0
