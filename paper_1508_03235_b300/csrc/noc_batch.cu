@@ -2,6 +2,8 @@
 // per L1/L2 way bound, and twice more per bound specialised like the plain
 // cycle loop: -DNOC_BASE=1, and -DNOC_FIXED_POLICY=0 -DNOC_FIXED_MODE=0
 // -DNOC_EXACT_WAYS=1)
+// the batch's rectangles are small and mostly edge: one poll in flight
+#define NOC_POLL_STAGE 0
 #include "noc_kernel.cuh"
 
 #if !defined(NOC_W1) || !defined(NOC_W2)
@@ -70,21 +72,21 @@ __global__ void __launch_bounds__(MAX_THREADS, 1) batch_kernel(const __grid_cons
 cudaError_t NOC_NAME(launch_batch, NOC_W1, NOC_W2, NOC_SPEC)(const BatchArgs& B, int grid, int threads,
                                                             cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(NOC_BATCH_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)run_smem_bytes_impl(MAX_THREADS));
+                                       (int)run_smem_bytes_impl(MAX_THREADS, false));
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&B};
   return cudaLaunchCooperativeKernel((const void*)NOC_BATCH_KERNEL, dim3(grid), dim3(threads), args,
-                                     run_smem_bytes_impl(threads), s);
+                                     run_smem_bytes_impl(threads, false), s);
 }
 
 cudaError_t NOC_NAME(max_coresident_batch, NOC_W1, NOC_W2, NOC_SPEC)(int threads, int* out) {
   cudaError_t e = cudaFuncSetAttribute(NOC_BATCH_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)run_smem_bytes_impl(MAX_THREADS));
+                                       (int)run_smem_bytes_impl(MAX_THREADS, false));
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, NOC_BATCH_KERNEL, threads, run_smem_bytes_impl(threads));
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, NOC_BATCH_KERNEL, threads, run_smem_bytes_impl(threads, false));
   if (e != cudaSuccess) return e;
   *out = per * sms;
   return cudaSuccess;

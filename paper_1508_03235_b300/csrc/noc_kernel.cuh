@@ -152,9 +152,27 @@ static __device__ unsigned long long block_sum(unsigned long long v, unsigned lo
 // ---------------------------------------------------------------- cycle kernel
 constexpr int MAX_THREADS = 384;
 
-inline size_t run_smem_bytes_impl(int threads) {
+// The plain cycle loop polls the tagged slots of the links entering its
+// rectangle either with one poll in flight (plain loads; NOC_POLL_STAGE 0, the
+// batch kernel) or with two (NOC_POLL_STAGE 1, the single-simulation kernels):
+// each round copies the needed slots into a per-thread shared-memory stage
+// with cp.async while the previous copy is read, so a flit written by another
+// SM is seen about half a global round trip sooner.  Rectangles that are all
+// edge (two tiles thin) pay for the doubled polling; the tiling search weighs
+// both.
+#ifndef NOC_POLL_STAGE
+#define NOC_POLL_STAGE 1
+#endif
+
+// shared memory before the poll stage: links [2 parity][4 port][threads],
+// histograms, reduction words
+__host__ __device__ inline size_t run_smem_base_bytes(int threads) {
   return (size_t)threads * 8 * sizeof(uint4) + (2 * HIST_BINS + 2) * sizeof(uint32_t) +
          32 * sizeof(unsigned long long);
+}
+// the poll stage: [threads][2 buffers][4 ports][2 halves] tagged slots
+__host__ __device__ inline size_t run_smem_bytes_impl(int threads, bool stage = NOC_POLL_STAGE != 0) {
+  return run_smem_base_bytes(threads) + (stage ? (size_t)threads * 16 * sizeof(uint4) : 0);
 }
 
 inline int block_threads_impl(int W, int H, int gx, int gy) {
@@ -351,6 +369,24 @@ constexpr int WARPS_PER_CTA = MAX_THREADS / 32;
 __device__ __forceinline__ unsigned ld_volatile_shared(const unsigned* p) {
   return *reinterpret_cast<const volatile unsigned*>(p);
 }
+__device__ __forceinline__ uint4 ld_volatile_shared_v4(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(p)))
+               : "memory");
+  return v;
+}
+// 16 bytes global -> shared through L2 (cp.async.cg), and the group controls
+__device__ __forceinline__ void cp_async16_cg(uint4* smem, const uint4* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most the newest group is still in flight
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // One CTA runs rectangle b of one simulation for A.n cycles, with no CTA-wide
 // barrier per cycle.  Inside the rectangle every warp publishes the cycle it
@@ -370,6 +406,10 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
   uint4* sl = reinterpret_cast<uint4*>(smem_raw);  // [2 parity][4 port][nt]
   uint32_t* sh_hist = reinterpret_cast<uint32_t*>(sl + 8 * nt);
   __shared__ unsigned wflag[WARPS_PER_CTA];
+#if NOC_POLL_STAGE
+  // this thread's poll stage: [2 buffers][4 ports][2 halves]
+  uint4* stg = reinterpret_cast<uint4*>(smem_raw + run_smem_base_bytes(nt)) + (size_t)threadIdx.x * 16;
+#endif
 
   const int cx = b % A.gx, cy = b / A.gx;
   const int X0 = cx * P.W / A.gx, X1 = (cx + 1) * P.W / A.gx;
@@ -455,13 +495,46 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
       // entry: the wait's limit then runs from that check
       unsigned long long start = 0;
       bool aborted = false;
+#if NOC_POLL_STAGE
+      // two polls in flight: each round issues the next copy of the needed
+      // slots into one stage buffer and then reads the copy in the other.  A
+      // copy still in flight when the wait ends lands in the buffer that the
+      // next cycle's first round writes; it holds the other parity's tags,
+      // which never match, and cp.async.wait_group retires it first.
+#pragma unroll
+      for (int d = 0; d < 4; ++d)
+        if (need & (1u << d)) {
+          cp_async16_cg(stg + d * 2, gt + rin[d]);
+          cp_async16_cg(stg + d * 2 + 1, gt + rin[d] + 1);
+        }
+      cp_async_commit();
+#endif
       for (unsigned it = 0;; ++it) {
+#if NOC_POLL_STAGE
+        const uint32_t bo = (it & 1u) * 8, bn = 8 - bo;
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+          if (need & (1u << d)) {
+            cp_async16_cg(stg + bn + d * 2, gt + rin[d]);
+            cp_async16_cg(stg + bn + d * 2 + 1, gt + rin[d] + 1);
+          }
+        cp_async_commit();
+        cp_async_wait1();
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+          if (need & (1u << d)) {
+            const uint4 a = ld_volatile_shared_v4(stg + bo + d * 2);
+            const uint4 c = ld_volatile_shared_v4(stg + bo + d * 2 + 1);
+            if (tag_decode(a, c, tag, in[d])) need &= ~(1u << d);
+          }
+#else
 #pragma unroll
         for (int d = 0; d < 4; ++d)
           if (need & (1u << d)) {
             const uint4 a = ld_relaxed_v4(gt + rin[d]), c = ld_relaxed_v4(gt + rin[d] + 1);
             if (tag_decode(a, c, tag, in[d])) need &= ~(1u << d);
           }
+#endif
         const bool ok = need == 0 && (!poll_local || (int)(ld_volatile_shared(&wflag[lane]) - t) >= 0);
         if (__all_sync(0xFFFFFFFFu, ok)) break;
         if ((it & 31u) == 31u) {
