@@ -158,8 +158,9 @@ constexpr int MAX_THREADS = 384;
 // each round copies the needed slots into a per-thread shared-memory stage
 // with cp.async while the previous copy is read, so a flit written by another
 // SM is seen about half a global round trip sooner.  Rectangles that are all
-// edge (two tiles thin) pay for the doubled polling; the tiling search weighs
-// both.
+// edge (two tiles thin) pay for the doubled polling, so the batch kernel, whose
+// 8x8 rectangles are mostly edge, keeps one poll.  The stage starts on a
+// 16-byte boundary, as cp.async needs: the bytes before it are a multiple of 16.
 #ifndef NOC_POLL_STAGE
 #define NOC_POLL_STAGE 1
 #endif
