@@ -257,6 +257,11 @@ int noc_batch_set_thread_map(noc_batch* batch, int map);
  * instead of side x side squares, so that east-west links stay inside a CTA.
  * A tuning knob only (default 0). */
 int noc_batch_set_strips(noc_batch* batch, int enable);
+/* Layout of instance i (i = -1: every instance): CTA rectangle side 1..19,
+ * strips on or off and tile-to-thread order, as the three setters above.
+ * Tuning knobs only; instances of one kernel-variant group with different
+ * sides run in separate launches. */
+int noc_batch_set_layout(noc_batch* batch, int i, int side, int strips, int thread_map);
 /* Collect each instance's full state hash after its wave (default on). */
 int noc_batch_set_collect_hash(noc_batch* batch, int enable);
 /* Run every instance to its cycle count.  Synchronous.  Returns the first
@@ -270,6 +275,14 @@ int noc_batch_stats(const noc_batch* batch, int i, noc_stats_t* out);
 int noc_batch_state_hash(const noc_batch* batch, int i, uint64_t* out);
 int noc_batch_latency_hist(const noc_batch* batch, int i, int which, uint64_t* bins, int nbins);
 int64_t noc_batch_kernel_launches(const noc_batch* batch);
+/* The build of the batch kernel that runs instance i (kind and way bounds as
+ * in noc_last_variant); fixed by the descriptors when the batch is created. */
+int noc_batch_variant(const noc_batch* batch, int i, int* kind, int* l1_bound, int* l2_bound);
+/* Kernel-variant group of instance i, 0..4 (-1 for a bad argument): 0, 1, 2 =
+ * the interleaved build of way class (4, 8), (4, 16), (16, 16); 3 = the base
+ * build; 4 = the general build.  Instances of one group and one rectangle
+ * side share work-queue launches; the autotuner picks a layout per group. */
+int noc_batch_group(const noc_batch* batch, int i);
 
 /* Allocation-free run.  No counterpart in the paper: this entry point serves
  * callers that must not allocate device memory -- a process whose HBM is
@@ -282,13 +295,16 @@ int64_t noc_batch_kernel_launches(const noc_batch* batch);
  * loaded on until the process exits; it calls no allocator.
  *   dev_stats_out: DEVICE memory, one noc_stats_t, written by the run.
  *   cuda_stream:   stream to run on (NULL = default); the call waits for it.
- * Returns NOC_ERR_ARG for an invalid configuration, for trace mode, or when
- * the state would exceed NOC_STATIC_SCRATCH_BYTES; a simulation error code
- * (e.g. NOC_ERR_QUEUE_OVERFLOW) if the run hit one; NOC_ERR_CUDA otherwise.
+ * Returns NOC_ERR_ARG for any configuration noc_create rejects, for trace
+ * mode, or when the state would exceed NOC_STATIC_SCRATCH_BYTES; a simulation
+ * error code (e.g. NOC_ERR_QUEUE_OVERFLOW) if the run hit one; NOC_ERR_CUDA
+ * when a CUDA call fails.  Every failure sets noc_last_error().
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.  Every
- * call reuses the same array and clears it first; calls that overlap on the
- * GPU (other streams or threads) race on it and must be serialised. */
+ * call reuses the same array and clears it first.  Calls in one process are
+ * serialised by an internal lock, and each call returns only after its
+ * stream has finished, so they never overlap on the GPU; each process has its
+ * own copy of the array.  cuda_stream must belong to the current device. */
 #define NOC_STATIC_SCRATCH_BYTES (16u << 20)
 int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* cache, int l2_policy,
                    const noc_traffic* traffic, uint64_t seed, int64_t n_cycles,
@@ -296,6 +312,21 @@ int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* cache, int l2_po
 
 /* Number of this library's kernels launched through this handle. */
 int64_t noc_kernel_launches(const noc_sim* sim);
+
+/* Which build of the cycle kernel served the handle's last launch.  Results
+ * never depend on it; it lets a caller (and the tests) see that a
+ * configuration ran on the specialised code it qualifies for.
+ *   *loop:  0 = the plain loop (per-warp neighbour waits; noc_step),
+ *           1 = the traced / draining loop (hash trace on, or noc_drain);
+ *   *kind:  0 = general (every policy, mode and option compiled in),
+ *           1 = base (every policy and mode; the packet, write-back,
+ *               directory-node and deflection-count-age options compiled out),
+ *           2 = interleaved L2 in cache mode only, with exactly the way counts
+ *               of its bounds;
+ *   *l1_bound, *l2_bound: the compile-time way bounds, (4, 8), (4, 16) or
+ *           (16, 16).
+ * Any output pointer may be NULL.  NOC_ERR_STATE before the first launch. */
+int noc_last_variant(const noc_sim* sim, int* loop, int* kind, int* l1_bound, int* l2_bound);
 
 /* Device time of the cycle kernel alone.  With enable != 0, every later
  * cycle-kernel launch through this handle is bracketed by a pair of CUDA

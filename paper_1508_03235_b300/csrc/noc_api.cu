@@ -16,7 +16,7 @@
 
 using namespace noc;
 
-namespace {
+namespace noc {
 
 thread_local std::string g_last_error;
 
@@ -29,6 +29,92 @@ int fail(int code, const char* fmt, ...) {
   g_last_error = buf;
   return code;
 }
+
+int configure(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, const noc_traffic* tr,
+              uint64_t seed, Params& P) {
+  if (!c || !tr) return fail(NOC_ERR_ARG, "null argument");
+  if (mesh_w < 1 || mesh_h < 1 || (long)mesh_w * mesh_h > 65535)
+    return fail(NOC_ERR_ARG, "mesh %dx%d: need 1..65535 tiles", mesh_w, mesh_h);
+  if (l2_policy < 0 || l2_policy > 2) return fail(NOC_ERR_ARG, "l2_policy %d", l2_policy);
+  if (c->l1_sets < 1 || c->l1_ways < 1 || c->l1_ways > MAX_WAYS || c->l2_sets < 1 || c->l2_ways < 1 ||
+      c->l2_ways > MAX_WAYS)
+    return fail(NOC_ERR_ARG, "cache geometry: sets >= 1, ways 1..16");
+  if (c->l1_miss_cycles < 0 || c->mem_latency < 1) return fail(NOC_ERR_ARG, "latencies");
+  if (c->core_q < 1 || c->svc_q < 1 || c->mem_q < 1 || c->core_q > 65535 || c->svc_q > 65535 ||
+      c->mem_q > 65535)
+    return fail(NOC_ERR_ARG, "queue capacities must be 1..65535");
+  if (l2_policy == NOC_L2_LSPD_MIGRATE &&
+      (c->mig_window < 1 || c->mig_window > HIST_MAX || c->mig_threshold < 1 ||
+       c->fwd_entries < 1 || c->fwd_entries > 65535))
+    return fail(NOC_ERR_ARG, "migration: window 1..30, threshold >= 1, forward entries >= 1");
+  if (c->packet_mode < 0 || c->packet_mode > 1 ||
+      (c->packet_mode && (c->rob_entries < 1 || c->rob_entries > 64 || c->svc_q < 16)))
+    return fail(NOC_ERR_ARG, "packets: mode 0/1, reorder entries 1..64, svc_q >= 16");
+  if (c->dir_central < 0 || c->dir_central > 1 ||
+      (c->dir_central && (c->dir_tile < 0 || (long)c->dir_tile >= (long)mesh_w * mesh_h)))
+    return fail(NOC_ERR_ARG, "directory node: dir_central 0/1, dir_tile a tile of the mesh");
+  if (c->l1_write_back < 0 || c->l1_write_back > 1) return fail(NOC_ERR_ARG, "l1_write_back 0/1");
+  if (c->age_mode < 0 || c->age_mode > 1) return fail(NOC_ERR_ARG, "age_mode 0/1");
+  if (tr->mode < 0 || tr->mode > 2 || tr->period < 0) return fail(NOC_ERR_ARG, "traffic mode/period");
+  if (tr->write_q16 > 65536 || tr->priv_q16 + (uint64_t)tr->shared_q16 > 65536 || tr->hot_q16 > 65536)
+    return fail(NOC_ERR_ARG, "q16 fractions out of range");
+  if (tr->mode == NOC_MODE_CACHE) {
+    if (tr->priv_q16 > 0 && tr->priv_lines < 1) return fail(NOC_ERR_ARG, "priv_lines");
+    if (tr->shared_q16 > 0 && tr->shared_lines < 1) return fail(NOC_ERR_ARG, "shared_lines");
+    if (tr->priv_q16 + tr->shared_q16 < 65536 && tr->remote_lines < 1)
+      return fail(NOC_ERR_ARG, "remote_lines");
+  }
+  if (tr->hot_side < 0 || tr->hot_side > mesh_w || tr->hot_side > mesh_h)
+    return fail(NOC_ERR_ARG, "hot_side");
+  const uint64_t N = (uint64_t)mesh_w * mesh_h;
+  const uint64_t total = (uint64_t)tr->remote_lines + tr->shared_lines + (uint64_t)tr->priv_lines * N;
+  if (total >= (1ull << 26)) return fail(NOC_ERR_ARG, "address space above 2^26 lines");
+
+  memset(&P, 0, sizeof P);
+  P.W = mesh_w;
+  P.H = mesh_h;
+  P.N = (int)N;
+  P.policy = l2_policy;
+  P.mode = tr->mode;
+  P.period = tr->period;
+  P.l1_sets = c->l1_sets;
+  P.l1_ways = c->l1_ways;
+  P.l2_sets = c->l2_sets;
+  P.l2_ways = c->l2_ways;
+  P.l1_miss = c->l1_miss_cycles;
+  P.mem_lat = c->mem_latency;
+  P.mig_window = c->mig_window;
+  P.mig_threshold = c->mig_threshold;
+  P.core_q = c->core_q;
+  P.svc_q = c->svc_q;
+  P.mem_q = c->mem_q;
+  P.fwd_cap = c->fwd_entries > 0 ? c->fwd_entries : 1;
+  P.packet_mode = c->packet_mode;
+  P.rob_entries = c->packet_mode ? c->rob_entries : 0;
+  P.dir_central = c->dir_central;
+  P.dir_tile = c->dir_central ? c->dir_tile : 0;
+  P.l1_write_back = c->l1_write_back;
+  P.age_mode = c->age_mode;
+  P.write_q16 = tr->write_q16;
+  P.priv_q16 = tr->priv_q16;
+  P.shared_q16 = tr->shared_q16;
+  P.hot_q16 = tr->hot_q16;
+  P.hot_side = tr->hot_side;
+  P.hot_x0 = mesh_w / 2 - tr->hot_side / 2;
+  P.hot_y0 = mesh_h / 2 - tr->hot_side / 2;
+  P.priv_lines = tr->priv_lines;
+  P.shared_lines = tr->shared_lines;
+  P.remote_lines = tr->remote_lines;
+  P.total_lines = (uint32_t)total;
+  set_divisors(P);
+  P.seed = seed;
+  P.stream = tr->stream;
+  return NOC_OK;
+}
+
+}  // namespace noc
+
+namespace {
 
 int cuda_fail(cudaError_t e, const char* what) {
   return fail(NOC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -88,6 +174,7 @@ struct noc_sim {
   int silent_cta = -1;
   int thread_map = 0;     // tile-to-thread order inside a CTA rectangle
   int64_t launches = 0;
+  int last_variant = -1;  // run_variant() of the last cycle-kernel launch
   // cycle-kernel timing: event pairs [2k, 2k + 1] around launch k
   bool time_kernels = false;
   std::vector<cudaEvent_t> tev;
@@ -351,6 +438,7 @@ int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
     }
     CU(launch_run(s->P, A, s->stream), "cycle kernel launch");
     s->launches++;
+    s->last_variant = run_variant(s->P, A);
     if (s->time_kernels) {
       CU(cudaEventRecord(s->tev[s->tev_used + 1], s->stream), "event record");
       s->tev_used += 2;
@@ -384,89 +472,16 @@ int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, co
                uint64_t seed, noc_sim** out) {
   if (!c || !tr || !out) return fail(NOC_ERR_ARG, "null argument");
   *out = nullptr;
-  if (mesh_w < 1 || mesh_h < 1 || (long)mesh_w * mesh_h > 65535)
-    return fail(NOC_ERR_ARG, "mesh %dx%d: need 1..65535 tiles", mesh_w, mesh_h);
-  if (l2_policy < 0 || l2_policy > 2) return fail(NOC_ERR_ARG, "l2_policy %d", l2_policy);
-  if (c->l1_sets < 1 || c->l1_ways < 1 || c->l1_ways > MAX_WAYS || c->l2_sets < 1 || c->l2_ways < 1 ||
-      c->l2_ways > MAX_WAYS)
-    return fail(NOC_ERR_ARG, "cache geometry: sets >= 1, ways 1..16");
-  if (c->l1_miss_cycles < 0 || c->mem_latency < 1) return fail(NOC_ERR_ARG, "latencies");
-  if (c->core_q < 1 || c->svc_q < 1 || c->mem_q < 1 || c->core_q > 65535 || c->svc_q > 65535 ||
-      c->mem_q > 65535)
-    return fail(NOC_ERR_ARG, "queue capacities must be 1..65535");
-  if (l2_policy == NOC_L2_LSPD_MIGRATE &&
-      (c->mig_window < 1 || c->mig_window > HIST_MAX || c->mig_threshold < 1 ||
-       c->fwd_entries < 1 || c->fwd_entries > 65535))
-    return fail(NOC_ERR_ARG, "migration: window 1..30, threshold >= 1, forward entries >= 1");
-  if (c->packet_mode < 0 || c->packet_mode > 1 ||
-      (c->packet_mode && (c->rob_entries < 1 || c->rob_entries > 64 || c->svc_q < 16)))
-    return fail(NOC_ERR_ARG, "packets: mode 0/1, reorder entries 1..64, svc_q >= 16");
-  if (c->dir_central < 0 || c->dir_central > 1 ||
-      (c->dir_central && (c->dir_tile < 0 || (long)c->dir_tile >= (long)mesh_w * mesh_h)))
-    return fail(NOC_ERR_ARG, "directory node: dir_central 0/1, dir_tile a tile of the mesh");
-  if (c->l1_write_back < 0 || c->l1_write_back > 1) return fail(NOC_ERR_ARG, "l1_write_back 0/1");
-  if (c->age_mode < 0 || c->age_mode > 1) return fail(NOC_ERR_ARG, "age_mode 0/1");
-  if (tr->mode < 0 || tr->mode > 2 || tr->period < 0) return fail(NOC_ERR_ARG, "traffic mode/period");
-  if (tr->write_q16 > 65536 || tr->priv_q16 + (uint64_t)tr->shared_q16 > 65536 || tr->hot_q16 > 65536)
-    return fail(NOC_ERR_ARG, "q16 fractions out of range");
-  if (tr->mode == NOC_MODE_CACHE) {
-    if (tr->priv_q16 > 0 && tr->priv_lines < 1) return fail(NOC_ERR_ARG, "priv_lines");
-    if (tr->shared_q16 > 0 && tr->shared_lines < 1) return fail(NOC_ERR_ARG, "shared_lines");
-    if (tr->priv_q16 + tr->shared_q16 < 65536 && tr->remote_lines < 1)
-      return fail(NOC_ERR_ARG, "remote_lines");
-  }
-  if (tr->hot_side < 0 || tr->hot_side > mesh_w || tr->hot_side > mesh_h)
-    return fail(NOC_ERR_ARG, "hot_side");
-  const uint64_t N = (uint64_t)mesh_w * mesh_h;
-  const uint64_t total = (uint64_t)tr->remote_lines + tr->shared_lines + (uint64_t)tr->priv_lines * N;
-  if (total >= (1ull << 26)) return fail(NOC_ERR_ARG, "address space above 2^26 lines");
-
+  Params P;
+  int rc = configure(mesh_w, mesh_h, c, l2_policy, tr, seed, P);
+  if (rc) return rc;
   noc_sim* s = new (std::nothrow) noc_sim();
   if (!s) return fail(NOC_ERR_OOM, "host allocation");
   s->cache = *c;
   s->traf = *tr;
   s->seed = seed;
-  Params& P = s->P;
-  memset(&P, 0, sizeof P);
-  P.W = mesh_w;
-  P.H = mesh_h;
-  P.N = (int)N;
-  P.policy = l2_policy;
-  P.mode = tr->mode;
-  P.period = tr->period;
-  P.l1_sets = c->l1_sets;
-  P.l1_ways = c->l1_ways;
-  P.l2_sets = c->l2_sets;
-  P.l2_ways = c->l2_ways;
-  P.l1_miss = c->l1_miss_cycles;
-  P.mem_lat = c->mem_latency;
-  P.mig_window = c->mig_window;
-  P.mig_threshold = c->mig_threshold;
-  P.core_q = c->core_q;
-  P.svc_q = c->svc_q;
-  P.mem_q = c->mem_q;
-  P.fwd_cap = c->fwd_entries > 0 ? c->fwd_entries : 1;
-  P.packet_mode = c->packet_mode;
-  P.rob_entries = c->packet_mode ? c->rob_entries : 0;
-  P.dir_central = c->dir_central;
-  P.dir_tile = c->dir_central ? c->dir_tile : 0;
-  P.l1_write_back = c->l1_write_back;
-  P.age_mode = c->age_mode;
-  P.write_q16 = tr->write_q16;
-  P.priv_q16 = tr->priv_q16;
-  P.shared_q16 = tr->shared_q16;
-  P.hot_q16 = tr->hot_q16;
-  P.hot_side = tr->hot_side;
-  P.hot_x0 = mesh_w / 2 - tr->hot_side / 2;
-  P.hot_y0 = mesh_h / 2 - tr->hot_side / 2;
-  P.priv_lines = tr->priv_lines;
-  P.shared_lines = tr->shared_lines;
-  P.remote_lines = tr->remote_lines;
-  P.total_lines = (uint32_t)total;
-  set_divisors(P);
-  P.seed = seed;
-  P.stream = tr->stream;
-  s->traces.resize(N);
+  s->P = P;
+  s->traces.resize((size_t)P.N);
   layout(s);
   *out = s;
   return NOC_OK;
@@ -868,6 +883,18 @@ int noc_debug_wait_limit(noc_sim* s, int64_t ns, int silent_cta) {
 
 int64_t noc_kernel_launches(const noc_sim* s) { return s ? s->launches : -1; }
 
+int noc_last_variant(const noc_sim* s, int* loop, int* kind, int* l1_bound, int* l2_bound) {
+  if (!s) return fail(NOC_ERR_ARG, "null handle");
+  if (s->last_variant < 0) return fail(NOC_ERR_STATE, "no cycle-kernel launch yet");
+  static const int bounds[3][2] = {{4, 8}, {4, 16}, {16, 16}};
+  const int v = s->last_variant, c = v & 15;
+  if (loop) *loop = v >> 8;
+  if (kind) *kind = (v >> 4) & 15;
+  if (l1_bound) *l1_bound = bounds[c][0];
+  if (l2_bound) *l2_bound = bounds[c][1];
+  return NOC_OK;
+}
+
 int noc_kernel_time(noc_sim* s, int enable, double* ms_out, int64_t* launches_out) {
   if (!s) return fail(NOC_ERR_ARG, "null handle");
   if (ms_out || launches_out) {
@@ -896,8 +923,9 @@ struct noc_batch {
   size_t pool_bytes = 0;
   bool pool_owned = false;
   cudaStream_t stream = nullptr;
-  int rect = 8;
-  bool strips = false;   // cut instances into strips of rect * rect tiles, not squares
+  std::vector<int> rect;       // per instance: CTA rectangle side (capacity rect * rect tiles)
+  std::vector<char> strips;    // per instance: cut into strips of that capacity, not squares
+  std::vector<int> group;      // per instance: kernel-variant group (0..4, see noc_batch_run)
   bool collect_hash = true;
   int waves = 0;
   int64_t launches = 0;
@@ -907,6 +935,7 @@ struct noc_batch {
   std::vector<std::vector<uint64_t>> hist;
   std::vector<int> err;
   std::vector<int64_t> err_cycle;
+  std::vector<int> variant;  // kind << 4 | way class of the kernel that ran each instance
   // device tables
   void* d_tab = nullptr;
   size_t tab_bytes = 0;
@@ -943,6 +972,29 @@ int noc_batch_create(int n, const noc_instance_desc* d, noc_batch** out) {
   b->hist.assign(n, std::vector<uint64_t>(2 * HIST_BINS, 0));
   b->err.assign(n, 0);
   b->err_cycle.assign(n, -1);
+  b->variant.assign(n, -1);
+  b->rect.assign(n, 8);
+  b->strips.assign(n, 0);
+  // kernel-variant groups: the instances the specialised kernel of way class
+  // 0, 1, 2 serves (interleaved L2, cache mode, exact ways), those without the
+  // packet, write-back, directory-node and age options on the base kernel, then
+  // the rest on the general kernel; the last two with the largest way bounds
+  // among their instances
+  b->group.assign(n, 0);
+  int gw1[5] = {1, 1, 1, 1, 1}, gw2[5] = {1, 1, 1, 1, 1};
+  for (int i = 0; i < n; ++i) {
+    const Params& P = b->sims[i]->P;
+    const int kind = variant_kind(P);
+    const int g = kind == KIND_IL ? batch_way_class(P.l1_ways, P.l2_ways) : kind == KIND_BASE ? 3 : 4;
+    b->group[i] = g;
+    gw1[g] = std::max(gw1[g], P.l1_ways);
+    gw2[g] = std::max(gw2[g], P.l2_ways);
+  }
+  for (int i = 0; i < n; ++i) {
+    const int g = b->group[i];
+    const int kind = g < 3 ? KIND_IL : g == 3 ? KIND_BASE : KIND_GEN;
+    b->variant[i] = (kind << 4) | batch_way_class(gw1[g], gw2[g]);
+  }
   *out = b;
   return NOC_OK;
 }
@@ -991,14 +1043,32 @@ int noc_batch_set_stream(noc_batch* b, void* stream) {
 
 int noc_batch_set_rect(noc_batch* b, int side) {
   if (!b || side < 1 || side * side > 384) return fail(NOC_ERR_ARG, "rectangle side 1..19");
-  b->rect = side;
+  for (int& r : b->rect) r = side;
   return NOC_OK;
 }
 
 int noc_batch_set_strips(noc_batch* b, int enable) {
   if (!b) return fail(NOC_ERR_ARG, "null handle");
-  b->strips = enable != 0;
+  for (char& v : b->strips) v = enable != 0;
   return NOC_OK;
+}
+
+int noc_batch_set_layout(noc_batch* b, int i, int side, int strips, int map) {
+  if (!b || i < -1 || i >= (int)b->sims.size()) return fail(NOC_ERR_ARG, "bad instance");
+  if (side < 1 || side * side > 384) return fail(NOC_ERR_ARG, "rectangle side 1..19");
+  if (map < 0 || map > 2) return fail(NOC_ERR_ARG, "thread map 0, 1 or 2");
+  const int lo = i < 0 ? 0 : i, hi = i < 0 ? (int)b->sims.size() : i + 1;
+  for (int k = lo; k < hi; ++k) {
+    b->rect[k] = side;
+    b->strips[k] = strips != 0;
+    b->sims[k]->thread_map = map;
+  }
+  return NOC_OK;
+}
+
+int noc_batch_group(const noc_batch* b, int i) {
+  if (!b || i < 0 || i >= (int)b->sims.size()) return -1;
+  return b->group[i];
 }
 
 int noc_batch_set_thread_map(noc_batch* b, int map) {
@@ -1015,9 +1085,9 @@ int noc_batch_set_collect_hash(noc_batch* b, int enable) {
 
 // run one kernel-variant group of a batch: memory waves over the pool, one
 // work-queue launch per wave, results read back per instance
-static int run_batch_group(noc_batch* b, const std::vector<int>& members, int threads, int w1, int w2,
+static int run_batch_group(noc_batch* b, const std::vector<int>& members, int side, int w1, int w2,
                            int kind, int* first_err) {
-  const int side = b->rect;
+  const int threads = ((side * side + 31) / 32) * 32;
   int cap = 0;
   CU(max_coresident_batch(w1, w2, kind, threads, &cap), "occupancy");
   std::vector<int> by_size = members;
@@ -1026,7 +1096,7 @@ static int run_batch_group(noc_batch* b, const std::vector<int>& members, int th
     // squares of side x side tiles, or strips of the same capacity: as wide as
     // the mesh (or the capacity) and as many rows as then fit
     int bw = side, bh = side;
-    if (b->strips) {
+    if (b->strips[i]) {
       bw = std::min(s->P.W, side * side);
       bh = std::max(1, side * side / bw);
     }
@@ -1194,32 +1264,21 @@ int noc_batch_run(noc_batch* b) {
   if (noc_batch_min_bytes(b) > b->pool_bytes)
     return fail(NOC_ERR_OOM, "pool of %zu bytes is below the largest instance (%zu)", b->pool_bytes,
                 noc_batch_min_bytes(b));
-  const int side = b->rect;
-  const int threads = ((side * side + 31) / 32) * 32;
-  // kernel-variant groups: the instances the specialised kernel of way class
-  // 0, 1, 2 serves (interleaved L2, cache mode, exact ways), those without the
-  // packet, write-back, directory-node and age options on the base kernel, then the
-  // rest on the general kernel; the last two with the largest way bounds among
-  // their instances
-  std::vector<int> group[5];
-  for (int i = 0; i < n; ++i) {
-    const Params& P = b->sims[i]->P;
-    const int kind = variant_kind(P);
-    group[kind == KIND_IL ? batch_way_class(P.l1_ways, P.l2_ways) : kind == KIND_BASE ? 3 : 4].push_back(i);
-  }
+  // one run per kernel-variant group (fixed at create) and rectangle side:
+  // the CTAs of one launch all have the side's thread count
   b->waves = 0;
   int first_err = NOC_OK;
-  for (int g = 0; g < 5; ++g) {
-    if (group[g].empty()) continue;
-    const int kind = g < 3 ? KIND_IL : g == 3 ? KIND_BASE : KIND_GEN;
-    int w1 = 1, w2 = 1;
-    for (int i : group[g]) {
-      w1 = std::max(w1, b->sims[i]->P.l1_ways);
-      w2 = std::max(w2, b->sims[i]->P.l2_ways);
+  static const int bounds[3][2] = {{4, 8}, {4, 16}, {16, 16}};
+  for (int g = 0; g < 5; ++g)
+    for (int side = 1; side * side <= 384; ++side) {
+      std::vector<int> members;
+      for (int i = 0; i < n; ++i)
+        if (b->group[i] == g && b->rect[i] == side) members.push_back(i);
+      if (members.empty()) continue;
+      const int v = b->variant[members[0]], kind = v >> 4, c = v & 15;
+      int rc = run_batch_group(b, members, side, bounds[c][0], bounds[c][1], kind, &first_err);
+      if (rc) return rc;
     }
-    int rc = run_batch_group(b, group[g], threads, w1, w2, kind, &first_err);
-    if (rc) return rc;
-  }
   b->done = true;
   if (first_err) return fail(first_err, "an instance ended with error %d", first_err);
   return NOC_OK;
@@ -1256,5 +1315,16 @@ int noc_batch_latency_hist(const noc_batch* b, int i, int which, uint64_t* bins,
 }
 
 int64_t noc_batch_kernel_launches(const noc_batch* b) { return b ? b->launches : -1; }
+
+int noc_batch_variant(const noc_batch* b, int i, int* kind, int* l1_bound, int* l2_bound) {
+  if (!b || i < 0 || i >= (int)b->sims.size()) return fail(NOC_ERR_ARG, "bad argument");
+  if (b->variant[i] < 0) return fail(NOC_ERR_STATE, "batch has not run");
+  static const int bounds[3][2] = {{4, 8}, {4, 16}, {16, 16}};
+  const int v = b->variant[i], c = v & 15;
+  if (kind) *kind = v >> 4;
+  if (l1_bound) *l1_bound = bounds[c][0];
+  if (l2_bound) *l2_bound = bounds[c][1];
+  return NOC_OK;
+}
 
 }  // extern "C"

@@ -5,7 +5,8 @@
 namespace noc {
 
 // ---------------------------------------------------------------- dispatch
-// Kernel variants shipped: per-cycle hash / drain records on or off, and the
+// Kernel variants shipped: the per-cycle hash record or the drain's busy
+// record on (the traced / draining loop) or neither (the plain loop), and the
 // compile-time way bounds (L1, L2) of the cache-set code: (4, 8), (4, 16) and
 // the general (16, 16).  The plain loop also comes as "base" (every policy and
 // mode, the packet, write-back, directory-node and age options compiled out) and as
@@ -18,7 +19,6 @@ namespace noc {
   NOC_DECL_RUN(0, 0, w1, w2, gen)                                               \
   NOC_DECL_RUN(1, 0, w1, w2, gen)                                               \
   NOC_DECL_RUN(0, 1, w1, w2, gen)                                               \
-  NOC_DECL_RUN(1, 1, w1, w2, gen)                                               \
   NOC_DECL_RUN(0, 0, w1, w2, il)                                                \
   NOC_DECL_RUN(0, 0, w1, w2, base)                                              \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_gen(int threads, int* out);  \
@@ -61,8 +61,15 @@ int variant_kind(const Params& P) {
     default: return launch_run_##h##_##d##_16_16_##sp(P, A, s);   \
   }
 
+int run_variant(const Params& P, const RunArgs& A) {
+  const int traced = (A.hash_trace || A.busy) ? 1 : 0;
+  const int kind = traced ? KIND_GEN : variant_kind(P);
+  return (traced << 8) | (kind << 4) | way_class(P.l1_ways, P.l2_ways);
+}
+
 cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
-  if (A.hash_trace && A.busy) { NOC_PICK_RUN(1, 1, gen) }
+  // a drain records its busy counts, never a hash trace
+  if (A.hash_trace && A.busy) return cudaErrorInvalidValue;
   if (A.hash_trace) { NOC_PICK_RUN(1, 0, gen) }
   if (A.busy) { NOC_PICK_RUN(0, 1, gen) }
   switch (variant_kind(P)) {

@@ -11,9 +11,10 @@
 //
 // The array is NOC_STATIC_SCRATCH_BYTES (16 MiB) and every GPU that loads the
 // library holds it until the process exits.  All calls share it and it keeps
-// the previous call's contents, so each call clears what must start at zero;
-// two calls whose work overlaps on the GPU (different streams or host
-// threads) race on it and must be serialised by the caller.
+// the previous call's contents, so each call clears what must start at zero.
+// Within one process the calls cannot overlap: an internal lock is held from
+// the first clear until the call's stream has finished.  Each process has its
+// own copy of the array.
 #include <cstring>
 #include <mutex>
 
@@ -49,76 +50,19 @@ __global__ void pack_stats_kernel(const unsigned long long* h, unsigned long lon
 extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy,
                               const noc_traffic* tr, uint64_t seed, int64_t n_cycles,
                               void* dev_stats_out, void* cuda_stream) {
-  if (!c || !tr || !dev_stats_out || n_cycles < 0 || n_cycles >= (1ll << 31))
-    return NOC_ERR_ARG;
-  if (mesh_w < 1 || mesh_h < 1 || (long)mesh_w * mesh_h > 65535 || l2_policy < 0 || l2_policy > 2)
-    return NOC_ERR_ARG;
-  auto ways_ok = [](int w) { return w >= 1 && w <= MAX_WAYS; };
-  if (c->l1_sets < 1 || !ways_ok(c->l1_ways) || c->l2_sets < 1 || !ways_ok(c->l2_ways) ||
-      c->l1_miss_cycles < 0 || c->mem_latency < 1 || c->core_q < 1 || c->svc_q < 1 ||
-      c->mem_q < 1 || c->core_q > 65535 || c->svc_q > 65535 || c->mem_q > 65535)
-    return NOC_ERR_ARG;
-  if (l2_policy == NOC_L2_LSPD_MIGRATE &&
-      (c->mig_window < 1 || c->mig_window > HIST_MAX || c->mig_threshold < 1 ||
-       c->fwd_entries < 1))
-    return NOC_ERR_ARG;
-  if (c->packet_mode < 0 || c->packet_mode > 1 ||
-      (c->packet_mode && (c->rob_entries < 1 || c->rob_entries > 64 || c->svc_q < 16)))
-    return NOC_ERR_ARG;
-  if (c->dir_central < 0 || c->dir_central > 1 ||
-      (c->dir_central && (c->dir_tile < 0 || (long)c->dir_tile >= (long)mesh_w * mesh_h)))
-    return NOC_ERR_ARG;
-  if (c->l1_write_back < 0 || c->l1_write_back > 1) return NOC_ERR_ARG;
-  if (c->age_mode < 0 || c->age_mode > 1 || (c->age_mode && n_cycles > (1ll << AGE_SHIFT))) return NOC_ERR_ARG;
-  // trace mode needs per-core reference lists, which live outside the array
-  if (tr->mode < 0 || tr->mode > 1 || tr->period < 0 || tr->write_q16 > 65536 ||
-      tr->priv_q16 + (uint64_t)tr->shared_q16 > 65536 || tr->hot_q16 > 65536 ||
-      tr->hot_side < 0 || tr->hot_side > mesh_w || tr->hot_side > mesh_h)
-    return NOC_ERR_ARG;
-  const size_t N = (size_t)mesh_w * mesh_h;
-  const uint64_t total = (uint64_t)tr->remote_lines + tr->shared_lines + (uint64_t)tr->priv_lines * N;
-  if (total >= (1ull << 26)) return NOC_ERR_ARG;
-
+  if (!c || !tr || !dev_stats_out) return fail(NOC_ERR_ARG, "null argument");
+  if (n_cycles < 0 || n_cycles >= (1ll << 31)) return fail(NOC_ERR_ARG, "n_cycles outside [0, 2^31)");
+  // the same configurations noc_create accepts, with the same messages
   Params P;
-  memset(&P, 0, sizeof P);
-  P.W = mesh_w;
-  P.H = mesh_h;
-  P.N = (int)N;
-  P.policy = l2_policy;
-  P.mode = tr->mode;
-  P.period = tr->period;
-  P.l1_sets = c->l1_sets;
-  P.l1_ways = c->l1_ways;
-  P.l2_sets = c->l2_sets;
-  P.l2_ways = c->l2_ways;
-  P.l1_miss = c->l1_miss_cycles;
-  P.mem_lat = c->mem_latency;
-  P.mig_window = c->mig_window;
-  P.mig_threshold = c->mig_threshold;
-  P.core_q = c->core_q;
-  P.svc_q = c->svc_q;
-  P.mem_q = c->mem_q;
-  P.fwd_cap = c->fwd_entries > 0 ? c->fwd_entries : 1;
-  P.packet_mode = c->packet_mode;
-  P.rob_entries = c->packet_mode ? c->rob_entries : 0;
-  P.dir_central = c->dir_central;
-  P.dir_tile = c->dir_central ? c->dir_tile : 0;
-  P.l1_write_back = c->l1_write_back;
-  P.age_mode = c->age_mode;
-  P.write_q16 = tr->write_q16;
-  P.priv_q16 = tr->priv_q16;
-  P.shared_q16 = tr->shared_q16;
-  P.hot_q16 = tr->hot_q16;
-  P.hot_side = tr->hot_side;
-  P.hot_x0 = mesh_w / 2 - tr->hot_side / 2;
-  P.hot_y0 = mesh_h / 2 - tr->hot_side / 2;
-  P.priv_lines = tr->priv_lines;
-  P.shared_lines = tr->shared_lines;
-  P.remote_lines = tr->remote_lines;
-  P.total_lines = (uint32_t)total;
-  set_divisors(P);
-  P.seed = seed;
-  P.stream = tr->stream;
+  int rc = configure(mesh_w, mesh_h, c, l2_policy, tr, seed, P);
+  if (rc) return rc;
+  // trace mode needs per-core reference lists, which live outside the array
+  if (tr->mode == NOC_MODE_TRACE)
+    return fail(NOC_ERR_ARG, "trace mode is not available without allocation");
+  if (c->age_mode && n_cycles > (1ll << AGE_SHIFT))
+    return fail(NOC_ERR_ARG, "age_mode 1 runs end at or before cycle 2^%d", AGE_SHIFT);
+  const size_t N = (size_t)P.N;
+  const uint64_t total = P.total_lines;
 
   // carve the state out of the static array
   const size_t w1 = N * P.l1_sets * P.l1_ways, w2 = N * P.l2_sets * P.l2_ways;
@@ -135,15 +79,21 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
     off[k] = a256(cur);
     cur = off[k] + sz[k];
   }
-  if (cur > NOC_STATIC_SCRATCH_BYTES) return NOC_ERR_ARG;
+  if (cur > NOC_STATIC_SCRATCH_BYTES)
+    return fail(NOC_ERR_ARG, "state needs %zu bytes > NOC_STATIC_SCRATCH_BYTES (%u)", cur,
+                (unsigned)NOC_STATIC_SCRATCH_BYTES);
 
   std::lock_guard<std::mutex> lock(g_mu);
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NOC_ERR_CUDA;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return fail(NOC_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
+  if (dev < 0 || dev >= 256) return fail(NOC_ERR_CUDA, "device %d out of range", dev);
   if (!g_dev_ready[dev]) {
     // first call on this device: the array's device address, with it current
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return NOC_ERR_CUDA;
+    ce = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (ce != cudaSuccess || !p)
+      return fail(NOC_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(ce));
     g_dev_ptr[dev] = static_cast<unsigned char*>(p);
     g_dev_ready[dev] = true;
   }
@@ -174,7 +124,8 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
   for (int k = 0; k < 20; ++k) {
     if (!sz[k] || k == 2 || k == 3 || k == 4) continue;  // queue slots are written before read
     int v = (k == 10 || k == 15) ? 0xFF : 0;              // directory NONE, no error
-    if (cudaMemsetAsync(b + off[k], v, sz[k], st) != cudaSuccess) return NOC_ERR_CUDA;
+    ce = cudaMemsetAsync(b + off[k], v, sz[k], st);
+    if (ce != cudaSuccess) return fail(NOC_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(ce));
   }
 
   // CTA rectangles: the fewest that hold at most 256 tiles each and fit co-resident
@@ -183,13 +134,14 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
     int tx = (mesh_w + side - 1) / side, ty = (mesh_h + side - 1) / side;
     int threads = block_threads(mesh_w, mesh_h, tx, ty), cap = 0;
     if (threads > 384 || (size_t)tx * ty * FLAG_SLOTS > n_flags) continue;
-    if (max_coresident_ctas(P, threads, &cap) != cudaSuccess) return NOC_ERR_CUDA;
+    ce = max_coresident_ctas(P, threads, &cap);
+    if (ce != cudaSuccess) return fail(NOC_ERR_CUDA, "occupancy: %s", cudaGetErrorString(ce));
     if (tx * ty <= cap) {
       gx = tx;
       gy = ty;
     }
   }
-  if (!gx) return NOC_ERR_ARG;
+  if (!gx) return fail(NOC_ERR_ARG, "mesh %dx%d does not fit one co-resident launch", mesh_w, mesh_h);
 
   uint32_t done = 0;
   while (done < (uint32_t)n_cycles) {
@@ -206,15 +158,21 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
     A.wait_ns = 2000000000ll;
     A.silent_cta = -1;
     A.thread_map = 0;
-    if (launch_run(P, A, st) != cudaSuccess) return NOC_ERR_CUDA;
+    ce = launch_run(P, A, st);
+    if (ce != cudaSuccess) return fail(NOC_ERR_CUDA, "cycle kernel launch: %s", cudaGetErrorString(ce));
     done += n;
   }
-  if (launch_reduce_stats(P, -1, totals, st) != cudaSuccess) return NOC_ERR_CUDA;
+  ce = launch_reduce_stats(P, -1, totals, st);
+  if (ce != cudaSuccess) return fail(NOC_ERR_CUDA, "counter reduction: %s", cudaGetErrorString(ce));
   pack_stats_kernel<<<1, 32, 0, st>>>(totals, (unsigned long long)n_cycles,
                                       static_cast<unsigned long long*>(dev_stats_out));
-  if (cudaGetLastError() != cudaSuccess) return NOC_ERR_CUDA;
+  ce = cudaGetLastError();
+  if (ce != cudaSuccess) return fail(NOC_ERR_CUDA, "counter packing: %s", cudaGetErrorString(ce));
   unsigned long long e = ~0ull;
-  if (cudaMemcpyAsync(&e, P.err, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return NOC_ERR_CUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return NOC_ERR_CUDA;
-  return e == ~0ull ? NOC_OK : (int)(e & 0xFF);
+  ce = cudaMemcpyAsync(&e, P.err, 8, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return fail(NOC_ERR_CUDA, "error word: %s", cudaGetErrorString(ce));
+  if (e == ~0ull) return NOC_OK;
+  const int code = (int)(e & 0xFF);
+  return fail(code, "simulation error %d at cycle %lld", code, (long long)(e >> 8));
 }

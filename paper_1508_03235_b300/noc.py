@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libnoc.so")
 
 NOC_OK = 0
 THREAD_MAPS = ("perimeter first", "rows", "columns")
+KERNEL_KINDS = ("general", "base", "interleaved")
 ERR_NAMES = {1: "NOC_ERR_ARG", 2: "NOC_ERR_OOM", 3: "NOC_ERR_QUEUE_OVERFLOW", 4: "NOC_ERR_TIMEOUT",
              5: "NOC_ERR_CUDA", 6: "NOC_ERR_PROTOCOL", 7: "NOC_ERR_STATE", 8: "NOC_ERR_RANGE"}
 HIST_BINS = 1025
@@ -100,6 +101,9 @@ def lib():
             "noc_debug_wait_limit": (i32, [vp, i64, i32]),
             "noc_kernel_launches": (i64, [vp]),
             "noc_kernel_time": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)]),
+            "noc_last_variant": (i32, [vp] + [C.POINTER(i32)] * 4),
+            "noc_run_static": (i32, [i32, i32, C.POINTER(CacheCfg), i32, C.POINTER(Traffic),
+                                     C.c_uint64, i64, vp, vp]),
             "noc_last_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -238,6 +242,14 @@ class Sim:
     def launches(self) -> int:
         return lib().noc_kernel_launches(self._h)
 
+    def variant(self) -> dict:
+        """The cycle-kernel build of the last launch: loop ("plain" or
+        "traced"), kind (KERNEL_KINDS) and its way bounds (l1, l2)."""
+        v = [C.c_int() for _ in range(4)]
+        _check(lib().noc_last_variant(self._h, *[C.byref(x) for x in v]))
+        return dict(loop=("plain", "traced")[v[0].value], kind=KERNEL_KINDS[v[1].value],
+                    bounds=(v[2].value, v[3].value))
+
     def kernel_time(self, enable: bool = True):
         """(ms, launches) of the cycle-kernel launches recorded since the last
         call (CUDA events around each launch), then keep recording iff enable."""
@@ -347,6 +359,9 @@ def _batch_sigs(L):
         "noc_batch_state_hash": (i32, [vp, i32, C.POINTER(C.c_uint64)]),
         "noc_batch_latency_hist": (i32, [vp, i32, i32, C.POINTER(C.c_uint64), i32]),
         "noc_batch_kernel_launches": (i64, [vp]),
+        "noc_batch_variant": (i32, [vp, i32] + [C.POINTER(i32)] * 3),
+        "noc_batch_group": (i32, [vp, i32]),
+        "noc_batch_set_layout": (i32, [vp, i32, i32, i32, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -354,32 +369,53 @@ def _batch_sigs(L):
         f.argtypes = args
 
 
+def _descs(params_list, cycles):
+    n = len(params_list)
+    if isinstance(cycles, int):
+        cycles = [cycles] * n
+    arr = (InstanceDesc * n)()
+    for d, p, c in zip(arr, params_list, cycles):
+        d.mesh_w, d.mesh_h, d.l2_policy = p["mesh_w"], p["mesh_h"], p.get("policy", 0)
+        d.cache = cache_struct(p)
+        d.traffic = traffic_struct(p)
+        d.seed = p.get("seed", 1)
+        d.cycles = int(c)
+    return arr
+
+
+def batch_groups(params_list):
+    """The kernel-variant group (noc_batch_group) of each instance: host-only,
+    no device memory is taken."""
+    L = lib()
+    _batch_sigs(L)
+    h = C.c_void_p()
+    _check(L.noc_batch_create(len(params_list), _descs(params_list, 1), C.byref(h)))
+    try:
+        return [L.noc_batch_group(h, i) for i in range(len(params_list))]
+    finally:
+        L.noc_batch_destroy(h)
+
+
 class Batch:
     """Independent simulations run together by the batch engine.  `params_list`
     holds inputs.sim_params() dicts; `cycles` is one count or one per instance.
     The instances' state lives in a torch uint8 pool of `pool_bytes` (default:
     all instances at once, capped at 80% of free device memory); instances
-    that do not fit run in later waves."""
+    that do not fit run in later waves.  The layout knobs (rect, strips,
+    thread_map) apply to every instance when given; otherwise each instance
+    takes the autotuner's cached choice for its kernel-variant group
+    (tuned=True) or the library default."""
 
-    def __init__(self, params_list, cycles, stream=None, rect=8, collect_hash=True,
-                 pool_bytes=None, thread_map=0, strips=False):
+    def __init__(self, params_list, cycles, stream=None, rect=None, collect_hash=True,
+                 pool_bytes=None, thread_map=None, strips=None, tuned=True):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the batch engine needs a CUDA device")
         L = lib()
         _batch_sigs(L)
         n = len(params_list)
-        if isinstance(cycles, int):
-            cycles = [cycles] * n
-        arr = (InstanceDesc * n)()
-        for d, p, c in zip(arr, params_list, cycles):
-            d.mesh_w, d.mesh_h, d.l2_policy = p["mesh_w"], p["mesh_h"], p.get("policy", 0)
-            d.cache = cache_struct(p)
-            d.traffic = traffic_struct(p)
-            d.seed = p.get("seed", 1)
-            d.cycles = int(c)
         h = C.c_void_p()
-        _check(L.noc_batch_create(n, arr, C.byref(h)))
+        _check(L.noc_batch_create(n, _descs(params_list, cycles), C.byref(h)))
         self._h = h
         self.n = n
         total = L.noc_batch_total_bytes(h)
@@ -392,9 +428,20 @@ class Batch:
         _check(L.noc_batch_bind_memory(h, C.c_void_p(ptr), want))
         st = stream if stream is not None else torch.cuda.current_stream()
         _check(L.noc_batch_set_stream(h, C.c_void_p(st.cuda_stream)))
-        _check(L.noc_batch_set_rect(h, rect))
-        _check(L.noc_batch_set_thread_map(h, thread_map))
-        _check(L.noc_batch_set_strips(h, 1 if strips else 0))
+        # layout: what the caller gives, else the autotuner's choice for each
+        # instance's kernel-variant group, else 8x8 squares, perimeter first
+        self.layouts = []
+        cache = {}
+        if tuned and rect is None and strips is None and thread_map is None:
+            from . import tune
+            for g in range(5):
+                cache[g] = tune.cached_batch_layout(g)
+        for i in range(n):
+            lay = cache.get(L.noc_batch_group(h, i)) or (8, False, 0)
+            lay = (rect if rect is not None else lay[0], strips if strips is not None else lay[1],
+                   thread_map if thread_map is not None else lay[2])
+            self.layouts.append(lay)
+            _check(L.noc_batch_set_layout(h, i, lay[0], 1 if lay[1] else 0, lay[2]))
         _check(L.noc_batch_set_collect_hash(h, 1 if collect_hash else 0))
 
     def close(self):
@@ -426,6 +473,21 @@ class Batch:
         cyc = C.c_int64()
         rc = lib().noc_batch_error(self._h, i, C.byref(cyc))
         return rc, cyc.value
+
+    def group(self, i) -> int:
+        """Kernel-variant group of instance i (0-2 interleaved builds by way
+        class, 3 base, 4 general)."""
+        return lib().noc_batch_group(self._h, i)
+
+    def set_layout(self, i, rect, strips, thread_map):
+        """CTA rectangle side, strips and thread order of instance i (-1: all)."""
+        _check(lib().noc_batch_set_layout(self._h, i, rect, 1 if strips else 0, thread_map))
+
+    def variant(self, i) -> dict:
+        """The batch-kernel build that runs instance i: kind and way bounds."""
+        v = [C.c_int() for _ in range(3)]
+        _check(lib().noc_batch_variant(self._h, i, *[C.byref(x) for x in v]))
+        return dict(kind=KERNEL_KINDS[v[0].value], bounds=(v[1].value, v[2].value))
 
     def stats(self, i) -> dict:
         s = Stats()

@@ -1,5 +1,5 @@
 """Autotuner for the CTA tiling and the router-to-thread mapping of the cycle
-kernel.
+kernel, for single simulations and for the batch engine.
 
 The mesh is cut into gx x gy rectangles, one CTA each (one thread per tile),
 and the tiles of a rectangle are handed to its threads in one of three orders
@@ -8,6 +8,13 @@ GPU tests check every tiling and order against the oracle); only the time per
 simulated cycle does.  The tuner times a handful of candidate tilings in
 every order on a short run of the actual configuration and keeps the fastest
 pair in a JSON cache next to this file.
+
+For the batch engine (many independent instances in work-queue launches) the
+knobs are each instance's rectangle side, square or strip cut, and thread
+order.  Instances are grouped by the kernel build that serves them (the
+library's noc_batch_group); per group the tuner times every candidate layout
+on a size-stratified sample of the workload's own descriptors and caches the
+fastest under the group's key.
 """
 from __future__ import annotations
 
@@ -129,17 +136,109 @@ def tune(params: dict, cycles: int = 2000, warm: int = 200, max_cands: int = 10,
     return best, timings
 
 
+# ------------------------------------------------------------------ batch engine
+BATCH_SIDES = (4, 6, 8, 10, 12, 16)
+GROUP_NAMES = ("interleaved 4x8", "interleaved 4x16", "interleaved 16x16", "base", "general")
+
+
+def batch_key(group: int) -> str:
+    return f"batch/group{group}"
+
+
+def cached_batch_layout(group: int):
+    """The tuned (rect side, strips, thread order) of a kernel-variant group,
+    or None."""
+    t = load_cache().get(batch_key(group))
+    return (t["rect"], bool(t["strips"]), t["thread_map"]) if t else None
+
+
+def stratified_sample(params_list, idx, k):
+    """k of the instances idx, spread evenly over their sizes."""
+    order = sorted(idx, key=lambda i: (params_list[i]["mesh_w"] * params_list[i]["mesh_h"], i))
+    if len(order) <= k:
+        return order
+    return [order[(j * len(order)) // k] for j in range(k)]
+
+
+def batch_candidates(sides=BATCH_SIDES, maps=(0, 1, 2)):
+    return [(side, strips, m) for side in sides for strips in (False, True) for m in maps]
+
+
+def tune_batch(params_list, cycles: int = 3000, sample: int = 48, reps: int = 2, save: bool = True,
+               cache_path: str = CACHE, verbose: bool = False):
+    """Per kernel-variant group of params_list: time every candidate layout
+    (batch_candidates) on a sample of the group's instances, `cycles` each,
+    best of `reps` runs after a warm-up run; cache the fastest.  Returns
+    {group: (best layout, {layout: seconds})}."""
+    import torch
+
+    from . import noc
+
+    groups = noc.batch_groups(params_list)
+    out = {}
+    for g in sorted(set(groups)):
+        idx = stratified_sample(params_list, [i for i, x in enumerate(groups) if x == g], sample)
+        pts = [params_list[i] for i in idx]
+        timings = {}
+        for side, strips, m in batch_candidates():
+            b = noc.Batch(pts, cycles, collect_hash=False, rect=side, strips=strips, thread_map=m)
+            try:
+                b.run()
+                dt = float("inf")
+                for _ in range(reps):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    b.run()
+                    dt = min(dt, time.perf_counter() - t0)
+            except noc.NocError:
+                continue                   # an instance does not fit at this side
+            finally:
+                b.close()
+            timings[(side, strips, m)] = dt
+            if verbose:
+                print(f"  group {GROUP_NAMES[g]}: side {side} {'strips' if strips else 'squares'} "
+                      f"{noc.THREAD_MAPS[m]}: {1e3 * dt:.1f} ms", flush=True)
+        best = min(timings, key=timings.get)
+        out[g] = (best, timings)
+        if save:
+            cache = load_cache() if cache_path == CACHE else (
+                json.load(open(cache_path)) if os.path.exists(cache_path) else load_cache())
+            cache[batch_key(g)] = {
+                "group": GROUP_NAMES[g], "rect": best[0], "strips": int(best[1]), "thread_map": best[2],
+                "sample_instances": len(pts), "cycles": cycles, "seconds": timings[best],
+                "sims_per_s_sample": len(pts) / timings[best],
+                "timings_ms": {f"{a}/{'strips' if b_ else 'squares'}/{noc.THREAD_MAPS[c]}": 1e3 * v
+                               for (a, b_, c), v in timings.items()},
+                "device": torch.cuda.get_device_name()}
+            with open(cache_path, "w") as f:
+                json.dump(cache, f, indent=1, sort_keys=True)
+    return out
+
+
 if __name__ == "__main__":
+    import argparse
     import sys
     sys.path.insert(0, os.path.dirname(HERE))
     from paper_1508_03235_b300 import inputs as I
-    from paper_1508_03235_b300.tune import tune as _tune
-    broad = "--broad" in sys.argv
-    for name, p in (("mesh208", I.mesh_208(10)), ("mesh64", I.mesh_64(1)),
-                    ("mesh8", I.MESH_8["params"])):
-        print(name, flush=True)
-        b, t = _tune(p, broad=broad, verbose=not broad)
-        if broad:
-            for k in sorted(t, key=t.get)[:10]:
-                print(f"  {k[0]}x{k[1]} order {k[2]}: {t[k]:.3f} us/cycle", flush=True)
-        print(f"  best {b}", flush=True)
+    from paper_1508_03235_b300 import tune as T
+    ap = argparse.ArgumentParser(description="autotune the cycle kernel's layouts")
+    ap.add_argument("--broad", action="store_true", help="every rectangle shape (single simulations)")
+    ap.add_argument("--batch", action="store_true",
+                    help="tune the batch engine on the 512-instance design-point workload")
+    ap.add_argument("--out", default=CACHE, help="cache file to update")
+    a = ap.parse_args()
+    if a.batch:
+        pts = I.batch_design_points(512, seed=0)
+        for p in pts:
+            p.pop("design")
+        for g, (best, t) in T.tune_batch(pts, cache_path=a.out, verbose=True).items():
+            print(f"group {T.GROUP_NAMES[g]}: best {best}", flush=True)
+    else:
+        for name, p in (("mesh208", I.mesh_208(10)), ("mesh64", I.mesh_64(1)),
+                        ("mesh8", I.MESH_8["params"])):
+            print(name, flush=True)
+            b, t = T.tune(p, broad=a.broad, verbose=not a.broad)
+            if a.broad:
+                for k in sorted(t, key=t.get)[:10]:
+                    print(f"  {k[0]}x{k[1]} order {k[2]}: {t[k]:.3f} us/cycle", flush=True)
+            print(f"  best {b}", flush=True)

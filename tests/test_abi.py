@@ -111,3 +111,23 @@ def test_library_and_oracle_accept_the_same_configurations(libnoc, oracle_mod, n
     assert (rc == 0) == want and oracle_ok == want, (rc, oracle_ok)
     if not want:
         assert rc == 1 and noc.lib().noc_last_error()
+
+
+@pytest.mark.parametrize("name", sorted(INVALID) + ["trace_mode", "priv_lines0_cache"])
+def test_static_entry_rejects_what_noc_create_rejects(libnoc, name):
+    """noc_run_static checks its arguments with noc_create's own checks (plus
+    trace mode, which it cannot hold) before any CUDA call, so a rejection
+    needs no GPU: NOC_ERR_ARG with a message."""
+    from paper_1508_03235_b300 import inputs as I
+    from paper_1508_03235_b300 import noc
+    p = dict(I.MESH_8["params"])
+    p.update(INVALID.get(name) or dict(trace_mode=dict(mode=I.MODE_TRACE),
+                                       priv_lines0_cache=dict(priv_lines=0, priv_q16=1000))[name])
+    out = (C.c_uint64 * 30)()
+    L = noc.lib()
+    L.noc_last_error()
+    rc = L.noc_run_static(p["mesh_w"], p["mesh_h"], C.byref(noc.cache_struct(p)), p["policy"],
+                          C.byref(noc.traffic_struct(p)), 1, 100, C.cast(out, C.c_void_p), None)
+    assert rc == 1
+    msg = L.noc_last_error()
+    assert msg and (name != "trace_mode" or b"trace" in msg)

@@ -1,6 +1,7 @@
 """Pins of the oracle against facts fixed outside it: a library generator,
 closed forms, brute force on tiny inputs and hand-worked timelines of the
 paper's rules.  No expected value here comes from either simulator."""
+import os
 from collections import Counter, OrderedDict
 
 import numpy as np
@@ -813,3 +814,26 @@ def test_deflection_age_limits(oracle_mod):
     assert t.step((1 << 20) - 999, check=False) == 1 and t.cycle == 1000
     u = oracle_mod.OracleSim(quiet_params(3, 3))                   # age_mode 0: no limit
     assert u.step((1 << 20) + 1, check=False) == 0
+
+
+def test_full_length_records_match_the_oracle_now(oracle_mod):
+    """The stored full-length records (tests/golden/full_length.json) are the
+    oracle's: the first checkpoint of a 64x64 run and of a 208x208 run,
+    recomputed now, equals the stored one (so a change to the oracle or to the
+    workload parameters cannot leave the GPU tests comparing against stale
+    values)."""
+    import json
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_length.json")
+    with open(path) as fh:
+        wl = json.load(fh)["workloads"]
+    from paper_1508_03235_b300 import inputs as I
+    assert wl["mesh64_hotspot_seed1"]["params"] == I.mesh_64(1)
+    assert wl["mesh208_period40"]["params"] == I.mesh_208(40)
+    for name in ("mesh64_hotspot_seed1", "mesh208_period40"):
+        rec = wl[name]["checkpoints"][0]
+        o = oracle_mod.OracleSim(wl[name]["params"])
+        o.step(rec["cycle"])
+        assert o.stats() == rec["stats"], name
+        assert str(o.dyn_hash()) == rec["dyn_hash"] and str(o.state_hash()) == rec["state_hash"]
+        assert [{str(i): int(v) for i, v in enumerate(o.hist(w)) if v} for w in (0, 1)] == rec["hist"]
+        o.close()

@@ -1,0 +1,46 @@
+"""Host-side logic of the autotuner and of the batch engine's kernel-variant
+groups (no GPU: noc_batch_create is host-only)."""
+import pytest
+
+from paper_1508_03235_b300 import inputs as I
+
+
+def test_batch_groups_follow_the_variant_rules():
+    """Interleaved cache-mode instances with a class's exact ways form the
+    class's interleaved group; LSPD without options the base group; any
+    option the general group."""
+    from paper_1508_03235_b300 import noc
+    base = dict(I.MESH_8["params"])
+    pts = [dict(base), dict(base, l2_ways=16, l2_sets=256), dict(base, l1_ways=16, l1_sets=32, l2_ways=16),
+           dict(base, policy=1), dict(base, policy=2), dict(base, l1_ways=3),
+           dict(base, packet_mode=1), dict(base, policy=1, age_mode=1), dict(base, l1_write_back=1),
+           dict(base, mode=I.MODE_NETWORK)]
+    assert noc.batch_groups(pts) == [0, 1, 2, 3, 3, 3, 4, 4, 4, 3]
+
+
+def test_design_point_groups():
+    from paper_1508_03235_b300 import noc
+    pts = I.batch_design_points(64, seed=0)
+    for p in pts:
+        p.pop("design")
+    g = noc.batch_groups(pts)
+    assert all(x == (0 if p["policy"] == 0 else 3) for x, p in zip(g, pts))
+
+
+def test_stratified_sample_spans_the_sizes():
+    from paper_1508_03235_b300 import tune
+    pts = I.batch_design_points(100, seed=1)
+    idx = list(range(100))
+    s = tune.stratified_sample(pts, idx, 10)
+    assert len(s) == len(set(s)) == 10
+    sizes = sorted(pts[i]["mesh_w"] for i in idx)
+    got = sorted(pts[i]["mesh_w"] for i in s)
+    assert got[0] == sizes[0] and got[-1] >= sizes[90]
+    assert tune.stratified_sample(pts, idx[:5], 10) == sorted(idx[:5], key=lambda i: (pts[i]["mesh_w"] ** 2, i))
+
+
+def test_batch_candidates():
+    from paper_1508_03235_b300 import tune
+    c = tune.batch_candidates()
+    assert len(c) == len(tune.BATCH_SIDES) * 2 * 3 == len(set(c))
+    assert all(1 <= side and side * side <= 384 for side, _, _ in c)
