@@ -2,9 +2,12 @@
 
 One step = the paper's largest configuration swept over injection periods
 {40, 20, 10, 5, 2}: for each period, reset the simulation to cycle 0 and run
-50,000 cycles (five persistent cooperative launches in all).  Timed on the
-device with CUDA events on the simulator's stream; the state touched per run
-(1.4 GB of L2 tags plus L1s, queues and links) is larger than the GPU's L2.
+50,000 cycles (persistent cooperative launches of up to a reference window's
+cycles each).  Timed on the device with CUDA events on the simulator's
+stream; the state touched per run (1.4 GB of L2 tags plus L1s, queues and
+links) is larger than the GPU's L2.  The timed runs' end states are checked
+against the oracle's stored records of the same runs, and the oracle itself
+times one whole run on a host core while the GPU arm runs.
 
 `--impl reference` times the oracle (the serial C simulator) on the host cores
 for the same metric on a bounded sample of the same workload.
@@ -111,19 +114,34 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def algorithmic_bytes(stats_delta, router_cycles, p):
-    """State bytes a cycle-stepped simulator must touch: per router-cycle the
-    four in-link and four out-link slots (8 x 16 B) and the tile's 13-word
-    core record read and written (2 x 52 B); per L1 lookup or fill one L1 set
-    read and written; per L2 access (lookup, install, write-through) one L2
-    set read and written; per injected flit one 16 B queue push and pop."""
-    l1set = 4 * p["l1_ways"]
-    l2set = 4 * p["l2_ways"]
-    d = stats_delta
-    l1_ops = d["l1_hit"] + d["l1_miss"] + d["l2lat_cnt"]          # lookups + fills
-    l2_ops = d["l2_hit"] + d["l2_miss"] + d["wt_hit"] + d["mem_write"] + d["mem_req"]
+def algorithmic_bytes(stats, router_cycles, p):
+    """The state bytes a cycle-stepped simulator of this model must touch
+    (the byte model of the measurement plan), from a run's own counters:
+
+    * per router-cycle: the four in-link and four out-link slots read and
+      written (8 x 16 B) and the core / queue scalars read and written
+      (2 x 24 B);
+    * per reference: one L1 set read (ways x 8 B) and one 8 B way written;
+    * per L1 miss: one L2 set read (ways x 8 B) and the line's way written (8 B);
+    * per ejected protocol flit: one L2 set at the handler (ways x 8 B), plus
+      one 4 B directory word under the LSPD policies."""
+    lspd = p.get("policy", 0) != 0
+    return (router_cycles * (8 * 16 + 2 * 24) + stats["refs"] * (8 * p["l1_ways"] + 8)
+            + stats["l1_miss"] * (8 * p["l2_ways"] + 8)
+            + stats["ejected"] * (8 * p["l2_ways"] + (4 if lspd else 0)))
+
+
+def implementation_bytes(stats, router_cycles, p):
+    """The bytes of this implementation's own state layout, for comparison:
+    per router-cycle the 8 link slots (8 x 16 B) and the 13-word core record
+    read and written (2 x 52 B); per L1 lookup or fill one L1 set of 32-bit
+    way words read and written; per L2 access one L2 set read and written; per
+    injected flit a 16 B queue push and pop."""
+    l1set, l2set = 4 * p["l1_ways"], 4 * p["l2_ways"]
+    l1_ops = stats["l1_hit"] + stats["l1_miss"] + stats["l2lat_cnt"]
+    l2_ops = stats["l2_hit"] + stats["l2_miss"] + stats["wt_hit"] + stats["mem_write"] + stats["mem_req"]
     return (router_cycles * (8 * 16 + 2 * 52) + l1_ops * 2 * l1set + l2_ops * 2 * l2set
-            + d["injected"] * 2 * 16)
+            + stats["injected"] * 2 * 16)
 
 
 KERNEL_SOURCES = ("noc_model.cuh", "noc_kernel.cuh", "noc_internal.h", "noc_run_variant.cu")
@@ -145,29 +163,78 @@ def kernel_sources_sha256() -> str:
     return h.hexdigest()
 
 
-def measured_traffic(cycles_per_launch):
-    """DRAM bytes (read + write) per cycle-kernel launch, scaled from the
-    committed ncu capture of the same kernel sources (by cycles per launch);
-    None when there is no capture or the kernel changed since it was taken."""
+def captured_per_cycle():
+    """DRAM and L2 bytes per simulated cycle of the cycle kernel, from the
+    committed ncu capture of the same kernel sources; None for each when there
+    is no capture or the kernel changed since it was taken."""
     import re
+    out = {"dram_bytes_per_cycle": None, "lts_bytes_per_cycle": None}
     if not os.path.exists(TRAFFIC_FILE):
-        return None
+        return out
     text = open(TRAFFIC_FILE).read()
     sha = re.search(r"kernel_sources_sha256:\s*([0-9a-f]{64})", text)
-    per = re.search(r"dram_bytes_per_cycle:\s*([0-9.eE+]+)", text)
-    if not sha or not per or sha.group(1) != kernel_sources_sha256():
+    if not sha or sha.group(1) != kernel_sources_sha256():
+        return out
+    for k in out:
+        m = re.search(k + r":\s*([0-9.eE+]+)", text)
+        out[k] = float(m.group(1)) if m else None
+    return out
+
+
+def measured_traffic(cycles_per_launch):
+    """DRAM bytes (read + write) per cycle-kernel launch, scaled from the
+    committed capture by cycles per launch (DRAM traffic grows in proportion
+    at a fixed mesh), or None."""
+    per = captured_per_cycle()["dram_bytes_per_cycle"]
+    return None if per is None else per * cycles_per_launch
+
+
+# --------------------------------------------------------------------- parity records
+GOLDEN = os.path.join(ROOT, "tests", "golden", "full_length.json")
+
+
+def golden_final(period):
+    """The oracle's stored end-of-run record of the 208x208 run at `period`
+    (written by tests/golden/make_full_length.py), or None."""
+    if not os.path.exists(GOLDEN):
         return None
-    return float(per.group(1)) * cycles_per_launch
+    w = json.load(open(GOLDEN))["workloads"].get(f"mesh208_period{period}")
+    return w["checkpoints"][-1] if w else None
+
+
+def oracle_full_run(job):
+    """A spawn-process worker: the oracle as it stands runs one whole period
+    run of the 208x208 workload, single-threaded; returns its wall seconds and
+    end state (counters, full state hash)."""
+    params, cycles = job
+    sys.path.insert(0, ROOT)
+    from oracle import oracle
+    oracle.build()
+    o = oracle.OracleSim(params)
+    t0 = time.perf_counter()
+    o.step(cycles)
+    dt = time.perf_counter() - t0
+    out = dict(seconds=dt, stats=o.stats(), state_hash=str(o.state_hash()))
+    o.close()
+    return out
 
 
 # --------------------------------------------------------------------- GPU arm
 def run_gpu(args):
+    # the oracle's full period-10 run starts first, in a spawned process on
+    # one host core, and runs while the GPU arm does
+    cpu_job = None
+    rank, world, local = dist_env()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import multiprocessing as mp
+        cpu_pool = mp.get_context("spawn").Pool(1)
+        cpu_job = cpu_pool.apply_async(oracle_full_run, ((I.mesh_208(args.cpu_period), args.cycles),))
+
     import torch
     import torch.distributed as dist
 
     from paper_1508_03235_b300 import noc
 
-    rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -227,11 +294,28 @@ def run_gpu(args):
     end_hashes = [s.state_hash() for s in sims]
     alg_total = args.steps * sum(algorithmic_bytes(st, TILES * cycles, sims[0].params)
                                  for st in stats)
+    impl_total = args.steps * sum(implementation_bytes(st, TILES * cycles, sims[0].params)
+                                  for st in stats)
     alg = alg_total / n_launch                 # per launch
     avg_launch_ms = kernel_ms / n_launch
     peak, peak_kind = measured_peaks()
     achieved = alg_total / (kernel_ms / 1e3) / 1e9
     traffic = measured_traffic(args.steps * len(PERIODS) * cycles / n_launch)
+    captured = captured_per_cycle()
+    us_per_cycle = 1e3 * kernel_ms / (args.steps * len(PERIODS) * cycles)
+
+    # bit-exact check of the timed runs (outside the timed region) against the
+    # oracle's stored full-length records of the same five runs
+    parity = {"runs_checked": 0, "runs_equal": 0}
+    if cycles == CYCLES:
+        for P, st, h in zip(PERIODS, stats, end_hashes):
+            rec = golden_final(P)
+            if rec is None:
+                continue
+            parity["runs_checked"] += 1
+            same = all(st[k] == v for k, v in rec["stats"].items()) and str(h) == rec["state_hash"]
+            parity["runs_equal"] += int(same)
+        parity["against"] = "tests/golden/full_length.json (the oracle's records of the five runs)"
 
     # end to end through the public API: reset, run, read the counters back
     e2e_steps = max(1, min(args.steps, 3))
@@ -251,12 +335,27 @@ def run_gpu(args):
 
     batch = surrogate = None
     if not args.no_batch:
-        batch = batch_section(args.batch_n, args.batch_cycles, args.batch_rect)
+        batch = batch_section(args.batch_n, args.batch_cycles, rank=rank, world=world)
         surrogate = surrogate_section()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(cycles_per_period=args.cpu_cycles)
+    if cpu_job is not None:
+        res = cpu_job.get()
+        cpu_pool.close()
+        cpu_pool.join()
+        P = args.cpu_period
+        rc = TILES * cycles
+        gpu_st = stats[PERIODS.index(P)] if P in PERIODS else None
+        cpu = {"value": rc / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "host_cores": os.cpu_count(),
+               "sample": f"one whole run of the workload: the 208x208 mesh at period {P}, "
+                         f"{cycles} cycles from cycle 0 ({rc} router-cycles, "
+                         f"{res['seconds']:.1f} s, single thread, in a spawned process while "
+                         f"the GPU arm ran)",
+               "gpu_equal": (gpu_st is not None and all(gpu_st[k] == v for k, v in res["stats"].items())
+                             and str(end_hashes[PERIODS.index(P)]) == res["state_hash"])}
+        if not args.no_c3_baseline:
+            cpu["batch_workload"] = oracle_batch_sample(args.c3_every, args.batch_cycles)
 
     if rank == 0:
         line = {
@@ -266,16 +365,26 @@ def run_gpu(args):
             "data": "synthetic (seeded Philox reference streams; the paper's traces are unavailable)",
             "config": workload_config({"cycles_per_run": cycles, "tiling": list(tiling),
                                        "thread_map": noc.THREAD_MAPS[sims[0].thread_map()],
+                                       "kernel_build": sims[0].variant(),
                                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "kernel": "noc::run_kernel",
                          "launches": n_launch, "avg_launch_ms": avg_launch_ms,
-                         "alg_bytes_per_launch": alg},
+                         "us_per_simulated_cycle": us_per_cycle,
+                         "alg_bytes_per_launch": alg,
+                         "alg_bytes_per_router_cycle": alg_total / (rc_per_rank),
+                         "byte_model": "128 B links + 48 B core/queue scalars per router-cycle; "
+                                       "L1 set per reference; L2 set per L1 miss; L2 set per "
+                                       "ejected flit (+4 B directory word under LSPD)",
+                         "implementation_bytes_frac": impl_total / (kernel_ms / 1e3) / 1e9 / peak,
+                         "dram_bytes_per_cycle": captured["dram_bytes_per_cycle"],
+                         "lts_bytes_per_cycle": captured["lts_bytes_per_cycle"]},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": gpu_launches,
             "clocks": clk,
+            "parity": parity,
             "period_runs": {"periods": list(PERIODS), "refs": [st["refs"] for st in stats],
                             "distinct_end_states": len(set(end_hashes))},
             "batch": batch,
@@ -300,34 +409,47 @@ def replica_throughput(ms, units_per_rank, world, device="cpu"):
 
 
 # --------------------------------------------------------------------- batch + surrogate
-def batch_section(n, cycles, rect, thread_map=2):
+def batch_section(n, cycles, rank=0, world=1, one_at_a_time_map=2):
     """The batched-engine half of the metric: n independent design points
     (mixed sizes, loads, mixes and L2 policies) in one persistent launch per
-    memory wave, against the same instances run one at a time through the
-    single-simulation path on the same GPU."""
+    kernel-variant group and memory wave, with the autotuner's layout for each
+    group, against the same instances run one at a time through the
+    single-simulation path on the same GPU.  With several ranks the instances
+    are split by cost (shard.partition_by_cost), each rank runs its share, the
+    job takes the slowest rank's time, and the per-instance results are
+    gathered on every rank and checked for completeness."""
     import torch
 
-    from paper_1508_03235_b300 import noc
+    from paper_1508_03235_b300 import noc, shard
     pts = I.batch_design_points(n, seed=0)
     for p in pts:
         p.pop("design")
+    parts = shard.partition_by_cost([shard.instance_cost(p, cycles) for p in pts], world)
+    mine = parts[rank]
+    local_pts = [pts[i] for i in mine]
     tiles = sum(p["mesh_w"] * p["mesh_h"] for p in pts)
-    b = noc.Batch(pts, cycles, rect=rect, collect_hash=False, thread_map=thread_map)
+    b = noc.Batch(local_pts, cycles, collect_hash=False)
+    layouts = {}
+    for k, i in enumerate(mine):
+        layouts.setdefault(b.group(k), b.layouts[k])
     b.run()                                   # warm-up (also checks every instance)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     b.run()
     tb = time.perf_counter() - t0
     waves, launches = b.waves, b.launches
+    local = {i: {k: b.stats(k)[k2] for k2 in ("ejected", "deflections", "l2lat_sum")}
+             for k, i in enumerate(mine)}
     b.close()
+    merged = shard.gather_results(local, n, world)
     # one at a time: each instance created (allocation untimed), run to its
     # cycle count and read back, before the next starts
-    for p in pts[:2]:
+    for p in local_pts[:2]:
         noc.Sim(p).step(100)
     torch.cuda.synchronize()
     t1 = 0.0
-    for p in pts:
-        s = noc.Sim(p, thread_map=thread_map)
+    for p in local_pts:
+        s = noc.Sim(p, thread_map=one_at_a_time_map)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s.reset()
@@ -336,13 +458,24 @@ def batch_section(n, cycles, rect, thread_map=2):
         t1 += time.perf_counter() - t0
         s.close()
         del s
-    return {"instances": n, "cycles": cycles, "rect": rect,
-            "thread_map": noc.THREAD_MAPS[thread_map], "waves": waves,
+    tb = replica_throughput(tb * 1e3, 1, world, device="cuda")[0] / 1e3   # the slowest rank's
+    t1 = replica_throughput(t1 * 1e3, 1, world, device="cuda")[0] / 1e3
+    return {"instances": n, "cycles": cycles, "waves": waves, "ranks": world,
+            "layouts": {tune_group_name(g): {"rect": lay[0], "strips": bool(lay[1]),
+                                             "thread_map": noc.THREAD_MAPS[lay[2]]}
+                        for g, lay in sorted(layouts.items())},
+            "layout_source": "autotuner (tune.tune_batch) per kernel-variant group",
+            "instances_gathered": len(merged),
             "batched_sims_per_s": n / tb, "one_at_a_time_sims_per_s": n / t1,
             "speedup": t1 / tb, "batched_router_cycles_per_s": tiles * cycles / tb,
             "one_at_a_time_router_cycles_per_s": tiles * cycles / t1,
             "workload": "design points: side U{8..128}, period U{2..40}, Dirichlet(2,2,1) "
                         "private/shared/remote, policy U{interleaved, LSPD, LSPD+migration}"}
+
+
+def tune_group_name(g):
+    from paper_1508_03235_b300 import tune
+    return tune.GROUP_NAMES[g]
 
 
 def surrogate_section(reps=20, replays=20):
@@ -388,23 +521,27 @@ def surrogate_section(reps=20, replays=20):
 
 
 # --------------------------------------------------------------------- CPU arms
-def cpu_baseline(cycles_per_period=400):
-    """The oracle as it stands, single-threaded, on the first
-    `cycles_per_period` cycles of each period's run."""
-    from oracle import oracle
-    oracle.build()
-    rc = 0
-    t = 0.0
-    for P in PERIODS:
-        o = oracle.OracleSim(I.mesh_208(P))
-        t0 = time.perf_counter()
-        o.step(cycles_per_period)
-        t += time.perf_counter() - t0
-        rc += TILES * cycles_per_period
-        o.close()
-    return {"value": rc / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {cycles_per_period} cycles of each of the {len(PERIODS)} period runs "
-                      f"of the 208x208 workload ({rc} router-cycles, {t:.1f} s)"}
+def oracle_batch_sample(every=32, cycles=20_000):
+    """The oracle as it stands on a sample of the batch workload (every
+    `every`-th of the 512 design points, `cycles` cycles each), one process
+    per host core: simulations per second over all cores (wall time) and on
+    one core (the processes' summed times)."""
+    import multiprocessing as mp
+    pts = I.batch_design_points(512, seed=0)[::every]
+    for p in pts:
+        p.pop("design")
+    jobs = sorted([(p, cycles) for p in pts], key=lambda j: -j[0]["mesh_w"])
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(cores, len(jobs))) as pool:
+        res = pool.map(_oracle_instance, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    busy = sum(dt for _, dt in res)
+    rc = sum(r for r, _ in res)
+    return {"instances": len(jobs), "cycles": cycles, "cores": min(cores, len(jobs)),
+            "all_cores_sims_per_s": len(jobs) / wall, "all_cores_router_cycles_per_s": rc / wall,
+            "one_core_sims_per_s": len(jobs) / busy, "one_core_router_cycles_per_s": rc / busy,
+            "sample": f"every {every}th of the 512 design points of the batch workload"}
 
 
 def _oracle_instance(job):
@@ -496,13 +633,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cycles", type=int, default=CYCLES, help="cycles per period run")
-    ap.add_argument("--cpu-cycles", type=int, default=400)
+    ap.add_argument("--cpu-period", type=int, default=10,
+                    help="period of the 208x208 run the oracle times (one whole run)")
     ap.add_argument("--ref-cycles", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c3-baseline", action="store_true",
+                    help="skip the oracle's sample of the batch workload over the host cores")
+    ap.add_argument("--c3-every", type=int, default=32)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-cycles", type=int, default=20_000)
-    ap.add_argument("--batch-rect", type=int, default=8)
     ap.add_argument("--oracle-configs", action="store_true",
                     help="time the oracle on the 8x8, 64x64 and batch workloads (host cores) and exit")
     args = ap.parse_args()

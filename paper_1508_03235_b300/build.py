@@ -22,6 +22,7 @@ UNITS = ([("noc_run_variant.cu", {"NOC_HASH": h, "NOC_DRAIN": d, "NOC_W1": w1, "
          + [("noc_batch.cu", {"NOC_W1": w1, "NOC_W2": w2, "NOC_BASE": 1}) for (w1, w2) in WAY_BOUNDS]
          + [("noc_batch.cu", {"NOC_W1": w1, "NOC_W2": w2, "NOC_FIXED_POLICY": 0, "NOC_FIXED_MODE": 0,
                               "NOC_EXACT_WAYS": 1}) for (w1, w2) in WAY_BOUNDS]
+         + [("noc_run_multi.cu", {"NOC_W1": w1, "NOC_W2": w2}) for (w1, w2) in WAY_BOUNDS]
          + [("noc_kernel.cu", {}), ("noc_api.cu", {}), ("noc_static.cu", {}), ("mlp.cu", {})])
 SOURCES = sorted({u[0] for u in UNITS})
 BUILD = os.path.join(ROOT, "_build")

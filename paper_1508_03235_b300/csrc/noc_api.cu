@@ -12,7 +12,7 @@
 #include <vector>
 
 #include "noc.h"
-#include "noc_internal.h"
+#include "noc_host.h"
 
 using namespace noc;
 

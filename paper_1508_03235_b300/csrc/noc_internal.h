@@ -3,19 +3,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
-#include "noc.h"
 #include "noc_model.cuh"
 
 namespace noc {
-
-// the C ABI's error reporting: stores the formatted message that
-// noc_last_error() returns (thread-local) and returns code
-int fail(int code, const char* fmt, ...);
-// check a configuration exactly as noc_create does (NOC_ERR_ARG with the
-// reason set through fail() when invalid) and fill every model field of P;
-// the device pointers of P are left null
-int configure(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, const noc_traffic* tr,
-              uint64_t seed, Params& P);
 
 // global cycle flags per CTA rectangle: one per warp (the plain cycle loop),
 // slot 0 for the CTA as a whole (the traced and draining loops)
@@ -64,10 +54,6 @@ int block_threads(int W, int H, int gx, int gy);
 size_t run_smem_bytes(int threads);
 
 cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s);
-// the build of the cycle kernel launch_run picks for (P, A): loop << 8 |
-// kind << 4 | way class, with loop 1 for the traced / draining loop, kind a
-// KIND_* value and way class 0 = (4, 8), 1 = (4, 16), 2 = (16, 16) bounds
-int run_variant(const Params& P, const RunArgs& A);
 cudaError_t max_coresident_ctas(const Params& P, int threads, int* out);
 cudaError_t launch_dyn_hash(const Params& P, uint32_t cycle, unsigned long long* out,
                             cudaStream_t s);

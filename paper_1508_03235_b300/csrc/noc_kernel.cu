@@ -1,5 +1,6 @@
 // noc_kernel.cu -- state-hash, statistics and drain helper kernels, and the
 // dispatch to the cycle-kernel variants.
+#include "noc_host.h"
 #include "noc_kernel.cuh"
 
 namespace noc {
@@ -33,6 +34,12 @@ namespace noc {
 NOC_DECL_WAYS(4, 8)
 NOC_DECL_WAYS(4, 16)
 NOC_DECL_WAYS(16, 16)
+#define NOC_DECL_MULTI(w1, w2)                                                                  \
+  cudaError_t launch_multi_##w1##_##w2(const Params&, const RunArgs&, cudaStream_t);           \
+  cudaError_t max_coresident_multi_##w1##_##w2(int threads, int* out);
+NOC_DECL_MULTI(4, 8)
+NOC_DECL_MULTI(4, 16)
+NOC_DECL_MULTI(16, 16)
 
 // way-bound class of a configuration: 0 = (4, 8), 1 = (4, 16), 2 = (16, 16)
 static int way_class(int l1_ways, int l2_ways) {
@@ -65,6 +72,30 @@ int run_variant(const Params& P, const RunArgs& A) {
   const int traced = (A.hash_trace || A.busy) ? 1 : 0;
   const int kind = traced ? KIND_GEN : variant_kind(P);
   return (traced << 8) | (kind << 4) | way_class(P.l1_ways, P.l2_ways);
+}
+
+int multi_variant(const Params& P) { return (2 << 8) | (KIND_GEN << 4) | way_class(P.l1_ways, P.l2_ways); }
+
+cudaError_t launch_multi(const Params& P, const RunArgs& A, cudaStream_t s) {
+  switch (way_class(P.l1_ways, P.l2_ways)) {
+    case 0: return launch_multi_4_8(P, A, s);
+    case 1: return launch_multi_4_16(P, A, s);
+    default: return launch_multi_16_16(P, A, s);
+  }
+}
+
+cudaError_t max_coresident_multi(const Params& P, int threads, int* out) {
+  switch (way_class(P.l1_ways, P.l2_ways)) {
+    case 0: return max_coresident_multi_4_8(threads, out);
+    case 1: return max_coresident_multi_4_16(threads, out);
+    default: return max_coresident_multi_16_16(threads, out);
+  }
+}
+
+int multi_threads(int W, int H, int gx, int gy) {
+  const int bw = (W + gx - 1) / gx, bh = (H + gy - 1) / gy;
+  const int per = (bw * bh + 1) / 2;
+  return ((per + 31) / 32) * 32;
 }
 
 cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {

@@ -164,6 +164,12 @@ constexpr int MAX_THREADS = 384;
 #ifndef NOC_POLL_STAGE
 #define NOC_POLL_STAGE 1
 #endif
+// With the staged polls, the first copy of the next cycle's edge slots can be
+// issued right after this warp publishes (NOC_EARLY_POLL 1), so that its L2
+// round trip overlaps Phase 3 and Phase 1 instead of following them.
+#ifndef NOC_EARLY_POLL
+#define NOC_EARLY_POLL 1
+#endif
 
 // shared memory before the poll stage: links [2 parity][4 port][threads],
 // histograms, reduction words
@@ -502,13 +508,18 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
       // copy still in flight when the wait ends lands in the buffer that the
       // next cycle's first round writes; it holds the other parity's tags,
       // which never match, and cp.async.wait_group retires it first.
+#if NOC_EARLY_POLL
+      if (t == t0 + 1)   // later cycles issued their first copy at the publish
+#endif
+      {
 #pragma unroll
-      for (int d = 0; d < 4; ++d)
-        if (need & (1u << d)) {
-          cp_async16_cg(stg + d * 2, gt + rin[d]);
-          cp_async16_cg(stg + d * 2 + 1, gt + rin[d] + 1);
-        }
-      cp_async_commit();
+        for (int d = 0; d < 4; ++d)
+          if (need & (1u << d)) {
+            cp_async16_cg(stg + d * 2, gt + rin[d]);
+            cp_async16_cg(stg + d * 2 + 1, gt + rin[d] + 1);
+          }
+        cp_async_commit();
+      }
 #endif
       for (unsigned it = 0;; ++it) {
 #if NOC_POLL_STAGE
@@ -574,6 +585,20 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
       __threadfence_block();
       *reinterpret_cast<volatile unsigned*>(&wflag[warp]) = t + 1;
     }
+#if NOC_POLL_STAGE && NOC_EARLY_POLL
+    // the first copy of the slots the next cycle's wait reads (the outputs of
+    // cycle t), into the stage half that wait reads first
+    if (t + 1 != tend && t != t0) {
+      const uint4* gtn = P.gtag + (t & 1u) * pstride;
+#pragma unroll
+      for (int d = 0; d < 4; ++d)
+        if (boundary & (1u << d)) {
+          cp_async16_cg(stg + d * 2, gtn + rin[d]);
+          cp_async16_cg(stg + d * 2 + 1, gtn + rin[d] + 1);
+        }
+      cp_async_commit();
+    }
+#endif
     // ---- Phase 3 of this cycle and Phase 1 of the next (own tile only)
     if (active) {
       phase3<W1, W2>(P, T, t, sh_hist);
@@ -582,6 +607,9 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
   }
 
   // ---- end of launch: full link state of the last cycle, tile state, counters
+#if NOC_POLL_STAGE
+  asm volatile("cp.async.wait_all;" ::: "memory");   // no stage copy outlives the CTA
+#endif
   __syncthreads();
   if (active) {
     const uint32_t plast = (t - (t == tend ? 1u : 0u)) & 1u;

@@ -19,7 +19,7 @@
 #include <mutex>
 
 #include "noc.h"
-#include "noc_internal.h"
+#include "noc_host.h"
 
 using namespace noc;
 

@@ -15,8 +15,8 @@ design points: capture `-k regex:infer_kernel -s 2 -c 1`.
     python -m paper_1508_03235_b300.profile_case --case batch --instances 64 --batch-cycles 2000
 
 runs the first `--instances` design points of the batch workload for
-`--batch-cycles` cycles through the batch engine (8x8 rectangles, column
-order): one work-queue launch per kernel-variant group; capture
+`--batch-cycles` cycles through the batch engine (the autotuner's layout per
+kernel-variant group): one work-queue launch per group; capture
 `-k regex:batch_kernel -c 1`.
 """
 from __future__ import annotations
@@ -55,7 +55,7 @@ def main(argv=None):
         pts = I.batch_design_points(512, seed=0)[: a.instances]
         for p in pts:
             p.pop("design")
-        b = noc.Batch(pts, a.batch_cycles, rect=8, collect_hash=False, thread_map=2)
+        b = noc.Batch(pts, a.batch_cycles, collect_hash=False)     # the tuned layouts
         b.run()
         torch.cuda.synchronize()
         tiles = sum(p["mesh_w"] * p["mesh_h"] for p in pts)

@@ -210,10 +210,11 @@ def targets(stats: dict, tiles: int) -> np.ndarray:
     return np.array([math.log(max(lat, 1e-9)), defl, acc], dtype=np.float64)
 
 
-def simulate(designs_params, cycles, rect=8):
-    """Exact outputs of design points through the batch engine."""
+def simulate(designs_params, cycles):
+    """Exact outputs of design points through the batch engine, in the
+    autotuner's layout for each kernel-variant group."""
     b = noc.Batch([{k: v for k, v in p.items() if k != "design"} for p in designs_params], cycles,
-                  rect=rect, collect_hash=False)
+                  collect_hash=False)
     b.run()
     ys = np.stack([targets(b.stats(i), p["mesh_w"] * p["mesh_h"])
                    for i, p in enumerate(designs_params)])
@@ -292,6 +293,59 @@ class Surrogate:
             out.append(y[:, :N_OUT].double().cpu().numpy())
         Z = np.concatenate(out)
         return Z * self.sd + self.mu
+
+
+# ----------------------------------------------------------------- screening
+def screen(pred, true, k, top_frac=0.01, objective=0, minimise=True, random_draws=200, seed=0):
+    """Design-space screening with the network: of a candidate pool whose
+    exact outputs `true` are known, pick the k candidates the network ranks
+    best on output `objective` (the ones the exact simulator would then run)
+    and report the recall of the pool's true best top_frac, against k picks
+    at random (the same simulator budget), averaged over random_draws draws.
+    Returns (network recall, mean random recall, the true top indices)."""
+    n = len(true)
+    m = max(1, int(round(top_frac * n)))
+    sign = 1.0 if minimise else -1.0
+    best = set(np.argsort(sign * true[:, objective], kind="stable")[:m].tolist())
+    picks = np.argsort(sign * pred[:, objective], kind="stable")[:k]
+    recall = len(best & set(picks.tolist())) / m
+    rng = np.random.default_rng(seed)
+    rnd = np.mean([len(best & set(rng.choice(n, size=k, replace=False).tolist())) / m
+                   for _ in range(random_draws)])
+    return recall, float(rnd), sorted(best)
+
+
+def evaluate(train=2_000, holdout=500, cycles=20_000, seeds=(0,), epochs=400, batch=256, lr=2e-3,
+             data_seed=11, screen_k=None, log=None):
+    """Simulate train + holdout design points of the batch workload with the
+    batch engine, train one network per seed on the first `train`, and score
+    each on the held-out points: per-output mean relative error (S-3
+    definitions, relative_errors) and, with the held-out points as a
+    candidate pool, the screening recall of the best 1% by mean L2 access
+    latency when the network picks screen_k of them (default 5%).  Returns a
+    dict of the per-seed results and the simulation / training times."""
+    import time
+    pts = I.batch_design_points(train + holdout, seed=data_seed)
+    X = np.stack([features(p["design"]) for p in pts])
+    a = time.perf_counter()
+    Y = simulate(pts, cycles)
+    sim_s = time.perf_counter() - a
+    k = screen_k or max(1, holdout // 20)
+    runs = []
+    for sd in seeds:
+        model = Surrogate(seed=sd, max_batch=4096)
+        a = time.perf_counter()
+        model.fit(X[:train], Y[:train], epochs=epochs, batch=batch, lr=lr, seed=sd)
+        train_s = time.perf_counter() - a
+        pred = model.predict(X[train:])
+        mre = relative_errors(pred, Y[train:]).mean(axis=0)
+        rec, rnd, _ = screen(pred, Y[train:], k, objective=0, seed=sd)
+        runs.append({"seed": sd, "mre": dict(zip(OUT_NAMES, map(float, mre))),
+                     "screen_recall": rec, "random_recall": rnd, "train_s": train_s})
+        if log:
+            log(f"seed {sd}: MRE {mre}, screening recall {rec:.2f} (random {rnd:.3f})")
+    return {"train": train, "holdout": holdout, "cycles": cycles, "screen_k": k,
+            "simulate_s": sim_s, "runs": runs}
 
 
 # ----------------------------------------------------------------- full run

@@ -1,11 +1,15 @@
 """The batch engine on the full 512-instance workload (sides 8..128, periods
 2..40, Dirichlet(2,2,1) address mixes, all three L2 policies, seeds 1..512,
-20,000 cycles each) in the launch configuration the bench times (8x8-tile
-rectangles, column-major thread order): every instance satisfies the model's conservation laws, and a
-stratified sample (each policy at its smallest and a mid-size mesh, plus a
-128x128 mesh) equals its oracle run bit for bit.  With NOC_FULL_C3=1 every one
-of the 512 instances is compared with its oracle run (about an hour of oracle
-time, spread over the host's cores)."""
+20,000 cycles each) in the launch configuration the bench times (the
+autotuner's layout for each kernel-variant group): every instance satisfies
+the model's conservation laws, and every one of the 512 equals the oracle's
+record of the same run (tests/golden/batch_c3.json, written by
+tests/golden/make_batch_c3.py) in all counters, the full state hash and both
+latency histograms.  A stratified sample (each policy at its smallest and a
+mid-size mesh, plus a 128x128 mesh) is also re-run through the oracle here,
+with full histograms."""
+import hashlib
+import json
 import os
 
 import numpy as np
@@ -16,8 +20,7 @@ from paper_1508_03235_b300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 CYCLES = 20_000
-RECT = 8
-THREAD_MAP = 2
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch_c3.json")
 
 
 @pytest.fixture(scope="module")
@@ -39,7 +42,7 @@ def c3_points():
 
 @pytest.fixture(scope="module")
 def c3_batch(noc, c3_points):
-    b = noc.Batch(c3_points, CYCLES, rect=RECT, thread_map=THREAD_MAP)
+    b = noc.Batch(c3_points, CYCLES)          # the tuned layouts, as the bench runs it
     b.run()
     res = [(b.stats(i), b.state_hash(i), b.hist(i, 0), b.hist(i, 1)) for i in range(len(c3_points))]
     b.close()
@@ -87,14 +90,18 @@ def test_c3_sample_matches_oracle(c3_points, c3_batch):
         compare(i, c3_batch[i], w)
 
 
-@pytest.mark.skipif(os.environ.get("NOC_FULL_C3") != "1", reason="set NOC_FULL_C3=1 (about an hour of oracle CPU time)")
-def test_c3_every_instance_matches_oracle(c3_points, c3_batch):
-    from tests.oracle_pool import run_many
-    want = run_many(c3_points, CYCLES)
+def hist_digest(h) -> str:
+    return hashlib.sha256(np.ascontiguousarray(h, dtype="<u8").tobytes()).hexdigest()[:16]
+
+
+def test_c3_every_instance_matches_oracle_records(c3_points, c3_batch):
+    with open(GOLDEN) as fh:
+        doc = json.load(fh)
+    assert doc["instances"] == len(c3_points) and doc["cycles"] == CYCLES
     bad = []
-    for i, w in enumerate(want):
-        try:
-            compare(i, c3_batch[i], w)
-        except AssertionError:
+    for i, (rec, (gs, gh, g0, g1)) in enumerate(zip(doc["records"], c3_batch)):
+        ok = (all(gs[k] == v for k, v in rec["stats"].items()) and str(gh) == rec["state_hash"]
+              and [hist_digest(g0), hist_digest(g1)] == rec["hist_sha"])
+        if not ok:
             bad.append(i)
     assert not bad, f"{len(bad)} of {len(c3_points)} instances differ: {bad[:10]}"

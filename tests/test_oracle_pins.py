@@ -837,3 +837,26 @@ def test_full_length_records_match_the_oracle_now(oracle_mod):
         assert str(o.dyn_hash()) == rec["dyn_hash"] and str(o.state_hash()) == rec["state_hash"]
         assert [{str(i): int(v) for i, v in enumerate(o.hist(w)) if v} for w in (0, 1)] == rec["hist"]
         o.close()
+
+
+def test_batch_records_match_the_oracle_now(oracle_mod):
+    """The stored 512-instance records (tests/golden/batch_c3.json) are the
+    oracle's: two small instances recomputed now equal their records."""
+    import hashlib
+    import json
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch_c3.json")
+    with open(path) as fh:
+        doc = json.load(fh)
+    pts = I.batch_design_points(doc["instances"], seed=doc["design_seed"])
+    small = sorted(range(len(pts)), key=lambda i: (pts[i]["mesh_w"], i))[:2]
+    for i in small:
+        p = dict(pts[i])
+        p.pop("design")
+        o = oracle_mod.OracleSim(p)
+        o.step(doc["cycles"])
+        rec = doc["records"][i]
+        assert o.stats() == rec["stats"] and str(o.state_hash()) == rec["state_hash"], i
+        dig = [hashlib.sha256(np.ascontiguousarray(o.hist(w), dtype="<u8").tobytes()).hexdigest()[:16]
+               for w in (0, 1)]
+        assert dig == rec["hist_sha"], i
+        o.close()
