@@ -128,7 +128,7 @@ typedef struct noc_sim noc_sim;
 /* Create a simulation handle (host-side only; device memory is taken at the
  * first call that needs it, from noc_bind_memory or else cudaMalloc on the
  * current device).  Returns NOC_ERR_ARG for an invalid configuration
- * (mesh_w * mesh_h above the co-resident limit, bad geometry). */
+ * (mesh_w * mesh_h above 65,535 tiles, bad geometry). */
 int noc_create(int mesh_w, int mesh_h, const noc_cache_cfg* cache, int l2_policy,
                const noc_traffic* traffic, uint64_t seed, noc_sim** out);
 void noc_destroy(noc_sim* sim);
@@ -185,6 +185,19 @@ int noc_hash_trace(noc_sim* sim, uint64_t* buf, int64_t n);
  * 0,0 = the library's choice.  Results never depend on it. */
 int noc_set_tiling(noc_sim* sim, int gx, int gy);
 int noc_get_tiling(const noc_sim* sim, int* gx, int* gy);
+
+/* Tiles per thread of the plain loop: 1 keeps each tile's state in its
+ * thread's registers for a whole launch (the fast loop; a mesh must then fit
+ * one co-resident launch, about 55,700 tiles on a B300); 2 runs two tiles per
+ * thread and moves each tile's state through its device records around every
+ * cycle (slower per tile, but every mesh of up to 65,535 tiles -- the limit of
+ * the 16-bit tile indices a flit carries -- fits a B300); 0 = automatic (1 if
+ * the mesh fits that way, else 2, the default).  With two, per-cycle hash
+ * traces and noc_drain are NOC_ERR_ARG (they need the one-tile loop); results
+ * never depend on it.  noc_get_tiles_per_thread returns the value in use
+ * (0 before the first launch, -1 for a null handle). */
+int noc_set_tiles_per_thread(noc_sim* sim, int k);
+int noc_get_tiles_per_thread(const noc_sim* sim);
 
 /* Tile-to-thread order inside each CTA rectangle: 0 = perimeter tiles first
  * (the default), 1 = row-major, 2 = column-major.  Results never depend on
@@ -317,7 +330,8 @@ int64_t noc_kernel_launches(const noc_sim* sim);
  * never depend on it; it lets a caller (and the tests) see that a
  * configuration ran on the specialised code it qualifies for.
  *   *loop:  0 = the plain loop (per-warp neighbour waits; noc_step),
- *           1 = the traced / draining loop (hash trace on, or noc_drain);
+ *           1 = the traced / draining loop (hash trace on, or noc_drain),
+ *           2 = the plain loop with two tiles per thread (always general);
  *   *kind:  0 = general (every policy, mode and option compiled in),
  *           1 = base (every policy and mode; the packet, write-back,
  *               directory-node and deflection-count-age options compiled out),

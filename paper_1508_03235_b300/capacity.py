@@ -5,11 +5,13 @@ the GPU's memory for four cache configurations (L1 sets/ways, L2 sets/ways,
 with and without migration).  Here three limits are reported per
 configuration: device memory (the library's own arena layout, noc_create +
 noc_required_bytes, no device needed), the 65,535 tiles that 16-bit tile
-indices in a flit can address, and -- the binding one -- how many tiles one
-co-resident launch holds: a tile's state lives in one thread's registers, so
-the register file of 148 SMs bounds the mesh.  With `--run` the largest square
-mesh that launches is found on the GPU (a search over sides) and simulated for
-a few cycles.
+indices in a flit can address -- the binding one -- and how many tiles the
+fast loop holds: with one tile per thread a tile's state lives in its
+thread's registers, so the register file of 148 SMs bounds the mesh (about
+236 x 236); larger meshes run with two tiles per thread.  With `--run` the
+largest square mesh of the fast loop is found on the GPU (a search over
+sides), and it and the largest mesh the tile indices allow (255 x 257) are
+simulated for a few cycles.
 
     python -m paper_1508_03235_b300.capacity [--mem-gb G] [--run --cycles C]
 
@@ -79,12 +81,13 @@ def capacity(cache_over, policy, mem_bytes):
     return per_tile, by_mem, min(by_mem, MAX_TILES)
 
 
-def launches(side, cache_over, policy) -> bool:
-    """Whether a side x side mesh runs as one co-resident launch."""
+def launches(side, cache_over, policy, tiles_per_thread=None) -> bool:
+    """Whether a side x side mesh runs as one co-resident launch (with the
+    given tiles per thread; None: the library's choice)."""
     from . import noc
     s = None
     try:
-        s = noc.Sim(params_for(side, side, cache_over, policy))
+        s = noc.Sim(params_for(side, side, cache_over, policy), tiles_per_thread=tiles_per_thread)
         s.step(1)
         return True
     except noc.NocError as e:
@@ -96,36 +99,34 @@ def launches(side, cache_over, policy) -> bool:
             s.close()
 
 
-def largest_square(cache_over, policy, hi=255) -> int:
+def largest_square(cache_over, policy, hi=255, tiles_per_thread=None) -> int:
     """The largest side whose square mesh launches (binary search)."""
     lo = 1
     while lo < hi:
         mid = (lo + hi + 1) // 2
-        if launches(mid, cache_over, policy):
+        if launches(mid, cache_over, policy, tiles_per_thread):
             lo = mid
         else:
             hi = mid - 1
     return lo
 
 
-def run_largest(cache_over, policy, cycles, side=None):
-    """Simulate the largest square mesh that launches; (side, router-cycles/s, counters)."""
+def run_mesh(w, h, cache_over, policy, cycles, tiles_per_thread=None):
+    """Simulate a w x h mesh; (router-cycles/s, counters, tiles per thread)."""
     import time
 
     import torch
 
     from . import noc
-    side = side or largest_square(cache_over, policy)
-    w = h = side
-    s = noc.Sim(params_for(w, h, cache_over, policy))
+    s = noc.Sim(params_for(w, h, cache_over, policy), tiles_per_thread=tiles_per_thread)
     s.step(50)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s.step(cycles)
     dt = time.perf_counter() - t0
-    st = s.stats()
+    st, tpt = s.stats(), s.tiles_per_thread()
     s.close()
-    return side, w * h * cycles / dt, st
+    return w * h * cycles / dt, st, tpt
 
 
 def main(argv=None):
@@ -149,10 +150,15 @@ def main(argv=None):
         row = {"config": label, "bytes_per_tile": round(per_tile), "tiles_by_memory": by_mem,
                "tiles_by_tile_ids": MAX_TILES}
         if a.run:
-            side, rate, st = run_largest(over, pol, a.cycles)
-            row.update(largest_mesh=f"{side}x{side}", max_simulated_cores=side * side,
-                       limit="co-resident registers", router_cycles_per_s=rate,
-                       injected=st["injected"], ejected=st["ejected"])
+            side = largest_square(over, pol, tiles_per_thread=1)
+            rate1, st1, _ = run_mesh(side, side, over, pol, a.cycles, tiles_per_thread=1)
+            w, h = LARGEST_MESH
+            rate2, st2, tpt = run_mesh(w, h, over, pol, a.cycles)
+            row.update(largest_mesh_one_tile_per_thread=f"{side}x{side}",
+                       one_tile_router_cycles_per_s=rate1,
+                       largest_mesh=f"{w}x{h}", max_simulated_cores=w * h, tiles_per_thread=tpt,
+                       limit="16-bit tile indices", router_cycles_per_s=rate2,
+                       injected=st2["injected"], ejected=st2["ejected"])
         rows.append(row)
     print(json.dumps({"device_bytes": mem, "rows": rows}, indent=1))
 

@@ -149,6 +149,8 @@ struct noc_sim {
   cudaStream_t stream = nullptr;
   int gx = 0, gy = 0;          // requested tiling (0 = automatic)
   int run_gx = 0, run_gy = 0;  // tiling in use
+  int tpt = 0;                 // requested tiles per thread (0 = automatic, 1, 2)
+  int run_tpt = 0;             // tiles per thread in use (0 = not chosen yet)
   uint32_t cycle = 0;
   bool draining = false;       // set by noc_drain, cleared by noc_reset
   // tagged edge slots: all zero, or last written by a plain launch ending at
@@ -300,15 +302,20 @@ int ensure_memory(noc_sim* s) {
   return NOC_OK;
 }
 
-// choose the CTA rectangle grid: the fewest CTAs whose rectangles hold at most
-// 128 tiles, else the smallest rectangles that still fit co-resident
-int choose_tiling(noc_sim* s, int* gx_out, int* gy_out) {
+// threads per CTA and co-resident CTAs of a launch with `tpt` tiles per thread
+int launch_threads(const noc_sim* s, int tpt, int gx, int gy) {
+  return tpt == 2 ? multi_threads(s->P.W, s->P.H, gx, gy) : block_threads(s->P.W, s->P.H, gx, gy);
+}
+int max_launch_threads(int tpt) { return tpt == 2 ? MULTI_MAX_THREADS : 384; }
+cudaError_t coresident(const noc_sim* s, int tpt, int threads, int* cap) {
+  return tpt == 2 ? max_coresident_multi(s->P, threads, cap) : max_coresident_ctas(s->P, threads, cap);
+}
+
+// choose the CTA rectangle grid for `tpt` tiles per thread: the fewest CTAs
+// whose rectangles hold at most 128 tiles, else the smallest rectangles that
+// still fit co-resident; NOC_ERR_ARG (without a message) if none does
+int choose_tiling_tpt(noc_sim* s, int tpt, int* gx_out, int* gy_out) {
   const int W = s->P.W, H = s->P.H;
-  if (s->gx > 0 && s->gy > 0) {
-    *gx_out = s->gx;
-    *gy_out = s->gy;
-    return NOC_OK;
-  }
   int cap_of[384 / 32 + 1];
   for (int k = 0; k <= 384 / 32; ++k) cap_of[k] = -1;
   int best_gx = 0, best_gy = 0;
@@ -316,13 +323,13 @@ int choose_tiling(noc_sim* s, int* gx_out, int* gy_out) {
   bool best_small = false;
   for (int gy = 1; gy <= H; ++gy)
     for (int gx = 1; gx <= W; ++gx) {
-      const int threads = block_threads(W, H, gx, gy);
-      if (threads > 384) continue;
+      const int threads = launch_threads(s, tpt, gx, gy);
+      if (threads > max_launch_threads(tpt)) continue;
       const long G = (long)gx * gy;
       if (G * FLAG_SLOTS > (long)s->n_flags) continue;
       int& cap = cap_of[threads / 32];
       if (cap < 0) {
-        cudaError_t e = max_coresident_ctas(s->P, threads, &cap);
+        cudaError_t e = coresident(s, tpt, threads, &cap);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy");
       }
       if (G > cap) continue;
@@ -342,10 +349,39 @@ int choose_tiling(noc_sim* s, int* gx_out, int* gy_out) {
         best_small = small;
       }
     }
-  if (!best_gx) return fail(NOC_ERR_ARG, "mesh %dx%d does not fit one co-resident launch", W, H);
+  if (!best_gx) return NOC_ERR_ARG;
   *gx_out = best_gx;
   *gy_out = best_gy;
   return NOC_OK;
+}
+
+// tiles per thread and CTA rectangle grid of the plain loop: the requested
+// ones, else one tile per thread if the mesh fits one co-resident launch that
+// way, else two
+int choose_layout(noc_sim* s) {
+  const int W = s->P.W, H = s->P.H;
+  const int tries[2] = {s->tpt ? s->tpt : 1, s->tpt ? 0 : 2};
+  for (int tpt : tries) {
+    if (!tpt) break;
+    int gx = s->gx, gy = s->gy;
+    if (gx > 0 && gy > 0) {
+      // the requested tiling, if it fits one co-resident launch this way
+      const int threads = launch_threads(s, tpt, gx, gy);
+      int cap = 0;
+      if (threads <= max_launch_threads(tpt)) CU(coresident(s, tpt, threads, &cap), "occupancy");
+      if (threads > max_launch_threads(tpt) || gx * gy > cap || gx * gy * FLAG_SLOTS > (int)s->n_flags)
+        continue;
+    } else {
+      int rc = choose_tiling_tpt(s, tpt, &gx, &gy);
+      if (rc == NOC_ERR_CUDA) return rc;
+      if (rc) continue;
+    }
+    s->run_tpt = tpt;
+    s->run_gx = gx;
+    s->run_gy = gy;
+    return NOC_OK;
+  }
+  return fail(NOC_ERR_ARG, "mesh %dx%d does not fit one co-resident launch", W, H);
 }
 
 int upload_traces(noc_sim* s) {
@@ -389,15 +425,21 @@ int read_error(noc_sim* s, int64_t* cyc) {
 int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
   int rc = upload_traces(s);
   if (rc) return rc;
-  if (!s->run_gx) {
-    rc = choose_tiling(s, &s->run_gx, &s->run_gy);
+  if (!s->run_gx || !s->run_tpt) {
+    rc = choose_layout(s);
     if (rc) return rc;
   }
-  const int threads = block_threads(s->P.W, s->P.H, s->run_gx, s->run_gy);
+  const int tpt = s->run_tpt;
+  if (tpt == 2 && (busy || s->hash_on))
+    return fail(NOC_ERR_ARG, "per-cycle hashes and drains need one tile per thread (a mesh of one "
+                             "co-resident launch); this one runs two");
+  const int threads = launch_threads(s, tpt, s->run_gx, s->run_gy);
   int cap = 0;
-  CU(max_coresident_ctas(s->P, threads, &cap), "occupancy");
-  if (threads > 384 || s->run_gx * s->run_gy > cap || s->run_gx * s->run_gy * FLAG_SLOTS > (int)s->n_flags)
-    return fail(NOC_ERR_ARG, "tiling %dx%d does not fit one co-resident launch", s->run_gx, s->run_gy);
+  CU(coresident(s, tpt, threads, &cap), "occupancy");
+  if (threads > max_launch_threads(tpt) || s->run_gx * s->run_gy > cap ||
+      s->run_gx * s->run_gy * FLAG_SLOTS > (int)s->n_flags)
+    return fail(NOC_ERR_ARG, "tiling %dx%d does not fit one co-resident launch with %d tile(s) per thread",
+                s->run_gx, s->run_gy, tpt);
   // with references drawn ahead, a launch covers at most refcap references of
   // an on-schedule core
   uint32_t chunk_max = kMaxChunk;
@@ -436,9 +478,14 @@ int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
       }
       CU(cudaEventRecord(s->tev[s->tev_used], s->stream), "event record");
     }
-    CU(launch_run(s->P, A, s->stream), "cycle kernel launch");
+    if (tpt == 2) {
+      CU(launch_multi(s->P, A, s->stream), "cycle kernel launch");
+      s->last_variant = multi_variant(s->P);
+    } else {
+      CU(launch_run(s->P, A, s->stream), "cycle kernel launch");
+      s->last_variant = run_variant(s->P, A);
+    }
     s->launches++;
-    s->last_variant = run_variant(s->P, A);
     if (s->time_kernels) {
       CU(cudaEventRecord(s->tev[s->tev_used + 1], s->stream), "event record");
       s->tev_used += 2;
@@ -560,6 +607,12 @@ int noc_drain(noc_sim* s, int64_t max_cycles, int64_t* taken) {
   if (rc) return rc;
   if (s->P.age_mode && (uint64_t)s->cycle + (uint64_t)max_cycles > (1ull << AGE_SHIFT))
     return fail(NOC_ERR_ARG, "age_mode 1 runs end at or before cycle 2^20");
+  if (!s->run_gx || !s->run_tpt) {
+    rc = choose_layout(s);
+    if (rc) return rc;
+  }
+  if (s->run_tpt == 2)
+    return fail(NOC_ERR_ARG, "a drain needs one tile per thread (a mesh of one co-resident launch)");
   s->draining = true;
   unsigned int busy0 = 0;
   unsigned int* d_b0 = reinterpret_cast<unsigned int*>(scratch_ptr(s));
@@ -705,6 +758,7 @@ int noc_set_tiling(noc_sim* s, int gx, int gy) {
   if (gx == 0 && gy == 0) {
     s->gx = s->gy = 0;
     s->run_gx = s->run_gy = 0;
+    s->run_tpt = 0;
     return NOC_OK;
   }
   if (gx < 1 || gy < 1 || gx > s->P.W || gy > s->P.H || block_threads(s->P.W, s->P.H, gx, gy) > 512 ||
@@ -712,8 +766,19 @@ int noc_set_tiling(noc_sim* s, int gx, int gy) {
     return fail(NOC_ERR_ARG, "tiling %dx%d invalid for mesh %dx%d", gx, gy, s->P.W, s->P.H);
   s->gx = s->run_gx = gx;
   s->gy = s->run_gy = gy;
+  s->run_tpt = 0;  // chosen again (with this tiling) at the next launch
   return NOC_OK;
 }
+
+int noc_set_tiles_per_thread(noc_sim* s, int k) {
+  if (!s) return fail(NOC_ERR_ARG, "null handle");
+  if (k < 0 || k > 2) return fail(NOC_ERR_ARG, "tiles per thread 0 (automatic), 1 or 2");
+  s->tpt = k;
+  s->run_tpt = 0;
+  return NOC_OK;
+}
+
+int noc_get_tiles_per_thread(const noc_sim* s) { return s ? s->run_tpt : -1; }
 
 int noc_get_tiling(const noc_sim* s, int* gx, int* gy) {
   if (!s || !gx || !gy) return fail(NOC_ERR_ARG, "null argument");

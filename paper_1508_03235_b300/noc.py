@@ -90,6 +90,8 @@ def lib():
             "noc_set_tiling": (i32, [vp, i32, i32]),
             "noc_get_tiling": (i32, [vp, C.POINTER(i32), C.POINTER(i32)]),
             "noc_set_thread_map": (i32, [vp, i32]),
+            "noc_set_tiles_per_thread": (i32, [vp, i32]),
+            "noc_get_tiles_per_thread": (i32, [vp]),
             "noc_get_thread_map": (i32, [vp]),
             "noc_set_trace": (i32, [vp, i32, i64, P32]),
             "noc_debug_enqueue": (i32, [vp, i32, i32, P32]),
@@ -145,7 +147,7 @@ class Sim:
     """One simulation on the current CUDA device.  `params` is a flat dict from
     paper_1508_03235_b300.inputs.sim_params()."""
 
-    def __init__(self, params: dict, stream=None, tiling=None, thread_map=None):
+    def __init__(self, params: dict, stream=None, tiling=None, thread_map=None, tiles_per_thread=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the simulator needs a CUDA device")
@@ -169,6 +171,8 @@ class Sim:
             self.set_tiling(*tiling)
         if thread_map is not None:
             self.set_thread_map(thread_map)
+        if tiles_per_thread is not None:
+            self.set_tiles_per_thread(tiles_per_thread)
         _check(lib().noc_reset(h))
 
     def close(self):
@@ -228,6 +232,14 @@ class Sim:
         _check(lib().noc_get_tiling(self._h, C.byref(gx), C.byref(gy)))
         return gx.value, gy.value
 
+    def set_tiles_per_thread(self, k: int):
+        """1: one tile per thread (the fast loop), 2: two (meshes beyond one
+        co-resident launch), 0: automatic."""
+        _check(lib().noc_set_tiles_per_thread(self._h, k))
+
+    def tiles_per_thread(self) -> int:
+        return lib().noc_get_tiles_per_thread(self._h)
+
     def set_thread_map(self, m: int):
         """Tile-to-thread order inside each CTA rectangle: THREAD_MAPS[m]."""
         _check(lib().noc_set_thread_map(self._h, m))
@@ -247,8 +259,8 @@ class Sim:
         "traced"), kind (KERNEL_KINDS) and its way bounds (l1, l2)."""
         v = [C.c_int() for _ in range(4)]
         _check(lib().noc_last_variant(self._h, *[C.byref(x) for x in v]))
-        return dict(loop=("plain", "traced")[v[0].value], kind=KERNEL_KINDS[v[1].value],
-                    bounds=(v[2].value, v[3].value))
+        return dict(loop=("plain", "traced", "plain, two tiles per thread")[v[0].value],
+                    kind=KERNEL_KINDS[v[1].value], bounds=(v[2].value, v[3].value))
 
     def kernel_time(self, enable: bool = True):
         """(ms, launches) of the cycle-kernel launches recorded since the last

@@ -1,7 +1,11 @@
-"""The largest square mesh that runs as one co-resident launch (found by a
-search over sides; one thread per tile bounds it) in each of the four cache
-configurations of Table 4 equals the oracle bit for bit (counters, histogram,
-full state hash), and the next side up is refused with NOC_ERR_ARG."""
+"""Table 4 on a B300.  For each of the four cache configurations:
+
+* the largest square mesh that runs with one tile per thread (the fast loop,
+  bounded by the co-resident threads) equals the oracle bit for bit, and the
+  next side up is refused in that loop;
+* the largest mesh the 16-bit tile indices allow, 255 x 257 = 65,535 tiles,
+  runs (automatically with two tiles per thread) and equals the oracle bit
+  for bit: counters, flit-latency histogram and full state hash."""
 import pytest
 
 from paper_1508_03235_b300 import capacity
@@ -19,16 +23,10 @@ def noc():
     return _noc
 
 
-@pytest.mark.parametrize("row", range(4))
-def test_largest_mesh_matches_oracle(noc, oracle_mod, row):
-    label, over, pol = capacity.table4_rows()[row]
-    side = capacity.largest_square(over, pol)
-    assert side >= 208 and not capacity.launches(side + 1, over, pol)
-    w = h = side
-    p = capacity.params_for(w, h, over, pol)
-    g = noc.Sim(p)
+def compare(noc, oracle_mod, p, label, tiles_per_thread=None):
+    g = noc.Sim(p, tiles_per_thread=tiles_per_thread)
     g.step(CYCLES)
-    gs, gh, g0 = g.stats(), g.state_hash(), g.hist(0)
+    gs, gh, g0, tpt = g.stats(), g.state_hash(), g.hist(0), g.tiles_per_thread()
     g.close()
     o = oracle_mod.OracleSim(p)
     o.step(CYCLES)
@@ -38,4 +36,21 @@ def test_largest_mesh_matches_oracle(noc, oracle_mod, row):
             assert gs[k] == v, (label, k, gs[k], v)
     assert (g0 == o.hist(0)).all(), label
     assert gh == o.state_hash(), label
+    o.close()
     assert gs["injected"] > 0 and gs["cycle"] == CYCLES
+    return tpt
+
+
+@pytest.mark.parametrize("row", range(4))
+def test_largest_one_tile_mesh_matches_oracle(noc, oracle_mod, row):
+    label, over, pol = capacity.table4_rows()[row]
+    side = capacity.largest_square(over, pol, tiles_per_thread=1)
+    assert side >= 208 and not capacity.launches(side + 1, over, pol, tiles_per_thread=1)
+    assert compare(noc, oracle_mod, capacity.params_for(side, side, over, pol), label, 1) == 1
+
+
+@pytest.mark.parametrize("row", range(4))
+def test_largest_mesh_matches_oracle(noc, oracle_mod, row):
+    label, over, pol = capacity.table4_rows()[row]
+    w, h = capacity.LARGEST_MESH
+    assert compare(noc, oracle_mod, capacity.params_for(w, h, over, pol), label) == 2
