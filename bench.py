@@ -336,7 +336,7 @@ def run_gpu(args):
     batch = surrogate = None
     if not args.no_batch:
         batch = batch_section(args.batch_n, args.batch_cycles, rank=rank, world=world)
-        surrogate = surrogate_section()
+        surrogate = surrogate_section(accuracy=not args.no_surrogate_accuracy)
 
     cpu = None
     if cpu_job is not None:
@@ -478,7 +478,7 @@ def tune_group_name(g):
     return tune.GROUP_NAMES[g]
 
 
-def surrogate_section(reps=20, replays=20):
+def surrogate_section(reps=20, replays=20, accuracy=True):
     """Design points per second of the surrogate's inference at batch 4096, in
     device time: `reps` calls captured in a CUDA graph and replayed, so the
     host's call overhead is not in the timed region.  The one-kernel fused
@@ -515,9 +515,22 @@ def surrogate_section(reps=20, replays=20):
     sec = rate(lambda: net.infer(xb, out=y))
     sec_layered = rate(lambda: net.forward(xb))
     flops = 2 * 4096 * sum(S.DIMS[l] * S.DIMS[l + 1] for l in range(len(S.DIMS) - 1))
-    return {"batch": 4096, "design_points_per_s": 4096 / sec, "tflops": flops / sec / 1e12,
-            "us_per_batch": sec * 1e6, "layered_us_per_batch": sec_layered * 1e6, "timing": "CUDA graph replay (device time)",
-            "kernel": "fused tcgen05 network (mlp_infer)", "network": list(S.DIMS)}
+    out = {"batch": 4096, "design_points_per_s": 4096 / sec, "tflops": flops / sec / 1e12,
+           "us_per_batch": sec * 1e6, "layered_us_per_batch": sec_layered * 1e6,
+           "timing": "CUDA graph replay (device time)",
+           "kernel": "fused tcgen05 network (mlp_infer)", "network": list(S.DIMS)}
+    if accuracy:
+        # held-out accuracy against the exact simulator: 2,000 training and
+        # 500 held-out design points of the batch workload, 20,000 cycles each
+        ev = S.evaluate(train=2_000, holdout=500, cycles=20_000, seeds=(0,))
+        run = ev["runs"][0]
+        sim_rate = (ev["train"] + ev["holdout"]) / ev["simulate_s"]
+        out.update(held_out_mre=run["mre"], held_out_points=ev["holdout"],
+                   train_points=ev["train"], screen_recall_top1pct=run["screen_recall"],
+                   screen_random_recall=run["random_recall"],
+                   simulator_design_points_per_s=sim_rate,
+                   speedup_vs_simulator=(4096 / sec) / sim_rate)
+    return out
 
 
 # --------------------------------------------------------------------- CPU arms
@@ -641,6 +654,8 @@ def main():
                     help="skip the oracle's sample of the batch workload over the host cores")
     ap.add_argument("--c3-every", type=int, default=32)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-surrogate-accuracy", action="store_true",
+                    help="skip the surrogate's held-out accuracy (2,500 simulated design points)")
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-cycles", type=int, default=20_000)
     ap.add_argument("--oracle-configs", action="store_true",
