@@ -159,6 +159,20 @@ int noc_drain(noc_sim* sim, int64_t max_cycles, int64_t* taken);
  * if err_cycle != NULL, the simulated cycle it happened in (-1 if none). */
 int noc_sync(noc_sim* sim, int64_t* err_cycle);
 
+/* Checkpoint and resume.  noc_save writes the whole simulation state -- the
+ * device arena byte for byte plus the cycle and a drain's reference stop --
+ * into host memory the caller owns (noc_checkpoint_bytes(sim) bytes; waits for
+ * the handle's stream).  noc_load restores it into a handle created with the
+ * same arguments (mesh, cache configuration, L2 policy, traffic, seed): every
+ * later step then gives exactly the results of the run that was saved.  A
+ * trace-mode handle must be given the same per-core reference lists again.
+ * noc_load returns NOC_ERR_ARG, before touching the device, for an image that
+ * is not a checkpoint or was saved from another configuration.  Not in the
+ * paper (an operational facility). */
+size_t noc_checkpoint_bytes(const noc_sim* sim);
+int noc_save(noc_sim* sim, void* host_buf, size_t bytes);
+int noc_load(noc_sim* sim, const void* host_buf, size_t bytes);
+
 /* Totals (tile < 0) or one tile's counters, copied to host memory. */
 int noc_stats(noc_sim* sim, int tile, noc_stats_t* out);
 /* which: 0 = flit latency, 1 = L2 access latency; bins: nbins >= NOC_HIST_BINS */

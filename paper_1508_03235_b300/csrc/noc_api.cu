@@ -590,6 +590,73 @@ int noc_step(noc_sim* s, int64_t n) {
   return run_cycles(s, (uint32_t)n, s->draining, nullptr);
 }
 
+// ---- checkpoint image: header, then the device arena byte for byte
+namespace {
+constexpr uint64_t kImageMagic = 0x314B504E4F434E42ull;  // "BNCONPK1"
+struct ImageHeader {
+  uint64_t magic;
+  uint64_t arena_bytes;
+  uint64_t seed;
+  int32_t mesh_w, mesh_h, policy, draining;
+  uint32_t cycle, reserved;
+  noc_cache_cfg cache;
+  noc_traffic traffic;
+};
+}  // namespace
+
+size_t noc_checkpoint_bytes(const noc_sim* s) { return s ? sizeof(ImageHeader) + s->bytes : 0; }
+
+int noc_save(noc_sim* s, void* buf, size_t bytes) {
+  if (!s || !buf) return fail(NOC_ERR_ARG, "null argument");
+  if (bytes < noc_checkpoint_bytes(s))
+    return fail(NOC_ERR_ARG, "checkpoint needs %zu bytes, got %zu", noc_checkpoint_bytes(s), bytes);
+  int rc = ensure_memory(s);
+  if (rc) return rc;
+  rc = noc_sync(s, nullptr);
+  if (rc) return rc;
+  ImageHeader h;
+  memset(&h, 0, sizeof h);
+  h.magic = kImageMagic;
+  h.arena_bytes = s->bytes;
+  h.seed = s->seed;
+  h.mesh_w = s->P.W;
+  h.mesh_h = s->P.H;
+  h.policy = s->P.policy;
+  h.draining = s->draining ? 1 : 0;
+  h.cycle = s->cycle;
+  h.cache = s->cache;
+  h.traffic = s->traf;
+  memcpy(buf, &h, sizeof h);
+  CU(cudaMemcpy(static_cast<unsigned char*>(buf) + sizeof h, s->base, s->bytes, cudaMemcpyDeviceToHost),
+     "checkpoint copy");
+  return NOC_OK;
+}
+
+int noc_load(noc_sim* s, const void* buf, size_t bytes) {
+  if (!s || !buf) return fail(NOC_ERR_ARG, "null argument");
+  ImageHeader h;
+  if (bytes < sizeof h) return fail(NOC_ERR_ARG, "not a checkpoint image");
+  memcpy(&h, buf, sizeof h);
+  if (h.magic != kImageMagic) return fail(NOC_ERR_ARG, "not a checkpoint image");
+  if (h.arena_bytes != s->bytes || bytes < sizeof h + h.arena_bytes || h.seed != s->seed ||
+      h.mesh_w != s->P.W || h.mesh_h != s->P.H || h.policy != s->P.policy ||
+      memcmp(&h.cache, &s->cache, sizeof h.cache) != 0 || memcmp(&h.traffic, &s->traf, sizeof h.traffic) != 0)
+    return fail(NOC_ERR_ARG, "checkpoint of a different configuration");
+  int rc = ensure_memory(s);
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(s->stream), "sync");
+  CU(cudaMemcpy(s->base, static_cast<const unsigned char*>(buf) + sizeof h, s->bytes, cudaMemcpyHostToDevice),
+     "checkpoint copy");
+  s->cycle = h.cycle;
+  s->draining = h.draining != 0;
+  s->hash_n = 0;
+  // the edge slots in the image belong to whatever ran before the save: the
+  // next plain launch clears them (its first cycle reads the complete links)
+  s->gtag_clean = false;
+  s->gtag_end = h.cycle + 1u;
+  return NOC_OK;
+}
+
 int noc_sync(noc_sim* s, int64_t* err_cycle) {
   if (!s) return fail(NOC_ERR_ARG, "null handle");
   if (err_cycle) *err_cycle = -1;

@@ -104,6 +104,9 @@ def lib():
             "noc_kernel_launches": (i64, [vp]),
             "noc_kernel_time": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)]),
             "noc_last_variant": (i32, [vp] + [C.POINTER(i32)] * 4),
+            "noc_checkpoint_bytes": (C.c_size_t, [vp]),
+            "noc_save": (i32, [vp, vp, C.c_size_t]),
+            "noc_load": (i32, [vp, vp, C.c_size_t]),
             "noc_run_static": (i32, [i32, i32, C.POINTER(CacheCfg), i32, C.POINTER(Traffic),
                                      C.c_uint64, i64, vp, vp]),
             "noc_last_error": (C.c_char_p, []),
@@ -268,6 +271,20 @@ class Sim:
         ms, n = C.c_double(), C.c_int64()
         _check(lib().noc_kernel_time(self._h, int(enable), C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    # --- checkpoint / resume ------------------------------------------------
+    def save(self) -> np.ndarray:
+        """The whole simulation state as a host image (uint8 array)."""
+        n = lib().noc_checkpoint_bytes(self._h)
+        buf = np.empty(n, dtype=np.uint8)
+        _check(lib().noc_save(self._h, buf.ctypes.data_as(C.c_void_p), n))
+        return buf
+
+    def load(self, image: np.ndarray):
+        """Restore a state saved by save() from a simulation of the same
+        configuration."""
+        a = np.ascontiguousarray(image, dtype=np.uint8)
+        _check(lib().noc_load(self._h, a.ctypes.data_as(C.c_void_p), a.nbytes))
 
     # --- results -----------------------------------------------------------
     def stats(self, tile: int = -1) -> dict:

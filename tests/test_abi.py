@@ -131,3 +131,21 @@ def test_static_entry_rejects_what_noc_create_rejects(libnoc, name):
     assert rc == 1
     msg = L.noc_last_error()
     assert msg and (name != "trace_mode" or b"trace" in msg)
+
+
+def test_checkpoint_images_are_checked_before_the_device(libnoc):
+    """noc_load rejects what is not an image of this configuration without a
+    GPU; the image size is header + arena (host-only)."""
+    from paper_1508_03235_b300 import inputs as I
+    from paper_1508_03235_b300 import noc
+    L = noc.lib()
+    p = I.MESH_8["params"]
+    h = C.c_void_p()
+    assert L.noc_create(8, 8, C.byref(noc.cache_struct(p)), 0, C.byref(noc.traffic_struct(p)), 1,
+                        C.byref(h)) == 0
+    n = L.noc_checkpoint_bytes(h)
+    assert n > L.noc_required_bytes(h)
+    junk = (C.c_uint8 * 256)()
+    assert L.noc_load(h, C.cast(junk, C.c_void_p), 256) == 1
+    assert b"checkpoint" in L.noc_last_error()
+    L.noc_destroy(h)
