@@ -333,6 +333,7 @@ def run_gpu(args):
     h2d = len(PERIODS) * (ctypes.sizeof(CacheCfg) + ctypes.sizeof(Traffic))
     d2h = len(PERIODS) * ctypes.sizeof(Stats)
 
+    load_sweep = None if args.no_load_sweep else load_sweep_section(tiling, sims[0].thread_map())
     batch = surrogate = None
     if not args.no_batch:
         batch = batch_section(args.batch_n, args.batch_cycles, rank=rank, world=world)
@@ -387,6 +388,7 @@ def run_gpu(args):
             "parity": parity,
             "period_runs": {"periods": list(PERIODS), "refs": [st["refs"] for st in stats],
                             "distinct_end_states": len(set(end_hashes))},
+            "load_sweep": load_sweep,
             "batch": batch,
             "surrogate": surrogate,
             "cpu_baseline": cpu,
@@ -406,6 +408,38 @@ def replica_throughput(ms, units_per_rank, world, device="cpu"):
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
         ms = float(tm.item())
     return ms, units_per_rank * world / (ms / 1e3)
+
+
+# --------------------------------------------------------------------- load dependence
+def load_sweep_section(tiling, thread_map, warm=2_000, cycles=5_000):
+    """Context for the period sweep, whose five runs are one simulation (on
+    the 208x208 mesh a core waits on its misses, never on its period): the
+    same mesh, tiling and thread order with network-only traffic (each core
+    sends a one-flit probe to a uniform random tile every `period` cycles), so
+    the offered load follows the period.  Kernel time per simulated cycle,
+    accepted flits per node-cycle and deflections per flit, per period."""
+    from paper_1508_03235_b300 import noc
+    out = []
+    for P in PERIODS:
+        p = I.sim_params(208, 208, seed=I.MESH_208_SEED, traf=I.traffic(period=P, mode=I.MODE_NETWORK),
+                         cache=I.cache_cfg(l1_kb=1, l1_ways=1, l2_kb=1, l2_ways=1, svc_q=1024))
+        s = noc.Sim(p, tiling=tiling, thread_map=thread_map)
+        s.step(warm)
+        a = s.stats()
+        s.kernel_time(True)
+        s.step(cycles)
+        ms, _ = s.kernel_time(False)
+        b = s.stats()
+        ej = b["ejected"] - a["ejected"]
+        out.append({"period": P, "us_per_cycle": 1e3 * ms / cycles,
+                    "router_cycles_per_s": TILES * cycles / (ms / 1e3),
+                    "offered_flits_per_node_cycle": 1.0 / P,
+                    "accepted_flits_per_node_cycle": ej / (TILES * cycles),
+                    "deflections_per_flit": (b["deflections"] - a["deflections"]) / max(ej, 1),
+                    "in_flight": b["in_flight"]})
+        s.close()
+    return {"traffic": "network-only probes to uniform random tiles, one per core per period",
+            "cycles": cycles, "after_warmup_cycles": warm, "runs": out}
 
 
 # --------------------------------------------------------------------- batch + surrogate
@@ -654,6 +688,7 @@ def main():
                     help="skip the oracle's sample of the batch workload over the host cores")
     ap.add_argument("--c3-every", type=int, default=32)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-load-sweep", action="store_true")
     ap.add_argument("--no-surrogate-accuracy", action="store_true",
                     help="skip the surrogate's held-out accuracy (2,500 simulated design points)")
     ap.add_argument("--batch-n", type=int, default=512)

@@ -1342,7 +1342,13 @@ static int run_batch_group(noc_batch* b, const std::vector<int>& members, int si
     B.claimed = reinterpret_cast<unsigned int*>(t + o_cl);
     B.next_item = reinterpret_cast<unsigned int*>(t + o_nx);
     B.n_items = ni;
-    B.gang_ns = 300ll * 1000000000ll;
+    // A CTA that pops a rectangle waits until its instance's other rectangles
+    // are popped, i.e. at most until instances already running end.  Those
+    // run at a few microseconds per simulated cycle; the bound allows 500 us
+    // per cycle of the wave's longest instance, plus 20 s.
+    int64_t max_cycles = 0;
+    for (int k = 0; k < m; ++k) max_cycles = std::max<int64_t>(max_cycles, b->cycles[wave[k]]);
+    B.gang_ns = 20ll * 1000000000ll + max_cycles * 500000ll;
     if (ni) {
       CU(launch_batch(B, std::min(cap, ni), threads, w1, w2, kind, st), "batch kernel launch");
       b->launches++;

@@ -472,6 +472,41 @@ def test_reference_stream_distribution(oracle_mod):
     assert abs(hot / shared - f_hot) < 5 * sd
 
 
+def test_hotspot_lines_exactly_the_hot_tiles_shared_lines(oracle_mod):
+    """Every shared reference sent to the hot block (hot fraction 1) is a line
+    of the shared region homed (line mod N) on one of the 4x4 centre tiles
+    x, y in [W/2-2, W/2+1]; over enough draws the lines drawn are exactly those
+    lines, each about equally often; with hot fraction 0 they are exactly
+    the whole shared region.  Checked per draw against the definition of the
+    region and of the home, not against the mapping's own arithmetic."""
+    W = H = 8
+    N = W * H
+    traf = I.traffic(period=1, priv=0.0, shared=1.0, hot=1.0, hot_side=4, shared_mb=0)
+    traf.update(shared_lines=640)
+    p = I.sim_params(W, H, traf=traf, seed=3)
+    sb = p["remote_lines"]
+    hot_tiles = {y * W + x for x in range(W // 2 - 2, W // 2 + 2) for y in range(H // 2 - 2, H // 2 + 2)}
+    want = {l for l in range(sb, sb + 640) if l % N in hot_tiles}
+    assert len(want) == 160
+    s = oracle_mod.OracleSim(p)
+    seen = Counter()
+    for i in range(24_000):
+        line, _ = s.draw_ref(i % N, i // N)
+        assert line in want, line
+        seen[line] += 1
+    assert set(seen) == want
+    # uniform over the 160 lines: chi-square with 159 degrees of freedom
+    e = 24_000 / 160
+    chi2 = sum((v - e) ** 2 / e for v in seen.values())
+    assert chi2 < 159 + 6 * np.sqrt(2 * 159)
+    s.close()
+    p0 = dict(p, hot_q16=0)
+    s = oracle_mod.OracleSim(p0)
+    lines = {s.draw_ref(i % N, i // N)[0] for i in range(20_000)}
+    assert lines == set(range(sb, sb + 640))
+    s.close()
+
+
 # --------------------------------------------------------------------------
 # packet mode (Table 1): a data reply is 4 flits, reassembled in a reorder
 # buffer; its handler runs once, when the last flit is in
