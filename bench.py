@@ -411,16 +411,21 @@ def replica_throughput(ms, units_per_rank, world, device="cpu"):
 
 
 # --------------------------------------------------------------------- load dependence
+# offered loads 0.0025 .. 0.04 flits per node-cycle, across the saturation of
+# uniform traffic on a 208-wide mesh (about 0.016)
+LOAD_PERIODS = (400, 200, 100, 50, 25)
+
+
 def load_sweep_section(tiling, thread_map, warm=2_000, cycles=5_000):
     """Context for the period sweep, whose five runs are one simulation (on
     the 208x208 mesh a core waits on its misses, never on its period): the
     same mesh, tiling and thread order with network-only traffic (each core
-    sends a one-flit probe to a uniform random tile every `period` cycles), so
-    the offered load follows the period.  Kernel time per simulated cycle,
+    sends a one-flit probe to a uniform random tile every `period` cycles, for
+    periods that take the offered load across the network's saturation).  Kernel time per simulated cycle,
     accepted flits per node-cycle and deflections per flit, per period."""
     from paper_1508_03235_b300 import noc
     out = []
-    for P in PERIODS:
+    for P in LOAD_PERIODS:
         p = I.sim_params(208, 208, seed=I.MESH_208_SEED, traf=I.traffic(period=P, mode=I.MODE_NETWORK),
                          cache=I.cache_cfg(l1_kb=1, l1_ways=1, l2_kb=1, l2_ways=1, svc_q=1024))
         s = noc.Sim(p, tiling=tiling, thread_map=thread_map)
