@@ -81,3 +81,31 @@ def test_random_configuration(noc, oracle_mod, seed):
         return
     assert g.drain(100_000) == taken
     assert g.state_hash() == o.state_hash()
+
+
+@pytest.mark.parametrize("seed", range(0, N_CASES, 2))
+def test_random_configuration_two_tiles_per_thread(noc, oracle_mod, seed):
+    """The same draws through the two-tile loop (plain steps only), switching
+    to the one-tile loop midway and back: every end state equal to the
+    oracle's, and a queue overflow at the same cycle."""
+    p, tiling, tmap = draw(seed)
+    # rectangles of up to 512 tiles hold two per thread; keep the draw's shape
+    g = noc.Sim(p, tiling=tiling, thread_map=tmap, tiles_per_thread=2)
+    o = oracle_mod.OracleSim(p)
+    for k, n in ((2, 600), (1, 300), (2, 600)):
+        g.set_tiles_per_thread(k)
+        o.step(n, check=False)
+        code, cyc = o.error()
+        if code:
+            g.step_async(n)
+            assert g.error() == (code, cyc), (p, tiling, tmap)
+            return
+        g.step(n)
+        assert g.tiles_per_thread() == k
+        assert g.state_hash() == o.state_hash(), (k, p, tiling, tmap)
+    gs, os_ = g.stats(), o.stats()
+    for key, v in os_.items():
+        if key in gs:
+            assert gs[key] == v, (key, p, tiling, tmap)
+    for w in (0, 1):
+        assert (g.hist(w) == o.hist(w)).all()
