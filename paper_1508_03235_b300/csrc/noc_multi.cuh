@@ -5,17 +5,19 @@
 // its thread's registers for a whole launch, so a mesh must fit the GPU's
 // co-resident threads (148 SMs x 384 at that register count: 55,696 tiles in a
 // square).  Here a thread runs tiles i and i + blockDim.x (K = 2) of its CTA
-// rectangle, so a rectangle holds up to 2 x 256 tiles; each tile's state is
-// read from and written back to its arena records around each cycle of
-// simulated work (load_tile / store_tile), which costs a round of global
-// loads and stores per tile-cycle but lets a B300 hold every mesh of up to
-// 65,535 tiles, the limit of the 16-bit tile indices a flit carries.
+// rectangle, so a rectangle holds up to 2 x 256 tiles.  A tile's state lives
+// in a 66-word record in shared memory for the whole launch (read from the
+// arena at the launch's start, written back at its end, as the one-tile loop
+// does with registers) and is moved into registers around each cycle of its
+// simulated work.  That lets a B300 hold every mesh of up to 65,535 tiles, the
+// limit of the 16-bit tile indices a flit carries.
 //
 // Per warp and cycle t: wait until every input of every one of its tiles
 // carries cycle t - 1 (shared-memory flags of the warps holding in-rectangle
 // neighbours, tagged global slots across the rectangle's edge, one poll in
-// flight), then for each of its tiles: load the state, route cycle t, Phase 3
-// of t, Phase 1 of t + 1, store the state; then publish t + 1.  The order of
+// flight), then for each of its tiles: take the state from its record, route
+// cycle t, Phase 3 of t, Phase 1 of t + 1, put the state back; then publish
+// t + 1.  The order of
 // the phases per tile is the one-tile loop's; only when the warp publishes
 // changes (after all its tiles' Phases 3 and 1 rather than before), which no
 // result depends on.  A warp waits for all its tiles' inputs before routing
@@ -29,10 +31,115 @@ namespace noc {
 constexpr int MULTI_K = 2;            // tiles per thread
 constexpr int MULTI_THREADS = 256;    // threads per CTA (all registers for 255 each)
 constexpr int MULTI_WARPS = MULTI_THREADS / 32;
+constexpr int REC_WORDS = 43 + NSMALL;  // 32-bit words of a tile's state record
 
-// shared memory: links [2 parity][4 port][K * threads], histograms
+// shared memory: tile records [REC_WORDS][K * threads], links
+// [2 parity][4 port][K * threads], histograms
 __host__ __device__ inline size_t multi_smem_bytes(int threads) {
-  return (size_t)MULTI_K * threads * 8 * sizeof(uint4) + (2 * HIST_BINS + 2) * sizeof(uint32_t);
+  return (size_t)MULTI_K * threads * (REC_WORDS * sizeof(uint32_t) + 8 * sizeof(uint4)) +
+         (2 * HIST_BINS + 2) * sizeof(uint32_t);
+}
+
+// A tile's state to and from its record: word w of the record of rectangle
+// slot j at rec[w * cap + j] (consecutive threads, consecutive words: no bank
+// conflicts).  Everything a tile carries from one cycle to the next; the
+// ejected flit is set by the router and consumed by Phase 3 in one cycle.
+__device__ __forceinline__ void rec_u64(uint32_t* rec, int cap, int w, unsigned long long v) {
+  rec[w * cap] = (uint32_t)v;
+  rec[(w + 1) * cap] = (uint32_t)(v >> 32);
+}
+__device__ __forceinline__ unsigned long long rec_get_u64(const uint32_t* rec, int cap, int w) {
+  return (unsigned long long)rec[w * cap] | ((unsigned long long)rec[(w + 1) * cap] << 32);
+}
+__device__ __forceinline__ void rec_uint4(uint32_t* rec, int cap, int w, uint4 v) {
+  rec[w * cap] = v.x;
+  rec[(w + 1) * cap] = v.y;
+  rec[(w + 2) * cap] = v.z;
+  rec[(w + 3) * cap] = v.w;
+}
+__device__ __forceinline__ uint4 rec_get_uint4(const uint32_t* rec, int cap, int w) {
+  return make_uint4(rec[w * cap], rec[(w + 1) * cap], rec[(w + 2) * cap], rec[(w + 3) * cap]);
+}
+static __device__ void tile_to_record(const Tile& T, uint32_t* rec, int cap) {
+  rec[0] = T.r;
+  rec[1 * cap] = T.x | (T.y << 16);
+  rec[2 * cap] = T.next_ref;
+  rec[3 * cap] = T.fsm | (T.fsm_write << 8) | (T.om_kind << 16) | (T.om_write << 24);
+  rec[4 * cap] = T.fsm_line;
+  rec[5 * cap] = T.fsm_timer;
+  rec[6 * cap] = T.fsm_start;
+  rec[7 * cap] = T.om_line;
+  rec[8 * cap] = T.om_start;
+  rec[9 * cap] = T.om_timer;
+  rec[10 * cap] = T.epoch | (T.om_epoch << 16);
+  rec[11 * cap] = T.cq_head | (T.cq_len << 16);
+  rec[12 * cap] = T.sq_head | (T.sq_len << 16);
+  rec[13 * cap] = T.mq_head | (T.mq_len << 16);
+  rec[14 * cap] = T.fwd_next | (T.fwd_n << 16);
+  rec_uint4(rec, cap, 15, T.cq_front);
+  rec_uint4(rec, cap, 19, T.sq_front);
+  rec_uint4(rec, cap, 23, T.mq_front);
+  rec[27 * cap] = T.pf_raw;
+  rec[28 * cap] = T.pf_ok;
+  rec[29 * cap] = T.rk0;
+  rec[30 * cap] = T.rcnt;
+  rec_u64(rec, cap, 31, T.inj);
+  rec_u64(rec, cap, 33, T.ejc);
+  rec_u64(rec, cap, 35, T.defl);
+  rec_u64(rec, cap, 37, T.latsum);
+  rec_u64(rec, cap, 39, T.latmax);
+  rec_u64(rec, cap, 41, T.l2lsum);
+#pragma unroll
+  for (int k = 0; k < NSMALL; ++k) rec[(43 + k) * cap] = T.sm[k];
+}
+static __device__ void tile_from_record(Tile& T, const uint32_t* rec, int cap) {
+  T.r = rec[0];
+  const uint32_t xy = rec[1 * cap];
+  T.x = xy & 0xFFFFu;
+  T.y = xy >> 16;
+  T.next_ref = rec[2 * cap];
+  const uint32_t b = rec[3 * cap];
+  T.fsm = b & 0xFFu;
+  T.fsm_write = (b >> 8) & 0xFFu;
+  T.om_kind = (b >> 16) & 0xFFu;
+  T.om_write = b >> 24;
+  T.fsm_line = rec[4 * cap];
+  T.fsm_timer = rec[5 * cap];
+  T.fsm_start = rec[6 * cap];
+  T.om_line = rec[7 * cap];
+  T.om_start = rec[8 * cap];
+  T.om_timer = rec[9 * cap];
+  const uint32_t e = rec[10 * cap];
+  T.epoch = e & 0xFFFFu;
+  T.om_epoch = e >> 16;
+  uint32_t q = rec[11 * cap];
+  T.cq_head = q & 0xFFFFu;
+  T.cq_len = q >> 16;
+  q = rec[12 * cap];
+  T.sq_head = q & 0xFFFFu;
+  T.sq_len = q >> 16;
+  q = rec[13 * cap];
+  T.mq_head = q & 0xFFFFu;
+  T.mq_len = q >> 16;
+  q = rec[14 * cap];
+  T.fwd_next = q & 0xFFFFu;
+  T.fwd_n = q >> 16;
+  T.cq_front = rec_get_uint4(rec, cap, 15);
+  T.sq_front = rec_get_uint4(rec, cap, 19);
+  T.mq_front = rec_get_uint4(rec, cap, 23);
+  T.ej = make_uint4(0, 0, 0, 0);
+  T.pf_raw = rec[27 * cap];
+  T.pf_ok = rec[28 * cap];
+  T.rk0 = rec[29 * cap];
+  T.rcnt = rec[30 * cap];
+  T.inj = rec_get_u64(rec, cap, 31);
+  T.ejc = rec_get_u64(rec, cap, 33);
+  T.defl = rec_get_u64(rec, cap, 35);
+  T.latsum = rec_get_u64(rec, cap, 37);
+  T.latmax = rec_get_u64(rec, cap, 39);
+  T.l2lsum = rec_get_u64(rec, cap, 41);
+#pragma unroll
+  for (int k = 0; k < NSMALL; ++k) T.sm[k] = rec[(43 + k) * cap];
 }
 inline int multi_block_threads(int W, int H, int gx, int gy) {
   const int bw = (W + gx - 1) / gx, bh = (H + gy - 1) / gy;
@@ -45,7 +152,8 @@ __device__ __forceinline__ void run_rect_multi(const Params& P, const RunArgs& A
                                                unsigned char* smem_raw) {
   constexpr int K = MULTI_K;
   const int nt = blockDim.x, cap = K * nt;
-  uint4* sl = reinterpret_cast<uint4*>(smem_raw);  // [2 parity][4 port][cap]
+  uint32_t* recs = reinterpret_cast<uint32_t*>(smem_raw);  // [REC_WORDS][cap]
+  uint4* sl = reinterpret_cast<uint4*>(recs + (size_t)REC_WORDS * cap);  // [2 parity][4 port][cap]
   uint32_t* sh_hist = reinterpret_cast<uint32_t*>(sl + 8 * cap);
   __shared__ unsigned wflag[MULTI_WARPS];
 
@@ -113,7 +221,7 @@ __device__ __forceinline__ void run_rect_multi(const Params& P, const RunArgs& A
       Tile T;
       load_tile(P, r[k], T);
       phase1<W1, W2>(P, T, t0, draining, sh_hist);
-      store_tile(P, T);
+      tile_to_record(T, recs + i + k * nt, cap);
     }
 
   uint32_t t = t0;
@@ -182,7 +290,7 @@ __device__ __forceinline__ void run_rect_multi(const Params& P, const RunArgs& A
       if (act[k]) {
         const int j = i + k * nt;
         Tile T;
-        load_tile(P, r[k], T);
+        tile_from_record(T, recs + j, cap);
         const InjCand ic = inj_candidate(P, T);
         uint4 in[4];
         const uint32_t local = exists[k] & ~boundary[k];
@@ -194,7 +302,7 @@ __device__ __forceinline__ void run_rect_multi(const Params& P, const RunArgs& A
                      P.gtag + pout * pstride + (size_t)r[k] * 2, 2 * N, edge_out[k], ic);
         phase3<W1, W2>(P, T, t, sh_hist);
         if (t + 1 != tend) phase1<W1, W2>(P, T, t + 1, draining, sh_hist);
-        store_tile(P, T);
+        tile_to_record(T, recs + j, cap);
       }
     // ---- publish: this warp has routed cycle t for all its tiles
     __syncwarp();
@@ -204,7 +312,7 @@ __device__ __forceinline__ void run_rect_multi(const Params& P, const RunArgs& A
     }
   }
 
-  // ---- end of launch: full link state of the last cycle, counters
+  // ---- end of launch: full link state of the last cycle, tile state, counters
   __syncthreads();
   {
     const uint32_t plast = (t - (t == tend ? 1u : 0u)) & 1u;
@@ -214,6 +322,9 @@ __device__ __forceinline__ void run_rect_multi(const Params& P, const RunArgs& A
         const int j = i + k * nt;
 #pragma unroll
         for (int d = 0; d < 4; ++d) P.glink[((size_t)plast * 4 + d) * N + r[k]] = sl[(plast * 4 + d) * cap + j];
+        Tile T;
+        tile_from_record(T, recs + j, cap);
+        store_tile(P, T);
       }
   }
   __syncthreads();
