@@ -355,6 +355,12 @@ int64_t noc_kernel_launches(const noc_sim* sim);
  *           (16, 16).
  * Any output pointer may be NULL.  NOC_ERR_STATE before the first launch. */
 int noc_last_variant(const noc_sim* sim, int* loop, int* kind, int* l1_bound, int* l2_bound);
+/* The launch bound of that build: the most threads a CTA of it may have.
+ * The plain loop is built twice, for CTAs of up to 320 threads (more
+ * registers per thread, faster) and up to 384; the traced loop is built for
+ * 384 and the two-tile loop for 256.  0 before the first launch, -1 for a null
+ * handle. */
+int noc_last_launch_bound(const noc_sim* sim);
 
 /* Device time of the cycle kernel alone.  With enable != 0, every later
  * cycle-kernel launch through this handle is bracketed by a pair of CUDA

@@ -18,6 +18,11 @@ UNITS = ([("noc_run_variant.cu", {"NOC_HASH": h, "NOC_DRAIN": d, "NOC_W1": w1, "
             for (w1, w2) in WAY_BOUNDS]
          + [("noc_run_variant.cu", {"NOC_HASH": 0, "NOC_DRAIN": 0, "NOC_W1": w1, "NOC_W2": w2,
                                     "NOC_BASE": 1}) for (w1, w2) in WAY_BOUNDS]
+         # the plain loop again, for CTAs of at most 320 threads (more registers)
+         + [("noc_run_variant.cu", dict(spec, NOC_HASH=0, NOC_DRAIN=0, NOC_W1=w1, NOC_W2=w2, NOC_NARROW=1))
+            for (w1, w2) in WAY_BOUNDS
+            for spec in ({}, {"NOC_BASE": 1},
+                         {"NOC_FIXED_POLICY": 0, "NOC_FIXED_MODE": 0, "NOC_EXACT_WAYS": 1})]
          + [("noc_batch.cu", {"NOC_W1": w1, "NOC_W2": w2}) for (w1, w2) in WAY_BOUNDS]
          + [("noc_batch.cu", {"NOC_W1": w1, "NOC_W2": w2, "NOC_BASE": 1}) for (w1, w2) in WAY_BOUNDS]
          + [("noc_batch.cu", {"NOC_W1": w1, "NOC_W2": w2, "NOC_FIXED_POLICY": 0, "NOC_FIXED_MODE": 0,

@@ -177,6 +177,7 @@ struct noc_sim {
   int thread_map = 0;     // tile-to-thread order inside a CTA rectangle
   int64_t launches = 0;
   int last_variant = -1;  // run_variant() of the last cycle-kernel launch
+  int last_bound = 0;     // launch bound (most threads per CTA) of that launch's build
   // cycle-kernel timing: event pairs [2k, 2k + 1] around launch k
   bool time_kernels = false;
   std::vector<cudaEvent_t> tev;
@@ -481,9 +482,11 @@ int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
     if (tpt == 2) {
       CU(launch_multi(s->P, A, s->stream), "cycle kernel launch");
       s->last_variant = multi_variant(s->P);
+      s->last_bound = MULTI_MAX_THREADS;
     } else {
       CU(launch_run(s->P, A, s->stream), "cycle kernel launch");
       s->last_variant = run_variant(s->P, A);
+      s->last_bound = run_launch_bound(s->P, A);
     }
     s->launches++;
     if (s->time_kernels) {
@@ -1014,6 +1017,8 @@ int noc_debug_wait_limit(noc_sim* s, int64_t ns, int silent_cta) {
 }
 
 int64_t noc_kernel_launches(const noc_sim* s) { return s ? s->launches : -1; }
+
+int noc_last_launch_bound(const noc_sim* s) { return s ? s->last_bound : -1; }
 
 int noc_last_variant(const noc_sim* s, int* loop, int* kind, int* l1_bound, int* l2_bound) {
   if (!s) return fail(NOC_ERR_ARG, "null handle");

@@ -19,6 +19,8 @@ int configure(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, con
 // kind << 4 | way class, with loop 1 for the traced / draining loop, kind a
 // KIND_* value and way class 0 = (4, 8), 1 = (4, 16), 2 = (16, 16) bounds
 int run_variant(const Params& P, const RunArgs& A);
+// the launch bound (most threads per CTA) of the build launch_run picks
+int run_launch_bound(const Params& P, const RunArgs& A);
 // the capacity loop (two tiles per thread, plain cycles only): launch, its
 // co-resident CTAs at `threads` per CTA, threads per CTA of a gx x gy
 // rectangle grid, and its run_variant() code (loop 2)

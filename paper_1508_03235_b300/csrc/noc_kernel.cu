@@ -22,9 +22,15 @@ namespace noc {
   NOC_DECL_RUN(0, 1, w1, w2, gen)                                               \
   NOC_DECL_RUN(0, 0, w1, w2, il)                                                \
   NOC_DECL_RUN(0, 0, w1, w2, base)                                              \
+  NOC_DECL_RUN(0, 0, w1, w2, gen_narrow)                                        \
+  NOC_DECL_RUN(0, 0, w1, w2, il_narrow)                                         \
+  NOC_DECL_RUN(0, 0, w1, w2, base_narrow)                                       \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_gen(int threads, int* out);  \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_il(int threads, int* out);   \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_base(int threads, int* out); \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_gen_narrow(int threads, int* out);  \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_il_narrow(int threads, int* out);   \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_base_narrow(int threads, int* out); \
   cudaError_t launch_batch_##w1##_##w2##_gen(const BatchArgs&, int, int, cudaStream_t); \
   cudaError_t launch_batch_##w1##_##w2##_il(const BatchArgs&, int, int, cudaStream_t);  \
   cudaError_t launch_batch_##w1##_##w2##_base(const BatchArgs&, int, int, cudaStream_t); \
@@ -74,6 +80,11 @@ int run_variant(const Params& P, const RunArgs& A) {
   return (traced << 8) | (kind << 4) | way_class(P.l1_ways, P.l2_ways);
 }
 
+int run_launch_bound(const Params& P, const RunArgs& A) {
+  const bool plain = !A.hash_trace && !A.busy;
+  return plain && block_threads_impl(P.W, P.H, A.gx, A.gy) <= NARROW_THREADS ? NARROW_THREADS : MAX_THREADS;
+}
+
 int multi_variant(const Params& P) { return (2 << 8) | (KIND_GEN << 4) | way_class(P.l1_ways, P.l2_ways); }
 
 cudaError_t launch_multi(const Params& P, const RunArgs& A, cudaStream_t s) {
@@ -103,6 +114,14 @@ cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
   if (A.hash_trace && A.busy) return cudaErrorInvalidValue;
   if (A.hash_trace) { NOC_PICK_RUN(1, 0, gen) }
   if (A.busy) { NOC_PICK_RUN(0, 1, gen) }
+  // the plain loop: the narrow build when the CTAs fit it
+  if (block_threads_impl(P.W, P.H, A.gx, A.gy) <= NARROW_THREADS) {
+    switch (variant_kind(P)) {
+      case KIND_IL: NOC_PICK_RUN(0, 0, il_narrow)
+      case KIND_BASE: NOC_PICK_RUN(0, 0, base_narrow)
+      default: NOC_PICK_RUN(0, 0, gen_narrow)
+    }
+  }
   switch (variant_kind(P)) {
     case KIND_IL: NOC_PICK_RUN(0, 0, il)
     case KIND_BASE: NOC_PICK_RUN(0, 0, base)
@@ -117,8 +136,24 @@ cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
     default: return fn##_##w1##_##w2##_gen(__VA_ARGS__);                        \
   }
 
+#define NOC_PICK_KIND_NARROW(fn, kind, w1, w2, ...)                             \
+  switch (kind) {                                                                \
+    case KIND_IL: return fn##_##w1##_##w2##_il_narrow(__VA_ARGS__);              \
+    case KIND_BASE: return fn##_##w1##_##w2##_base_narrow(__VA_ARGS__);          \
+    default: return fn##_##w1##_##w2##_gen_narrow(__VA_ARGS__);                  \
+  }
+
+// co-resident CTAs of the plain loop at `threads` per CTA, for the build a
+// launch of that size uses
 cudaError_t max_coresident_ctas(const Params& P, int threads, int* out) {
   const int kind = variant_kind(P);
+  if (threads <= NARROW_THREADS) {
+    switch (way_class(P.l1_ways, P.l2_ways)) {
+      case 0: NOC_PICK_KIND_NARROW(max_coresident_run_0_0, kind, 4, 8, threads, out)
+      case 1: NOC_PICK_KIND_NARROW(max_coresident_run_0_0, kind, 4, 16, threads, out)
+      default: NOC_PICK_KIND_NARROW(max_coresident_run_0_0, kind, 16, 16, threads, out)
+    }
+  }
   switch (way_class(P.l1_ways, P.l2_ways)) {
     case 0: NOC_PICK_KIND(max_coresident_run_0_0, kind, 4, 8, threads, out)
     case 1: NOC_PICK_KIND(max_coresident_run_0_0, kind, 4, 16, threads, out)

@@ -4,7 +4,8 @@
 // more per way bound: without the options beyond the paper's workloads
 // (-DNOC_BASE=1), and specialised to the interleaved L2 in cache mode with
 // exactly those way counts (-DNOC_FIXED_POLICY=0 -DNOC_FIXED_MODE=0
-// -DNOC_EXACT_WAYS=1).
+// -DNOC_EXACT_WAYS=1); the plain-loop builds once more each with
+// -DNOC_NARROW=1, for CTAs of at most NARROW_THREADS threads.
 #include "noc_kernel.cuh"
 
 #if !defined(NOC_HASH) || !defined(NOC_DRAIN) || !defined(NOC_W1) || !defined(NOC_W2)
@@ -12,13 +13,23 @@
 #endif
 #if defined(NOC_FIXED_POLICY)
 #define NOC_POLV NOC_FIXED_POLICY
-#define NOC_SPEC il
+#define NOC_SPEC0 il
 #elif defined(NOC_BASE)
 #define NOC_POLV (-2)
-#define NOC_SPEC base
+#define NOC_SPEC0 base
 #else
 #define NOC_POLV (-1)
-#define NOC_SPEC gen
+#define NOC_SPEC0 gen
+#endif
+// -DNOC_NARROW=1: the build for CTAs of at most NARROW_THREADS threads
+#if defined(NOC_NARROW) && NOC_NARROW
+#define NOC_LB NARROW_THREADS
+#define NOC_PASTE2(a, b) a##_##b
+#define NOC_CAT2(a, b) NOC_PASTE2(a, b)
+#define NOC_SPEC NOC_CAT2(NOC_SPEC0, narrow)
+#else
+#define NOC_LB MAX_THREADS
+#define NOC_SPEC NOC_SPEC0
 #endif
 
 #define NOC_PASTE6(a, b, c, d, e, f) a##_##b##_##c##_##d##_##e##_##f
@@ -29,12 +40,12 @@ namespace noc {
 cudaError_t NOC_NAME(launch_run, NOC_HASH, NOC_DRAIN, NOC_W1, NOC_W2, NOC_SPEC)(const Params& P,
                                                                               const RunArgs& A,
                                                                               cudaStream_t s) {
-  return launch_run_t<NOC_HASH != 0, NOC_DRAIN != 0, NOC_W1, NOC_W2, NOC_POLV>(P, A, s);
+  return launch_run_t<NOC_HASH != 0, NOC_DRAIN != 0, NOC_W1, NOC_W2, NOC_POLV, NOC_LB>(P, A, s);
 }
 
 #if NOC_HASH == 0 && NOC_DRAIN == 0
 cudaError_t NOC_NAME(max_coresident_run, 0, 0, NOC_W1, NOC_W2, NOC_SPEC)(int threads, int* out) {
-  return max_coresident_run_t<NOC_W1, NOC_W2, NOC_POLV>(threads, out);
+  return max_coresident_run_t<NOC_W1, NOC_W2, NOC_POLV, NOC_LB>(threads, out);
 }
 #endif
 

@@ -104,6 +104,7 @@ def lib():
             "noc_kernel_launches": (i64, [vp]),
             "noc_kernel_time": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)]),
             "noc_last_variant": (i32, [vp] + [C.POINTER(i32)] * 4),
+            "noc_last_launch_bound": (i32, [vp]),
             "noc_checkpoint_bytes": (C.c_size_t, [vp]),
             "noc_save": (i32, [vp, vp, C.c_size_t]),
             "noc_load": (i32, [vp, vp, C.c_size_t]),
@@ -264,6 +265,11 @@ class Sim:
         _check(lib().noc_last_variant(self._h, *[C.byref(x) for x in v]))
         return dict(loop=("plain", "traced", "plain, two tiles per thread")[v[0].value],
                     kind=KERNEL_KINDS[v[1].value], bounds=(v[2].value, v[3].value))
+
+    def launch_bound(self) -> int:
+        """Most threads per CTA of the last launch's build (320 or 384 for
+        the plain loop)."""
+        return lib().noc_last_launch_bound(self._h)
 
     def kernel_time(self, enable: bool = True):
         """(ms, launches) of the cycle-kernel launches recorded since the last

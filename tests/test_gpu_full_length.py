@@ -86,6 +86,7 @@ def test_mesh208_full_length(noc, golden, period):
     name = f"mesh208_period{period}"
     g = run_checkpoints(noc, golden, name)
     assert g.variant() == dict(loop="plain", kind="interleaved", bounds=(4, 16))
+    assert g.launch_bound() == 320              # 104x3 strips: the narrow build
     # the benchmark's own sequence: reset, then the whole run in one call
     g.reset()
     last = golden[name]["checkpoints"][-1]

@@ -87,6 +87,7 @@ def test_plain_traced_and_draining_builds(noc, oracle_mod, kind, bounds):
     g.step(2500)
     o.step(2500)
     assert g.variant() == dict(loop="plain", kind=kind, bounds=bounds)
+    assert g.launch_bound() == 320            # small CTAs: the narrow build
     g.step(1500)                              # a second launch continues the first
     o.step(1500)
     assert g.variant() == dict(loop="plain", kind=kind, bounds=bounds)
@@ -127,3 +128,21 @@ def test_batch_builds(noc, oracle_mod, bounds):
         assert_busy(os_, p["policy"] != 0)
         o.close()
     b.close()
+
+
+@pytest.mark.parametrize("bounds", BOUNDS, ids=lambda b: f"{b[0]}x{b[1]}")
+@pytest.mark.parametrize("kind", KINDS)
+def test_wide_plain_builds(noc, oracle_mod, kind, bounds):
+    """The plain loop's build for CTAs of more than 320 threads: a 19 x 18
+    mesh in one CTA (342 tiles), two launches, against the oracle."""
+    p = variant_params(kind, bounds, w=19, h=18, seed=7)
+    if p.get("dir_central"):
+        p["dir_tile"] = 200
+    g = noc.Sim(p, tiling=(1, 1))
+    o = oracle_mod.OracleSim(p)
+    for n in (1200, 800):
+        g.step(n)
+        o.step(n)
+        assert g.variant() == dict(loop="plain", kind=kind, bounds=bounds)
+        assert g.launch_bound() == 384
+    assert_same(g, o)
