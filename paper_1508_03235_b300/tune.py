@@ -90,7 +90,7 @@ def cached_thread_map(params: dict):
 
 def tune(params: dict, cycles: int = 2000, warm: int = 200, max_cands: int = 10,
          maps=(0, 1, 2), reps: int = 2, broad: bool = False, save: bool = True,
-         verbose: bool = False):
+         verbose: bool = False, cache_path: str = CACHE):
     """Time candidate tilings in each tile-to-thread order (the best of `reps`
     timed runs each); return (best (gx, gy, order), {(gx, gy, order): us per
     cycle}).  With `broad`, every rectangle shape of broad_candidates() is
@@ -125,13 +125,13 @@ def tune(params: dict, cycles: int = 2000, warm: int = 200, max_cands: int = 10,
     sim.close()
     best = min(timings, key=timings.get)
     if save:
-        cache = load_cache()
+        cache = (json.load(open(cache_path)) if os.path.exists(cache_path) else load_cache())
         cache[key(params)] = {"tiling": list(best[:2]), "thread_map": best[2],
                               "us_per_cycle": timings[best],
                               "timings": {f"{a}x{b}/{noc.THREAD_MAPS[m]}": v
                                           for (a, b, m), v in timings.items()},
                               "device": torch.cuda.get_device_name()}
-        with open(CACHE, "w") as f:
+        with open(cache_path, "w") as f:
             json.dump(cache, f, indent=1, sort_keys=True)
     return best, timings
 
@@ -237,7 +237,7 @@ if __name__ == "__main__":
         for name, p in (("mesh208", I.mesh_208(10)), ("mesh64", I.mesh_64(1)),
                         ("mesh8", I.MESH_8["params"])):
             print(name, flush=True)
-            b, t = T.tune(p, broad=a.broad, verbose=not a.broad)
+            b, t = T.tune(p, broad=a.broad, verbose=not a.broad, cache_path=a.out)
             if a.broad:
                 for k in sorted(t, key=t.get)[:10]:
                     print(f"  {k[0]}x{k[1]} order {k[2]}: {t[k]:.3f} us/cycle", flush=True)
