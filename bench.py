@@ -334,6 +334,7 @@ def run_gpu(args):
     d2h = len(PERIODS) * ctypes.sizeof(Stats)
 
     load_sweep = None if args.no_load_sweep else load_sweep_section(tiling, sims[0].thread_map())
+    phases = None if args.no_load_sweep else phase_section(tiling, sims[0].thread_map())
     batch = surrogate = None
     if not args.no_batch:
         batch = batch_section(args.batch_n, args.batch_cycles, rank=rank, world=world)
@@ -389,6 +390,7 @@ def run_gpu(args):
             "period_runs": {"periods": list(PERIODS), "refs": [st["refs"] for st in stats],
                             "distinct_end_states": len(set(end_hashes))},
             "load_sweep": load_sweep,
+            "phase_profile": phases,
             "batch": batch,
             "surrogate": surrogate,
             "cpu_baseline": cpu,
@@ -408,6 +410,26 @@ def replica_throughput(ms, units_per_rank, world, device="cpu"):
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
         ms = float(tm.item())
     return ms, units_per_rank * world / (ms / 1e3)
+
+
+# --------------------------------------------------------------------- phase profile
+def phase_section(tiling, thread_map, warm=2_000, cycles=4_000):
+    """Where a warp's time goes in the plain loop (context): the 208x208
+    period-10 run on the build with per-phase clock reads (noc_set_phase_profile;
+    that build keeps its own registers, so its cycle is a little slower), SM
+    clocks per warp and simulated cycle after a warm-up."""
+    from paper_1508_03235_b300 import noc
+    s = noc.Sim(I.mesh_208(10), tiling=tiling, thread_map=thread_map)
+    s.step(warm)
+    s.set_phase_profile(True)
+    s.kernel_time(True)
+    s.step(cycles)
+    ms, _ = s.kernel_time(False)
+    prof = s.phase_profile()
+    s.close()
+    return {"clocks_per_warp_cycle": {k: round(prof[k], 1) for k in noc.Sim.PHASES},
+            "warp_cycles": prof["warp_cycles"], "us_per_cycle_profiled_build": 1e3 * ms / cycles,
+            "cycles": f"{warm}..{warm + cycles} of the period-10 run"}
 
 
 # --------------------------------------------------------------------- load dependence

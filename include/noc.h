@@ -362,6 +362,20 @@ int noc_last_variant(const noc_sim* sim, int* loop, int* kind, int* l1_bound, in
  * handle. */
 int noc_last_launch_bound(const noc_sim* sim);
 
+/* Per-phase clock profile of the plain loop (one tile per thread).  With
+ * enable != 0 (the first call takes a 48-byte device buffer), later plain
+ * launches through this handle run a build of the loop that reads the SM
+ * clock at each phase boundary of every warp and cycle; that build keeps its
+ * own registers (the 384-thread bound), so it runs somewhat slower than the
+ * production build.  noc_phase_profile waits for the handle's stream, writes
+ * six sums over warps and cycles -- SM clocks spent waiting for the
+ * neighbours' outputs, routing, publishing, in Phase 3, in Phase 1, and the
+ * number of warp-cycles -- and clears them.  Results never depend on it; the
+ * traced loop and the two-tile loop are not profiled.  Not in the paper (an
+ * observability facility). */
+int noc_set_phase_profile(noc_sim* sim, int enable);
+int noc_phase_profile(noc_sim* sim, uint64_t* out6);
+
 /* Device time of the cycle kernel alone.  With enable != 0, every later
  * cycle-kernel launch through this handle is bracketed by a pair of CUDA
  * events on the handle's stream (reference draws and other helper kernels

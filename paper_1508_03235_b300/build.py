@@ -23,6 +23,12 @@ UNITS = ([("noc_run_variant.cu", {"NOC_HASH": h, "NOC_DRAIN": d, "NOC_W1": w1, "
             for (w1, w2) in WAY_BOUNDS
             for spec in ({}, {"NOC_BASE": 1},
                          {"NOC_FIXED_POLICY": 0, "NOC_FIXED_MODE": 0, "NOC_EXACT_WAYS": 1})]
+         # and with per-phase clock reads (noc_set_phase_profile)
+         + [("noc_run_variant.cu", dict(spec, NOC_HASH=0, NOC_DRAIN=0, NOC_W1=w1, NOC_W2=w2,
+                                        NOC_PHASE_PROFILE=1))
+            for (w1, w2) in WAY_BOUNDS
+            for spec in ({}, {"NOC_BASE": 1},
+                         {"NOC_FIXED_POLICY": 0, "NOC_FIXED_MODE": 0, "NOC_EXACT_WAYS": 1})]
          + [("noc_batch.cu", {"NOC_W1": w1, "NOC_W2": w2}) for (w1, w2) in WAY_BOUNDS]
          + [("noc_batch.cu", {"NOC_W1": w1, "NOC_W2": w2, "NOC_BASE": 1}) for (w1, w2) in WAY_BOUNDS]
          + [("noc_batch.cu", {"NOC_W1": w1, "NOC_W2": w2, "NOC_FIXED_POLICY": 0, "NOC_FIXED_MODE": 0,

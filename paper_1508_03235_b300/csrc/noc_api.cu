@@ -178,6 +178,9 @@ struct noc_sim {
   int64_t launches = 0;
   int last_variant = -1;  // run_variant() of the last cycle-kernel launch
   int last_bound = 0;     // launch bound (most threads per CTA) of that launch's build
+  // per-phase clock profile of the plain loop (noc_set_phase_profile)
+  bool prof_on = false;
+  unsigned long long* d_prof = nullptr;  // 6 words, device
   // cycle-kernel timing: event pairs [2k, 2k + 1] around launch k
   bool time_kernels = false;
   std::vector<cudaEvent_t> tev;
@@ -465,6 +468,15 @@ int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
     A.wait_ns = s->wait_ns;
     A.silent_cta = s->silent_cta;
     A.thread_map = s->thread_map;
+    A.prof = (s->prof_on && !A.hash_trace && !A.busy && tpt == 1) ? s->d_prof : nullptr;
+    if (A.prof) {
+      // the profiled build keeps its own register count: check it fits too
+      int pcap = 0;
+      CU(max_coresident_prof(s->P, threads, &pcap), "occupancy");
+      if (s->run_gx * s->run_gy > pcap)
+        return fail(NOC_ERR_ARG, "tiling %dx%d does not fit one co-resident launch of the profiled loop",
+                    s->run_gx, s->run_gy);
+    }
     const bool plain = !A.hash_trace && !A.busy;
     if (plain && !s->gtag_clean && s->gtag_end != s->cycle) {
       CU(cudaMemsetAsync(s->P.gtag, 0, 2 * 4 * (size_t)s->P.N * 2 * sizeof(uint4), s->stream),
@@ -544,6 +556,7 @@ void noc_destroy(noc_sim* s) {
   if (s->d_busy) cudaFree(s->d_busy);
   if (s->d_trace) cudaFree(s->d_trace);
   if (s->d_trace_off) cudaFree(s->d_trace_off);
+  if (s->d_prof) cudaFree(s->d_prof);
   for (cudaEvent_t e : s->tev) cudaEventDestroy(e);
   delete s;
 }
@@ -1019,6 +1032,27 @@ int noc_debug_wait_limit(noc_sim* s, int64_t ns, int silent_cta) {
 int64_t noc_kernel_launches(const noc_sim* s) { return s ? s->launches : -1; }
 
 int noc_last_launch_bound(const noc_sim* s) { return s ? s->last_bound : -1; }
+
+int noc_set_phase_profile(noc_sim* s, int enable) {
+  if (!s) return fail(NOC_ERR_ARG, "null handle");
+  if (enable && !s->d_prof) {
+    CU(cudaMalloc(&s->d_prof, 6 * sizeof(unsigned long long)), "profile buffer");
+    CU(cudaMemsetAsync(s->d_prof, 0, 6 * sizeof(unsigned long long), s->stream), "profile clear");
+  }
+  s->prof_on = enable != 0;
+  return NOC_OK;
+}
+
+int noc_phase_profile(noc_sim* s, uint64_t* out6) {
+  if (!s || !out6) return fail(NOC_ERR_ARG, "null argument");
+  for (int k = 0; k < 6; ++k) out6[k] = 0;
+  if (!s->d_prof) return NOC_OK;
+  CU(cudaMemcpyAsync(out6, s->d_prof, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream),
+     "profile copy");
+  CU(cudaMemsetAsync(s->d_prof, 0, 6 * sizeof(unsigned long long), s->stream), "profile clear");
+  CU(cudaStreamSynchronize(s->stream), "sync");
+  return NOC_OK;
+}
 
 int noc_last_variant(const noc_sim* s, int* loop, int* kind, int* l1_bound, int* l2_bound) {
   if (!s) return fail(NOC_ERR_ARG, "null handle");

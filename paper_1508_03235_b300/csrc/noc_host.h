@@ -21,6 +21,8 @@ int configure(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, con
 int run_variant(const Params& P, const RunArgs& A);
 // the launch bound (most threads per CTA) of the build launch_run picks
 int run_launch_bound(const Params& P, const RunArgs& A);
+// co-resident CTAs of the plain loop's profiled build at `threads` per CTA
+cudaError_t max_coresident_prof(const Params& P, int threads, int* out);
 // the capacity loop (two tiles per thread, plain cycles only): launch, its
 // co-resident CTAs at `threads` per CTA, threads per CTA of a gx x gy
 // rectangle grid, and its run_variant() code (loop 2)

@@ -22,6 +22,10 @@ struct RunArgs {
   long long wait_ns;               // limit of each device-side wait
   int silent_cta;                  // test fault: this CTA never publishes
   int thread_map;                  // tile-to-thread order inside a rectangle (MAP_*)
+  // per-phase SM clocks of the plain loop, summed over warps (the profiled
+  // build only; nullptr otherwise): waiting, routing, publishing, Phase 3,
+  // Phase 1, and the number of warp-cycles
+  unsigned long long* prof;
 };
 
 // batch work queue: per-instance parameters, and items (instance, rectangle)

@@ -25,6 +25,12 @@ namespace noc {
   NOC_DECL_RUN(0, 0, w1, w2, gen_narrow)                                        \
   NOC_DECL_RUN(0, 0, w1, w2, il_narrow)                                         \
   NOC_DECL_RUN(0, 0, w1, w2, base_narrow)                                       \
+  NOC_DECL_RUN(0, 0, w1, w2, gen_prof)                                          \
+  NOC_DECL_RUN(0, 0, w1, w2, il_prof)                                           \
+  NOC_DECL_RUN(0, 0, w1, w2, base_prof)                                         \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_gen_prof(int threads, int* out);  \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_il_prof(int threads, int* out);   \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_base_prof(int threads, int* out); \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_gen(int threads, int* out);  \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_il(int threads, int* out);   \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_base(int threads, int* out); \
@@ -81,7 +87,7 @@ int run_variant(const Params& P, const RunArgs& A) {
 }
 
 int run_launch_bound(const Params& P, const RunArgs& A) {
-  const bool plain = !A.hash_trace && !A.busy;
+  const bool plain = !A.hash_trace && !A.busy && !A.prof;
   return plain && block_threads_impl(P.W, P.H, A.gx, A.gy) <= NARROW_THREADS ? NARROW_THREADS : MAX_THREADS;
 }
 
@@ -114,7 +120,15 @@ cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
   if (A.hash_trace && A.busy) return cudaErrorInvalidValue;
   if (A.hash_trace) { NOC_PICK_RUN(1, 0, gen) }
   if (A.busy) { NOC_PICK_RUN(0, 1, gen) }
-  // the plain loop: the narrow build when the CTAs fit it
+  // the plain loop: the profiled build when asked for, else the narrow build
+  // when the CTAs fit it
+  if (A.prof) {
+    switch (variant_kind(P)) {
+      case KIND_IL: NOC_PICK_RUN(0, 0, il_prof)
+      case KIND_BASE: NOC_PICK_RUN(0, 0, base_prof)
+      default: NOC_PICK_RUN(0, 0, gen_prof)
+    }
+  }
   if (block_threads_impl(P.W, P.H, A.gx, A.gy) <= NARROW_THREADS) {
     switch (variant_kind(P)) {
       case KIND_IL: NOC_PICK_RUN(0, 0, il_narrow)
@@ -145,6 +159,22 @@ cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
 
 // co-resident CTAs of the plain loop at `threads` per CTA, for the build a
 // launch of that size uses
+#define NOC_PICK_KIND_PROF(fn, kind, w1, w2, ...)                               \
+  switch (kind) {                                                                \
+    case KIND_IL: return fn##_##w1##_##w2##_il_prof(__VA_ARGS__);                \
+    case KIND_BASE: return fn##_##w1##_##w2##_base_prof(__VA_ARGS__);            \
+    default: return fn##_##w1##_##w2##_gen_prof(__VA_ARGS__);                    \
+  }
+
+cudaError_t max_coresident_prof(const Params& P, int threads, int* out) {
+  const int kind = variant_kind(P);
+  switch (way_class(P.l1_ways, P.l2_ways)) {
+    case 0: NOC_PICK_KIND_PROF(max_coresident_run_0_0, kind, 4, 8, threads, out)
+    case 1: NOC_PICK_KIND_PROF(max_coresident_run_0_0, kind, 4, 16, threads, out)
+    default: NOC_PICK_KIND_PROF(max_coresident_run_0_0, kind, 16, 16, threads, out)
+  }
+}
+
 cudaError_t max_coresident_ctas(const Params& P, int threads, int* out) {
   const int kind = variant_kind(P);
   if (threads <= NARROW_THREADS) {

@@ -175,6 +175,25 @@ constexpr int NARROW_THREADS = 320;
 #ifndef NOC_EARLY_POLL
 #define NOC_EARLY_POLL 1
 #endif
+// The profiled build of the plain loop (-DNOC_PHASE_PROFILE=1) reads the SM
+// clock at each phase boundary, after the warp has reconverged, and adds each
+// phase's clocks to A.prof at the end of the launch.
+#ifndef NOC_PHASE_PROFILE
+#define NOC_PHASE_PROFILE 0
+#endif
+#if NOC_PHASE_PROFILE
+#define NOC_PROF_MARK(k)                   \
+  do {                                     \
+    __syncwarp();                          \
+    const long long now_ = clock64();      \
+    prof_[k] += (unsigned long long)(now_ - prof_t_); \
+    prof_t_ = now_;                        \
+  } while (0)
+#else
+#define NOC_PROF_MARK(k) \
+  do {                   \
+  } while (0)
+#endif
 
 // shared memory before the poll stage: links [2 parity][4 port][threads],
 // histograms, reduction words
@@ -480,6 +499,10 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
   }
   __syncthreads();
   if (active) phase1<W1, W2>(P, T, t0, draining, sh_hist);
+#if NOC_PHASE_PROFILE
+  unsigned long long prof_[5] = {0, 0, 0, 0, 0};
+  long long prof_t_ = clock64();
+#endif
 
   uint32_t t = t0;
   for (; t < tend; ++t) {
@@ -573,6 +596,7 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
       if (aborted) break;
       __threadfence_block();
     }
+    NOC_PROF_MARK(0);
     // ---- Phase 2 (own tile): the in-rectangle arrivals, route, store outputs
     if (active) {
       const uint4* sp = sl + pin * 4 * nt;
@@ -583,6 +607,7 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
       route_ranked(P, T, t, in, exists, sl + pout * 4 * nt + i, nt, P.gtag + pout * pstride + (size_t)r * 2,
                   2 * N, edge_out, ic);
     }
+    NOC_PROF_MARK(1);
     // ---- publish: this warp has routed cycle t (the warp barrier orders every
     // lane's shared link stores before lane 0's flag store)
     __syncwarp();
@@ -604,12 +629,20 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
       cp_async_commit();
     }
 #endif
+    NOC_PROF_MARK(2);
     // ---- Phase 3 of this cycle and Phase 1 of the next (own tile only)
-    if (active) {
-      phase3<W1, W2>(P, T, t, sh_hist);
-      if (t + 1 != tend) phase1<W1, W2>(P, T, t + 1, draining, sh_hist);
-    }
+    if (active) phase3<W1, W2>(P, T, t, sh_hist);
+    NOC_PROF_MARK(3);
+    if (active && t + 1 != tend) phase1<W1, W2>(P, T, t + 1, draining, sh_hist);
+    NOC_PROF_MARK(4);
   }
+#if NOC_PHASE_PROFILE
+  if (lane == 0 && A.prof) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) atomicAdd(&A.prof[k], prof_[k]);
+    atomicAdd(&A.prof[5], (unsigned long long)(t - t0));
+  }
+#endif
 
   // ---- end of launch: full link state of the last cycle, tile state, counters
 #if NOC_POLL_STAGE

@@ -22,11 +22,15 @@
 #define NOC_SPEC0 gen
 #endif
 // -DNOC_NARROW=1: the build for CTAs of at most NARROW_THREADS threads
-#if defined(NOC_NARROW) && NOC_NARROW
-#define NOC_LB NARROW_THREADS
 #define NOC_PASTE2(a, b) a##_##b
 #define NOC_CAT2(a, b) NOC_PASTE2(a, b)
+#if defined(NOC_NARROW) && NOC_NARROW
+#define NOC_LB NARROW_THREADS
 #define NOC_SPEC NOC_CAT2(NOC_SPEC0, narrow)
+#elif NOC_PHASE_PROFILE
+// -DNOC_PHASE_PROFILE=1: the plain loop with per-phase clock reads
+#define NOC_LB MAX_THREADS
+#define NOC_SPEC NOC_CAT2(NOC_SPEC0, prof)
 #else
 #define NOC_LB MAX_THREADS
 #define NOC_SPEC NOC_SPEC0

@@ -158,6 +158,7 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
     A.wait_ns = 2000000000ll;
     A.silent_cta = -1;
     A.thread_map = 0;
+    A.prof = nullptr;
     ce = launch_run(P, A, st);
     if (ce != cudaSuccess) return fail(NOC_ERR_CUDA, "cycle kernel launch: %s", cudaGetErrorString(ce));
     done += n;

@@ -105,6 +105,8 @@ def lib():
             "noc_kernel_time": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(i64)]),
             "noc_last_variant": (i32, [vp] + [C.POINTER(i32)] * 4),
             "noc_last_launch_bound": (i32, [vp]),
+            "noc_set_phase_profile": (i32, [vp, i32]),
+            "noc_phase_profile": (i32, [vp, P64]),
             "noc_checkpoint_bytes": (C.c_size_t, [vp]),
             "noc_save": (i32, [vp, vp, C.c_size_t]),
             "noc_load": (i32, [vp, vp, C.c_size_t]),
@@ -265,6 +267,22 @@ class Sim:
         _check(lib().noc_last_variant(self._h, *[C.byref(x) for x in v]))
         return dict(loop=("plain", "traced", "plain, two tiles per thread")[v[0].value],
                     kind=KERNEL_KINDS[v[1].value], bounds=(v[2].value, v[3].value))
+
+    PHASES = ("wait", "route", "publish", "phase3", "phase1")
+
+    def set_phase_profile(self, enable: bool = True):
+        """Run later plain launches on the build with per-phase clock reads."""
+        _check(lib().noc_set_phase_profile(self._h, 1 if enable else 0))
+
+    def phase_profile(self) -> dict:
+        """SM clocks per warp-cycle in each phase since the last call (and
+        the number of warp-cycles), then cleared."""
+        v = np.zeros(6, dtype=np.uint64)
+        _check(lib().noc_phase_profile(self._h, _p64(v)))
+        n = int(v[5])
+        out = {name: (int(v[k]) / n if n else 0.0) for k, name in enumerate(self.PHASES)}
+        out["warp_cycles"] = n
+        return out
 
     def launch_bound(self) -> int:
         """Most threads per CTA of the last launch's build (320 or 384 for

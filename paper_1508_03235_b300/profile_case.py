@@ -6,6 +6,9 @@ runs `--warm` cycles (one or more cycle-kernel launches), then exactly one
 launch of `--cycles` cycles, and prints the cycle count.  Capture that last
 launch with `-k regex:run_kernel -s <launches of the warm-up> -c 1`; the number
 of warm-up launches is printed as well.  The 208x208 state is about 1.6 GB.
+With `--phases` the timed launch runs on the build with per-phase clock reads
+(noc_set_phase_profile) and the SM clocks per warp-cycle of each phase are
+printed.
 
     python -m paper_1508_03235_b300.profile_case --case surrogate
 
@@ -35,6 +38,8 @@ def main(argv=None):
     ap.add_argument("--case", default="cycle", choices=("cycle", "surrogate", "batch"))
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--batch-cycles", type=int, default=2000)
+    ap.add_argument("--phases", action="store_true",
+                    help="run the timed launch on the build with per-phase clock reads and print them")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import torch
@@ -69,11 +74,17 @@ def main(argv=None):
     s.kernel_time(True)
     s.step(a.warm)
     _, warm_launches = s.kernel_time(True)
+    if a.phases:
+        s.set_phase_profile(True)
     s.step(a.cycles)
     torch.cuda.synchronize()
     ms, n = s.kernel_time(False)
     print(f"mesh {a.mesh}x{a.mesh} tiling {s.tiling()} warm-up launches {warm_launches} "
           f"then {n} launch of {a.cycles} cycles ({ms:.3f} ms); cycle {s.stats()['cycle']}")
+    if a.phases:
+        prof = s.phase_profile()
+        print("SM clocks per warp-cycle: " + ", ".join(f"{k} {prof[k]:.0f}" for k in s.PHASES)
+              + f" ({prof['warp_cycles']} warp-cycles)")
 
 
 if __name__ == "__main__":

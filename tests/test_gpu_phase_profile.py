@@ -1,0 +1,51 @@
+"""The per-phase clock profile of the plain loop: turning it on runs another
+build of the loop, which must give the same results (counters, histograms,
+full state hash, equal to the oracle), and its sums must add up: one count per
+warp and simulated cycle, every phase a positive number of clocks."""
+import pytest
+
+from paper_1508_03235_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def noc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_03235_b300 import noc as _noc
+    return _noc
+
+
+@pytest.mark.parametrize("name,params,tiling,warps", [
+    ("mesh8_one_cta", dict(I.MESH_8["params"]), (1, 1), 2),
+    ("lspd_four_ctas", I.sim_params(16, 12, policy=2, seed=9,
+                                    traf=I.traffic(period=3, priv=0.4, shared=0.5, shared_mb=1)),
+     (2, 2), 4 * 2),
+])
+def test_profile_changes_nothing_and_adds_up(noc, oracle_mod, name, params, tiling, warps):
+    g = noc.Sim(params, tiling=tiling)
+    g.set_phase_profile(True)
+    o = oracle_mod.OracleSim(params)
+    for n in (700, 900):
+        g.step(n)
+        o.step(n)
+    prof = g.phase_profile()
+    assert prof["warp_cycles"] == warps * 1600, prof
+    for ph in noc.Sim.PHASES:
+        assert prof[ph] > 0, (ph, prof)
+    assert g.launch_bound() == 384
+    gs, os_ = g.stats(), o.stats()
+    for k, v in os_.items():
+        assert gs[k] == v, (k, gs[k], v)
+    assert g.state_hash() == o.state_hash()
+    assert (g.hist(0) == o.hist(0)).all() and (g.hist(1) == o.hist(1)).all()
+    # read once: cleared
+    assert g.phase_profile()["warp_cycles"] == 0
+    # off again: the production build, same results
+    g.set_phase_profile(False)
+    g.step(300)
+    o.step(300)
+    assert g.phase_profile()["warp_cycles"] == 0
+    assert g.state_hash() == o.state_hash()
