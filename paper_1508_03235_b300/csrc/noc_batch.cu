@@ -4,6 +4,7 @@
 // -DNOC_EXACT_WAYS=1)
 // the batch's rectangles are small and mostly edge: one poll in flight
 #define NOC_POLL_STAGE 0
+#define NOC_PREFETCH_HOME 0
 #include "noc_kernel.cuh"
 
 #if !defined(NOC_W1) || !defined(NOC_W2)

@@ -397,6 +397,10 @@ __device__ __forceinline__ void run_rect(const Params& P, const RunArgs& A, cons
 // ---------------------------------------------------------------- warp-flag loop
 constexpr int WARPS_PER_CTA = MAX_THREADS / 32;
 
+__device__ __forceinline__ void st_release_cta_shared(unsigned* p, unsigned v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v)
+               : "memory");
+}
 __device__ __forceinline__ unsigned ld_volatile_shared(const unsigned* p) {
   return *reinterpret_cast<const volatile unsigned*>(p);
 }
@@ -594,7 +598,8 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
         }
       }
       if (aborted) break;
-      __threadfence_block();
+      // acquire: the flag loads above, then the neighbours' link stores
+      asm volatile("fence.acq_rel.cta;" ::: "memory");
     }
     NOC_PROF_MARK(0);
     // ---- Phase 2 (own tile): the in-rectangle arrivals, route, store outputs
@@ -609,12 +614,10 @@ __device__ __forceinline__ void run_rect_warps(const Params& P, const RunArgs& A
     }
     NOC_PROF_MARK(1);
     // ---- publish: this warp has routed cycle t (the warp barrier orders every
-    // lane's shared link stores before lane 0's flag store)
+    // lane's shared link stores before lane 0's flag store, a release at CTA
+    // scope that the waiting warps' acquire fence pairs with)
     __syncwarp();
-    if (lane == 0) {
-      __threadfence_block();
-      *reinterpret_cast<volatile unsigned*>(&wflag[warp]) = t + 1;
-    }
+    if (lane == 0) st_release_cta_shared(&wflag[warp], t + 1);
 #if NOC_POLL_STAGE && NOC_EARLY_POLL
     // the first copy of the slots the next cycle's wait reads (the outputs of
     // cycle t), into the stage half that wait reads first

@@ -564,6 +564,21 @@ __device__ __forceinline__ size_t l1_base(const Params& P, uint32_t r, uint32_t 
 __device__ __forceinline__ size_t l2_base(const Params& P, uint32_t r, uint32_t set) {
   return ((size_t)r * P.l2_sets + set) * L2WAYS(P);
 }
+// The L2 set a request or write-through for `line` will look up at tile `h`,
+// pulled into the GPU's L2 cache when the message leaves.  A large mesh's
+// slice tag arrays are far larger than that cache, so without this the
+// lookup, some hundred simulated cycles later, would wait on DRAM inside
+// Phase 3 of the home's warp.  A prefetch has no effect on any result.  The
+// batch kernel, whose small instances stay in the cache, builds without it
+// (NOC_PREFETCH_HOME 0).
+#ifndef NOC_PREFETCH_HOME
+#define NOC_PREFETCH_HOME 1
+#endif
+__device__ __forceinline__ void prefetch_home_set(const Params& P, uint32_t h, uint32_t line) {
+#if NOC_PREFETCH_HOME
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(P.l2 + l2_base(P, h, l2_set(P, line))));
+#endif
+}
 
 
 __device__ __forceinline__ uint16_t* hist_ptr(const Params& P, size_t way_index) {
@@ -637,7 +652,10 @@ __device__ __forceinline__ void write_to_owner(const Params& P, Tile& T, uint32_
                                                uint32_t t) {
   if (owner == T.r) local_wt<W2>(P, T, line);
   else if (owner == NO_TILE) SMALL(S_MEMW)++;
-  else send_svc(P, T, mkflit(T_WT, T.r, owner, line, 0, 0), t);
+  else {
+    prefetch_home_set(P, owner, line);
+    send_svc(P, T, mkflit(T_WT, T.r, owner, line, 0, 0), t);
+  }
 }
 
 // fill the L1 with `line` (insert if absent, else touch); `owner` is the tile
@@ -721,6 +739,7 @@ static __device__ bool l1_step(const Params& P, Tile& T, uint32_t t, uint32_t li
           SMALL(S_CQST)++;
           return false;
         }
+        prefetch_home_set(P, owner, line);
         send_core(P, T, mkflit(T_WT, T.r, owner, line, 0, 0));
       }
     }
@@ -784,6 +803,7 @@ static __device__ void l2_step(const Params& P, Tile& T, uint32_t t, uint32_t* s
       SMALL(S_CQST)++;
       return;
     }
+    prefetch_home_set(P, h, line);
     send_core(P, T, mkflit(T_REQ, T.r, h, line, T.r, 0));
     set_om(T, OM_WAIT_DATA, line, write, start);
     T.fsm = FSM_IDLE;

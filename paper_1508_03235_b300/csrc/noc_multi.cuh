@@ -281,7 +281,7 @@ __device__ __forceinline__ void run_rect_multi(const Params& P, const RunArgs& A
         }
       }
       if (aborted) break;
-      __threadfence_block();
+      asm volatile("fence.acq_rel.cta;" ::: "memory");   // acquire
     }
     // ---- each tile: route cycle t, Phase 3 of t, Phase 1 of t + 1
     const uint4* sp = sl + pin * 4 * cap;
@@ -306,10 +306,7 @@ __device__ __forceinline__ void run_rect_multi(const Params& P, const RunArgs& A
       }
     // ---- publish: this warp has routed cycle t for all its tiles
     __syncwarp();
-    if (lane == 0) {
-      __threadfence_block();
-      *reinterpret_cast<volatile unsigned*>(&wflag[warp]) = t + 1;
-    }
+    if (lane == 0) st_release_cta_shared(&wflag[warp], t + 1);
   }
 
   // ---- end of launch: full link state of the last cycle, tile state, counters
