@@ -193,10 +193,11 @@ __device__ __forceinline__ uint32_t fage(const Params& P, uint4 f) {
 }
 // priority key, smaller first: older (smaller inject cycle), then smaller
 // source; under age_mode 1 more deflections before both (the age bits of x
-// inverted, so that a larger age gives a smaller key)
+// inverted, so that a larger age gives a smaller key).  The word x is the
+// key's high half as it is, the source its low half.
 __device__ __forceinline__ unsigned long long fkey(const Params& P, uint4 f) {
   const uint32_t flip = AGE1(P) ? (AGE_MAX << AGE_SHIFT) : 0u;
-  return ((unsigned long long)(f.x ^ flip) << 16) | (f.y & 0xFFFFu);
+  return ((unsigned long long)(f.x ^ flip) << 32) | (f.y & 0xFFFFu);
 }
 
 // Tagged link slots (cross-rectangle links of the plain cycle loop).  Every
@@ -1202,7 +1203,8 @@ __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t 
 #pragma unroll
   for (int d = 0; d < 4; ++d)
     if (((vm >> d) & 1u) && fdst(in[d]) == T.r) emr |= 1u << rk[d];
-  const uint32_t rej = emr ? (uint32_t)(__ffs(emr) - 1) : 4u;
+  // the lowest set bit's index; ~0u (above every rank) when none is set
+  const uint32_t rej = 31u - (uint32_t)__clz(emr & (0u - emr));
   T.ej = make_uint4(0, 0, 0, 0);
   uint32_t rm = vm;
 #pragma unroll
@@ -1247,6 +1249,7 @@ __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t 
     freem &= ~pick;
     pkp |= pick << (4 * r);
   }
+  // grants are one-hot: a port's index is the position of its bit (31 - clz)
   uint32_t pk[4];
 #pragma unroll
   for (int d = 0; d < 4; ++d) pk[d] = (pkp >> (4u * rk[d])) & 15u;
@@ -1264,15 +1267,15 @@ __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t 
       if ((rm >> d) & 1u) {
         uint4 f = in[d];
         if (!(pk[d] & (prod[d] | (prod[d] >> 4)))) age_deflected(P, f, t);
-        so[(__ffs(pk[d]) - 1) * so_stride] = f;
+        so[(31 - __clz(pk[d])) * so_stride] = f;
       }
     if (has_inj && !(pki & (ic.prod | (ic.prod >> 4)))) age_deflected(P, inj, t);
   } else {
 #pragma unroll
     for (int d = 0; d < 4; ++d)
-      if ((rm >> d) & 1u) so[(__ffs(pk[d]) - 1) * so_stride] = in[d];
+      if ((rm >> d) & 1u) so[(31 - __clz(pk[d])) * so_stride] = in[d];
   }
-  if (has_inj) so[(__ffs(pki) - 1) * so_stride] = inj;
+  if (has_inj) so[(31 - __clz(pki)) * so_stride] = inj;
   if (edge) {
     const uint32_t tag = link_tag(t);
 #pragma unroll
