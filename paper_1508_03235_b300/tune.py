@@ -70,6 +70,19 @@ def broad_candidates(W: int, H: int, lo: int = 48, hi: int = MAX_THREADS):
     return sorted(best.values(), key=lambda g: (-(-(-W // g[0]) * -(-H // g[1])), g))
 
 
+def spread_candidates(W: int, H: int, gx: int, gy: int, max_ctas: int):
+    """The other grids that cut the mesh into rectangles of the same largest
+    shape as (gx, gy) -- ceil(W/gx) x ceil(H/gy) -- with more CTAs, at most
+    max_ctas: the same warps per CTA spread over more SMs (their rectangles
+    are one row or column smaller where the cut falls unevenly).  Fewest CTAs
+    first; (gx, gy) itself is not included."""
+    bw, bh = -(-W // gx), -(-H // gy)
+    xs = [g for g in range(gx, W + 1) if -(-W // g) == bw]
+    ys = [g for g in range(gy, H + 1) if -(-H // g) == bh]
+    out = [(a, b) for a in xs for b in ys if (a, b) != (gx, gy) and a * b <= max_ctas]
+    return sorted(out, key=lambda g: (g[0] * g[1], g))
+
+
 def load_cache() -> dict:
     if os.path.exists(CACHE):
         with open(CACHE) as f:
@@ -134,6 +147,51 @@ def tune(params: dict, cycles: int = 2000, warm: int = 200, max_cands: int = 10,
         with open(cache_path, "w") as f:
             json.dump(cache, f, indent=1, sort_keys=True)
     return best, timings
+
+
+def spread(params: dict, cycles: int = 2000, warm: int = 200, reps: int = 2, save: bool = True,
+           verbose: bool = False, cache_path: str = CACHE):
+    """Refine a cached tuning: time its tiling and every spread_candidates()
+    grid of the same rectangle shape (up to one CTA per SM), in its thread
+    order, and keep the fastest.  Returns (best (gx, gy, order), {grid: us
+    per cycle})."""
+    import torch
+
+    from . import noc
+
+    cache = json.load(open(cache_path)) if os.path.exists(cache_path) else load_cache()
+    entry = cache[key(params)]
+    gx, gy = entry["tiling"]
+    m = entry.get("thread_map", 0)
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sim = noc.Sim(params, thread_map=m)
+    timings = {}
+    for g in [(gx, gy)] + spread_candidates(params["mesh_w"], params["mesh_h"], gx, gy, sms):
+        try:
+            sim.set_tiling(*g)
+            dt = float("inf")
+            for _ in range(reps):
+                sim.reset()
+                sim.step(warm)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sim.step(cycles)
+                dt = min(dt, time.perf_counter() - t0)
+        except noc.NocError:
+            continue                       # not co-resident on this GPU
+        timings[g] = 1e6 * dt / cycles
+        if verbose:
+            print(f"  tiling {g[0]}x{g[1]} {noc.THREAD_MAPS[m]}: {timings[g]:.3f} us/cycle", flush=True)
+    sim.close()
+    best = min(timings, key=timings.get)
+    if save:
+        entry["tiling"] = list(best)
+        entry["us_per_cycle"] = timings[best]
+        entry["spread_timings"] = {f"{a}x{b}/{noc.THREAD_MAPS[m]}": v for (a, b), v in timings.items()}
+        cache[key(params)] = entry
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+    return (best[0], best[1], m), timings
 
 
 # ------------------------------------------------------------------ batch engine
@@ -225,9 +283,17 @@ if __name__ == "__main__":
     ap.add_argument("--broad", action="store_true", help="every rectangle shape (single simulations)")
     ap.add_argument("--batch", action="store_true",
                     help="tune the batch engine on the 512-instance design-point workload")
+    ap.add_argument("--spread", action="store_true",
+                    help="refine the cached single-simulation tilings over more CTAs of the same shape")
     ap.add_argument("--out", default=CACHE, help="cache file to update")
     a = ap.parse_args()
-    if a.batch:
+    if a.spread:
+        for name, p in (("mesh208", I.mesh_208(10)), ("mesh64", I.mesh_64(1)),
+                        ("mesh8", I.MESH_8["params"])):
+            print(name, flush=True)
+            b, t = T.spread(p, verbose=True, cache_path=a.out)
+            print(f"  best {b}", flush=True)
+    elif a.batch:
         pts = I.batch_design_points(512, seed=0)
         for p in pts:
             p.pop("design")
