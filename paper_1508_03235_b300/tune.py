@@ -72,13 +72,13 @@ def broad_candidates(W: int, H: int, lo: int = 48, hi: int = MAX_THREADS):
 
 def spread_candidates(W: int, H: int, gx: int, gy: int, max_ctas: int):
     """The other grids that cut the mesh into rectangles of the same largest
-    shape as (gx, gy) -- ceil(W/gx) x ceil(H/gy) -- with more CTAs, at most
-    max_ctas: the same warps per CTA spread over more SMs (their rectangles
-    are one row or column smaller where the cut falls unevenly).  Fewest CTAs
-    first; (gx, gy) itself is not included."""
+    shape as (gx, gy) -- ceil(W/gx) x ceil(H/gy) -- with at most max_ctas
+    CTAs: the same warps per CTA spread over fewer or more SMs (where the cut
+    falls unevenly, some rectangles are a row or column smaller).  Fewest
+    CTAs first; (gx, gy) itself is not included."""
     bw, bh = -(-W // gx), -(-H // gy)
-    xs = [g for g in range(gx, W + 1) if -(-W // g) == bw]
-    ys = [g for g in range(gy, H + 1) if -(-H // g) == bh]
+    xs = [g for g in range(1, W + 1) if -(-W // g) == bw]
+    ys = [g for g in range(1, H + 1) if -(-H // g) == bh]
     out = [(a, b) for a in xs for b in ys if (a, b) != (gx, gy) and a * b <= max_ctas]
     return sorted(out, key=lambda g: (g[0] * g[1], g))
 
@@ -149,12 +149,13 @@ def tune(params: dict, cycles: int = 2000, warm: int = 200, max_cands: int = 10,
     return best, timings
 
 
-def spread(params: dict, cycles: int = 2000, warm: int = 200, reps: int = 2, save: bool = True,
+def spread(params: dict, cycles: int = 8000, warm: int = 2000, reps: int = 3, save: bool = True,
            verbose: bool = False, cache_path: str = CACHE):
     """Refine a cached tuning: time its tiling and every spread_candidates()
-    grid of the same rectangle shape (up to one CTA per SM), in its thread
-    order, and keep the fastest.  Returns (best (gx, gy, order), {grid: us
-    per cycle})."""
+    grid of the same largest rectangle shape (up to one CTA per SM), in its
+    thread order, and keep the fastest.  The grids differ by tenths of a percent, so
+    each is timed longer than in tune() (8,000 cycles after 2,000, best of
+    three).  Returns (best (gx, gy, order), {grid: us per cycle})."""
     import torch
 
     from . import noc

@@ -49,17 +49,15 @@ def test_batch_candidates():
 def test_spread_candidates_keep_the_rectangle_shape():
     from paper_1508_03235_b300 import tune as T
     assert T.spread_candidates(208, 208, 2, 70, 148) == [(2, 71), (2, 72), (2, 73), (2, 74)]
+    assert T.spread_candidates(208, 208, 2, 74, 148) == [(2, 70), (2, 71), (2, 72), (2, 73)]
     assert T.spread_candidates(8, 8, 1, 1, 148) == []
     for (W, H, gx, gy, cap) in ((208, 208, 2, 70, 148), (64, 64, 1, 32, 148), (100, 60, 4, 6, 40),
-                                (255, 257, 3, 40, 148)):
+                                (255, 257, 3, 40, 148), (208, 208, 2, 73, 148)):
         out = T.spread_candidates(W, H, gx, gy, cap)
         shape = (-(-W // gx), -(-H // gy))
         assert (gx, gy) not in out and len(set(out)) == len(out)
         assert [a * b for a, b in out] == sorted(a * b for a, b in out)
-        for a, b in out:
-            assert (-(-W // a), -(-H // b)) == shape
-            assert gx * gy < a * b <= cap or (a * b == gx * gy and (a, b) != (gx, gy))
-        # and every grid of that shape within the cap is there
+        # exactly every other grid of that largest shape within the cap
         every = {(a, b) for a in range(1, W + 1) for b in range(1, H + 1)
-                 if (-(-W // a), -(-H // b)) == shape and a * b <= cap and a >= gx and b >= gy}
+                 if (-(-W // a), -(-H // b)) == shape and a * b <= cap}
         assert set(out) == every - {(gx, gy)}
