@@ -295,7 +295,7 @@ int noc_batch_set_collect_hash(noc_batch* batch, int enable);
  * instance error (see noc_batch_error for each). */
 int noc_batch_run(noc_batch* batch);
 /* Work-queue launches of the last run: at least one per kernel-variant group
- * (at most four groups), more when a group's state exceeds the pool. */
+ * present, more when a group's state exceeds the pool. */
 int noc_batch_waves(const noc_batch* batch);
 int noc_batch_error(const noc_batch* batch, int i, int64_t* err_cycle);
 int noc_batch_stats(const noc_batch* batch, int i, noc_stats_t* out);
@@ -305,10 +305,12 @@ int64_t noc_batch_kernel_launches(const noc_batch* batch);
 /* The build of the batch kernel that runs instance i (kind and way bounds as
  * in noc_last_variant); fixed by the descriptors when the batch is created. */
 int noc_batch_variant(const noc_batch* batch, int i, int* kind, int* l1_bound, int* l2_bound);
-/* Kernel-variant group of instance i, 0..4 (-1 for a bad argument): 0, 1, 2 =
+/* Kernel-variant group of instance i, 0..10 (-1 for a bad argument): 0, 1, 2 =
  * the interleaved build of way class (4, 8), (4, 16), (16, 16); 3 = the base
- * build; 4 = the general build.  Instances of one group and one rectangle
- * side share work-queue launches; the autotuner picks a layout per group. */
+ * build; 4 = the general build; 5, 6, 7 = the LSPD local-placement build and
+ * 8, 9, 10 = the LSPD migration build of those way classes.  Instances of one
+ * group and one rectangle side share work-queue launches; the autotuner picks
+ * a layout per group. */
 int noc_batch_group(const noc_batch* batch, int i);
 
 /* Allocation-free run.  No counterpart in the paper: this entry point serves
@@ -350,7 +352,11 @@ int64_t noc_kernel_launches(const noc_sim* sim);
  *           1 = base (every policy and mode; the packet, write-back,
  *               directory-node and deflection-count-age options compiled out),
  *           2 = interleaved L2 in cache mode only, with exactly the way counts
- *               of its bounds;
+ *               of its bounds,
+ *           3 = the same for the LSPD L2 with local placement (Sec. 3.2),
+ *           4 = the same for the LSPD L2 with migration (Sec. 3.3), both
+ *               without the directory node (the per-phase profiled build of
+ *               these two is the base one);
  *   *l1_bound, *l2_bound: the compile-time way bounds, (4, 8), (4, 16) or
  *           (16, 16).
  * Any output pointer may be NULL.  NOC_ERR_STATE before the first launch. */

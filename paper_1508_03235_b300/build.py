@@ -11,18 +11,21 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnoc.so")
 # (source, preprocessor defines): the cycle kernel is compiled once per variant
 WAY_BOUNDS = ((4, 8), (4, 16), (16, 16))
+POLICIES = (0, 1, 2)   # interleaved, LSPD local placement, LSPD migration
 UNITS = ([("noc_run_variant.cu", {"NOC_HASH": h, "NOC_DRAIN": d, "NOC_W1": w1, "NOC_W2": w2})
           for (w1, w2) in WAY_BOUNDS for (h, d) in ((0, 0), (1, 0), (0, 1))]
+         # the plain loop specialised to one L2 policy (0 interleaved, 1 LSPD
+         # local placement, 2 LSPD migration) with the class's exact ways
          + [("noc_run_variant.cu", {"NOC_HASH": 0, "NOC_DRAIN": 0, "NOC_W1": w1, "NOC_W2": w2,
-                                    "NOC_FIXED_POLICY": 0, "NOC_FIXED_MODE": 0, "NOC_EXACT_WAYS": 1})
-            for (w1, w2) in WAY_BOUNDS]
+                                    "NOC_FIXED_POLICY": pol, "NOC_FIXED_MODE": 0, "NOC_EXACT_WAYS": 1})
+            for (w1, w2) in WAY_BOUNDS for pol in POLICIES]
          + [("noc_run_variant.cu", {"NOC_HASH": 0, "NOC_DRAIN": 0, "NOC_W1": w1, "NOC_W2": w2,
                                     "NOC_BASE": 1}) for (w1, w2) in WAY_BOUNDS]
          # the plain loop again, for CTAs of at most 320 threads (more registers)
          + [("noc_run_variant.cu", dict(spec, NOC_HASH=0, NOC_DRAIN=0, NOC_W1=w1, NOC_W2=w2, NOC_NARROW=1))
             for (w1, w2) in WAY_BOUNDS
-            for spec in ({}, {"NOC_BASE": 1},
-                         {"NOC_FIXED_POLICY": 0, "NOC_FIXED_MODE": 0, "NOC_EXACT_WAYS": 1})]
+            for spec in [{}, {"NOC_BASE": 1}]
+            + [{"NOC_FIXED_POLICY": pol, "NOC_FIXED_MODE": 0, "NOC_EXACT_WAYS": 1} for pol in POLICIES]]
          # and with per-phase clock reads (noc_set_phase_profile)
          + [("noc_run_variant.cu", dict(spec, NOC_HASH=0, NOC_DRAIN=0, NOC_W1=w1, NOC_W2=w2,
                                         NOC_PHASE_PROFILE=1))
@@ -31,8 +34,8 @@ UNITS = ([("noc_run_variant.cu", {"NOC_HASH": h, "NOC_DRAIN": d, "NOC_W1": w1, "
                          {"NOC_FIXED_POLICY": 0, "NOC_FIXED_MODE": 0, "NOC_EXACT_WAYS": 1})]
          + [("noc_batch.cu", {"NOC_W1": w1, "NOC_W2": w2}) for (w1, w2) in WAY_BOUNDS]
          + [("noc_batch.cu", {"NOC_W1": w1, "NOC_W2": w2, "NOC_BASE": 1}) for (w1, w2) in WAY_BOUNDS]
-         + [("noc_batch.cu", {"NOC_W1": w1, "NOC_W2": w2, "NOC_FIXED_POLICY": 0, "NOC_FIXED_MODE": 0,
-                              "NOC_EXACT_WAYS": 1}) for (w1, w2) in WAY_BOUNDS]
+         + [("noc_batch.cu", {"NOC_W1": w1, "NOC_W2": w2, "NOC_FIXED_POLICY": pol, "NOC_FIXED_MODE": 0,
+                              "NOC_EXACT_WAYS": 1}) for (w1, w2) in WAY_BOUNDS for pol in POLICIES]
          + [("noc_run_multi.cu", {"NOC_W1": w1, "NOC_W2": w2}) for (w1, w2) in WAY_BOUNDS]
          + [("noc_kernel.cu", {}), ("noc_api.cu", {}), ("noc_static.cu", {}), ("mlp.cu", {})])
 SOURCES = sorted({u[0] for u in UNITS})

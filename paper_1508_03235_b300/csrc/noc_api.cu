@@ -1146,24 +1146,30 @@ int noc_batch_create(int n, const noc_instance_desc* d, noc_batch** out) {
   b->variant.assign(n, -1);
   b->rect.assign(n, 8);
   b->strips.assign(n, 0);
-  // kernel-variant groups: the instances the specialised kernel of way class
-  // 0, 1, 2 serves (interleaved L2, cache mode, exact ways), those without the
-  // packet, write-back, directory-node and age options on the base kernel, then
-  // the rest on the general kernel; the last two with the largest way bounds
-  // among their instances
+  // kernel-variant groups: the instances the specialised kernels of way class
+  // 0, 1, 2 serve -- interleaved L2 (groups 0-2), LSPD with local placement
+  // (5-7), LSPD with migration (8-10), each in cache mode with exact ways --
+  // those without the packet, write-back, directory-node and age options on
+  // the base kernel (3), then the rest on the general kernel (4); those two
+  // with the largest way bounds among their instances
   b->group.assign(n, 0);
-  int gw1[5] = {1, 1, 1, 1, 1}, gw2[5] = {1, 1, 1, 1, 1};
+  int gw1[NOC_BATCH_GROUPS], gw2[NOC_BATCH_GROUPS];
+  for (int g = 0; g < NOC_BATCH_GROUPS; ++g) gw1[g] = gw2[g] = 1;
   for (int i = 0; i < n; ++i) {
     const Params& P = b->sims[i]->P;
-    const int kind = variant_kind(P);
-    const int g = kind == KIND_IL ? batch_way_class(P.l1_ways, P.l2_ways) : kind == KIND_BASE ? 3 : 4;
+    const int kind = variant_kind(P), c = batch_way_class(P.l1_ways, P.l2_ways);
+    const int g = kind == KIND_IL        ? c
+                  : kind == KIND_LOCAL   ? 5 + c
+                  : kind == KIND_MIGRATE ? 8 + c
+                  : kind == KIND_BASE    ? 3
+                                         : 4;
     b->group[i] = g;
     gw1[g] = std::max(gw1[g], P.l1_ways);
     gw2[g] = std::max(gw2[g], P.l2_ways);
   }
   for (int i = 0; i < n; ++i) {
     const int g = b->group[i];
-    const int kind = g < 3 ? KIND_IL : g == 3 ? KIND_BASE : KIND_GEN;
+    const int kind = g < 3 ? KIND_IL : g == 3 ? KIND_BASE : g == 4 ? KIND_GEN : g < 8 ? KIND_LOCAL : KIND_MIGRATE;
     b->variant[i] = (kind << 4) | batch_way_class(gw1[g], gw2[g]);
   }
   *out = b;
@@ -1446,7 +1452,7 @@ int noc_batch_run(noc_batch* b) {
   b->waves = 0;
   int first_err = NOC_OK;
   static const int bounds[3][2] = {{4, 8}, {4, 16}, {16, 16}};
-  for (int g = 0; g < 5; ++g)
+  for (int g = 0; g < NOC_BATCH_GROUPS; ++g)
     for (int side = 1; side * side <= 384; ++side) {
       std::vector<int> members;
       for (int i = 0; i < n; ++i)

@@ -1,7 +1,7 @@
 // noc_batch.cu -- the batch engine's persistent work-queue kernel (compiled once
-// per L1/L2 way bound, and twice more per bound specialised like the plain
-// cycle loop: -DNOC_BASE=1, and -DNOC_FIXED_POLICY=0 -DNOC_FIXED_MODE=0
-// -DNOC_EXACT_WAYS=1)
+// per L1/L2 way bound, and more per bound specialised like the plain cycle
+// loop: -DNOC_BASE=1, and -DNOC_FIXED_POLICY=<p> -DNOC_FIXED_MODE=0
+// -DNOC_EXACT_WAYS=1 for p = 0, 1, 2)
 // the batch's rectangles are small and mostly edge: one poll in flight
 #define NOC_POLL_STAGE 0
 #define NOC_PREFETCH_HOME 0
@@ -10,7 +10,13 @@
 #if !defined(NOC_W1) || !defined(NOC_W2)
 #error "compile with -DNOC_W1= -DNOC_W2="
 #endif
-#if defined(NOC_FIXED_POLICY)
+#if defined(NOC_FIXED_POLICY) && NOC_FIXED_POLICY == 1
+#define NOC_POLV NOC_FIXED_POLICY
+#define NOC_SPEC local
+#elif defined(NOC_FIXED_POLICY) && NOC_FIXED_POLICY == 2
+#define NOC_POLV NOC_FIXED_POLICY
+#define NOC_SPEC migrate
+#elif defined(NOC_FIXED_POLICY)
 #define NOC_POLV NOC_FIXED_POLICY
 #define NOC_SPEC il
 #elif defined(NOC_BASE)

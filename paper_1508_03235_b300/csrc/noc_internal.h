@@ -41,12 +41,16 @@ struct BatchArgs {
   int n_items;
   long long gang_ns;        // limit of the wait for an instance's rectangles
 };
-// kind: which specialisation of the device code runs -- KIND_IL (interleaved
-// L2 in cache mode with exactly the way counts of the class of (l1_ways,
-// l2_ways)), KIND_BASE (every policy and mode, none of the packet, write-back,
-// directory-node or age options) or KIND_GEN (everything); variant_kind(P) is the
-// narrowest one a configuration may run on
-enum { KIND_GEN = 0, KIND_BASE = 1, KIND_IL = 2 };
+// kind: which specialisation of the device code runs -- KIND_IL, KIND_LOCAL
+// and KIND_MIGRATE (one L2 policy -- interleaved, LSPD with local placement,
+// LSPD with migration -- in cache mode with exactly the way counts of the
+// class of (l1_ways, l2_ways), no packet, write-back, directory-node or age
+// option), KIND_BASE (every policy and mode, none of those options) or
+// KIND_GEN (everything); variant_kind(P) is the narrowest one a configuration
+// may run on
+enum { KIND_GEN = 0, KIND_BASE = 1, KIND_IL = 2, KIND_LOCAL = 3, KIND_MIGRATE = 4 };
+// batch kernel-variant groups (noc_batch_group)
+constexpr int NOC_BATCH_GROUPS = 11;
 int variant_kind(const Params& P);
 cudaError_t launch_batch(const BatchArgs& B, int grid, int threads, int l1_ways, int l2_ways, int kind,
                          cudaStream_t s);

@@ -11,9 +11,11 @@ namespace noc {
 // compile-time way bounds (L1, L2) of the cache-set code: (4, 8), (4, 16) and
 // the general (16, 16).  The plain loop also comes as "base" (every policy and
 // mode, the packet, write-back, directory-node and age options compiled out) and as
-// "il", specialised to the interleaved L2 in cache mode with the class's exact
-// way counts (the other policies' code compiled out, the way loops of fixed
-// length).
+// "il", "local" and "migrate", each specialised to one L2 policy (interleaved,
+// LSPD with local placement, LSPD with migration) in cache mode with the
+// class's exact way counts (the other policies' code compiled out, the way
+// loops of fixed length).  The per-phase profiled builds exist for gen, base
+// and il; a local or migrate configuration is profiled on the base build.
 #define NOC_DECL_RUN(h, d, w1, w2, sp) \
   cudaError_t launch_run_##h##_##d##_##w1##_##w2##_##sp(const Params&, const RunArgs&, cudaStream_t);
 #define NOC_DECL_WAYS(w1, w2)                                                   \
@@ -28,6 +30,18 @@ namespace noc {
   NOC_DECL_RUN(0, 0, w1, w2, gen_prof)                                          \
   NOC_DECL_RUN(0, 0, w1, w2, il_prof)                                           \
   NOC_DECL_RUN(0, 0, w1, w2, base_prof)                                         \
+  NOC_DECL_RUN(0, 0, w1, w2, local)                                             \
+  NOC_DECL_RUN(0, 0, w1, w2, migrate)                                           \
+  NOC_DECL_RUN(0, 0, w1, w2, local_narrow)                                      \
+  NOC_DECL_RUN(0, 0, w1, w2, migrate_narrow)                                    \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_local(int threads, int* out);        \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_migrate(int threads, int* out);      \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_local_narrow(int threads, int* out); \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_migrate_narrow(int threads, int* out); \
+  cudaError_t launch_batch_##w1##_##w2##_local(const BatchArgs&, int, int, cudaStream_t); \
+  cudaError_t launch_batch_##w1##_##w2##_migrate(const BatchArgs&, int, int, cudaStream_t); \
+  cudaError_t max_coresident_batch_##w1##_##w2##_local(int threads, int* out);            \
+  cudaError_t max_coresident_batch_##w1##_##w2##_migrate(int threads, int* out);          \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_gen_prof(int threads, int* out);  \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_il_prof(int threads, int* out);   \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_base_prof(int threads, int* out); \
@@ -58,20 +72,26 @@ static int way_class(int l1_ways, int l2_ways) {
   if (l1_ways > 4) return 2;
   return l2_ways <= 8 ? 0 : 1;
 }
-// the plain loop has a variant specialised to the interleaved L2 in cache mode
-// with exactly the way counts of its class
-static bool interleaved_cache(const Params& P) {
+// the plain loop has variants specialised to one L2 policy in cache mode with
+// exactly the way counts of its class and none of the options
+static bool exact_cache(const Params& P) {
   static const int exact[3][2] = {{4, 8}, {4, 16}, {16, 16}};
   const int c = way_class(P.l1_ways, P.l2_ways);
-  return P.policy == POL_INTERLEAVED && P.mode == MODE_CACHE && !P.packet_mode &&
-         !P.l1_write_back && !P.age_mode && P.l1_ways == exact[c][0] && P.l2_ways == exact[c][1];
+  return P.mode == MODE_CACHE && !P.packet_mode && !P.l1_write_back && !P.age_mode &&
+         P.l1_ways == exact[c][0] && P.l2_ways == exact[c][1];
 }
-// the plain-loop variant a configuration runs on
+// the plain-loop variant a configuration runs on (the interleaved L2 keeps no
+// directory, so the directory node makes no difference to it)
 int variant_kind(const Params& P) {
-  if (interleaved_cache(P)) return KIND_IL;
+  if (exact_cache(P)) {
+    if (P.policy == POL_INTERLEAVED) return KIND_IL;
+    if (!P.dir_central) return P.policy == POL_LOCAL ? KIND_LOCAL : KIND_MIGRATE;
+  }
   if (!P.packet_mode && !P.l1_write_back && !P.dir_central && !P.age_mode) return KIND_BASE;
   return KIND_GEN;
 }
+// the kind whose profiled build a configuration runs on
+static int prof_kind(int kind) { return kind == KIND_LOCAL || kind == KIND_MIGRATE ? KIND_BASE : kind; }
 
 #define NOC_PICK_RUN(h, d, sp)                                    \
   switch (way_class(P.l1_ways, P.l2_ways)) {                      \
@@ -82,7 +102,7 @@ int variant_kind(const Params& P) {
 
 int run_variant(const Params& P, const RunArgs& A) {
   const int traced = (A.hash_trace || A.busy) ? 1 : 0;
-  const int kind = traced ? KIND_GEN : variant_kind(P);
+  const int kind = traced ? KIND_GEN : A.prof ? prof_kind(variant_kind(P)) : variant_kind(P);
   return (traced << 8) | (kind << 4) | way_class(P.l1_ways, P.l2_ways);
 }
 
@@ -123,7 +143,7 @@ cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
   // the plain loop: the profiled build when asked for, else the narrow build
   // when the CTAs fit it
   if (A.prof) {
-    switch (variant_kind(P)) {
+    switch (prof_kind(variant_kind(P))) {
       case KIND_IL: NOC_PICK_RUN(0, 0, il_prof)
       case KIND_BASE: NOC_PICK_RUN(0, 0, base_prof)
       default: NOC_PICK_RUN(0, 0, gen_prof)
@@ -132,12 +152,16 @@ cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
   if (block_threads_impl(P.W, P.H, A.gx, A.gy) <= NARROW_THREADS) {
     switch (variant_kind(P)) {
       case KIND_IL: NOC_PICK_RUN(0, 0, il_narrow)
+      case KIND_LOCAL: NOC_PICK_RUN(0, 0, local_narrow)
+      case KIND_MIGRATE: NOC_PICK_RUN(0, 0, migrate_narrow)
       case KIND_BASE: NOC_PICK_RUN(0, 0, base_narrow)
       default: NOC_PICK_RUN(0, 0, gen_narrow)
     }
   }
   switch (variant_kind(P)) {
     case KIND_IL: NOC_PICK_RUN(0, 0, il)
+    case KIND_LOCAL: NOC_PICK_RUN(0, 0, local)
+    case KIND_MIGRATE: NOC_PICK_RUN(0, 0, migrate)
     case KIND_BASE: NOC_PICK_RUN(0, 0, base)
     default: NOC_PICK_RUN(0, 0, gen)
   }
@@ -146,6 +170,8 @@ cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
 #define NOC_PICK_KIND(fn, kind, w1, w2, ...)                                    \
   switch (kind) {                                                                \
     case KIND_IL: return fn##_##w1##_##w2##_il(__VA_ARGS__);                     \
+    case KIND_LOCAL: return fn##_##w1##_##w2##_local(__VA_ARGS__);               \
+    case KIND_MIGRATE: return fn##_##w1##_##w2##_migrate(__VA_ARGS__);           \
     case KIND_BASE: return fn##_##w1##_##w2##_base(__VA_ARGS__);                 \
     default: return fn##_##w1##_##w2##_gen(__VA_ARGS__);                        \
   }
@@ -153,6 +179,8 @@ cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
 #define NOC_PICK_KIND_NARROW(fn, kind, w1, w2, ...)                             \
   switch (kind) {                                                                \
     case KIND_IL: return fn##_##w1##_##w2##_il_narrow(__VA_ARGS__);              \
+    case KIND_LOCAL: return fn##_##w1##_##w2##_local_narrow(__VA_ARGS__);        \
+    case KIND_MIGRATE: return fn##_##w1##_##w2##_migrate_narrow(__VA_ARGS__);    \
     case KIND_BASE: return fn##_##w1##_##w2##_base_narrow(__VA_ARGS__);          \
     default: return fn##_##w1##_##w2##_gen_narrow(__VA_ARGS__);                  \
   }
@@ -167,7 +195,7 @@ cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
   }
 
 cudaError_t max_coresident_prof(const Params& P, int threads, int* out) {
-  const int kind = variant_kind(P);
+  const int kind = prof_kind(variant_kind(P));
   switch (way_class(P.l1_ways, P.l2_ways)) {
     case 0: NOC_PICK_KIND_PROF(max_coresident_run_0_0, kind, 4, 8, threads, out)
     case 1: NOC_PICK_KIND_PROF(max_coresident_run_0_0, kind, 4, 16, threads, out)

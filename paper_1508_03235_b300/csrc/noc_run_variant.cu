@@ -2,16 +2,23 @@
 // build compiles this file once for each (per-cycle hash record, drain record,
 // L1 way bound, L2 way bound) combination it ships, and the plain loop twice
 // more per way bound: without the options beyond the paper's workloads
-// (-DNOC_BASE=1), and specialised to the interleaved L2 in cache mode with
-// exactly those way counts (-DNOC_FIXED_POLICY=0 -DNOC_FIXED_MODE=0
-// -DNOC_EXACT_WAYS=1); the plain-loop builds once more each with
-// -DNOC_NARROW=1, for CTAs of at most NARROW_THREADS threads.
+// (-DNOC_BASE=1), and specialised to one L2 policy in cache mode with exactly
+// those way counts (-DNOC_FIXED_POLICY=<p> -DNOC_FIXED_MODE=0
+// -DNOC_EXACT_WAYS=1: p = 0 interleaved, 1 LSPD with local placement, 2 LSPD
+// with migration); the plain-loop builds once more each with -DNOC_NARROW=1,
+// for CTAs of at most NARROW_THREADS threads.
 #include "noc_kernel.cuh"
 
 #if !defined(NOC_HASH) || !defined(NOC_DRAIN) || !defined(NOC_W1) || !defined(NOC_W2)
 #error "compile with -DNOC_HASH= -DNOC_DRAIN= -DNOC_W1= -DNOC_W2="
 #endif
-#if defined(NOC_FIXED_POLICY)
+#if defined(NOC_FIXED_POLICY) && NOC_FIXED_POLICY == 1
+#define NOC_POLV NOC_FIXED_POLICY
+#define NOC_SPEC0 local
+#elif defined(NOC_FIXED_POLICY) && NOC_FIXED_POLICY == 2
+#define NOC_POLV NOC_FIXED_POLICY
+#define NOC_SPEC0 migrate
+#elif defined(NOC_FIXED_POLICY)
 #define NOC_POLV NOC_FIXED_POLICY
 #define NOC_SPEC0 il
 #elif defined(NOC_BASE)

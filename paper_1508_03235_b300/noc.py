@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libnoc.so")
 
 NOC_OK = 0
 THREAD_MAPS = ("perimeter first", "rows", "columns")
-KERNEL_KINDS = ("general", "base", "interleaved")
+KERNEL_KINDS = ("general", "base", "interleaved", "lspd-local", "lspd-migrate")
 ERR_NAMES = {1: "NOC_ERR_ARG", 2: "NOC_ERR_OOM", 3: "NOC_ERR_QUEUE_OVERFLOW", 4: "NOC_ERR_TIMEOUT",
              5: "NOC_ERR_CUDA", 6: "NOC_ERR_PROTOCOL", 7: "NOC_ERR_STATE", 8: "NOC_ERR_RANGE"}
 HIST_BINS = 1025
@@ -487,7 +487,7 @@ class Batch:
         cache = {}
         if tuned and rect is None and strips is None and thread_map is None:
             from . import tune
-            for g in range(5):
+            for g in range(len(tune.GROUP_NAMES)):
                 cache[g] = tune.cached_batch_layout(g)
         for i in range(n):
             lay = cache.get(L.noc_batch_group(h, i)) or (8, False, 0)

@@ -197,7 +197,9 @@ def spread(params: dict, cycles: int = 8000, warm: int = 2000, reps: int = 3, sa
 
 # ------------------------------------------------------------------ batch engine
 BATCH_SIDES = (4, 6, 8, 10, 12, 16)
-GROUP_NAMES = ("interleaved 4x8", "interleaved 4x16", "interleaved 16x16", "base", "general")
+GROUP_NAMES = ("interleaved 4x8", "interleaved 4x16", "interleaved 16x16", "base", "general",
+               "lspd-local 4x8", "lspd-local 4x16", "lspd-local 16x16",
+               "lspd-migrate 4x8", "lspd-migrate 4x16", "lspd-migrate 16x16")
 
 
 def batch_key(group: int) -> str:

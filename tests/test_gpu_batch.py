@@ -33,15 +33,10 @@ def small_points(n=20, cycles=1200, seed=3):
 
 
 def n_variant_groups(pts):
-    """Kernel-variant groups of a batch: interleaved cache-mode instances whose
-    ways are exactly a class's bounds (4/8, 4/16, 16/16) each form a group per
-    class; every other instance shares the general group."""
-    keys = set()
-    for p in pts:
-        cls = 2 if p["l1_ways"] > 4 else (0 if p["l2_ways"] <= 8 else 1)
-        exact = (p["l1_ways"], p["l2_ways"]) == ((4, 8), (4, 16), (16, 16))[cls]
-        keys.add(cls if p["policy"] == 0 and p["mode"] == 0 and exact else 3)
-    return len(keys)
+    """Kernel-variant groups among pts (the library's rule, pinned by
+    tests/test_tune.py): each group runs in its own work-queue launches."""
+    from paper_1508_03235_b300 import noc
+    return len(set(noc.batch_groups(pts)))
 
 
 @pytest.fixture(scope="module")

@@ -18,13 +18,14 @@ def noc():
     return _noc
 
 
-@pytest.mark.parametrize("name,params,tiling,warps", [
-    ("mesh8_one_cta", dict(I.MESH_8["params"]), (1, 1), 2),
+@pytest.mark.parametrize("name,params,tiling,warps,kinds", [
+    ("mesh8_one_cta", dict(I.MESH_8["params"]), (1, 1), 2, ("interleaved", "interleaved")),
+    # an LSPD migration configuration is profiled on the base build
     ("lspd_four_ctas", I.sim_params(16, 12, policy=2, seed=9,
                                     traf=I.traffic(period=3, priv=0.4, shared=0.5, shared_mb=1)),
-     (2, 2), 4 * 2),
+     (2, 2), 4 * 2, ("base", "lspd-migrate")),
 ])
-def test_profile_changes_nothing_and_adds_up(noc, oracle_mod, name, params, tiling, warps):
+def test_profile_changes_nothing_and_adds_up(noc, oracle_mod, name, params, tiling, warps, kinds):
     g = noc.Sim(params, tiling=tiling)
     g.set_phase_profile(True)
     o = oracle_mod.OracleSim(params)
@@ -36,6 +37,7 @@ def test_profile_changes_nothing_and_adds_up(noc, oracle_mod, name, params, tili
     for ph in noc.Sim.PHASES:
         assert prof[ph] > 0, (ph, prof)
     assert g.launch_bound() == 384
+    assert g.variant()["kind"] == kinds[0]
     gs, os_ = g.stats(), o.stats()
     for k, v in os_.items():
         assert gs[k] == v, (k, gs[k], v)
@@ -48,4 +50,5 @@ def test_profile_changes_nothing_and_adds_up(noc, oracle_mod, name, params, tili
     g.step(300)
     o.step(300)
     assert g.phase_profile()["warp_cycles"] == 0
+    assert g.variant()["kind"] == kinds[1]
     assert g.state_hash() == o.state_hash()

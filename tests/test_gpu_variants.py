@@ -2,12 +2,12 @@
 for bit, on configurations that evict all the time.
 
 The library compiles the cycle kernel once per way-bound class, (L1, L2) ways
-(4, 8), (4, 16) and (16, 16), and per specialisation: "interleaved" (the
-interleaved L2 in cache mode with exactly the class's way counts), "base"
-(every policy, no packet / write-back / directory-node / age option) and
-"general" (everything); the traced loop (per-cycle hash record) and the
-draining loop are general builds of each class; the batch kernel comes in the
-same nine builds.  Each case here is built so that its configuration selects
+(4, 8), (4, 16) and (16, 16), and per specialisation: "interleaved",
+"lspd-local" and "lspd-migrate" (one L2 policy in cache mode with exactly the
+class's way counts and no option), "base" (every policy, no packet /
+write-back / directory-node / age option) and "general" (everything); the
+traced loop (per-cycle hash record) and the draining loop are general builds
+of each class; the batch kernel comes in the same fifteen builds.  Each case here is built so that its configuration selects
 one build, asserts through noc_last_variant / noc_batch_variant that this
 build ran, and compares counters, both histograms and the dynamic and full
 state hashes with the oracle.  The caches are tiny (16 lines of L1, 16 of L2
@@ -23,7 +23,7 @@ from paper_1508_03235_b300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 BOUNDS = ((4, 8), (4, 16), (16, 16))
-KINDS = ("interleaved", "base", "general")
+KINDS = ("interleaved", "lspd-local", "lspd-migrate", "base", "general")
 COUNTERS = ("injected", "ejected", "in_flight", "deflections", "lat_sum", "lat_max", "refs",
             "l1_hit", "l1_miss", "l2_hit", "l2_miss", "req_made", "req_rcvd", "reply_sent",
             "reply_rcvd", "dir_search", "mem_req", "mem_write", "mem_wb", "wt_sent", "wt_hit",
@@ -43,8 +43,9 @@ def noc():
 def variant_params(kind, bounds, w=7, h=6, seed=5):
     """A configuration that runs on build (kind, bounds)."""
     opts, policy = {}, 0
-    if kind == "interleaved":
+    if kind in ("interleaved", "lspd-local", "lspd-migrate"):
         l1w, l2w = bounds
+        policy = ("interleaved", "lspd-local", "lspd-migrate").index(kind)
     elif kind == "base":
         l1w, l2w = {(4, 8): (3, 6), (4, 16): (4, 12), (16, 16): (8, 16)}[bounds]
         policy = {(4, 8): 1, (4, 16): 2, (16, 16): 2}[bounds]
@@ -106,7 +107,7 @@ def test_plain_traced_and_draining_builds(noc, oracle_mod, kind, bounds):
 
 @pytest.mark.parametrize("bounds", BOUNDS, ids=lambda b: f"{b[0]}x{b[1]}")
 def test_batch_builds(noc, oracle_mod, bounds):
-    """One batch per way class, holding instances of all three kinds (two
+    """One batch per way class, holding instances of all five kinds (two
     interleaved ones, one spanning 3 x 2 rectangles): each instance runs on
     its kind's batch build of that class and equals its oracle run."""
     pts = [variant_params(k, bounds, seed=20 + j) for j, k in enumerate(KINDS)]
@@ -115,7 +116,7 @@ def test_batch_builds(noc, oracle_mod, bounds):
     b = noc.Batch(pts, cycles, rect=4)
     b.run()
     for i, p in enumerate(pts):
-        kind = KINDS[i] if i < 3 else "interleaved"
+        kind = KINDS[i] if i < len(KINDS) else "interleaved"
         assert b.variant(i) == dict(kind=kind, bounds=bounds), i
         o = oracle_mod.OracleSim(p)
         o.step(cycles)

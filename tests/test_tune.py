@@ -6,16 +6,23 @@ from paper_1508_03235_b300 import inputs as I
 
 
 def test_batch_groups_follow_the_variant_rules():
-    """Interleaved cache-mode instances with a class's exact ways form the
-    class's interleaved group; LSPD without options the base group; any
-    option the general group."""
+    """Cache-mode instances with a class's exact ways and no option form the
+    class's group of their L2 policy (interleaved 0-2, LSPD local placement
+    5-7, LSPD migration 8-10); other instances without options the base
+    group; any option -- the directory node among them, which the
+    interleaved L2 ignores -- the general group."""
     from paper_1508_03235_b300 import noc
     base = dict(I.MESH_8["params"])
-    pts = [dict(base), dict(base, l2_ways=16, l2_sets=256), dict(base, l1_ways=16, l1_sets=32, l2_ways=16),
+    w16 = dict(l2_ways=16, l2_sets=256)
+    w1616 = dict(l1_ways=16, l1_sets=32, l2_ways=16)
+    pts = [dict(base), dict(base, **w16), dict(base, **w1616),
            dict(base, policy=1), dict(base, policy=2), dict(base, l1_ways=3),
            dict(base, packet_mode=1), dict(base, policy=1, age_mode=1), dict(base, l1_write_back=1),
-           dict(base, mode=I.MODE_NETWORK)]
-    assert noc.batch_groups(pts) == [0, 1, 2, 3, 3, 3, 4, 4, 4, 3]
+           dict(base, mode=I.MODE_NETWORK),
+           dict(base, policy=1, **w16), dict(base, policy=1, **w1616), dict(base, policy=2, **w16),
+           dict(base, policy=2, **w1616), dict(base, policy=1, dir_central=1), dict(base, dir_central=1),
+           dict(base, policy=2, l2_ways=12), dict(base, policy=2, mode=I.MODE_NETWORK)]
+    assert noc.batch_groups(pts) == [0, 1, 2, 5, 8, 3, 4, 4, 4, 3, 6, 7, 9, 10, 4, 0, 3, 3]
 
 
 def test_design_point_groups():
@@ -24,7 +31,7 @@ def test_design_point_groups():
     for p in pts:
         p.pop("design")
     g = noc.batch_groups(pts)
-    assert all(x == (0 if p["policy"] == 0 else 3) for x, p in zip(g, pts))
+    assert all(x == {0: 0, 1: 5, 2: 8}[p["policy"]] for x, p in zip(g, pts))
 
 
 def test_stratified_sample_spans_the_sizes():
