@@ -202,11 +202,13 @@ int noc_get_tiling(const noc_sim* sim, int* gx, int* gy);
 
 /* Tiles per thread of the plain loop: 1 keeps each tile's state in its
  * thread's registers for a whole launch (the fast loop; a mesh must then fit
- * one co-resident launch, about 55,700 tiles on a B300); 2 runs two tiles per
- * thread and moves each tile's state through its device records around every
- * cycle (slower per tile, but every mesh of up to 65,535 tiles -- the limit of
- * the 16-bit tile indices a flit carries -- fits a B300); 0 = automatic (1 if
- * the mesh fits that way, else 2, the default).  With two, per-cycle hash
+ * one co-resident launch: at most 148 rectangles of at most 448 tiles on a
+ * B300, which every mesh up to the 65,535 tiles that 16-bit tile indices allow
+ * meets when its shape cuts that way, e.g. 255 x 257 as 4 x 37 rectangles of
+ * 64 x 7); 2 runs two tiles per thread and moves each tile's state through its
+ * device records around every cycle (slower per tile, for the shapes that do
+ * not cut that way); 0 = automatic (1 if the mesh fits that way, else 2, the
+ * default).  With two, per-cycle hash
  * traces and noc_drain are NOC_ERR_ARG (they need the one-tile loop); results
  * never depend on it.  noc_get_tiles_per_thread returns the value in use
  * (0 before the first launch, -1 for a null handle). */
@@ -363,8 +365,10 @@ int64_t noc_kernel_launches(const noc_sim* sim);
 int noc_last_variant(const noc_sim* sim, int* loop, int* kind, int* l1_bound, int* l2_bound);
 /* The launch bound of that build: the most threads a CTA of it may have.
  * The plain loop is built twice, for CTAs of up to 320 threads (more
- * registers per thread, faster) and up to 384; the traced loop is built for
- * 384 and the two-tile loop for 256.  0 before the first launch, -1 for a null
+ * registers per thread, faster) and up to 448 (128 registers a thread: a
+ * CTA of more than 12 warps puts four warps on some of an SM's four register
+ * files of 16,384); the traced loop is built for 448, the per-phase profiled
+ * loop for 384 and the two-tile loop for 256.  0 before the first launch, -1 for a null
  * handle. */
 int noc_last_launch_bound(const noc_sim* sim);
 
@@ -372,7 +376,8 @@ int noc_last_launch_bound(const noc_sim* sim);
  * enable != 0 (the first call takes a 48-byte device buffer), later plain
  * launches through this handle run a build of the loop that reads the SM
  * clock at each phase boundary of every warp and cycle; that build keeps its
- * own registers (the 384-thread bound), so it runs somewhat slower than the
+ * own registers (the 384-thread bound; a tiling with larger CTAs is
+ * NOC_ERR_ARG while the profile is on), so it runs somewhat slower than the
  * production build.  noc_phase_profile waits for the handle's stream, writes
  * six sums over warps and cycles -- SM clocks spent waiting for the
  * neighbours' outputs, routing, publishing, in Phase 3, in Phase 1, and the

@@ -7,11 +7,13 @@ configuration: device memory (the library's own arena layout, noc_create +
 noc_required_bytes, no device needed), the 65,535 tiles that 16-bit tile
 indices in a flit can address -- the binding one -- and how many tiles the
 fast loop holds: with one tile per thread a tile's state lives in its
-thread's registers, so the register file of 148 SMs bounds the mesh (about
-236 x 236); larger meshes run with two tiles per thread.  With `--run` the
-largest square mesh of the fast loop is found on the GPU (a search over
-sides), and it and the largest mesh the tile indices allow (255 x 257) are
-simulated for a few cycles.
+thread's registers, so the register file of 148 SMs bounds the mesh; with
+CTAs of up to 448 threads at 128 registers that is 148 x 448 = 66,304 tiles,
+past the tile-index limit, so every mesh the indices allow whose shape cuts
+into at most 148 such rectangles runs that way (the others with two tiles
+per thread).  With `--run` the largest square mesh of the fast loop is found
+on the GPU (a search over sides), and it and the largest mesh the tile
+indices allow (255 x 257) are simulated for a few cycles.
 
     python -m paper_1508_03235_b300.capacity [--mem-gb G] [--run --cycles C]
 

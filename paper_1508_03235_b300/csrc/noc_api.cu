@@ -310,7 +310,7 @@ int ensure_memory(noc_sim* s) {
 int launch_threads(const noc_sim* s, int tpt, int gx, int gy) {
   return tpt == 2 ? multi_threads(s->P.W, s->P.H, gx, gy) : block_threads(s->P.W, s->P.H, gx, gy);
 }
-int max_launch_threads(int tpt) { return tpt == 2 ? MULTI_MAX_THREADS : 384; }
+int max_launch_threads(int tpt) { return tpt == 2 ? MULTI_MAX_THREADS : RUN_MAX_THREADS; }
 cudaError_t coresident(const noc_sim* s, int tpt, int threads, int* cap) {
   return tpt == 2 ? max_coresident_multi(s->P, threads, cap) : max_coresident_ctas(s->P, threads, cap);
 }
@@ -320,8 +320,8 @@ cudaError_t coresident(const noc_sim* s, int tpt, int threads, int* cap) {
 // still fit co-resident; NOC_ERR_ARG (without a message) if none does
 int choose_tiling_tpt(noc_sim* s, int tpt, int* gx_out, int* gy_out) {
   const int W = s->P.W, H = s->P.H;
-  int cap_of[384 / 32 + 1];
-  for (int k = 0; k <= 384 / 32; ++k) cap_of[k] = -1;
+  int cap_of[RUN_MAX_THREADS / 32 + 1];
+  for (int k = 0; k <= RUN_MAX_THREADS / 32; ++k) cap_of[k] = -1;
   int best_gx = 0, best_gy = 0;
   long best_g = 0, best_a = 0, best_p = 0;
   bool best_small = false;
@@ -471,6 +471,9 @@ int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
     A.prof = (s->prof_on && !A.hash_trace && !A.busy && tpt == 1) ? s->d_prof : nullptr;
     if (A.prof) {
       // the profiled build keeps its own register count: check it fits too
+      if (threads > RUN_PROF_THREADS)
+        return fail(NOC_ERR_ARG, "the profiled loop takes CTAs of at most %d threads (tiling %dx%d has %d)",
+                    RUN_PROF_THREADS, s->run_gx, s->run_gy, threads);
       int pcap = 0;
       CU(max_coresident_prof(s->P, threads, &pcap), "occupancy");
       if (s->run_gx * s->run_gy > pcap)

@@ -39,7 +39,7 @@ namespace noc {
 // of the instance's cycles.  Items are popped in order, so every instance
 // before the current one is already running to completion: the waits end.
 template <int W1, int W2, int POLV>
-__global__ void __launch_bounds__(MAX_THREADS, 1) batch_kernel(const __grid_constant__ BatchArgs B) {
+__global__ void __launch_bounds__(BATCH_MAX_THREADS, 1) batch_kernel(const __grid_constant__ BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Params sP;
   __shared__ RunArgs sA;
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(MAX_THREADS, 1) batch_kernel(const __grid_cons
 cudaError_t NOC_NAME(launch_batch, NOC_W1, NOC_W2, NOC_SPEC)(const BatchArgs& B, int grid, int threads,
                                                             cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(NOC_BATCH_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)run_smem_bytes_impl(MAX_THREADS, false));
+                                       (int)run_smem_bytes_impl(BATCH_MAX_THREADS, false));
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&B};
   return cudaLaunchCooperativeKernel((const void*)NOC_BATCH_KERNEL, dim3(grid), dim3(threads), args,
@@ -88,7 +88,7 @@ cudaError_t NOC_NAME(launch_batch, NOC_W1, NOC_W2, NOC_SPEC)(const BatchArgs& B,
 
 cudaError_t NOC_NAME(max_coresident_batch, NOC_W1, NOC_W2, NOC_SPEC)(int threads, int* out) {
   cudaError_t e = cudaFuncSetAttribute(NOC_BATCH_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)run_smem_bytes_impl(MAX_THREADS, false));
+                                       (int)run_smem_bytes_impl(BATCH_MAX_THREADS, false));
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;

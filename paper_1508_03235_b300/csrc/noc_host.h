@@ -19,6 +19,11 @@ int configure(int mesh_w, int mesh_h, const noc_cache_cfg* c, int l2_policy, con
 // kind << 4 | way class, with loop 1 for the traced / draining loop, kind a
 // KIND_* value and way class 0 = (4, 8), 1 = (4, 16), 2 = (16, 16) bounds
 int run_variant(const Params& P, const RunArgs& A);
+// the most threads a CTA of the one-tile loop may have (MAX_THREADS of the
+// device code; one CTA per SM at the wide builds' register cap)
+constexpr int RUN_MAX_THREADS = 448;
+// and of its per-phase profiled build (PROF_THREADS of the device code)
+constexpr int RUN_PROF_THREADS = 384;
 // the launch bound (most threads per CTA) of the build launch_run picks
 int run_launch_bound(const Params& P, const RunArgs& A);
 // co-resident CTAs of the plain loop's profiled build at `threads` per CTA

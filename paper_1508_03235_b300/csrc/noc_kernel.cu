@@ -5,6 +5,9 @@
 
 namespace noc {
 
+static_assert(RUN_MAX_THREADS == MAX_THREADS && RUN_PROF_THREADS == PROF_THREADS,
+              "host and device thread limits agree");
+
 // ---------------------------------------------------------------- dispatch
 // Kernel variants shipped: the per-cycle hash record or the drain's busy
 // record on (the traced / draining loop) or neither (the plain loop), and the
@@ -107,8 +110,9 @@ int run_variant(const Params& P, const RunArgs& A) {
 }
 
 int run_launch_bound(const Params& P, const RunArgs& A) {
-  const bool plain = !A.hash_trace && !A.busy && !A.prof;
-  return plain && block_threads_impl(P.W, P.H, A.gx, A.gy) <= NARROW_THREADS ? NARROW_THREADS : MAX_THREADS;
+  if (A.hash_trace || A.busy) return MAX_THREADS;
+  if (A.prof) return PROF_THREADS;
+  return block_threads_impl(P.W, P.H, A.gx, A.gy) <= NARROW_THREADS ? NARROW_THREADS : MAX_THREADS;
 }
 
 int multi_variant(const Params& P) { return (2 << 8) | (KIND_GEN << 4) | way_class(P.l1_ways, P.l2_ways); }

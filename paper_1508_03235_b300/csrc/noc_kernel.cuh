@@ -150,12 +150,21 @@ static __device__ unsigned long long block_sum(unsigned long long v, unsigned lo
 }
 
 // ---------------------------------------------------------------- cycle kernel
-constexpr int MAX_THREADS = 384;
-// The plain loop is also built for CTAs of at most NARROW_THREADS threads
-// (the 208x208 workload's 104x3 strips are 320): a smaller launch bound lets
-// the compiler keep more values in registers (166 instead of 154), worth 2 %
-// per simulated cycle.  Launches of more threads use the MAX_THREADS build.
+// The cycle kernel runs CTAs of up to MAX_THREADS threads, one CTA per SM.
+// Each of an SM's four sub-partitions holds 16,384 registers and a CTA of
+// more than 12 warps puts four warps on some of them, so the wide builds
+// (launch bound 448) keep 128 registers a thread; then every mesh of up to
+// 148 x 448 tiles -- beyond the 65,535 that 16-bit tile indices allow -- fits
+// one co-resident launch with one tile per thread.  The plain loop is also
+// built for CTAs of at most NARROW_THREADS threads (the 208x208 workload's
+// 104x3 strips are 320), where the compiler keeps 166 registers, and its
+// per-phase profiled build for CTAs of at most PROF_THREADS (161 registers,
+// close to the production build's timing).  The batch kernel's CTAs hold at
+// most BATCH_MAX_THREADS threads (rectangles of at most 19 x 19 tiles).
+constexpr int MAX_THREADS = 448;
 constexpr int NARROW_THREADS = 320;
+constexpr int PROF_THREADS = 384;
+constexpr int BATCH_MAX_THREADS = 384;
 
 // The plain cycle loop polls the tagged slots of the links entering its
 // rectangle either with one poll in flight (plain loads; NOC_POLL_STAGE 0, the

@@ -1,16 +1,18 @@
 // noc_multi.cuh -- the plain cycle loop with K tiles per thread, for meshes
-// larger than one co-resident launch of one thread per tile.
+// that do not fit one co-resident launch of one thread per tile.
 //
 // The one-tile loop keeps each tile's core record, queue heads and counters in
 // its thread's registers for a whole launch, so a mesh must fit the GPU's
-// co-resident threads (148 SMs x 384 at that register count: 55,696 tiles in a
-// square).  Here a thread runs tiles i and i + blockDim.x (K = 2) of its CTA
-// rectangle, so a rectangle holds up to 2 x 256 tiles.  A tile's state lives
-// in a 66-word record in shared memory for the whole launch (read from the
-// arena at the launch's start, written back at its end, as the one-tile loop
-// does with registers) and is moved into registers around each cycle of its
-// simulated work.  That lets a B300 hold every mesh of up to 65,535 tiles, the
-// limit of the 16-bit tile indices a flit carries.
+// co-resident threads: 148 SMs x 448 at the wide builds' 128 registers, which
+// covers every mesh the 16-bit tile indices allow whose shape cuts into at
+// most 148 rectangles of at most 448 tiles.  Here a thread runs tiles i and
+// i + blockDim.x (K = 2) of its CTA rectangle, so a rectangle holds up to
+// 2 x 256 tiles, for the shapes that do not cut that way.  A tile's state
+// lives in a 66-word record in shared memory for the whole launch (read from
+// the arena at the launch's start, written back at its end, as the one-tile
+// loop does with registers) and is moved into registers around each cycle of
+// its simulated work.  With it a B300 holds every mesh of up to 65,535 tiles,
+// the limit of the 16-bit tile indices a flit carries.
 //
 // Per warp and cycle t: wait until every input of every one of its tiles
 // carries cycle t - 1 (shared-memory flags of the warps holding in-rectangle

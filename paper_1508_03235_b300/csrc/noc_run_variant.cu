@@ -36,7 +36,7 @@
 #define NOC_SPEC NOC_CAT2(NOC_SPEC0, narrow)
 #elif NOC_PHASE_PROFILE
 // -DNOC_PHASE_PROFILE=1: the plain loop with per-phase clock reads
-#define NOC_LB MAX_THREADS
+#define NOC_LB PROF_THREADS
 #define NOC_SPEC NOC_CAT2(NOC_SPEC0, prof)
 #else
 #define NOC_LB MAX_THREADS

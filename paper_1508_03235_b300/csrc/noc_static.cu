@@ -133,7 +133,7 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
   for (int side = 16; side >= 1 && !gx; side /= 2) {
     int tx = (mesh_w + side - 1) / side, ty = (mesh_h + side - 1) / side;
     int threads = block_threads(mesh_w, mesh_h, tx, ty), cap = 0;
-    if (threads > 384 || (size_t)tx * ty * FLAG_SLOTS > n_flags) continue;
+    if (threads > RUN_MAX_THREADS || (size_t)tx * ty * FLAG_SLOTS > n_flags) continue;
     ce = max_coresident_ctas(P, threads, &cap);
     if (ce != cudaSuccess) return fail(NOC_ERR_CUDA, "occupancy: %s", cudaGetErrorString(ce));
     if (tx * ty <= cap) {

@@ -285,7 +285,7 @@ class Sim:
         return out
 
     def launch_bound(self) -> int:
-        """Most threads per CTA of the last launch's build (320 or 384 for
+        """Most threads per CTA of the last launch's build (320 or 448 for
         the plain loop)."""
         return lib().noc_last_launch_bound(self._h)
 

@@ -25,7 +25,7 @@ import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "tuning_cache.json")
-MAX_THREADS = 384
+MAX_THREADS = 448
 
 
 def key(params: dict) -> str:
@@ -34,7 +34,7 @@ def key(params: dict) -> str:
             f"/l1_{p['l1_sets']}x{p['l1_ways']}/l2_{p['l2_sets']}x{p['l2_ways']}")
 
 
-def candidates(W: int, H: int, targets=(384, 320, 256, 192, 160, 128, 96, 64, 32)):
+def candidates(W: int, H: int, targets=(448, 384, 320, 256, 192, 160, 128, 96, 64, 32)):
     """For each rectangle-size target, the grid with the fewest CTAs whose
     rectangles hold at most that many tiles, preferring aspect ratios <= 2.5."""
     out = []

@@ -134,9 +134,10 @@ def test_batch_builds(noc, oracle_mod, bounds):
 @pytest.mark.parametrize("bounds", BOUNDS, ids=lambda b: f"{b[0]}x{b[1]}")
 @pytest.mark.parametrize("kind", KINDS)
 def test_wide_plain_builds(noc, oracle_mod, kind, bounds):
-    """The plain loop's build for CTAs of more than 320 threads: a 19 x 18
-    mesh in one CTA (342 tiles), two launches, against the oracle."""
-    p = variant_params(kind, bounds, w=19, h=18, seed=7)
+    """The plain loop's build for CTAs of more than 320 threads (up to 448,
+    at the wide builds' register cap): a 21 x 21 mesh in one CTA (441 tiles,
+    14 warps), two launches, against the oracle."""
+    p = variant_params(kind, bounds, w=21, h=21, seed=7)
     if p.get("dir_central"):
         p["dir_tile"] = 200
     g = noc.Sim(p, tiling=(1, 1))
@@ -145,5 +146,5 @@ def test_wide_plain_builds(noc, oracle_mod, kind, bounds):
         g.step(n)
         o.step(n)
         assert g.variant() == dict(loop="plain", kind=kind, bounds=bounds)
-        assert g.launch_bound() == 384
+        assert g.launch_bound() == 448
     assert_same(g, o)
