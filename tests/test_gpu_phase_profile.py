@@ -52,3 +52,17 @@ def test_profile_changes_nothing_and_adds_up(noc, oracle_mod, name, params, tili
     assert g.phase_profile()["warp_cycles"] == 0
     assert g.variant()["kind"] == kinds[1]
     assert g.state_hash() == o.state_hash()
+
+
+def test_profile_refuses_ctas_beyond_its_build(noc):
+    """The profiled build takes CTAs of at most 384 threads: a 21 x 21 mesh in
+    one CTA (441 threads, the wide build's range) is NOC_ERR_ARG while the
+    profile is on, and runs once it is off."""
+    g = noc.Sim(I.sim_params(21, 21, seed=3), tiling=(1, 1), tiles_per_thread=1)
+    g.set_phase_profile(True)
+    with pytest.raises(noc.NocError) as e:
+        g.step(10)
+    assert e.value.code == 1 and "profiled loop" in str(e.value)
+    g.set_phase_profile(False)
+    g.step(10)
+    assert g.launch_bound() == 448 and g.stats()["cycle"] == 10
