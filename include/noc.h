@@ -364,11 +364,12 @@ int64_t noc_kernel_launches(const noc_sim* sim);
  * Any output pointer may be NULL.  NOC_ERR_STATE before the first launch. */
 int noc_last_variant(const noc_sim* sim, int* loop, int* kind, int* l1_bound, int* l2_bound);
 /* The launch bound of that build: the most threads a CTA of it may have.
- * The plain loop is built twice, for CTAs of up to 320 threads (more
- * registers per thread, faster) and up to 448 (128 registers a thread: a
- * CTA of more than 12 warps puts four warps on some of an SM's four register
- * files of 16,384); the traced loop is built for 448, the per-phase profiled
- * loop for 384 and the two-tile loop for 256.  0 before the first launch, -1 for a null
+ * The plain loop is built three times, for CTAs of up to 320, 384 and 448
+ * threads; a launch takes the smallest that fits, since more registers per
+ * thread run faster (the 448 build keeps 128: a CTA of more than 12 warps puts
+ * four warps on some of an SM's four register files of 16,384).  The traced
+ * loop is built for 448, the per-phase profiled loop for 384 and the two-tile
+ * loop for 256.  0 before the first launch, -1 for a null
  * handle. */
 int noc_last_launch_bound(const noc_sim* sim);
 

@@ -26,6 +26,11 @@ UNITS = ([("noc_run_variant.cu", {"NOC_HASH": h, "NOC_DRAIN": d, "NOC_W1": w1, "
             for (w1, w2) in WAY_BOUNDS
             for spec in [{}, {"NOC_BASE": 1}]
             + [{"NOC_FIXED_POLICY": pol, "NOC_FIXED_MODE": 0, "NOC_EXACT_WAYS": 1} for pol in POLICIES]]
+         # and for CTAs of up to 448 threads (128 registers)
+         + [("noc_run_variant.cu", dict(spec, NOC_HASH=0, NOC_DRAIN=0, NOC_W1=w1, NOC_W2=w2, NOC_XL=1))
+            for (w1, w2) in WAY_BOUNDS
+            for spec in [{}, {"NOC_BASE": 1}]
+            + [{"NOC_FIXED_POLICY": pol, "NOC_FIXED_MODE": 0, "NOC_EXACT_WAYS": 1} for pol in POLICIES]]
          # and with per-phase clock reads (noc_set_phase_profile)
          + [("noc_run_variant.cu", dict(spec, NOC_HASH=0, NOC_DRAIN=0, NOC_W1=w1, NOC_W2=w2,
                                         NOC_PHASE_PROFILE=1))

@@ -36,6 +36,16 @@ static_assert(RUN_MAX_THREADS == MAX_THREADS && RUN_PROF_THREADS == PROF_THREADS
   NOC_DECL_RUN(0, 0, w1, w2, local)                                             \
   NOC_DECL_RUN(0, 0, w1, w2, migrate)                                           \
   NOC_DECL_RUN(0, 0, w1, w2, local_narrow)                                      \
+  NOC_DECL_RUN(0, 0, w1, w2, gen_xl)                                            \
+  NOC_DECL_RUN(0, 0, w1, w2, base_xl)                                           \
+  NOC_DECL_RUN(0, 0, w1, w2, il_xl)                                             \
+  NOC_DECL_RUN(0, 0, w1, w2, local_xl)                                          \
+  NOC_DECL_RUN(0, 0, w1, w2, migrate_xl)                                        \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_gen_xl(int threads, int* out);     \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_base_xl(int threads, int* out);    \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_il_xl(int threads, int* out);      \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_local_xl(int threads, int* out);   \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_migrate_xl(int threads, int* out); \
   NOC_DECL_RUN(0, 0, w1, w2, migrate_narrow)                                    \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_local(int threads, int* out);        \
   cudaError_t max_coresident_run_0_0_##w1##_##w2##_migrate(int threads, int* out);      \
@@ -109,10 +119,15 @@ int run_variant(const Params& P, const RunArgs& A) {
   return (traced << 8) | (kind << 4) | way_class(P.l1_ways, P.l2_ways);
 }
 
+// the plain loop's launch bound for CTAs of `threads`: the smallest that fits
+static int plain_bound(int threads) {
+  return threads <= NARROW_THREADS ? NARROW_THREADS : threads <= WIDE_THREADS ? WIDE_THREADS : MAX_THREADS;
+}
+
 int run_launch_bound(const Params& P, const RunArgs& A) {
   if (A.hash_trace || A.busy) return MAX_THREADS;
   if (A.prof) return PROF_THREADS;
-  return block_threads_impl(P.W, P.H, A.gx, A.gy) <= NARROW_THREADS ? NARROW_THREADS : MAX_THREADS;
+  return plain_bound(block_threads_impl(P.W, P.H, A.gx, A.gy));
 }
 
 int multi_variant(const Params& P) { return (2 << 8) | (KIND_GEN << 4) | way_class(P.l1_ways, P.l2_ways); }
@@ -153,7 +168,17 @@ cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
       default: NOC_PICK_RUN(0, 0, gen_prof)
     }
   }
-  if (block_threads_impl(P.W, P.H, A.gx, A.gy) <= NARROW_THREADS) {
+  const int bound = plain_bound(block_threads_impl(P.W, P.H, A.gx, A.gy));
+  if (bound == MAX_THREADS) {
+    switch (variant_kind(P)) {
+      case KIND_IL: NOC_PICK_RUN(0, 0, il_xl)
+      case KIND_LOCAL: NOC_PICK_RUN(0, 0, local_xl)
+      case KIND_MIGRATE: NOC_PICK_RUN(0, 0, migrate_xl)
+      case KIND_BASE: NOC_PICK_RUN(0, 0, base_xl)
+      default: NOC_PICK_RUN(0, 0, gen_xl)
+    }
+  }
+  if (bound == NARROW_THREADS) {
     switch (variant_kind(P)) {
       case KIND_IL: NOC_PICK_RUN(0, 0, il_narrow)
       case KIND_LOCAL: NOC_PICK_RUN(0, 0, local_narrow)
@@ -189,6 +214,15 @@ cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
     default: return fn##_##w1##_##w2##_gen_narrow(__VA_ARGS__);                  \
   }
 
+#define NOC_PICK_KIND_XL(fn, kind, w1, w2, ...)                                 \
+  switch (kind) {                                                                \
+    case KIND_IL: return fn##_##w1##_##w2##_il_xl(__VA_ARGS__);                  \
+    case KIND_LOCAL: return fn##_##w1##_##w2##_local_xl(__VA_ARGS__);            \
+    case KIND_MIGRATE: return fn##_##w1##_##w2##_migrate_xl(__VA_ARGS__);        \
+    case KIND_BASE: return fn##_##w1##_##w2##_base_xl(__VA_ARGS__);              \
+    default: return fn##_##w1##_##w2##_gen_xl(__VA_ARGS__);                      \
+  }
+
 // co-resident CTAs of the plain loop at `threads` per CTA, for the build a
 // launch of that size uses
 #define NOC_PICK_KIND_PROF(fn, kind, w1, w2, ...)                               \
@@ -209,6 +243,13 @@ cudaError_t max_coresident_prof(const Params& P, int threads, int* out) {
 
 cudaError_t max_coresident_ctas(const Params& P, int threads, int* out) {
   const int kind = variant_kind(P);
+  if (plain_bound(threads) == MAX_THREADS) {
+    switch (way_class(P.l1_ways, P.l2_ways)) {
+      case 0: NOC_PICK_KIND_XL(max_coresident_run_0_0, kind, 4, 8, threads, out)
+      case 1: NOC_PICK_KIND_XL(max_coresident_run_0_0, kind, 4, 16, threads, out)
+      default: NOC_PICK_KIND_XL(max_coresident_run_0_0, kind, 16, 16, threads, out)
+    }
+  }
   if (threads <= NARROW_THREADS) {
     switch (way_class(P.l1_ways, P.l2_ways)) {
       case 0: NOC_PICK_KIND_NARROW(max_coresident_run_0_0, kind, 4, 8, threads, out)

@@ -151,17 +151,21 @@ static __device__ unsigned long long block_sum(unsigned long long v, unsigned lo
 
 // ---------------------------------------------------------------- cycle kernel
 // The cycle kernel runs CTAs of up to MAX_THREADS threads, one CTA per SM.
+// The plain loop is built for three launch bounds: NARROW_THREADS (320; the
+// 208x208 workload's 104x3 strips), where the compiler keeps 166 registers a
+// thread; WIDE_THREADS (384, 154-166 registers); and MAX_THREADS (448, "xl").
 // Each of an SM's four sub-partitions holds 16,384 registers and a CTA of
-// more than 12 warps puts four warps on some of them, so the wide builds
-// (launch bound 448) keep 128 registers a thread; then every mesh of up to
+// more than 12 warps puts four warps on some of them, so the xl builds keep
+// 128 registers a thread (and spill a little): with them every mesh of up to
 // 148 x 448 tiles -- beyond the 65,535 that 16-bit tile indices allow -- fits
-// one co-resident launch with one tile per thread.  The plain loop is also
-// built for CTAs of at most NARROW_THREADS threads (the 208x208 workload's
-// 104x3 strips are 320), where the compiler keeps 166 registers, and its
-// per-phase profiled build for CTAs of at most PROF_THREADS (161 registers,
-// close to the production build's timing).  The batch kernel's CTAs hold at
-// most BATCH_MAX_THREADS threads (rectangles of at most 19 x 19 tiles).
+// one co-resident launch with one tile per thread.  A launch takes the
+// smallest bound its CTAs fit, since more registers run faster (about 10 %
+// between the 384 and 448 builds).  The traced and draining loops are built
+// for MAX_THREADS, the per-phase profiled plain loop for PROF_THREADS (161
+// registers, close to the production builds' timing).  The batch kernel's
+// CTAs hold at most BATCH_MAX_THREADS threads (rectangles of at most 19 x 19).
 constexpr int MAX_THREADS = 448;
+constexpr int WIDE_THREADS = 384;
 constexpr int NARROW_THREADS = 320;
 constexpr int PROF_THREADS = 384;
 constexpr int BATCH_MAX_THREADS = 384;

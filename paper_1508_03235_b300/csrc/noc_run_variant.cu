@@ -6,7 +6,8 @@
 // those way counts (-DNOC_FIXED_POLICY=<p> -DNOC_FIXED_MODE=0
 // -DNOC_EXACT_WAYS=1: p = 0 interleaved, 1 LSPD with local placement, 2 LSPD
 // with migration); the plain-loop builds once more each with -DNOC_NARROW=1,
-// for CTAs of at most NARROW_THREADS threads.
+// for CTAs of at most NARROW_THREADS threads, and with -DNOC_XL=1, for CTAs of
+// more than WIDE_THREADS.
 #include "noc_kernel.cuh"
 
 #if !defined(NOC_HASH) || !defined(NOC_DRAIN) || !defined(NOC_W1) || !defined(NOC_W2)
@@ -38,8 +39,16 @@
 // -DNOC_PHASE_PROFILE=1: the plain loop with per-phase clock reads
 #define NOC_LB PROF_THREADS
 #define NOC_SPEC NOC_CAT2(NOC_SPEC0, prof)
-#else
+#elif defined(NOC_XL) && NOC_XL
+// -DNOC_XL=1: the plain loop for CTAs of up to MAX_THREADS threads
 #define NOC_LB MAX_THREADS
+#define NOC_SPEC NOC_CAT2(NOC_SPEC0, xl)
+#elif NOC_HASH || NOC_DRAIN
+// the traced and draining loops take every CTA size the plain loop does
+#define NOC_LB MAX_THREADS
+#define NOC_SPEC NOC_SPEC0
+#else
+#define NOC_LB WIDE_THREADS
 #define NOC_SPEC NOC_SPEC0
 #endif
 

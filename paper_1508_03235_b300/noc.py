@@ -285,8 +285,8 @@ class Sim:
         return out
 
     def launch_bound(self) -> int:
-        """Most threads per CTA of the last launch's build (320 or 448 for
-        the plain loop)."""
+        """Most threads per CTA of the last launch's build (320, 384 or 448
+        for the plain loop)."""
         return lib().noc_last_launch_bound(self._h)
 
     def kernel_time(self, enable: bool = True):

@@ -131,13 +131,16 @@ def test_batch_builds(noc, oracle_mod, bounds):
     b.close()
 
 
+@pytest.mark.parametrize("mesh,launch_bound", [((19, 18), 384), ((21, 21), 448)],
+                         ids=("384-thread build", "448-thread build"))
 @pytest.mark.parametrize("bounds", BOUNDS, ids=lambda b: f"{b[0]}x{b[1]}")
 @pytest.mark.parametrize("kind", KINDS)
-def test_wide_plain_builds(noc, oracle_mod, kind, bounds):
-    """The plain loop's build for CTAs of more than 320 threads (up to 448,
-    at the wide builds' register cap): a 21 x 21 mesh in one CTA (441 tiles,
-    14 warps), two launches, against the oracle."""
-    p = variant_params(kind, bounds, w=21, h=21, seed=7)
+def test_wide_plain_builds(noc, oracle_mod, kind, bounds, mesh, launch_bound):
+    """The plain loop's builds for CTAs of more than 320 threads: a 19 x 18
+    mesh in one CTA (342 tiles) runs on the build for up to 384 threads, a
+    21 x 21 mesh (441 tiles, 14 warps) on the one for up to 448 (128
+    registers a thread); two launches each, against the oracle."""
+    p = variant_params(kind, bounds, w=mesh[0], h=mesh[1], seed=7)
     if p.get("dir_central"):
         p["dir_tile"] = 200
     g = noc.Sim(p, tiling=(1, 1))
@@ -146,5 +149,5 @@ def test_wide_plain_builds(noc, oracle_mod, kind, bounds):
         g.step(n)
         o.step(n)
         assert g.variant() == dict(loop="plain", kind=kind, bounds=bounds)
-        assert g.launch_bound() == 448
+        assert g.launch_bound() == launch_bound
     assert_same(g, o)
