@@ -302,7 +302,9 @@ static int grid_for(size_t n, int threads) {
 // cycles [t0, t0 + n), at most refcap, and no more than twice what the core
 // took from its previous window plus 32 (a core that runs behind schedule
 // takes far fewer than the schedule allows; past the window the cycle kernel
-// draws in place, so the window's size never changes a result).  Lanes draw
+// draws in place, so the window's size never changes a result).  A window
+// that still holds twice what the core took since it was drawn, plus 8, is
+// kept as it is, so such cores redraw only every few launches.  Lanes draw
 // consecutive references, so the window's stores are coalesced.
 __global__ void gen_refs_kernel(const Params P, uint32_t t0, uint32_t n) {
   const size_t N = (size_t)P.N;
@@ -317,6 +319,9 @@ __global__ void gen_refs_kernel(const Params P, uint32_t t0, uint32_t n) {
       const uint32_t prev_cnt = P.refcnt[c], prev_k0 = P.refk0[c];
       if (prev_cnt > 0 && k0 >= prev_k0) {
         const unsigned long long used = k0 - prev_k0;
+        // the window drawn earlier still holds twice what the core took
+        // since then, and a margin: keep it (warp-uniform)
+        if ((unsigned long long)prev_k0 + prev_cnt >= k0 + 2 * used + 8) continue;
         cnt = (uint32_t)min((unsigned long long)cnt, 2 * used + 32);
       }
     }
