@@ -580,6 +580,14 @@ def surrogate_section(reps=20, replays=20, accuracy=True):
            "us_per_batch": sec * 1e6, "layered_us_per_batch": sec_layered * 1e6,
            "timing": "CUDA graph replay (device time)",
            "kernel": "fused tcgen05 network (mlp_infer)", "network": list(S.DIMS)}
+    # a pool screened four batches at a time: one CTA per 128 design points,
+    # so 128 SMs work instead of 32
+    pool = S.MLP(seed=0, max_batch=16384)
+    xp = torch.rand(16384, S.DIMS[0], device="cuda").to(torch.bfloat16)
+    yp = torch.empty(16384, S.DIMS[-1], device="cuda")
+    pool.infer(xp, out=yp)
+    sec_pool = rate(lambda: pool.infer(xp, out=yp))
+    out["pool_batch_16384"] = {"design_points_per_s": 16384 / sec_pool, "us_per_batch": sec_pool * 1e6}
     if accuracy:
         # held-out accuracy against the exact simulator: 2,000 training and
         # 500 held-out design points of the batch workload, 20,000 cycles each
