@@ -32,6 +32,28 @@ def test_every_declared_symbol_is_exported(libnoc):
     assert not missing, missing
 
 
+def test_every_kernel_build_the_dispatcher_names_is_linked(libnoc):
+    """The library defines a launcher for every build the dispatcher picks --
+    each way class x kind x launch bound of the plain loop, the profiled
+    builds, the batch kernels -- and leaves no internal symbol undefined."""
+    import shutil
+    import subprocess
+    from paper_1508_03235_b300 import build
+    if shutil.which("nm") is None:
+        pytest.skip("nm not available")
+    out = subprocess.run(["nm", "-D", "-C", build.LIB], capture_output=True, text=True, check=True).stdout
+    assert not [l for l in out.splitlines() if " U " in l and "noc::" in l]
+    defined = {m.group(1) for m in re.finditer(r" T (noc::\w+)\(", out)}
+    classes = ("4_8", "4_16", "16_16")
+    kinds = ("gen", "base", "il", "local", "migrate")
+    want = {f"noc::launch_run_0_0_{c}_{k}{s}" for c in classes for k in kinds for s in ("", "_narrow", "_xl")}
+    want |= {f"noc::launch_run_0_0_{c}_{k}_prof" for c in classes for k in ("gen", "base", "il")}
+    want |= {f"noc::launch_run_{h}_{c}_gen" for c in classes for h in ("1_0", "0_1")}
+    want |= {f"noc::launch_batch_{c}_{k}" for c in classes for k in kinds}
+    want |= {f"noc::launch_multi_{c}" for c in classes}
+    assert not sorted(want - defined), sorted(want - defined)[:10]
+
+
 def test_struct_layouts_match_header(libnoc):
     from paper_1508_03235_b300 import noc
     assert C.sizeof(noc.CacheCfg) == 18 * 4
