@@ -42,6 +42,8 @@ extern "C" {
 #define NOC_ERR_PROTOCOL 6       /* a reply arrived that matches no request      */
 #define NOC_ERR_STATE 7          /* call not valid in the handle's current state */
 #define NOC_ERR_RANGE 8          /* age_mode 1: a flit deflected with age 4095   */
+#define NOC_ERR_OWNER 9          /* checked build: a directory entry touched away
+                                    from its line's directory tile (noc_set_checks) */
 
 /* L2 placement (Sec. 3): interleaved homes; LSPD with local placement and a
  * home-tile directory (Sec. 3.2, Sec. 6.2.2); LSPD plus migration and
@@ -372,6 +374,21 @@ int noc_last_variant(const noc_sim* sim, int* loop, int* kind, int* l1_bound, in
  * loop for 256.  0 before the first launch, -1 for a null
  * handle. */
 int noc_last_launch_bound(const noc_sim* sim);
+
+/* Checked build of the plain loop (one tile per thread).  No counterpart in
+ * the paper: a single-writer check.  Every per-tile structure is indexed by
+ * the tile's own id; the LSPD directory, indexed by the line a message
+ * carries, is the one structure a second writer could reach, and the model
+ * lets only a line's directory tile (its home, or the directory node) touch
+ * its entry (Sec. 3.2, 3.3).  With enable != 0, later noc_step calls run the
+ * general plain loop built with that check in the handlers of the messages
+ * that touch the directory (DA, DINV, DIRUPD): a message that reaches another
+ * tile, or carries a line outside the address space, ends the step with
+ * NOC_ERR_OWNER or NOC_ERR_RANGE at its cycle instead of touching the entry.
+ * Results are otherwise those of the production builds.  While checks are on,
+ * per-cycle hashes, noc_drain and two tiles per thread are NOC_ERR_ARG and the
+ * phase profile is off. */
+int noc_set_checks(noc_sim* sim, int enable);
 
 /* Per-phase clock profile of the plain loop (one tile per thread).  With
  * enable != 0 (the first call takes a 48-byte device buffer), later plain

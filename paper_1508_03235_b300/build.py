@@ -31,6 +31,9 @@ UNITS = ([("noc_run_variant.cu", {"NOC_HASH": h, "NOC_DRAIN": d, "NOC_W1": w1, "
             for (w1, w2) in WAY_BOUNDS
             for spec in [{}, {"NOC_BASE": 1}]
             + [{"NOC_FIXED_POLICY": pol, "NOC_FIXED_MODE": 0, "NOC_EXACT_WAYS": 1} for pol in POLICIES]]
+         # the general plain loop with the single-writer checks (noc_set_checks)
+         + [("noc_run_variant.cu", {"NOC_HASH": 0, "NOC_DRAIN": 0, "NOC_W1": w1, "NOC_W2": w2, "NOC_CHECKS": 1})
+            for (w1, w2) in WAY_BOUNDS]
          # and with per-phase clock reads (noc_set_phase_profile)
          + [("noc_run_variant.cu", dict(spec, NOC_HASH=0, NOC_DRAIN=0, NOC_W1=w1, NOC_W2=w2,
                                         NOC_PHASE_PROFILE=1))

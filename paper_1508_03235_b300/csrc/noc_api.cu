@@ -178,6 +178,8 @@ struct noc_sim {
   int64_t launches = 0;
   int last_variant = -1;  // run_variant() of the last cycle-kernel launch
   int last_bound = 0;     // launch bound (most threads per CTA) of that launch's build
+  // plain launches on the checked build (noc_set_checks)
+  bool checks_on = false;
   // per-phase clock profile of the plain loop (noc_set_phase_profile)
   bool prof_on = false;
   unsigned long long* d_prof = nullptr;  // 6 words, device
@@ -437,9 +439,17 @@ int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
   if (tpt == 2 && (busy || s->hash_on))
     return fail(NOC_ERR_ARG, "per-cycle hashes and drains need one tile per thread (a mesh of one "
                              "co-resident launch); this one runs two");
+  if (s->checks_on && (tpt == 2 || busy || s->hash_on))
+    return fail(NOC_ERR_ARG, "the checked build is the plain loop with one tile per thread: no per-cycle "
+                             "hashes, drains or two tiles per thread while checks are on");
   const int threads = launch_threads(s, tpt, s->run_gx, s->run_gy);
   int cap = 0;
   CU(coresident(s, tpt, threads, &cap), "occupancy");
+  if (s->checks_on) {
+    int ccap = 0;
+    CU(max_coresident_checked(s->P, threads, &ccap), "occupancy");
+    cap = std::min(cap, ccap);
+  }
   if (threads > max_launch_threads(tpt) || s->run_gx * s->run_gy > cap ||
       s->run_gx * s->run_gy * FLAG_SLOTS > (int)s->n_flags)
     return fail(NOC_ERR_ARG, "tiling %dx%d does not fit one co-resident launch with %d tile(s) per thread",
@@ -468,7 +478,8 @@ int run_cycles(noc_sim* s, uint32_t n, bool draining, unsigned int* busy) {
     A.wait_ns = s->wait_ns;
     A.silent_cta = s->silent_cta;
     A.thread_map = s->thread_map;
-    A.prof = (s->prof_on && !A.hash_trace && !A.busy && tpt == 1) ? s->d_prof : nullptr;
+    A.checked = s->checks_on ? 1 : 0;
+    A.prof = (s->prof_on && !s->checks_on && !A.hash_trace && !A.busy && tpt == 1) ? s->d_prof : nullptr;
     if (A.prof) {
       // the profiled build keeps its own register count: check it fits too
       if (threads > RUN_PROF_THREADS)
@@ -1035,6 +1046,12 @@ int noc_debug_wait_limit(noc_sim* s, int64_t ns, int silent_cta) {
 int64_t noc_kernel_launches(const noc_sim* s) { return s ? s->launches : -1; }
 
 int noc_last_launch_bound(const noc_sim* s) { return s ? s->last_bound : -1; }
+
+int noc_set_checks(noc_sim* s, int enable) {
+  if (!s) return fail(NOC_ERR_ARG, "null handle");
+  s->checks_on = enable != 0;
+  return NOC_OK;
+}
 
 int noc_set_phase_profile(noc_sim* s, int enable) {
   if (!s) return fail(NOC_ERR_ARG, "null handle");

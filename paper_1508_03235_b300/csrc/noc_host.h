@@ -26,6 +26,8 @@ constexpr int RUN_MAX_THREADS = 448;
 constexpr int RUN_PROF_THREADS = 384;
 // the launch bound (most threads per CTA) of the build launch_run picks
 int run_launch_bound(const Params& P, const RunArgs& A);
+// co-resident CTAs of the plain loop's checked build at `threads` per CTA
+cudaError_t max_coresident_checked(const Params& P, int threads, int* out);
 // co-resident CTAs of the plain loop's profiled build at `threads` per CTA
 cudaError_t max_coresident_prof(const Params& P, int threads, int* out);
 // the capacity loop (two tiles per thread, plain cycles only): launch, its

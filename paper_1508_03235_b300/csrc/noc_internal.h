@@ -26,6 +26,8 @@ struct RunArgs {
   // build only; nullptr otherwise): waiting, routing, publishing, Phase 3,
   // Phase 1, and the number of warp-cycles
   unsigned long long* prof;
+  // 1: run the plain loop on the checked build (noc_set_checks)
+  int checked;
 };
 
 // batch work queue: per-instance parameters, and items (instance, rectangle)

@@ -37,6 +37,8 @@ static_assert(RUN_MAX_THREADS == MAX_THREADS && RUN_PROF_THREADS == PROF_THREADS
   NOC_DECL_RUN(0, 0, w1, w2, migrate)                                           \
   NOC_DECL_RUN(0, 0, w1, w2, local_narrow)                                      \
   NOC_DECL_RUN(0, 0, w1, w2, gen_xl)                                            \
+  NOC_DECL_RUN(0, 0, w1, w2, gen_checked)                                       \
+  cudaError_t max_coresident_run_0_0_##w1##_##w2##_gen_checked(int threads, int* out); \
   NOC_DECL_RUN(0, 0, w1, w2, base_xl)                                           \
   NOC_DECL_RUN(0, 0, w1, w2, il_xl)                                             \
   NOC_DECL_RUN(0, 0, w1, w2, local_xl)                                          \
@@ -115,7 +117,7 @@ static int prof_kind(int kind) { return kind == KIND_LOCAL || kind == KIND_MIGRA
 
 int run_variant(const Params& P, const RunArgs& A) {
   const int traced = (A.hash_trace || A.busy) ? 1 : 0;
-  const int kind = traced ? KIND_GEN : A.prof ? prof_kind(variant_kind(P)) : variant_kind(P);
+  const int kind = traced || A.checked ? KIND_GEN : A.prof ? prof_kind(variant_kind(P)) : variant_kind(P);
   return (traced << 8) | (kind << 4) | way_class(P.l1_ways, P.l2_ways);
 }
 
@@ -125,7 +127,7 @@ static int plain_bound(int threads) {
 }
 
 int run_launch_bound(const Params& P, const RunArgs& A) {
-  if (A.hash_trace || A.busy) return MAX_THREADS;
+  if (A.hash_trace || A.busy || A.checked) return MAX_THREADS;
   if (A.prof) return PROF_THREADS;
   return plain_bound(block_threads_impl(P.W, P.H, A.gx, A.gy));
 }
@@ -159,8 +161,9 @@ cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
   if (A.hash_trace && A.busy) return cudaErrorInvalidValue;
   if (A.hash_trace) { NOC_PICK_RUN(1, 0, gen) }
   if (A.busy) { NOC_PICK_RUN(0, 1, gen) }
-  // the plain loop: the profiled build when asked for, else the narrow build
-  // when the CTAs fit it
+  // the plain loop: the checked build when asked for, the profiled build when
+  // asked for, else the build of the smallest launch bound the CTAs fit
+  if (A.checked) { NOC_PICK_RUN(0, 0, gen_checked) }
   if (A.prof) {
     switch (prof_kind(variant_kind(P))) {
       case KIND_IL: NOC_PICK_RUN(0, 0, il_prof)
@@ -231,6 +234,14 @@ cudaError_t launch_run(const Params& P, const RunArgs& A, cudaStream_t s) {
     case KIND_BASE: return fn##_##w1##_##w2##_base_prof(__VA_ARGS__);            \
     default: return fn##_##w1##_##w2##_gen_prof(__VA_ARGS__);                    \
   }
+
+cudaError_t max_coresident_checked(const Params& P, int threads, int* out) {
+  switch (way_class(P.l1_ways, P.l2_ways)) {
+    case 0: return max_coresident_run_0_0_4_8_gen_checked(threads, out);
+    case 1: return max_coresident_run_0_0_4_16_gen_checked(threads, out);
+    default: return max_coresident_run_0_0_16_16_gen_checked(threads, out);
+  }
+}
 
 cudaError_t max_coresident_prof(const Params& P, int threads, int* out) {
   const int kind = prof_kind(variant_kind(P));

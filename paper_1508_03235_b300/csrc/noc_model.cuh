@@ -63,7 +63,7 @@ enum : uint32_t { OM_NONE = 0, OM_WAIT_DR = 1, OM_WAIT_DATA = 2, OM_MEM_L2 = 3, 
 enum : int { P_N = 0, P_S = 1, P_E = 2, P_W = 3 };
 enum : int { POL_INTERLEAVED = 0, POL_LOCAL = 1, POL_MIGRATE = 2 };
 enum : int { MODE_CACHE = 0, MODE_NETWORK = 1, MODE_TRACE = 2 };
-enum : int { ERR_OVERFLOW = 3, ERR_TIMEOUT = 4, ERR_PROTOCOL = 6, ERR_RANGE = 8 };
+enum : int { ERR_OVERFLOW = 3, ERR_TIMEOUT = 4, ERR_PROTOCOL = 6, ERR_RANGE = 8, ERR_OWNER = 9 };
 
 constexpr uint32_t NO_TILE = 0xFFFFu;
 constexpr uint32_t DIR_NONE = 0xFFFFFFFFu;
@@ -584,6 +584,30 @@ __device__ __forceinline__ void prefetch_home_set(const Params& P, uint32_t h, u
 
 __device__ __forceinline__ uint16_t* hist_ptr(const Params& P, size_t way_index) {
   return P.l2hist + way_index * (size_t)P.hist_stride;
+}
+
+// The checked build (-DNOC_CHECKS=1, noc_set_checks) verifies the single-writer
+// discipline the model relies on.  Every per-tile structure is indexed by the
+// tile's own id, so the directory -- indexed by a line that a message carries
+// -- is the one structure a second writer could reach: its entry for a line
+// may be touched only at that line's directory tile.  The message handlers
+// that touch it (DA, DINV, DIRUPD) check the tile and the line's range first
+// and report ERR_OWNER or ERR_RANGE instead of touching the entry.
+#ifndef NOC_CHECKS
+#define NOC_CHECKS 0
+#endif
+__device__ __forceinline__ bool dir_owned(const Params& P, const Tile& T, uint32_t line, uint32_t t) {
+#if NOC_CHECKS
+  if (line >= (uint32_t)P.total_lines) {
+    set_error(P, t, ERR_RANGE);
+    return false;
+  }
+  if (dir_home(P, line) != T.r) {
+    set_error(P, t, ERR_OWNER);
+    return false;
+  }
+#endif
+  return true;
 }
 
 // directory entry delete for an evicted L2 victim (Sec. 3.4)
@@ -1421,6 +1445,7 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
 
 #if NOC_WITH_LSPD
     case T_DA: {
+      if (!dir_owned(P, T, line, t)) break;
       uint32_t q = fsrc(f), D = P.dir[line];
       SMALL(S_DIRS)++;
       if (D == DIR_NONE || (D & 0xFFFFu) == q) {
@@ -1466,6 +1491,7 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
       break;
 
     case T_DINV:
+      if (!dir_owned(P, T, line, t)) break;
       if (P.dir[line] == (fsrc(f) | (fe(f) << 16))) P.dir[line] = DIR_NONE;
       break;
 
@@ -1491,6 +1517,7 @@ static __device__ void phase3(const Params& P, Tile& T, uint32_t t, uint32_t* sh
     case T_INV: {
       uint32_t m;
       if (ty == T_DIRUPD) {
+        if (!dir_owned(P, T, line, t)) break;
         m = fsrc(f);
         uint32_t o = fa(f);
         P.dir[line] = m | (fe(f) << 16);

@@ -7,7 +7,7 @@
 // -DNOC_EXACT_WAYS=1: p = 0 interleaved, 1 LSPD with local placement, 2 LSPD
 // with migration); the plain-loop builds once more each with -DNOC_NARROW=1,
 // for CTAs of at most NARROW_THREADS threads, and with -DNOC_XL=1, for CTAs of
-// more than WIDE_THREADS.
+// more than WIDE_THREADS; the general plain loop once more with -DNOC_CHECKS=1.
 #include "noc_kernel.cuh"
 
 #if !defined(NOC_HASH) || !defined(NOC_DRAIN) || !defined(NOC_W1) || !defined(NOC_W2)
@@ -32,7 +32,11 @@
 // -DNOC_NARROW=1: the build for CTAs of at most NARROW_THREADS threads
 #define NOC_PASTE2(a, b) a##_##b
 #define NOC_CAT2(a, b) NOC_PASTE2(a, b)
-#if defined(NOC_NARROW) && NOC_NARROW
+#if NOC_CHECKS
+// -DNOC_CHECKS=1: the plain loop with the single-writer checks, for every CTA size
+#define NOC_LB MAX_THREADS
+#define NOC_SPEC NOC_CAT2(NOC_SPEC0, checked)
+#elif defined(NOC_NARROW) && NOC_NARROW
 #define NOC_LB NARROW_THREADS
 #define NOC_SPEC NOC_CAT2(NOC_SPEC0, narrow)
 #elif NOC_PHASE_PROFILE

@@ -159,6 +159,7 @@ extern "C" int noc_run_static(int mesh_w, int mesh_h, const noc_cache_cfg* c, in
     A.silent_cta = -1;
     A.thread_map = 0;
     A.prof = nullptr;
+    A.checked = 0;
     ce = launch_run(P, A, st);
     if (ce != cudaSuccess) return fail(NOC_ERR_CUDA, "cycle kernel launch: %s", cudaGetErrorString(ce));
     done += n;

@@ -19,7 +19,8 @@ NOC_OK = 0
 THREAD_MAPS = ("perimeter first", "rows", "columns")
 KERNEL_KINDS = ("general", "base", "interleaved", "lspd-local", "lspd-migrate")
 ERR_NAMES = {1: "NOC_ERR_ARG", 2: "NOC_ERR_OOM", 3: "NOC_ERR_QUEUE_OVERFLOW", 4: "NOC_ERR_TIMEOUT",
-             5: "NOC_ERR_CUDA", 6: "NOC_ERR_PROTOCOL", 7: "NOC_ERR_STATE", 8: "NOC_ERR_RANGE"}
+             5: "NOC_ERR_CUDA", 6: "NOC_ERR_PROTOCOL", 7: "NOC_ERR_STATE", 8: "NOC_ERR_RANGE",
+             9: "NOC_ERR_OWNER"}
 HIST_BINS = 1025
 FLIT_TYPES = dict(NONE=0, REQ=1, DATA=2, WT=3, DA=4, DRPOS=5, DRNEG=6, NACK=7, DINV=8, MIG=9,
                   DIRUPD=10, INV=11, PROBE=12)
@@ -106,6 +107,7 @@ def lib():
             "noc_last_variant": (i32, [vp] + [C.POINTER(i32)] * 4),
             "noc_last_launch_bound": (i32, [vp]),
             "noc_set_phase_profile": (i32, [vp, i32]),
+            "noc_set_checks": (i32, [vp, i32]),
             "noc_phase_profile": (i32, [vp, P64]),
             "noc_checkpoint_bytes": (C.c_size_t, [vp]),
             "noc_save": (i32, [vp, vp, C.c_size_t]),
@@ -269,6 +271,12 @@ class Sim:
                     kind=KERNEL_KINDS[v[1].value], bounds=(v[2].value, v[3].value))
 
     PHASES = ("wait", "route", "publish", "phase3", "phase1")
+
+    def set_checks(self, enable: bool = True):
+        """Run later plain launches on the checked build (noc_set_checks): a
+        directory entry touched away from its line's directory tile ends the
+        step with NOC_ERR_OWNER."""
+        _check(lib().noc_set_checks(self._h, 1 if enable else 0))
 
     def set_phase_profile(self, enable: bool = True):
         """Run later plain launches on the build with per-phase clock reads."""

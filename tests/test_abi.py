@@ -48,6 +48,7 @@ def test_every_kernel_build_the_dispatcher_names_is_linked(libnoc):
     kinds = ("gen", "base", "il", "local", "migrate")
     want = {f"noc::launch_run_0_0_{c}_{k}{s}" for c in classes for k in kinds for s in ("", "_narrow", "_xl")}
     want |= {f"noc::launch_run_0_0_{c}_{k}_prof" for c in classes for k in ("gen", "base", "il")}
+    want |= {f"noc::launch_run_0_0_{c}_gen_checked" for c in classes}
     want |= {f"noc::launch_run_{h}_{c}_gen" for c in classes for h in ("1_0", "0_1")}
     want |= {f"noc::launch_batch_{c}_{k}" for c in classes for k in kinds}
     want |= {f"noc::launch_multi_{c}" for c in classes}
