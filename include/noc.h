@@ -370,9 +370,9 @@ int noc_last_variant(const noc_sim* sim, int* loop, int* kind, int* l1_bound, in
  * threads; a launch takes the smallest that fits, since more registers per
  * thread run faster (the 448 build keeps 128: a CTA of more than 12 warps puts
  * four warps on some of an SM's four register files of 16,384).  The traced
- * loop is built for 448, the per-phase profiled loop for 384 and the two-tile
- * loop for 256.  0 before the first launch, -1 for a null
- * handle. */
+ * loop and the checked build (noc_set_checks) are built for 448, the per-phase
+ * profiled loop for 384 and the two-tile loop for 256.  0 before the first
+ * launch, -1 for a null handle. */
 int noc_last_launch_bound(const noc_sim* sim);
 
 /* Checked build of the plain loop (one tile per thread).  No counterpart in
