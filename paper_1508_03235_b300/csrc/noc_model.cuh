@@ -1189,13 +1189,27 @@ __device__ __forceinline__ InjCand inj_candidate(const Params& P, const Tile& T)
   return c;
 }
 
+// Copy this tile's outputs of cycle t on the links in `edge` (leaving the CTA
+// rectangle) from their shared-memory slots to the tagged global slots.
+__device__ __forceinline__ void store_edges(const uint4* so, int so_stride, uint4* go, size_t go_stride,
+                                            uint32_t edge, uint32_t t) {
+  if (edge) {
+    const uint32_t tag = link_tag(t);
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+      if ((edge >> d) & 1u) tag_store(&go[d * go_stride], so[d * so_stride], tag);
+  }
+}
+
 // The router of Sec. 4.3 as route() computes it, for the plain cycle loop:
 // arrivals are ranked by pairwise key comparisons instead of being sorted, so
 // flits never move between registers; the ejected flit is the lowest-ranked
 // arrival addressed here, and the others' ranks close up behind it.  Each flit
 // is stored once, to its port's slot, after all four slots were cleared.
 // Links in `edge` (leaving the CTA rectangle) are then copied from the slots
-// to tagged global slots.  `ic` is inj_candidate() of the tile's state.
+// to tagged global slots (store_edges; the single-simulation plain loop
+// passes none and copies them after publishing its warp's flag).  `ic` is
+// inj_candidate() of the tile's state.
 __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t t, const uint4 (&in)[4],
                                              uint32_t exists, uint4* so, int so_stride, uint4* go,
                                              size_t go_stride, uint32_t edge, const InjCand& ic) {
@@ -1300,12 +1314,7 @@ __device__ __forceinline__ void route_ranked(const Params& P, Tile& T, uint32_t 
       if ((rm >> d) & 1u) so[(31 - __clz(pk[d])) * so_stride] = in[d];
   }
   if (has_inj) so[(31 - __clz(pki)) * so_stride] = inj;
-  if (edge) {
-    const uint32_t tag = link_tag(t);
-#pragma unroll
-    for (int d = 0; d < 4; ++d)
-      if ((edge >> d) & 1u) tag_store(&go[d * go_stride], so[d * so_stride], tag);
-  }
+  store_edges(so, so_stride, go, go_stride, edge, t);
 }
 
 // ---------------------------------------------------------------- Phase 3
